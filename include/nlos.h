@@ -1,0 +1,198 @@
+/*
+ * nlos.h -- C ABI of the GB300 (sm_103a) curvature-regularised confocal NLOS
+ * reconstruction library (arXiv 2301.00406).
+ *
+ * The library computes, on one GPU, the per-iteration work of the paper's two
+ * ADMM solvers: the confocal light-cone-transform operator A = R_t^{-1} H R_z
+ * of Sec. 2 (Eq. 3) and its transpose, the scan-grid sampling D (A_D = D A,
+ * Sec. 3.1.2), and the curvature-regularisation sub-steps of Algorithm 1
+ * (Sec. 3, Eq. 4-12) and Algorithm 2 (Sec. 4.1, Eq. 13).
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns an nlos_status; NLOS_OK (0) is success and the
+ *    other codes are negative.  No function aborts, throws or exits across
+ *    the ABI.  nlos_last_error() copies a thread-local message describing the
+ *    most recent failure on the calling thread.
+ *  - Volumes (albedo u) and transients (tau) are float32, contiguous,
+ *    row-major [nx][ny][nt] (time/depth fastest).  Pointers named *_dev are
+ *    device pointers in the current CUDA context; *_host pointers are host
+ *    memory.  The caller owns every pointer it passes and must keep it valid
+ *    until the work queued on `stream` has completed.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *    stream.  Work is queued on that stream without host synchronisation
+ *    unless the function says otherwise.
+ *  - Sizes: nx, ny are powers of two in [8, 128]; nt is a power of two in
+ *    [16, 1024].  Other sizes return NLOS_ERR_INVALID_ARG.
+ *  - A plan is not thread-safe: serialise calls that use the same plan.
+ *    Server entry points (nlos_submit, nlos_poll) are thread-safe.
+ */
+#ifndef NLOS_H
+#define NLOS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t nlos_status;
+#define NLOS_OK 0
+#define NLOS_ERR_INVALID_ARG (-1) /* bad pointer, size or parameter            */
+#define NLOS_ERR_OOM (-2)         /* device or host allocation failed          */
+#define NLOS_ERR_CUDA (-3)        /* a CUDA runtime call or launch failed      */
+#define NLOS_ERR_BUSY (-4)        /* server queue full                         */
+#define NLOS_ERR_NOT_READY (-5)   /* job still queued or running               */
+#define NLOS_ERR_TIMEOUT (-6)     /* a bounded wait gave up                    */
+#define NLOS_ERR_DIVERGED (-7)    /* non-finite energy or backtracking gave up */
+
+/* Radiometric weight of R_t^{-1} (the t-axis resampling of Eq. 3). */
+#define NLOS_RADIOMETRY_COMPENSATED 0 /* transient pre-multiplied by t^4: weight rho   */
+#define NLOS_RADIOMETRY_RAW 1         /* 1/d^4 fall-off of Eq. 2: weight rho^-3       */
+
+/* phi(kappa) of Sec. 3 (below Eq. 4). */
+#define NLOS_PHI_TSC 0 /* a + b kappa^2 (the paper's choice) */
+#define NLOS_PHI_TAC 1 /* a + b |kappa|                      */
+#define NLOS_PHI_TRV 2 /* sqrt(a + b kappa^2)                */
+
+typedef struct nlos_plan_s* nlos_plan;
+typedef struct nlos_server_s* nlos_server;
+
+/* Scan geometry of one confocal scene (Sec. 2).  The voxel grid shares the
+ * scan grid laterally (nx x ny points over a wall_width_m square) and the time
+ * axis in depth: depth bin k and time bin k both sit at rho_k = (k + 1/2)/nt of
+ * the range R = c * nt * bin_width_s / 2. */
+typedef struct {
+  int32_t nx, ny, nt;
+  double bin_width_s;   /* time-bin width in seconds, > 0                      */
+  double wall_width_m;  /* side of the scanned wall patch in metres, > 0       */
+  int32_t radiometry;   /* NLOS_RADIOMETRY_*                                    */
+  const uint8_t* mask;  /* host, nx*ny bytes, nonzero = scan point measured
+                           (the complement is the missing region X); NULL =
+                           fully sampled.  Copied by nlos_plan_create.         */
+} nlos_geometry;
+
+/* Solver parameters.  nlos_params_default() fills the paper's values. */
+typedef struct {
+  int32_t model;         /* 1 = object domain (Algorithm 1), 2 = dual domain (Algorithm 2) */
+  int32_t phi;           /* NLOS_PHI_*                                                      */
+  double a, b;           /* Algorithm 1 phi parameters                                      */
+  double mu;             /* Algorithm 1 penalty (Eq. 5)                                     */
+  double a_u, b_u, a_tau, b_tau, lambda; /* Algorithm 2 (Eq. 13)                            */
+  double mu1, mu2, mu3;  /* Algorithm 2 penalties (Sec. 4.1)                                */
+  int32_t iters;         /* T_max                                                           */
+  double eps_stop;       /* relative-energy stop of Algorithms 1/2; 0 = run all iters       */
+  double L0;             /* initial L; <= 0 means 2 ||A_D||_2^2 (below Eq. 10)              */
+  double eta;            /* backtracking growth factor for L (> 1)                          */
+  int32_t max_backtracks;/* rejections allowed in one iteration before NLOS_ERR_DIVERGED    */
+  double eps_normal;     /* regulariser of |grad u| in the normal field                     */
+  int32_t restart;       /* FISTA restart on energy increase: 0 off, 1 on, -1 model default
+                            (off for model 1, on for model 2)                              */
+} nlos_params;
+
+/* Per-reconstruction statistics (host struct, filled after the run). */
+typedef struct {
+  int32_t iters_done;
+  int32_t backtracks;    /* total rejected L trials                           */
+  int32_t restarts;      /* FISTA restarts taken                              */
+  int32_t status;        /* NLOS_OK or the error that stopped the run         */
+  double L;              /* final L                                           */
+  double energy;         /* E at the last iteration (Eq. 4 or Eq. 13)         */
+  double rel_change;     /* e = |E_prev - E| / |E| at the last iteration      */
+  double data_fit;       /* 1/2 ||A_D u - tau0||^2 (model 1) or 1/2 ||A u - tau||^2 (model 2) */
+  double primal_res;     /* ||v - grad u|| at the last iteration              */
+} nlos_stats;
+
+/* Copy the most recent error message of the calling thread into buf
+ * (NUL-terminated, truncated to n bytes).  Returns NLOS_OK. */
+nlos_status nlos_last_error(char* buf, size_t n);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int32_t nlos_version(void);
+
+/* Fill *out with the defaults for `model` (1 or 2): the Bowling 8x8
+ * settings of Sec. 5.2.1 (a = 9e-5, b = 2e-5, mu = 0.1; lambda = 235,
+ * a_tau = 4e-4, b_tau = 3e-2, a_u = 2e-4, b_u = 4.5e-4), mu1..3 = 1, 800, 2 and
+ * T_max = 200 / 300 (Sec. 5.1), eps_stop = 0, L0 = 0 (= 2||A_D||^2), eta = 2,
+ * max_backtracks = 30, eps_normal = 1e-6, restart = -1.  Host only. */
+nlos_status nlos_params_default(int32_t model, nlos_params* out);
+
+/* Create a plan for one geometry (Sec. 2, Eq. 3): builds the R_z and R_t^{-1}
+ * two-tap tables in FP64 on the host, the sampled-column list of the mask,
+ * and the cone-kernel spectrum H on the device (queued on `stream`, which is
+ * synchronised before return).  All device memory the plan needs for the
+ * operator is allocated here.  *out is set only on success. */
+nlos_status nlos_plan_create(const nlos_geometry* geom, void* stream, nlos_plan* out);
+
+/* Release a plan and all its device memory.  Synchronises the device first.
+ * NULL is accepted. */
+nlos_status nlos_plan_destroy(nlos_plan plan);
+
+/* ||A_D||_2^2 (masked != 0) or ||A||_2^2 by power iteration on A_D^T A_D from
+ * the all-ones vector (up to 200 steps, relative change < 1e-12), as used for
+ * L0 = 2 ||A_D||^2 (below Eq. 10).  Computed once per plan and cached;
+ * synchronises `stream`. */
+nlos_status nlos_plan_norm2(nlos_plan plan, int32_t masked, void* stream, double* out);
+
+/* Host-side tables of a geometry, computed exactly as nlos_plan_create does
+ * (FP64 on the host, no GPU needed), for inspection and testing:
+ *   rz_i0[nt], rt_k0[nt] (int32): first tap of R_z / R_t^{-1} per bin;
+ *   rz_w[3*nt] = (w0, w1, g) per v-bin, rt_w[3*nt] = (w0, w1, wt) per t-bin
+ *   (float32, rounded from FP64);
+ *   cols[nx*ny] (int32): sampled columns x*ny + y, ascending; *n_cols set.
+ * Any output pointer may be NULL.  Same validation as nlos_plan_create. */
+nlos_status nlos_geometry_tables(const nlos_geometry* geom, int32_t* rz_i0, float* rz_w, int32_t* rt_k0,
+                                 float* rt_w, int32_t* cols, int32_t* n_cols);
+
+/* tau = A u (apply_mask = 0) or tau = D A u with zeros on unsampled columns
+ * (apply_mask != 0): Eq. 3 and A_D = D A (Sec. 3.1.2).  u_dev, tau_dev:
+ * [nx][ny][nt] float32; they must not overlap. */
+nlos_status nlos_forward(nlos_plan plan, const float* u_dev, float* tau_dev, int32_t apply_mask,
+                         void* stream);
+
+/* u = A^T tau (apply_mask = 0) or A_D^T tau = A^T D tau (apply_mask != 0,
+ * unsampled columns of tau ignored): the transpose used in grad f = A_D^T
+ * (A_D u - tau0) (Eq. 10-11). */
+nlos_status nlos_adjoint(nlos_plan plan, const float* tau_dev, float* u_dev, int32_t apply_mask,
+                         void* stream);
+
+/* x = F^{-1}[F(rhs) / (c0 + c1 lambda(k))] on the periodic nx x ny x nt grid,
+ * lambda(k) = sum_d 4 sin^2(pi k_d / N_d): the solve of (c0 I + c1 nabla^*
+ * nabla) x = rhs of Eq. 11 (forward differences, unit spacing).  c0 > 0,
+ * c1 >= 0.  rhs_dev and x_dev may alias. */
+nlos_status nlos_solve(nlos_plan plan, const float* rhs_dev, float* x_dev, double c0, double c1,
+                       void* stream);
+
+/* phi_out = phi(kappa(u)) with kappa = div(grad u / sqrt(|grad u|^2 + eps^2))
+ * (Sec. 3, below Eq. 4), forward-difference gradient and backward-difference
+ * divergence, periodic; phi_kind = NLOS_PHI_*. */
+nlos_status nlos_curvature_weight(nlos_plan plan, const float* u_dev, float* phi_dev, double a,
+                                  double b, int32_t phi_kind, double eps, void* stream);
+
+/* Reconstruct u from the measured transient tau0 (full grid [nx][ny][nt];
+ * unsampled columns ignored) with Algorithm 1 or 2 (params->model).
+ * u_out_dev receives u; tau_out_dev (nullable) receives Algorithm 2's
+ * recovered signal tau.  stats_host (nullable) is filled after the run.
+ * All iteration state lives on the device; device memory for it is allocated
+ * on the first call with a given model and kept by the plan.  Synchronises
+ * `stream` before returning (the statistics are read back). */
+nlos_status nlos_reconstruct(nlos_plan plan, const nlos_params* params, const float* tau0_dev,
+                             float* u_out_dev, float* tau_out_dev, nlos_stats* stats_host,
+                             void* stream);
+
+/* Per-launch timing of a plan's kernels, for profiling.  When enabled, every
+ * kernel the plan launches is bracketed by a pair of CUDA events recorded on
+ * its launch stream.  nlos_timing_read synchronises the device, returns per
+ * category the summed milliseconds and launch counts (categories: 0 lateral
+ * convolution, 1 forward t-pass, 2 inverse t-pass, 3 adjoint end / solve
+ * rhs, 4 lateral solve, 5 periodic t-FFT, 6 periodic inverse t-FFT,
+ * 7 pre-solve stencil, 8 post-solve stencil, 9 scalar and small kernels,
+ * 10 kernel spectrum), fills n entries and resets the record. */
+nlos_status nlos_timing_enable(nlos_plan plan, int32_t enable);
+nlos_status nlos_timing_read(nlos_plan plan, double* ms, int32_t* launches, int32_t n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NLOS_H */

@@ -1,0 +1,819 @@
+// Curvature-regularisation sub-steps and the ADMM drivers of Algorithm 1
+// (Sec. 3, Eq. 5-12) and Algorithm 2 (Sec. 4.1, Eq. 13), plus the operator
+// norm by power iteration.
+//
+// Every iteration is a fixed sequence of launches on the caller's stream.
+// Scalars that change between iterations (L, the FISTA t and beta, energies)
+// live in a DevScalars block in device memory and are updated by one-thread
+// kernels, so no host synchronisation is needed per iteration unless the
+// backtracking rule can still reject a step (L below 1.5 ||A_D||^2).
+#include <cmath>
+#include <cstring>
+
+#include "passes.cuh"
+#include "stencil.cuh"
+
+namespace nlos {
+
+constexpr int kStencilThreads = 256;
+constexpr int kStencilBlocks = 152 * 8;  // grid-stride; also the partial-sum count
+
+__host__ __device__ inline int ilog2i(int n) {
+  int r = 0;
+  while ((1 << r) < n) ++r;
+  return r;
+}
+
+struct VoxIter {
+  int lt, ly;
+  __device__ __forceinline__ void decode(size_t i, const Vox& g, int& x, int& y, int& t) const {
+    t = (int)(i & g.mt);
+    y = (int)((i >> lt) & g.my);
+    x = (int)(i >> (lt + ly));
+  }
+};
+
+template <int NTERMS>
+__device__ __forceinline__ void block_reduce_to(double (&v)[NTERMS], double* partials) {
+  __shared__ double red[32][NTERMS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < NTERMS; ++t) {
+    double x = v[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    v[t] = x;
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int t = 0; t < NTERMS; ++t) red[warp][t] = v[t];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int t = 0; t < NTERMS; ++t) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += red[w][t];
+      partials[(size_t)blockIdx.x * kMaxTerms + t] = s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Elementwise and reduction utilities
+// ---------------------------------------------------------------------------
+__global__ void k_fill(float* __restrict__ a, float v, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) a[i] = v;
+}
+
+__global__ void k_scale(float* __restrict__ a, const double* __restrict__ s, size_t n) {
+  const float f = (float)(1.0 / *s);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) a[i] *= f;
+}
+
+// partials[b][0] = sum a^2 (optionally only over columns with colpos >= 0)
+__global__ void __launch_bounds__(kStencilThreads)
+    k_sumsq(const float* __restrict__ a, size_t n, double* __restrict__ partials) {
+  double acc[1] = {0.0};
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double v = __ldg(a + i);
+    acc[0] += v * v;
+  }
+  block_reduce_to<1>(acc, partials);
+}
+
+// Sum the first nb partials of term `term` in a fixed order (one thread).
+__device__ __forceinline__ double sum_partials(const double* p, int nb, int term) {
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += p[(size_t)b * kMaxTerms + term];
+  return s;
+}
+
+__global__ void k_sum_to(const double* __restrict__ p, int nb, int term, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *out = sum_partials(p, nb, term);
+}
+
+__global__ void k_sqrt_sum_to(const double* __restrict__ p, int nb, int term, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *out = sqrt(sum_partials(p, nb, term));
+}
+
+// Copy the sampled columns of a full [nx*ny][nt] array into compact form.
+__global__ void k_gather_cols(const float* __restrict__ full, const int32_t* __restrict__ cols, int ncols, int nt,
+                              float* __restrict__ out) {
+  const size_t n = (size_t)ncols * nt;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(i / nt), t = (int)(i % nt);
+    out[i] = __ldg(full + (size_t)__ldg(cols + j) * nt + t);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Curvature weight phi(kappa(u)) (Sec. 3)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kStencilThreads)
+    k_curv_weight(const float* __restrict__ u, float* __restrict__ ph, Vox g, VoxIter vi, float a, float b, int kind,
+                  float eps2, size_t V) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V; i += (size_t)gridDim.x * blockDim.x) {
+    int x, y, t;
+    vi.decode(i, g, x, y, t);
+    ph[i] = phi_of(curvature_at(u, g, x, y, t, eps2, nullptr), a, b, kind);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1 stencils
+// ---------------------------------------------------------------------------
+// reg = mu nabla^*(v + Lam/mu), v = shrink(grad ubar - Lam/mu, phi/mu) (Eq. 7 and
+// the right-hand side of the PDE above Eq. 11); nabla^* q = -div_b q.
+__global__ void __launch_bounds__(kStencilThreads)
+    k_pre1(const float* __restrict__ ub, const float* __restrict__ lam, const float* __restrict__ ph,
+           float* __restrict__ reg, Vox g, VoxIter vi, float mu, size_t V) {
+  const float inv_mu = 1.0f / mu;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V; i += (size_t)gridDim.x * blockDim.x) {
+    int x, y, t;
+    vi.decode(i, g, x, y, t);
+    const float3 vc = v_at(ub, lam, V, ph, g, x, y, t, inv_mu);
+    const int ixm = g.idx((x - 1) & g.mx, y, t), iym = g.idx(x, (y - 1) & g.my, t), itm = g.idx(x, y, (t - 1) & g.mt);
+    const float qxm = v_at(ub, lam, V, ph, g, (x - 1) & g.mx, y, t, inv_mu).x + __ldg(lam + ixm) * inv_mu;
+    const float qym = v_at(ub, lam, V, ph, g, x, (y - 1) & g.my, t, inv_mu).y + __ldg(lam + V + iym) * inv_mu;
+    const float qtm = v_at(ub, lam, V, ph, g, x, y, (t - 1) & g.mt, inv_mu).z + __ldg(lam + 2 * V + itm) * inv_mu;
+    const float qcx = vc.x + __ldg(lam + i) * inv_mu;
+    const float qcy = vc.y + __ldg(lam + V + i) * inv_mu;
+    const float qct = vc.z + __ldg(lam + 2 * V + i) * inv_mu;
+    reg[i] = -mu * ((qcx - qxm) + (qcy - qym) + (qct - qtm));
+  }
+}
+
+// After an accepted u-step: Lam += mu (v - grad u+) (Eq. 12), phi = phi(kappa(u+)),
+// ubar_next = u+ + beta (u+ - u^k) (Algorithm 1); partials 0 = sum phi |grad u+|,
+// 1 = sum |v - grad u+|^2.
+__global__ void __launch_bounds__(kStencilThreads)
+    k_post1(const float* __restrict__ unew, const float* __restrict__ uk, const float* __restrict__ ub,
+            float* __restrict__ lam, float* __restrict__ ph, float* __restrict__ ubn, const DevScalars* __restrict__ sc,
+            Vox g, VoxIter vi, float mu, float a, float b, int kind, float eps2, size_t V, double* __restrict__ partials) {
+  const float inv_mu = 1.0f / mu;
+  const float beta = (float)sc->beta;
+  double acc[2] = {0.0, 0.0};
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V; i += (size_t)gridDim.x * blockDim.x) {
+    int x, y, t;
+    vi.decode(i, g, x, y, t);
+    const float3 v = v_at(ub, lam, V, ph, g, x, y, t, inv_mu);
+    float3 gu;
+    const float kap = curvature_at(unew, g, x, y, t, eps2, &gu);
+    const float3 d = make_float3(v.x - gu.x, v.y - gu.y, v.z - gu.z);
+    lam[i] += mu * d.x;
+    lam[V + i] += mu * d.y;
+    lam[2 * V + i] += mu * d.z;
+    const float pn = phi_of(kap, a, b, kind);
+    ph[i] = pn;
+    const float un = __ldg(unew + i);
+    ubn[i] = un + beta * (un - __ldg(uk + i));
+    acc[0] += (double)pn * (double)sqrtf(gu.x * gu.x + gu.y * gu.y + gu.z * gu.z);
+    acc[1] += (double)d.x * d.x + (double)d.y * d.y + (double)d.z * d.z;
+  }
+  block_reduce_to<2>(acc, partials);
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 2 stencils
+// ---------------------------------------------------------------------------
+struct Alg2Coef {
+  float mu1, mu2, mu3, lam_w;
+  float a_u, b_u, a_t, b_t;
+  int kind;
+  float eps2;
+};
+
+__device__ __forceinline__ float mask_at(const int32_t* __restrict__ colpos, const Vox& g, int x, int y) {
+  return colpos ? (__ldg(colpos + x * g.ny + y) >= 0 ? 1.0f : 0.0f) : 1.0f;
+}
+
+// f = (lambda M tau0 + mu3 tau-bar - Lam3) / (lambda M + mu3)
+__device__ __forceinline__ float f_at(float m, float t0, float tb, float l3, const Alg2Coef& c) {
+  return (c.lam_w * m * t0 + c.mu3 * tb - l3) / (c.lam_w * m + c.mu3);
+}
+
+__global__ void __launch_bounds__(kStencilThreads)
+    k_pre2(const float* __restrict__ ub, const float* __restrict__ tb, const float* __restrict__ lam1,
+           const float* __restrict__ lam2, const float* __restrict__ lam3, const float* __restrict__ phu,
+           const float* __restrict__ pht, const float* __restrict__ tau0, const int32_t* __restrict__ colpos,
+           float* __restrict__ regu, float* __restrict__ regt, Vox g, VoxIter vi, Alg2Coef c, size_t V) {
+  const float im1 = 1.0f / c.mu1, im2 = 1.0f / c.mu2;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V; i += (size_t)gridDim.x * blockDim.x) {
+    int x, y, t;
+    vi.decode(i, g, x, y, t);
+    const int xm = (x - 1) & g.mx, ym = (y - 1) & g.my, tm = (t - 1) & g.mt;
+    const int ixm = g.idx(xm, y, t), iym = g.idx(x, ym, t), itm = g.idx(x, y, tm);
+    {
+      const float3 vc = v_at(ub, lam1, V, phu, g, x, y, t, im1);
+      const float qxm = v_at(ub, lam1, V, phu, g, xm, y, t, im1).x + __ldg(lam1 + ixm) * im1;
+      const float qym = v_at(ub, lam1, V, phu, g, x, ym, t, im1).y + __ldg(lam1 + V + iym) * im1;
+      const float qtm = v_at(ub, lam1, V, phu, g, x, y, tm, im1).z + __ldg(lam1 + 2 * V + itm) * im1;
+      regu[i] = -c.mu1 * ((vc.x + __ldg(lam1 + i) * im1 - qxm) + (vc.y + __ldg(lam1 + V + i) * im1 - qym) +
+                          (vc.z + __ldg(lam1 + 2 * V + i) * im1 - qtm));
+    }
+    {
+      const float3 wc = v_at(tb, lam2, V, pht, g, x, y, t, im2);
+      const float pxm = v_at(tb, lam2, V, pht, g, xm, y, t, im2).x + __ldg(lam2 + ixm) * im2;
+      const float pym = v_at(tb, lam2, V, pht, g, x, ym, t, im2).y + __ldg(lam2 + V + iym) * im2;
+      const float ptm = v_at(tb, lam2, V, pht, g, x, y, tm, im2).z + __ldg(lam2 + 2 * V + itm) * im2;
+      const float div = (wc.x + __ldg(lam2 + i) * im2 - pxm) + (wc.y + __ldg(lam2 + V + i) * im2 - pym) +
+                        (wc.z + __ldg(lam2 + 2 * V + i) * im2 - ptm);
+      const float l3 = __ldg(lam3 + i);
+      const float f = f_at(mask_at(colpos, g, x, y), __ldg(tau0 + i), __ldg(tb + i), l3, c);
+      regt[i] = -c.mu2 * div + c.mu3 * (f + l3 / c.mu3);
+    }
+  }
+}
+
+// Post step of Algorithm 2: multipliers, phi_u, phi_tau, extrapolation, and
+// partials 0 sum phi_u|grad u|, 1 sum phi_t|grad tau|, 2 sum (A u - tau)^2,
+// 3 sum M (tau - tau0)^2, 4 |v - grad u|^2, 5 |w - grad tau|^2, 6 (f - tau)^2.
+__global__ void __launch_bounds__(kStencilThreads)
+    k_post2(const float* __restrict__ unew, const float* __restrict__ uk, const float* __restrict__ ub,
+            const float* __restrict__ tnew, const float* __restrict__ tk, const float* __restrict__ tb,
+            float* __restrict__ lam1, float* __restrict__ lam2, float* __restrict__ lam3, float* __restrict__ phu,
+            float* __restrict__ pht, float* __restrict__ ubn, float* __restrict__ tbn, const float* __restrict__ au,
+            const float* __restrict__ tau0, const int32_t* __restrict__ colpos, const DevScalars* __restrict__ sc, Vox g,
+            VoxIter vi, Alg2Coef c, size_t V, double* __restrict__ partials) {
+  const float im1 = 1.0f / c.mu1, im2 = 1.0f / c.mu2;
+  const float beta = (float)sc->beta;
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V; i += (size_t)gridDim.x * blockDim.x) {
+    int x, y, t;
+    vi.decode(i, g, x, y, t);
+    const float3 v = v_at(ub, lam1, V, phu, g, x, y, t, im1);
+    const float3 w = v_at(tb, lam2, V, pht, g, x, y, t, im2);
+    const float m = mask_at(colpos, g, x, y);
+    const float t0 = __ldg(tau0 + i);
+    const float l3 = lam3[i];
+    const float f = f_at(m, t0, __ldg(tb + i), l3, c);
+    float3 gu, gt;
+    const float ku = curvature_at(unew, g, x, y, t, c.eps2, &gu);
+    const float kt = curvature_at(tnew, g, x, y, t, c.eps2, &gt);
+    const float3 dv = make_float3(v.x - gu.x, v.y - gu.y, v.z - gu.z);
+    const float3 dw = make_float3(w.x - gt.x, w.y - gt.y, w.z - gt.z);
+    const float tn = __ldg(tnew + i), un = __ldg(unew + i);
+    lam1[i] += c.mu1 * dv.x;
+    lam1[V + i] += c.mu1 * dv.y;
+    lam1[2 * V + i] += c.mu1 * dv.z;
+    lam2[i] += c.mu2 * dw.x;
+    lam2[V + i] += c.mu2 * dw.y;
+    lam2[2 * V + i] += c.mu2 * dw.z;
+    lam3[i] = l3 + c.mu3 * (f - tn);
+    const float pu = phi_of(ku, c.a_u, c.b_u, c.kind), pt = phi_of(kt, c.a_t, c.b_t, c.kind);
+    phu[i] = pu;
+    pht[i] = pt;
+    ubn[i] = un + beta * (un - __ldg(uk + i));
+    tbn[i] = tn + beta * (tn - __ldg(tk + i));
+    const float r = __ldg(au + i) - tn;
+    const float s = m * (tn - t0);
+    acc[0] += (double)pu * (double)sqrtf(gu.x * gu.x + gu.y * gu.y + gu.z * gu.z);
+    acc[1] += (double)pt * (double)sqrtf(gt.x * gt.x + gt.y * gt.y + gt.z * gt.z);
+    acc[2] += (double)r * r;
+    acc[3] += (double)s * s;
+    acc[4] += (double)dv.x * dv.x + (double)dv.y * dv.y + (double)dv.z * dv.z;
+    acc[5] += (double)dw.x * dw.x + (double)dw.y * dw.y + (double)dw.z * dw.z;
+    acc[6] += (double)(f - tn) * (f - tn);
+  }
+  block_reduce_to<7>(acc, partials);
+}
+
+// rhs of the tau-solve: x = A u+ + regt (used as the input of the periodic FFT)
+__global__ void k_add(const float* __restrict__ a, const float* __restrict__ b, float* __restrict__ o, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    o[i] = __ldg(a + i) + __ldg(b + i);
+}
+
+// ---------------------------------------------------------------------------
+// Scalar kernels (one thread)
+// ---------------------------------------------------------------------------
+// Backtracking test of the linearised u-step: f is quadratic, so
+// f(u+) - f(ubar) - <grad f(ubar), d> = 1/2 ||A d||^2 and the rule
+// f(u+) <= f(ubar) + <grad f, d> + L/2 ||d||^2 is ||A d||^2 <= L ||d||^2.
+__global__ void k_test(DevScalars* sc, const double* __restrict__ pd, int nbd, const double* __restrict__ pf, int nbf,
+                       double eta, int max_bt, int force_accept) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (sc->status != NLOS_OK) return;
+  const double dn2 = sum_partials(pd, nbd, 0);
+  const double r2 = sum_partials(pf, nbf, 0);
+  const double ad2 = sum_partials(pf, nbf, 1);
+  sc->test_lhs = ad2;
+  sc->test_rhs = sc->L * dn2;
+  const bool ok = ad2 <= sc->L * dn2;
+  if (ok || force_accept) {
+    sc->accept = 1;
+    sc->f_fit = 0.5 * r2;
+    const double tn = (1.0 + sqrt(1.0 + 4.0 * sc->t * sc->t)) / 2.0;
+    sc->beta = (sc->t - 1.0) / tn;
+    sc->t = tn;
+    sc->rej_iter = 0;
+  } else {
+    sc->accept = 0;
+    sc->L *= eta;
+    sc->backtracks += 1;
+    sc->rej_iter += 1;
+    if (sc->rej_iter > max_bt) sc->status = NLOS_ERR_DIVERGED;
+  }
+}
+
+// End of an iteration: energy, relative change, restart, bookkeeping.
+// model 1: E = f_fit + sum phi |grad u|; model 2: E from the post partials.
+__global__ void k_finalize(DevScalars* sc, const double* __restrict__ pp, int nb, int model, double lam_w,
+                           int restart, double eps_stop) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (sc->status != NLOS_OK) return;
+  double E, pres2;
+  if (model == 1) {
+    E = sc->f_fit + sum_partials(pp, nb, 0);
+    pres2 = sum_partials(pp, nb, 1);
+  } else {
+    const double fit = 0.5 * sum_partials(pp, nb, 2);
+    E = fit + 0.5 * lam_w * sum_partials(pp, nb, 3) + sum_partials(pp, nb, 0) + sum_partials(pp, nb, 1);
+    sc->f_fit = fit;
+    pres2 = sum_partials(pp, nb, 4);
+  }
+  const double e = E != 0.0 ? fabs(sc->E_prev - E) / fabs(E) : 0.0;
+  if (!isfinite(E)) sc->status = NLOS_ERR_DIVERGED;
+  if (restart && E > sc->E_prev) {
+    sc->t = 1.0;
+    sc->restarts += 1;
+  }
+  sc->beta_prev = sc->beta;
+  sc->E = E;
+  sc->e = e;
+  sc->E_prev = E;
+  sc->primal_res = sqrt(pres2);
+  sc->iter += 1;
+  if (eps_stop > 0.0 && e <= eps_stop) sc->stop = 1;
+}
+
+__global__ void k_init_scalars(DevScalars* sc, double L0, const double* __restrict__ pe, int nb, double e_scale) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  memset(sc, 0, sizeof(DevScalars));
+  sc->L = L0;
+  sc->t = 1.0;
+  sc->E_prev = e_scale * sum_partials(pe, nb, 0);
+  sc->status = NLOS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+struct SolverState {
+  int model = 0;
+  size_t V = 0;
+  float *uk = nullptr, *unew = nullptr, *ub = nullptr, *ubn = nullptr, *lam = nullptr, *ph = nullptr, *reg = nullptr;
+  float *tk = nullptr, *tnew = nullptr, *tb = nullptr, *tbn = nullptr, *lam2 = nullptr, *lam3 = nullptr,
+        *pht = nullptr, *regt = nullptr, *tmp = nullptr;
+  float* tau0c = nullptr;
+  float* cache[3] = {nullptr, nullptr, nullptr};
+  double *pa = nullptr, *pb = nullptr, *pc = nullptr;
+  DevScalars* sc = nullptr;
+  DevScalars* h_sc = nullptr;
+  std::vector<void*> allocs;
+};
+
+static nlos_status dalloc(SolverState* s, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(NLOS_ERR_OOM, std::string("cudaMalloc of solver state failed: ") + cudaGetErrorString(e));
+  }
+  s->allocs.push_back(*p);
+  return NLOS_OK;
+}
+
+void free_solver(SolverState* s) {
+  if (!s) return;
+  for (void* p : s->allocs) cudaFree(p);
+  if (s->h_sc) cudaFreeHost(s->h_sc);
+  delete s;
+}
+
+static nlos_status get_solver(Plan& P, int model, SolverState** out) {
+  if (P.solver[model]) {
+    *out = P.solver[model];
+    return NLOS_OK;
+  }
+  SolverState* s = new SolverState();
+  s->model = model;
+  const size_t V = (size_t)P.nx * P.ny * P.nt;
+  s->V = V;
+  const size_t F = V * sizeof(float);
+  nlos_status st = NLOS_OK;
+  auto A = [&](float** p, size_t bytes) {
+    if (st == NLOS_OK) st = dalloc(s, reinterpret_cast<void**>(p), bytes);
+  };
+  A(&s->uk, F); A(&s->unew, F); A(&s->ub, F); A(&s->ubn, F); A(&s->lam, 3 * F); A(&s->ph, F); A(&s->reg, F);
+  const size_t cachesz = model == 1 ? (size_t)P.ncols * P.nt * sizeof(float) : F;
+  for (int i = 0; i < 3; ++i) A(&s->cache[i], cachesz);
+  if (model == 1) {
+    A(&s->tau0c, (size_t)P.ncols * P.nt * sizeof(float));
+  } else {
+    A(&s->tk, F); A(&s->tnew, F); A(&s->tb, F); A(&s->tbn, F); A(&s->lam2, 3 * F); A(&s->lam3, F);
+    A(&s->pht, F); A(&s->regt, F); A(&s->tmp, F);
+  }
+  const size_t pbytes = sizeof(double) * kMaxTerms * 4096;
+  if (st == NLOS_OK) st = dalloc(s, reinterpret_cast<void**>(&s->pa), pbytes);
+  if (st == NLOS_OK) st = dalloc(s, reinterpret_cast<void**>(&s->pb), pbytes);
+  if (st == NLOS_OK) st = dalloc(s, reinterpret_cast<void**>(&s->pc), pbytes);
+  if (st == NLOS_OK) st = dalloc(s, reinterpret_cast<void**>(&s->sc), sizeof(DevScalars));
+  if (st == NLOS_OK) {
+    cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&s->h_sc), sizeof(DevScalars));
+    if (e != cudaSuccess) st = fail(NLOS_ERR_OOM, "cudaMallocHost failed");
+  }
+  if (st != NLOS_OK) {
+    free_solver(s);
+    return st;
+  }
+  P.solver[model] = s;
+  *out = s;
+  return NLOS_OK;
+}
+
+static int elem_grid(size_t n) { return (int)std::min<size_t>((n + 255) / 256, (size_t)152 * 16); }
+
+// Operator applications shared by the C API and the solvers.
+nlos_status apply_forward(const Plan& P, const float* u, float* out, bool compact, cudaStream_t st) {
+  const int full = P.nx * P.ny;
+  NLOS_TRY(launch_tfwd_rz(P, u, full, P.d_S, full, st));
+  if (compact) {
+    NLOS_TRY(launch_conv(P, P.d_S, false, P.d_Sc, true, false, st));
+    NLOS_TRY(launch_tinv_store(P, P.d_Sc, P.ncols, P.ncols, out, nullptr, st));
+  } else {
+    NLOS_TRY(launch_conv(P, P.d_S, false, P.d_S, false, false, st));
+    NLOS_TRY(launch_tinv_store(P, P.d_S, full, full, out, nullptr, st));
+  }
+  return NLOS_OK;
+}
+
+nlos_status apply_adjoint(const Plan& P, const float* r, float* u, bool compact, cudaStream_t st) {
+  const int full = P.nx * P.ny;
+  Lin3 src{{r, nullptr, nullptr}, {1.f, 0.f, 0.f}, nullptr};
+  if (compact) {
+    NLOS_TRY(launch_tfwd_rtt(P, src, P.ncols, P.d_Sc, P.ncols, st));
+    NLOS_TRY(launch_conv(P, P.d_Sc, true, P.d_S, false, true, st));
+  } else {
+    NLOS_TRY(launch_tfwd_rtt(P, src, full, P.d_S, full, st));
+    NLOS_TRY(launch_conv(P, P.d_S, false, P.d_S, false, true, st));
+  }
+  NLOS_TRY(launch_tadj_store(P, P.d_S, full, full, u, st));
+  return NLOS_OK;
+}
+
+nlos_status gather_columns(const Plan& P, const float* full, float* compact, cudaStream_t st) {
+  const size_t n = (size_t)P.ncols * P.nt;
+  { KTimer kt_(P, KC_SMALL, st);
+  k_gather_cols<<<elem_grid(n), 256, 0, st>>>(full, P.d_cols, P.ncols, P.nt, compact);
+  }
+  NLOS_LAUNCH_CHECK("k_gather_cols");
+  return NLOS_OK;
+}
+
+nlos_status apply_solve(const Plan& P, const float* rhs, float* x, double c0, double c1, cudaStream_t st) {
+  const int full = P.nx * P.ny;
+  NLOS_TRY(launch_sfwd(P, rhs, full, P.d_Sp, st));
+  NLOS_TRY(launch_sxy(P, P.d_Sp, nullptr, c0, c1, st));
+  NLOS_TRY(launch_sinv(P, P.d_Sp, full, x, nullptr, nullptr, nullptr, st));
+  return NLOS_OK;
+}
+
+nlos_status apply_curvature_weight(const Plan& P, const float* u, float* ph, double a, double b, int kind, double eps,
+                                   cudaStream_t st) {
+  const Vox g = make_vox(P.nx, P.ny, P.nt);
+  VoxIter vi{ilog2i(P.nt), ilog2i(P.ny)};
+  const size_t V = (size_t)P.nx * P.ny * P.nt;
+  { KTimer kt_(P, KC_SMALL, st);
+  k_curv_weight<<<kStencilBlocks, kStencilThreads, 0, st>>>(u, ph, g, vi, (float)a, (float)b, kind,
+                                                            (float)(eps * eps), V);
+  }
+  NLOS_LAUNCH_CHECK("k_curv_weight");
+  return NLOS_OK;
+}
+
+// Sum of squares of n floats, read back to the host (synchronises st).
+static nlos_status host_sumsq(const Plan& P, const float* a, size_t n, double* out, cudaStream_t st) {
+  { KTimer kt_(P, KC_SMALL, st);
+  k_sumsq<<<kStencilBlocks, kStencilThreads, 0, st>>>(a, n, P.d_partials);
+  }
+  NLOS_LAUNCH_CHECK("k_sumsq");
+  double* d_out = reinterpret_cast<double*>(P.d_scal);
+  { KTimer kt_(P, KC_SMALL, st);
+  k_sum_to<<<1, 1, 0, st>>>(P.d_partials, kStencilBlocks, 0, d_out);
+  }
+  NLOS_LAUNCH_CHECK("k_sum_to");
+  NLOS_CUDA(cudaMemcpyAsync(out, d_out, sizeof(double), cudaMemcpyDeviceToHost, st));
+  NLOS_CUDA(cudaStreamSynchronize(st));
+  return NLOS_OK;
+}
+
+// ||A_D||^2 by power iteration on A_D^T A_D from the all-ones vector.
+nlos_status plan_norm2(Plan& P, bool masked, cudaStream_t st, double* out) {
+  double& cached = masked ? P.norm2_masked : P.norm2_full;
+  if (cached >= 0.0) {
+    *out = cached;
+    return NLOS_OK;
+  }
+  const size_t V = (size_t)P.nx * P.ny * P.nt;
+  const bool compact = masked && !P.full_mask;
+  const size_t ny_elems = compact ? (size_t)P.ncols * P.nt : V;
+  float *x = nullptr, *y = nullptr;
+  if (cudaMalloc(&x, V * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(NLOS_ERR_OOM, "power iteration buffers");
+  }
+  if (cudaMalloc(&y, ny_elems * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(x);
+    return fail(NLOS_ERR_OOM, "power iteration buffers");
+  }
+  nlos_status s = NLOS_OK;
+  double lam = 0.0, lam_new = 0.0;
+  { KTimer kt_(P, KC_SMALL, st);
+  k_fill<<<elem_grid(V), 256, 0, st>>>(x, (float)(1.0 / std::sqrt((double)V)), V);
+  }
+  for (int it = 1; it <= 200 && s == NLOS_OK; ++it) {
+    s = apply_forward(P, x, y, compact, st);
+    if (s != NLOS_OK) break;
+    s = host_sumsq(P, y, ny_elems, &lam_new, st);
+    if (s != NLOS_OK) break;
+    s = apply_adjoint(P, y, x, compact, st);
+    if (s != NLOS_OK) break;
+    double nz2 = 0.0;
+    s = host_sumsq(P, x, V, &nz2, st);
+    if (s != NLOS_OK) break;
+    if (nz2 == 0.0) {
+      lam_new = 0.0;
+      break;
+    }
+    const double nz = std::sqrt(nz2);
+    double* d_nz = reinterpret_cast<double*>(P.d_scal) + 1;
+    cudaMemcpyAsync(d_nz, &nz, sizeof(double), cudaMemcpyHostToDevice, st);
+    { KTimer kt_(P, KC_SMALL, st);
+    k_scale<<<elem_grid(V), 256, 0, st>>>(x, d_nz, V);
+    }
+    if (it > 1 && std::fabs(lam_new - lam) <= 1e-12 * lam_new) break;
+    lam = lam_new;
+  }
+  cudaStreamSynchronize(st);
+  cudaFree(x);
+  cudaFree(y);
+  if (s != NLOS_OK) return s;
+  cached = lam_new;
+  *out = lam_new;
+  return NLOS_OK;
+}
+
+static nlos_status read_scalars(SolverState* s, cudaStream_t st) {
+  NLOS_CUDA(cudaMemcpyAsync(s->h_sc, s->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
+  NLOS_CUDA(cudaStreamSynchronize(st));
+  return NLOS_OK;
+}
+
+static void fill_stats(const DevScalars& d, nlos_stats* o) {
+  if (!o) return;
+  o->iters_done = d.iter;
+  o->backtracks = d.backtracks;
+  o->restarts = d.restarts;
+  o->status = d.status;
+  o->L = d.L;
+  o->energy = d.E;
+  o->rel_change = d.e;
+  o->data_fit = d.f_fit;
+  o->primal_res = d.primal_res;
+}
+
+template <typename T>
+static void swap_ptr(T*& a, T*& b) {
+  T* t = a;
+  a = b;
+  b = t;
+}
+
+// One linearised u-step with the backtracking loop (shared by both
+// algorithms): the adjoint end + solve rhs (the adjoint spectrum is in d_S),
+// the lateral solve, the periodic inverse (u+ and ||u+ - ubar||^2), the
+// forward operator on u+ (spectrum in d_S2) and the fit/test.
+struct UStepArgs {
+  const float* reg;
+  double mu;
+  bool compact;        // model 1: sampled columns only
+  const float* data;   // model 1: compact tau0; model 2: tau-bar (full)
+  double eta;
+  int max_bt;
+  float* au_out;       // cache slot receiving A u+
+  const float* auk;
+  const float* aukm1;
+};
+
+static nlos_status u_step(Plan& P, SolverState* s, const UStepArgs& a, bool host_check, double* L_host,
+                          cudaStream_t st) {
+  const int full = P.nx * P.ny;
+  const int ncols = a.compact ? P.ncols : full;
+  for (;;) {
+    SolveRhs sr{s->ub, a.reg, s->sc, 0.0};
+    NLOS_TRY(launch_tadj_solve(P, P.d_S, full, full, sr, P.d_Sp, st));
+    NLOS_TRY(launch_sxy(P, P.d_Sp, s->sc, 0.0, a.mu, st));
+    int nbd = 0, nbf = 0;
+    NLOS_TRY(launch_sinv(P, P.d_Sp, full, s->unew, s->ub, s->pa, &nbd, st));
+    NLOS_TRY(launch_tfwd_rz(P, s->unew, full, P.d_S2, full, st));
+    float2* Sfit = P.d_S2;
+    if (a.compact) {
+      NLOS_TRY(launch_conv(P, P.d_S2, false, P.d_Sc, true, false, st));
+      Sfit = P.d_Sc;
+    } else {
+      NLOS_TRY(launch_conv(P, P.d_S2, false, P.d_S2, false, false, st));
+    }
+    FitArgs fa{a.data, a.auk, a.aukm1, s->sc, s->pb};
+    NLOS_TRY(launch_tinv_fit(P, Sfit, ncols, ncols, a.au_out, fa, &nbf, st));
+    { KTimer kt_(P, KC_SMALL, st);
+    k_test<<<1, 1, 0, st>>>(s->sc, s->pa, nbd, s->pb, nbf, a.eta, a.max_bt, host_check ? 0 : 1);
+    }
+    NLOS_LAUNCH_CHECK("k_test");
+    if (!host_check) return NLOS_OK;
+    NLOS_TRY(read_scalars(s, st));
+    if (s->h_sc->status != NLOS_OK) return fail(NLOS_ERR_DIVERGED, "backtracking did not terminate");
+    if (s->h_sc->accept) return NLOS_OK;
+    *L_host = s->h_sc->L;  // rejected: L grew on the device, solve again
+  }
+}
+
+static nlos_status zero(float* p, size_t n, cudaStream_t st) {
+  NLOS_CUDA(cudaMemsetAsync(p, 0, n * sizeof(float), st));
+  return NLOS_OK;
+}
+
+static nlos_status fill(float* p, float v, size_t n, cudaStream_t st) {
+  k_fill<<<elem_grid(n), 256, 0, st>>>(p, v, n);
+  NLOS_LAUNCH_CHECK("k_fill");
+  return NLOS_OK;
+}
+
+static float phi_zero(double a, double b, int kind) {
+  (void)b;
+  return kind == NLOS_PHI_TRV ? (float)std::sqrt(a) : (float)a;
+}
+
+static nlos_status init_scalars(Plan& P, SolverState* s, double L0, const float* sumsq_src, size_t n, double scale,
+                                cudaStream_t st) {
+  { KTimer kt_(P, KC_SMALL, st);
+  k_sumsq<<<kStencilBlocks, kStencilThreads, 0, st>>>(sumsq_src, n, s->pc);
+  }
+  NLOS_LAUNCH_CHECK("k_sumsq");
+  { KTimer kt_(P, KC_SMALL, st);
+  k_init_scalars<<<1, 1, 0, st>>>(s->sc, L0, s->pc, kStencilBlocks, scale);
+  }
+  NLOS_LAUNCH_CHECK("k_init_scalars");
+  return NLOS_OK;
+}
+
+static nlos_status finish(Plan& P, SolverState* s, float* u_out, float* tau_out, nlos_stats* stats, cudaStream_t st) {
+  const size_t F = s->V * sizeof(float);
+  NLOS_CUDA(cudaMemcpyAsync(u_out, s->uk, F, cudaMemcpyDeviceToDevice, st));
+  if (tau_out && s->model == 2) NLOS_CUDA(cudaMemcpyAsync(tau_out, s->tk, F, cudaMemcpyDeviceToDevice, st));
+  NLOS_TRY(read_scalars(s, st));
+  fill_stats(*s->h_sc, stats);
+  if (s->h_sc->status != NLOS_OK) return fail(s->h_sc->status, "reconstruction stopped: non-finite energy or backtracking gave up");
+  return NLOS_OK;
+}
+
+static nlos_status run_alg1(Plan& P, const nlos_params& p, const float* tau0, float* u_out, nlos_stats* stats,
+                            cudaStream_t st) {
+  SolverState* s = nullptr;
+  NLOS_TRY(get_solver(P, 1, &s));
+  const size_t V = s->V;
+  const size_t C = (size_t)P.ncols * P.nt;
+  const Vox g = make_vox(P.nx, P.ny, P.nt);
+  const VoxIter vi{ilog2i(P.nt), ilog2i(P.ny)};
+  double norm2 = 0.0;
+  NLOS_TRY(plan_norm2(P, true, st, &norm2));
+  const double L0 = p.L0 > 0.0 ? p.L0 : 2.0 * norm2;
+  const int restart = p.restart < 0 ? 0 : p.restart;
+
+  NLOS_TRY(zero(s->uk, V, st));
+  NLOS_TRY(zero(s->ub, V, st));
+  NLOS_TRY(zero(s->lam, 3 * V, st));
+  for (int i = 0; i < 3; ++i) NLOS_TRY(zero(s->cache[i], C, st));
+  NLOS_TRY(fill(s->ph, phi_zero(p.a, p.b, p.phi), V, st));
+  NLOS_TRY(gather_columns(P, tau0, s->tau0c, st));
+  NLOS_TRY(init_scalars(P, s, L0, s->tau0c, C, 0.5, st));
+
+  int cur = 0, prev = 1, nxt = 2;
+  double L_host = L0;
+  const float eps2 = (float)(p.eps_normal * p.eps_normal);
+  for (int it = 0; it < p.iters; ++it) {
+    { KTimer kt_(P, KC_PRE, st);
+    k_pre1<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->ub, s->lam, s->ph, s->reg, g, vi, (float)p.mu, V);
+    }
+    NLOS_LAUNCH_CHECK("k_pre1");
+    Lin3 r{{s->cache[cur], s->cache[prev], s->tau0c}, {0.f, 0.f, 0.f}, s->sc};
+    NLOS_TRY(launch_tfwd_rtt(P, r, P.ncols, P.d_Sc, P.ncols, st));
+    NLOS_TRY(launch_conv(P, P.d_Sc, true, P.d_S, false, true, st));
+    const bool host_check = L_host < 1.5 * norm2;
+    UStepArgs ua{s->reg, p.mu, true, s->tau0c, p.eta, p.max_backtracks, s->cache[nxt], s->cache[cur], s->cache[prev]};
+    NLOS_TRY(u_step(P, s, ua, host_check, &L_host, st));
+    { KTimer kt_(P, KC_POST, st);
+    k_post1<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->unew, s->uk, s->ub, s->lam, s->ph, s->ubn, s->sc, g, vi,
+                                                        (float)p.mu, (float)p.a, (float)p.b, p.phi, eps2, V, s->pc);
+    }
+    NLOS_LAUNCH_CHECK("k_post1");
+    { KTimer kt_(P, KC_SMALL, st);
+    k_finalize<<<1, 1, 0, st>>>(s->sc, s->pc, kStencilBlocks, 1, 0.0, restart, p.eps_stop);
+    }
+    NLOS_LAUNCH_CHECK("k_finalize");
+    swap_ptr(s->uk, s->unew);
+    swap_ptr(s->ub, s->ubn);
+    const int t = prev;
+    prev = cur;
+    cur = nxt;
+    nxt = t;
+    if (p.eps_stop > 0.0) {
+      NLOS_TRY(read_scalars(s, st));
+      if (s->h_sc->stop || s->h_sc->status != NLOS_OK) break;
+    }
+  }
+  return finish(P, s, u_out, nullptr, stats, st);
+}
+
+static nlos_status run_alg2(Plan& P, const nlos_params& p, const float* tau0, float* u_out, float* tau_out,
+                            nlos_stats* stats, cudaStream_t st) {
+  SolverState* s = nullptr;
+  NLOS_TRY(get_solver(P, 2, &s));
+  const size_t V = s->V;
+  const Vox g = make_vox(P.nx, P.ny, P.nt);
+  const VoxIter vi{ilog2i(P.nt), ilog2i(P.ny)};
+  const int full = P.nx * P.ny;
+  double norm2 = 0.0;
+  NLOS_TRY(plan_norm2(P, false, st, &norm2));
+  const double L0 = p.L0 > 0.0 ? p.L0 : 2.0 * norm2;
+  const int restart = p.restart < 0 ? 1 : p.restart;
+  const int32_t* colpos = P.full_mask ? nullptr : P.d_colpos;
+
+  for (float* f : {s->uk, s->ub, s->tk, s->tb, s->lam3}) NLOS_TRY(zero(f, V, st));
+  NLOS_TRY(zero(s->lam, 3 * V, st));
+  NLOS_TRY(zero(s->lam2, 3 * V, st));
+  for (int i = 0; i < 3; ++i) NLOS_TRY(zero(s->cache[i], V, st));
+  NLOS_TRY(fill(s->ph, phi_zero(p.a_u, p.b_u, p.phi), V, st));
+  NLOS_TRY(fill(s->pht, phi_zero(p.a_tau, p.b_tau, p.phi), V, st));
+  // E(0, 0) = lambda/2 ||tau0||^2 over the sampled columns
+  NLOS_TRY(gather_columns(P, tau0, s->tmp, st));
+  NLOS_TRY(init_scalars(P, s, L0, s->tmp, (size_t)P.ncols * P.nt, 0.5 * p.lambda, st));
+
+  Alg2Coef c{(float)p.mu1, (float)p.mu2, (float)p.mu3, (float)p.lambda, (float)p.a_u, (float)p.b_u,
+             (float)p.a_tau, (float)p.b_tau, p.phi, (float)(p.eps_normal * p.eps_normal)};
+  int cur = 0, prev = 1, nxt = 2;
+  double L_host = L0;
+  for (int it = 0; it < p.iters; ++it) {
+    { KTimer kt_(P, KC_PRE, st);
+    k_pre2<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->ub, s->tb, s->lam, s->lam2, s->lam3, s->ph, s->pht, tau0,
+                                                       colpos, s->reg, s->regt, g, vi, c, V);
+    }
+    NLOS_LAUNCH_CHECK("k_pre2");
+    Lin3 r{{s->cache[cur], s->cache[prev], s->tb}, {0.f, 0.f, 0.f}, s->sc};
+    NLOS_TRY(launch_tfwd_rtt(P, r, full, P.d_S, full, st));
+    NLOS_TRY(launch_conv(P, P.d_S, false, P.d_S, false, true, st));
+    const bool host_check = L_host < 1.5 * norm2;
+    UStepArgs ua{s->reg, p.mu1, false, s->tb, p.eta, p.max_backtracks, s->cache[nxt], s->cache[cur], s->cache[prev]};
+    NLOS_TRY(u_step(P, s, ua, host_check, &L_host, st));
+    { KTimer kt_(P, KC_SMALL, st);
+    k_add<<<elem_grid(V), 256, 0, st>>>(s->cache[nxt], s->regt, s->tmp, V);
+    }
+    NLOS_LAUNCH_CHECK("k_add");
+    NLOS_TRY(launch_sfwd(P, s->tmp, full, P.d_Sp, st));
+    NLOS_TRY(launch_sxy(P, P.d_Sp, nullptr, 1.0 + p.mu3, p.mu2, st));
+    NLOS_TRY(launch_sinv(P, P.d_Sp, full, s->tnew, nullptr, nullptr, nullptr, st));
+    { KTimer kt_(P, KC_POST, st);
+    k_post2<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->unew, s->uk, s->ub, s->tnew, s->tk, s->tb, s->lam, s->lam2,
+                                                        s->lam3, s->ph, s->pht, s->ubn, s->tbn, s->cache[nxt], tau0,
+                                                        colpos, s->sc, g, vi, c, V, s->pc);
+    }
+    NLOS_LAUNCH_CHECK("k_post2");
+    { KTimer kt_(P, KC_SMALL, st);
+    k_finalize<<<1, 1, 0, st>>>(s->sc, s->pc, kStencilBlocks, 2, p.lambda, restart, p.eps_stop);
+    }
+    NLOS_LAUNCH_CHECK("k_finalize");
+    swap_ptr(s->uk, s->unew);
+    swap_ptr(s->ub, s->ubn);
+    swap_ptr(s->tk, s->tnew);
+    swap_ptr(s->tb, s->tbn);
+    const int t = prev;
+    prev = cur;
+    cur = nxt;
+    nxt = t;
+    if (p.eps_stop > 0.0) {
+      NLOS_TRY(read_scalars(s, st));
+      if (s->h_sc->stop || s->h_sc->status != NLOS_OK) break;
+    }
+  }
+  return finish(P, s, u_out, tau_out, stats, st);
+}
+
+nlos_status reconstruct(Plan& P, const nlos_params& p, const float* tau0, float* u_out, float* tau_out,
+                        nlos_stats* stats, cudaStream_t st) {
+  if (p.model == 1) return run_alg1(P, p, tau0, u_out, stats, st);
+  if (p.model == 2) return run_alg2(P, p, tau0, u_out, tau_out, stats, st);
+  return fail(NLOS_ERR_INVALID_ARG, "params->model must be 1 or 2");
+}
+
+}  // namespace nlos

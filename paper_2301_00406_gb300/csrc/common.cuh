@@ -1,0 +1,183 @@
+// Shared definitions of the CUDA implementation: error plumbing, complex
+// helpers, the plan structure and the device-side scalar block.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/nlos.h"
+
+namespace nlos {
+
+// ---------------------------------------------------------------------------
+// Errors: every internal failure becomes a status plus a thread-local message.
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+nlos_status fail(nlos_status code, const std::string& msg);
+nlos_status cuda_fail(cudaError_t e, const char* what);
+
+#define NLOS_CUDA(call)                                              \
+  do {                                                               \
+    cudaError_t e_ = (call);                                         \
+    if (e_ != cudaSuccess) return ::nlos::cuda_fail(e_, #call);      \
+  } while (0)
+
+#define NLOS_LAUNCH_CHECK(name)                                      \
+  do {                                                               \
+    cudaError_t e_ = cudaGetLastError();                             \
+    if (e_ != cudaSuccess) return ::nlos::cuda_fail(e_, name);       \
+  } while (0)
+
+#define NLOS_TRY(call)                                               \
+  do {                                                               \
+    nlos_status s_ = (call);                                         \
+    if (s_ != NLOS_OK) return s_;                                    \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Complex helpers (float2 = re, im)
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+__host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// ---------------------------------------------------------------------------
+// Device scalar block of one reconstruction: everything the iteration's
+// kernels need that changes from one iteration to the next lives here, so an
+// iteration is a fixed launch sequence (graph-capturable).
+// ---------------------------------------------------------------------------
+struct DevScalars {
+  double L;           // current Lipschitz estimate of the linearised u-step
+  double t;           // FISTA t_k
+  double beta_prev;   // weight that formed the current u-bar (cached A u-bar)
+  double beta;        // weight for the next extrapolation (set after the test)
+  double E_prev;      // energy before this iteration
+  double E, e;        // energy and relative change of the last iteration
+  double f_fit;       // data term of the last accepted iterate
+  double L_norm_ok;   // L above which acceptance is guaranteed (||A_D||^2 (1 + margin))
+  int32_t iter;       // iterations done
+  int32_t backtracks; // total rejections
+  int32_t restarts;   // FISTA restarts
+  int32_t status;     // NLOS_OK or an error code
+  int32_t accept;     // outcome of the last test (1 accepted)
+  int32_t rej_iter;   // rejections in the current iteration
+  int32_t stop;       // relative-energy stop reached
+  int32_t pad_;
+  double primal_res;  // ||v - grad u|| of the last iteration
+  double test_lhs, test_rhs;  // ||A d||^2 and L ||d||^2 of the last test
+};
+
+// Number of FP64 partial-sum slots per block used by the reductions.
+constexpr int kMaxTerms = 8;
+
+// ---------------------------------------------------------------------------
+// Plan
+// ---------------------------------------------------------------------------
+struct SolverState;  // defined in admm.cu
+
+struct Plan {
+  int nx, ny, nt;
+  double bin_width_s, wall_width_m, range_m;
+  int radiometry;
+  int ncols;          // number of sampled columns
+  bool full_mask;     // every column sampled
+  int device;
+
+  // host tables (FP64-derived, stored as the device uses them)
+  std::vector<int32_t> h_rz_i0, h_rt_k0, h_cols;
+  std::vector<float> h_rz_w, h_rt_w;  // 3 per bin
+  std::vector<uint8_t> h_mask;
+
+  // device tables
+  int32_t* d_rz_i0 = nullptr;    // [nt]
+  float* d_rz_w = nullptr;       // [3 nt]: w0, w1, g
+  int32_t* d_rzt_start = nullptr;// [nt+1]: v-bins j with i0_j == i are [start[i], start[i+1])
+  int32_t* d_rt_k0 = nullptr;    // [nt]
+  float* d_rt_w = nullptr;       // [3 nt]: w0, w1, wt
+  int32_t* d_rtt_start = nullptr;// [nt+1]: t-bins k with k0_k == j are [start[j], start[j+1])
+  int32_t* d_cols = nullptr;     // [ncols] sampled columns x*ny + y
+  int32_t* d_colpos = nullptr;   // [nx*ny] position of a column in d_cols, -1 if unsampled
+  float2* d_tw2t = nullptr;      // [2 nt]  exp(-2 pi i n / (2 nt))
+  float2* d_twt = nullptr;       // [nt]    exp(-2 pi i n / nt)
+  float2* d_twx = nullptr;       // [2 nx]  exp(-2 pi i n / (2 nx))
+  float2* d_twy = nullptr;       // [2 ny]
+  float* d_lamx = nullptr;       // [nx] 4 sin^2(pi k / nx)
+  float* d_lamy = nullptr;       // [ny]
+  float* d_lamt = nullptr;       // [nt]
+  float2* d_H = nullptr;         // [(nt+1)][(nx+1)][(ny+1)] cone-kernel spectrum
+
+  // scratch owned by the plan
+  float2* d_S = nullptr;         // [(nt+1)][nx][ny] padded t-spectrum (adjoint side)
+  float2* d_S2 = nullptr;        // [(nt+1)][nx][ny] padded t-spectrum (forward side)
+  float2* d_Sc = nullptr;        // [(nt+1)][ncols] compact spectrum of sampled columns
+  float2* d_Sp = nullptr;        // [(nt/2+1)][nx][ny] periodic spectrum (solve)
+  float* d_tmpc = nullptr;       // [ncols][nt] compact transient scratch
+  double* d_partials = nullptr;  // reduction partials
+  int partial_blocks = 0;
+  DevScalars* d_scal = nullptr;  // scratch scalars (norm, diagnostics)
+
+  double norm2_masked = -1.0, norm2_full = -1.0;
+  SolverState* solver[3] = {nullptr, nullptr, nullptr};
+
+  // optional per-launch timing (nlos_timing_enable): event pairs recorded
+  // around every kernel launch on the launch stream, harvested on read.
+  mutable bool timing = false;
+  mutable std::vector<cudaEvent_t> ev;
+  mutable std::vector<int> ev_cat;
+  mutable size_t ev_used = 0;
+};
+
+// Launch categories of the timer (index into nlos_timing_read's arrays).
+enum KernelCat {
+  KC_CONV = 0,      // k_conv: lateral padded convolution per kt plane
+  KC_TFWD = 1,      // k_tfwd: R_z or R_t^T + padded t-FFT
+  KC_TINV = 2,      // k_tinv: padded inverse t-FFT + R_t^{-1} (+ fit)
+  KC_TADJ = 3,      // k_tadj: inverse t-FFT + R_z^T (+ solve rhs, periodic t-FFT)
+  KC_SXY = 4,       // k_sxy: lateral periodic solve
+  KC_SFWD = 5,      // k_sfwd: periodic t-FFT of a field
+  KC_SINV = 6,      // k_sinv: periodic inverse t-FFT
+  KC_PRE = 7,       // k_pre1 / k_pre2: shrinkage + nabla^* stencils
+  KC_POST = 8,      // k_post1 / k_post2: multipliers, curvature, extrapolation
+  KC_SMALL = 9,     // one-thread scalar kernels, fills, gathers, reductions
+  KC_KSPEC = 10,    // k_kspec: cone-kernel spectrum (plan time)
+  KC_COUNT = 11
+};
+
+// RAII timer: records an event pair around the launches in its scope when
+// timing is enabled on the plan.
+struct KTimer {
+  const Plan& P;
+  cudaStream_t st;
+  size_t slot;
+  bool on;
+  KTimer(const Plan& p, int cat, cudaStream_t s);
+  ~KTimer();
+};
+
+// Operator applications (admm.cu)
+nlos_status apply_forward(const Plan& P, const float* u, float* out, bool compact, cudaStream_t st);
+nlos_status apply_adjoint(const Plan& P, const float* r, float* u, bool compact, cudaStream_t st);
+nlos_status gather_columns(const Plan& P, const float* full, float* compact, cudaStream_t st);
+nlos_status apply_solve(const Plan& P, const float* rhs, float* x, double c0, double c1, cudaStream_t st);
+nlos_status apply_curvature_weight(const Plan& P, const float* u, float* ph, double a, double b, int kind, double eps,
+                                   cudaStream_t st);
+nlos_status plan_norm2(Plan& P, bool masked, cudaStream_t st, double* out);
+nlos_status reconstruct(Plan& P, const nlos_params& p, const float* tau0, float* u_out, float* tau_out,
+                        nlos_stats* stats, cudaStream_t st);
+void free_solver(SolverState* s);
+
+// Launch configuration helpers
+inline int div_up(int a, int b) { return (a + b - 1) / b; }
+
+}  // namespace nlos

@@ -1,0 +1,70 @@
+// Declarations of the FFT-pass launchers implemented in lct.cu and the
+// stencil/reduction launchers implemented in admm.cu.
+#pragma once
+
+#include "common.cuh"
+
+namespace nlos {
+
+// A linear combination of up to three [cols][nt] sources, with coefficients
+// either fixed or taken from the device scalars (extrapolated residual
+// r = (1 + beta) P0 - beta P1 - P2, beta = sc->beta_prev).
+struct Lin3 {
+  const float* p[3];
+  float c[3];
+  const DevScalars* sc;  // non-null: c = {1 + beta_prev, -beta_prev, -1}
+};
+
+// Epilogue of the forward t-inverse pass.
+struct FitArgs {
+  const float* data;   // [cols][nt] data the fit is measured against (tau0 or tau-bar)
+  const float* auk;    // [cols][nt] A u^k (cache)
+  const float* aukm1;  // [cols][nt] A u^{k-1} (cache)
+  const DevScalars* sc;
+  double* partials;    // [gridDim][kMaxTerms]: 0 = sum (A u - data)^2, 1 = sum (A u - A u-bar)^2
+};
+
+// Solve-mode arguments of the adjoint end pass: rhs = c0 * ubar - grad f + reg.
+struct SolveRhs {
+  const float* ubar;
+  const float* reg;
+  const DevScalars* sc;  // c0 = sc->L when non-null, else c0_host
+  double c0_host;
+};
+
+// Forward t-pass of A: u~ = R_z u, zero-pad to 2 nt, real FFT -> S[kt][col],
+// kt in [0, nt].  u: [ncols][nt] (column col at u + col*nt).
+nlos_status launch_tfwd_rz(const Plan& P, const float* u, int ncols, float2* S, int pitch, cudaStream_t st);
+// Adjoint start: c = R_t^{-T} r with r from Lin3, then the same padded FFT.
+nlos_status launch_tfwd_rtt(const Plan& P, const Lin3& r, int ncols, float2* S, int pitch, cudaStream_t st);
+// Forward t-inverse: C2R of length 2 nt, keep [0, nt), tau = R_t^{-1} c.
+// outmap (nullable) maps column j to the output column index.
+nlos_status launch_tinv_store(const Plan& P, const float2* S, int pitch, int ncols, float* out,
+                              const int32_t* outmap, cudaStream_t st);
+nlos_status launch_tinv_fit(const Plan& P, const float2* S, int pitch, int ncols, float* out,
+                            const FitArgs& fa, int* nblocks, cudaStream_t st);
+// Adjoint end: C2R, crop, R_z^T -> g.  Store g, or form the solve rhs and
+// run the periodic real FFT into Sp[k][col], k in [0, nt/2].
+nlos_status launch_tadj_store(const Plan& P, const float2* S, int pitch, int ncols, float* out, cudaStream_t st);
+nlos_status launch_tadj_solve(const Plan& P, const float2* S, int pitch, int ncols, const SolveRhs& sr,
+                              float2* Sp, cudaStream_t st);
+// Periodic real FFT of a field, and its inverse (optionally with partial
+// sums of (x - ref)^2 into partials[block][0]).
+nlos_status launch_sfwd(const Plan& P, const float* x, int ncols, float2* Sp, cudaStream_t st);
+nlos_status launch_sinv(const Plan& P, const float2* Sp, int ncols, float* x, const float* ref,
+                        double* partials, int* nblocks, cudaStream_t st);
+// Lateral 2-D zero-padded convolution of each kt plane with H (adj: conj H).
+// in_cols/out_cols: nullptr = full plane [nx][ny]; else compact column lists
+// (the plan's sampled columns) with plane pitch ncols.
+nlos_status launch_conv(const Plan& P, const float2* Sin, bool in_compact, float2* Sout, bool out_compact,
+                        bool adj, cudaStream_t st);
+// Periodic lateral solve per kt plane: divide by c0 + c1 (lx + ly + lt).
+nlos_status launch_sxy(const Plan& P, float2* Sp, const DevScalars* sc, double c0_host, double c1,
+                       cudaStream_t st);
+// Cone-kernel spectrum of the plan (plan time).
+nlos_status launch_kernel_spectrum(const Plan& P, const int32_t* m0, const float2* hw, cudaStream_t st);
+
+// Shared-memory sizes (for attribute setup).
+size_t tpass_smem_bytes(int nt, int variant);
+
+}  // namespace nlos

@@ -1,0 +1,542 @@
+// Per-column t-passes of the LCT operator and of the periodic solve (see
+// lct.cu for the factorisation).  The kernels are templates on the number of
+// time bins; TpassOps<NT> holds the launchers of one size and is explicitly
+// instantiated in one translation unit per size so the build runs in parallel.
+#pragma once
+
+#include <type_traits>
+
+#include "fft.cuh"
+#include "passes.cuh"
+
+namespace nlos {
+
+template <int NT>
+struct TpassOps {
+  static nlos_status tfwd_rz(const Plan& P, const float* u, int ncols, float2* S, int pitch, cudaStream_t st);
+  static nlos_status tfwd_rtt(const Plan& P, const Lin3& r, int ncols, float2* S, int pitch, cudaStream_t st);
+  static nlos_status tinv_store(const Plan& P, const float2* S, int pitch, int ncols, float* out,
+                                const int32_t* outmap, cudaStream_t st);
+  static nlos_status tinv_fit(const Plan& P, const float2* S, int pitch, int ncols, float* out, const FitArgs& fa,
+                              int* nblocks, cudaStream_t st);
+  static nlos_status tadj_store(const Plan& P, const float2* S, int pitch, int ncols, float* out, cudaStream_t st);
+  static nlos_status tadj_solve(const Plan& P, const float2* S, int pitch, int ncols, const SolveRhs& sr, float2* Sp,
+                                cudaStream_t st);
+  static nlos_status sfwd(const Plan& P, const float* x, int ncols, float2* Sp, cudaStream_t st);
+  static nlos_status sinv(const Plan& P, const float2* Sp, int ncols, float* x, const float* ref, double* partials,
+                          int* nblocks, cudaStream_t st);
+};
+
+#ifdef NLOS_TPASS_IMPL
+
+// ---------------------------------------------------------------------------
+// t-pass geometry
+// ---------------------------------------------------------------------------
+template <int NT>
+struct TP {
+  static constexpr int COLS = NT >= 1024 ? 8 : 16;  // columns per CTA
+  static constexpr int PAIRS = COLS / 2;
+  static constexpr int WP = NT + 1;                 // odd pitch of a work transform
+  static constexpr size_t smem_base = sizeof(float2) * (2 * NT + PAIRS * WP) + sizeof(float) * COLS * NT;
+};
+constexpr int kTpassThreads = 256;
+
+
+// Block-wide FP64 reduction of NTERMS values; thread 0 writes partials[blockIdx.x * kMaxTerms + t].
+template <int NTERMS>
+__device__ __forceinline__ void block_reduce_store(double (&v)[NTERMS], double* partials) {
+  __shared__ double red[32][NTERMS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < NTERMS; ++t) {
+    double x = v[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    v[t] = x;
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int t = 0; t < NTERMS; ++t) red[warp][t] = v[t];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int t = 0; t < NTERMS; ++t) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += red[w][t];
+      partials[(size_t)blockIdx.x * kMaxTerms + t] = s;
+    }
+  }
+}
+
+// Post-processing of the padded forward t-FFT of packed pairs: writes bins
+// kt = 2 k' + half of both columns of every pair to S.
+template <int NT>
+__device__ __forceinline__ void tfwd_post_store(const float2* work, int half, float2* S, int pitch, int col0,
+                                                int ncols, int tid, int nthr) {
+  constexpr int COLS = TP<NT>::COLS, WP = TP<NT>::WP;
+  const int nk = half ? NT / 2 : NT / 2 + 1;
+  for (int i = tid; i < nk * COLS; i += nthr) {
+    const int kp = i / COLS, c = i % COLS, p = c >> 1;
+    if (col0 + c >= ncols) continue;
+    const int m = half ? (NT - 1 - kp) : ((NT - kp) & (NT - 1));
+    const float2 za = work[p * WP + fpos<NT>(kp)];
+    const float2 zb = work[p * WP + fpos<NT>(m)];
+    float2 x;
+    if ((c & 1) == 0)
+      x = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
+    else
+      x = make_float2(0.5f * (za.y + zb.y), -0.5f * (za.x - zb.x));
+    S[(size_t)(2 * kp + half) * pitch + col0 + c] = x;
+  }
+}
+
+// Loads the padded spectrum bins kt = 2 k' + half (k' in [0, nt)) of the CTA's
+// column pairs into `work` in the permuted input order of the inverse FFT,
+// using Hermitian symmetry for kt > nt, packed as Z = X_a + i X_b.
+template <int NT>
+__device__ __forceinline__ void tinv_load(const float2* __restrict__ S, int pitch, int col0, int ncols, int half,
+                                          float2* work, int tid, int nthr) {
+  constexpr int PAIRS = TP<NT>::PAIRS, WP = TP<NT>::WP;
+  for (int i = tid; i < NT * PAIRS; i += nthr) {
+    const int kp = i / PAIRS, p = i % PAIRS;
+    int kt = 2 * kp + half;
+    bool mir = kt > NT;
+    if (mir) kt = 2 * NT - kt;
+    const int ca = col0 + 2 * p, cb = ca + 1;
+    float2 A = ca < ncols ? __ldg(S + (size_t)kt * pitch + ca) : make_float2(0.f, 0.f);
+    float2 B = cb < ncols ? __ldg(S + (size_t)kt * pitch + cb) : make_float2(0.f, 0.f);
+    if (mir) {
+      A.y = -A.y;
+      B.y = -B.y;
+    }
+    work[p * WP + fpos<NT>(kp)] = make_float2(A.x - B.y, A.y + B.x);
+  }
+}
+
+// Inverse padded t-FFT of the CTA's pairs: cbuf[c][n] = (1/(2nt)) * real signal
+// of column c at n in [0, nt).
+template <int NT>
+__device__ __forceinline__ void tinv_core(const float2* __restrict__ S, int pitch, int col0, int ncols,
+                                          float2* work, float* cbuf, const float2* tw2, int tid, int nthr) {
+  constexpr int PAIRS = TP<NT>::PAIRS, WP = TP<NT>::WP;
+  const float scale = 1.0f / (2.0f * NT);
+  for (int half = 0; half < 2; ++half) {
+    tinv_load<NT>(S, pitch, col0, ncols, half, work, tid, nthr);
+    __syncthreads();
+    team_fft<NT, true>(work, PAIRS, WP, 1, tw2, 2, tid, nthr);
+    for (int i = tid; i < PAIRS * NT; i += nthr) {
+      const int p = i / NT, n = i % NT;
+      float2 z = work[p * WP + n];
+      if (half) z = cmulc(z, tw2[n]);
+      float* ca = cbuf + (2 * p) * NT;
+      float* cb = ca + NT;
+      if (half) {
+        ca[n] = (ca[n] + z.x) * scale;
+        cb[n] = (cb[n] + z.y) * scale;
+      } else {
+        ca[n] = z.x;
+        cb[n] = z.y;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Forward t-pass: R_z (MODE 0) or R_t^{-T} of a residual (MODE 1), then the
+// padded real FFT.
+// ---------------------------------------------------------------------------
+template <int NT, int MODE>
+__global__ void __launch_bounds__(kTpassThreads)
+    k_tfwd(Lin3 src, int ncols, float2* __restrict__ S, int pitch, const int32_t* __restrict__ i0t,
+           const float* __restrict__ wt3, const int32_t* __restrict__ tstart, const float2* __restrict__ tw2g) {
+  constexpr int COLS = TP<NT>::COLS, PAIRS = TP<NT>::PAIRS, WP = TP<NT>::WP;
+  extern __shared__ float4 smem_f4[];
+  float2* tw2 = reinterpret_cast<float2*>(smem_f4);
+  float2* work = tw2 + 2 * NT;
+  float* cbuf = reinterpret_cast<float*>(work + PAIRS * WP);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int col0 = blockIdx.x * COLS;
+  for (int i = tid; i < 2 * NT; i += nthr) tw2[i] = __ldg(tw2g + i);
+
+  // stage the CTA's input columns in shared memory
+  float c0 = src.c[0], c1 = src.c[1], c2 = src.c[2];
+  if (src.sc) {
+    const float b = (float)src.sc->beta_prev;
+    c0 = 1.0f + b;
+    c1 = -b;
+    c2 = -1.0f;
+  }
+  for (int i = tid; i < COLS * NT / 4; i += nthr) {
+    const int c = (i * 4) / NT;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (col0 + c < ncols) {
+      const size_t off = (size_t)col0 * NT / 4 + i;
+      const float4 a = __ldg(reinterpret_cast<const float4*>(src.p[0]) + off);
+      v = make_float4(c0 * a.x, c0 * a.y, c0 * a.z, c0 * a.w);
+      if (src.p[1]) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(src.p[1]) + off);
+        v.x += c1 * q.x; v.y += c1 * q.y; v.z += c1 * q.z; v.w += c1 * q.w;
+      }
+      if (src.p[2]) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(src.p[2]) + off);
+        v.x += c2 * q.x; v.y += c2 * q.y; v.z += c2 * q.z; v.w += c2 * q.w;
+      }
+    }
+    reinterpret_cast<float4*>(cbuf)[i] = v;
+  }
+  __syncthreads();
+
+  for (int half = 0; half < 2; ++half) {
+    for (int i = tid; i < PAIRS * NT; i += nthr) {
+      const int p = i / NT, n = i % NT;
+      const float* ca = cbuf + (2 * p) * NT;
+      const float* cb = ca + NT;
+      float a, b;
+      if (MODE == 0) {
+        // u~_n = g_n (w0_n u[i0_n] + w1_n u[i0_n + 1])
+        const int i0 = __ldg(i0t + n);
+        const float w0 = __ldg(wt3 + 3 * n), w1 = __ldg(wt3 + 3 * n + 1), g = __ldg(wt3 + 3 * n + 2);
+        a = g * (w0 * ca[i0] + w1 * ca[i0 + 1]);
+        b = g * (w0 * cb[i0] + w1 * cb[i0 + 1]);
+      } else {
+        // c_n = sum over t-bins k with k0_k = n of wt_k w0_k r_k
+        //     + sum over t-bins k with k0_k = n - 1 of wt_k w1_k r_k
+        a = 0.f;
+        b = 0.f;
+        const int s0 = __ldg(tstart + n), s1 = __ldg(tstart + n + 1);
+        for (int k = s0; k < s1; ++k) {
+          const float w = __ldg(wt3 + 3 * k) * __ldg(wt3 + 3 * k + 2);
+          a += w * ca[k];
+          b += w * cb[k];
+        }
+        if (n > 0) {
+          const int sm = __ldg(tstart + n - 1);
+          for (int k = sm; k < s0; ++k) {
+            const float w = __ldg(wt3 + 3 * k + 1) * __ldg(wt3 + 3 * k + 2);
+            a += w * ca[k];
+            b += w * cb[k];
+          }
+        }
+      }
+      float2 z = make_float2(a, b);
+      if (half) z = cmul(z, tw2[n]);
+      work[p * WP + n] = z;
+    }
+    __syncthreads();
+    team_fft<NT, false>(work, PAIRS, WP, 1, tw2, 2, tid, nthr);
+    tfwd_post_store<NT>(work, half, S, pitch, col0, ncols, tid, nthr);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Forward t-inverse: C2R, crop, R_t^{-1}; store or fit epilogue.
+// ---------------------------------------------------------------------------
+template <int NT, int EPI>
+__global__ void __launch_bounds__(kTpassThreads)
+    k_tinv(const float2* __restrict__ S, int pitch, int ncols, float* __restrict__ out,
+           const int32_t* __restrict__ outmap, FitArgs fa, const int32_t* __restrict__ k0t,
+           const float* __restrict__ wt3, const float2* __restrict__ tw2g) {
+  constexpr int COLS = TP<NT>::COLS, PAIRS = TP<NT>::PAIRS, WP = TP<NT>::WP;
+  extern __shared__ float4 smem_f4[];
+  float2* tw2 = reinterpret_cast<float2*>(smem_f4);
+  float2* work = tw2 + 2 * NT;
+  float* cbuf = reinterpret_cast<float*>(work + PAIRS * WP);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int col0 = blockIdx.x * COLS;
+  for (int i = tid; i < 2 * NT; i += nthr) tw2[i] = __ldg(tw2g + i);
+  __syncthreads();
+  tinv_core<NT>(S, pitch, col0, ncols, work, cbuf, tw2, tid, nthr);
+
+  double acc[2] = {0.0, 0.0};
+  float bp = 0.f;
+  if (EPI == 1) bp = (float)fa.sc->beta_prev;
+  for (int i = tid; i < COLS * NT; i += nthr) {
+    const int c = i / NT, k = i % NT;
+    if (col0 + c >= ncols) continue;
+    const float* cc = cbuf + c * NT;
+    const int k0 = __ldg(k0t + k);
+    const float tau = __ldg(wt3 + 3 * k + 2) * (__ldg(wt3 + 3 * k) * cc[k0] + __ldg(wt3 + 3 * k + 1) * cc[k0 + 1]);
+    const int oc = outmap ? __ldg(outmap + col0 + c) : col0 + c;
+    const size_t o = (size_t)oc * NT + k;
+    out[o] = tau;
+    if (EPI == 1) {
+      const size_t g = (size_t)(col0 + c) * NT + k;
+      const float r = tau - __ldg(fa.data + g);
+      const float aub = (1.0f + bp) * __ldg(fa.auk + g) - bp * __ldg(fa.aukm1 + g);
+      const float d = tau - aub;
+      acc[0] += (double)r * (double)r;
+      acc[1] += (double)d * (double)d;
+    }
+  }
+  if (EPI == 1) block_reduce_store<2>(acc, fa.partials);
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint end: C2R, crop, R_z^T.  MODE 0 stores g; MODE 1 forms the solve
+// right-hand side rhs = L u-bar - g + reg and runs the periodic real FFT.
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ __forceinline__ void periodic_fwd_post(const float2* work, float2* Sp, int col0, int ncols, int pitch,
+                                                  int tid, int nthr) {
+  constexpr int COLS = TP<NT>::COLS, WP = TP<NT>::WP;
+  for (int i = tid; i < (NT / 2 + 1) * COLS; i += nthr) {
+    const int k = i / COLS, c = i % COLS, p = c >> 1;
+    if (col0 + c >= ncols) continue;
+    const float2 za = work[p * WP + fpos<NT>(k)];
+    const float2 zb = work[p * WP + fpos<NT>((NT - k) & (NT - 1))];
+    float2 x;
+    if ((c & 1) == 0)
+      x = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
+    else
+      x = make_float2(0.5f * (za.y + zb.y), -0.5f * (za.x - zb.x));
+    Sp[(size_t)k * pitch + col0 + c] = x;
+  }
+}
+
+template <int NT, int MODE>
+__global__ void __launch_bounds__(kTpassThreads)
+    k_tadj(const float2* __restrict__ S, int pitch, int ncols, float* __restrict__ out, SolveRhs sr,
+           float2* __restrict__ Sp, const int32_t* __restrict__ i0t, const float* __restrict__ wt3,
+           const int32_t* __restrict__ zstart, const float2* __restrict__ tw2g) {
+  constexpr int COLS = TP<NT>::COLS, PAIRS = TP<NT>::PAIRS, WP = TP<NT>::WP;
+  extern __shared__ float4 smem_f4[];
+  float2* tw2 = reinterpret_cast<float2*>(smem_f4);
+  float2* work = tw2 + 2 * NT;
+  float* cbuf = reinterpret_cast<float*>(work + PAIRS * WP);
+  float* gbuf = cbuf + COLS * NT;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int col0 = blockIdx.x * COLS;
+  for (int i = tid; i < 2 * NT; i += nthr) tw2[i] = __ldg(tw2g + i);
+  __syncthreads();
+  tinv_core<NT>(S, pitch, col0, ncols, work, cbuf, tw2, tid, nthr);
+
+  // g_i = sum_{j: i0_j = i} g_j w0_j c_j + sum_{j: i0_j = i - 1} g_j w1_j c_j
+  for (int idx = tid; idx < COLS * NT; idx += nthr) {
+    const int c = idx / NT, i = idx % NT;
+    const float* cc = cbuf + c * NT;
+    float acc = 0.f;
+    const int s0 = __ldg(zstart + i), s1 = __ldg(zstart + i + 1);
+    for (int j = s0; j < s1; ++j) acc += __ldg(wt3 + 3 * j) * __ldg(wt3 + 3 * j + 2) * cc[j];
+    if (i > 0) {
+      const int sm = __ldg(zstart + i - 1);
+      for (int j = sm; j < s0; ++j) acc += __ldg(wt3 + 3 * j + 1) * __ldg(wt3 + 3 * j + 2) * cc[j];
+    }
+    gbuf[idx] = acc;
+  }
+  __syncthreads();
+
+  if (MODE == 0) {
+    for (int i = tid; i < COLS * NT / 4; i += nthr) {
+      const int c = (i * 4) / NT;
+      if (col0 + c < ncols)
+        reinterpret_cast<float4*>(out)[(size_t)col0 * NT / 4 + i] = reinterpret_cast<const float4*>(gbuf)[i];
+    }
+    return;
+  }
+  const float L = sr.sc ? (float)sr.sc->L : (float)sr.c0_host;
+  for (int i = tid; i < PAIRS * NT; i += nthr) {
+    const int p = i / NT, n = i % NT;
+    const int ca = col0 + 2 * p, cb = ca + 1;
+    float a = 0.f, b = 0.f;
+    if (ca < ncols) {
+      const size_t g = (size_t)ca * NT + n;
+      a = L * __ldg(sr.ubar + g) - gbuf[(2 * p) * NT + n] + __ldg(sr.reg + g);
+    }
+    if (cb < ncols) {
+      const size_t g = (size_t)cb * NT + n;
+      b = L * __ldg(sr.ubar + g) - gbuf[(2 * p + 1) * NT + n] + __ldg(sr.reg + g);
+    }
+    work[p * WP + n] = make_float2(a, b);
+  }
+  __syncthreads();
+  team_fft<NT, false>(work, PAIRS, WP, 1, tw2, 2, tid, nthr);
+  periodic_fwd_post<NT>(work, Sp, col0, ncols, ncols, tid, nthr);
+}
+
+// Periodic real FFT of a field (rhs of a solve).
+template <int NT>
+__global__ void __launch_bounds__(kTpassThreads)
+    k_sfwd(const float* __restrict__ x, int ncols, float2* __restrict__ Sp, const float2* __restrict__ tw2g) {
+  constexpr int PAIRS = TP<NT>::PAIRS, WP = TP<NT>::WP, COLS = TP<NT>::COLS;
+  extern __shared__ float4 smem_f4[];
+  float2* tw2 = reinterpret_cast<float2*>(smem_f4);
+  float2* work = tw2 + 2 * NT;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int col0 = blockIdx.x * COLS;
+  for (int i = tid; i < 2 * NT; i += nthr) tw2[i] = __ldg(tw2g + i);
+  for (int i = tid; i < PAIRS * NT; i += nthr) {
+    const int p = i / NT, n = i % NT;
+    const int ca = col0 + 2 * p, cb = ca + 1;
+    const float a = ca < ncols ? __ldg(x + (size_t)ca * NT + n) : 0.f;
+    const float b = cb < ncols ? __ldg(x + (size_t)cb * NT + n) : 0.f;
+    work[p * WP + n] = make_float2(a, b);
+  }
+  __syncthreads();
+  team_fft<NT, false>(work, PAIRS, WP, 1, tw2, 2, tid, nthr);
+  periodic_fwd_post<NT>(work, Sp, col0, ncols, ncols, tid, nthr);
+}
+
+// Periodic inverse real FFT to a field; optional partial sums of (x - ref)^2.
+template <int NT>
+__global__ void __launch_bounds__(kTpassThreads)
+    k_sinv(const float2* __restrict__ Sp, int ncols, float* __restrict__ x, const float* __restrict__ ref,
+           double* __restrict__ partials, const float2* __restrict__ tw2g) {
+  constexpr int PAIRS = TP<NT>::PAIRS, WP = TP<NT>::WP, COLS = TP<NT>::COLS;
+  extern __shared__ float4 smem_f4[];
+  float2* tw2 = reinterpret_cast<float2*>(smem_f4);
+  float2* work = tw2 + 2 * NT;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int col0 = blockIdx.x * COLS;
+  for (int i = tid; i < 2 * NT; i += nthr) tw2[i] = __ldg(tw2g + i);
+  for (int i = tid; i < NT * PAIRS; i += nthr) {
+    const int k = i / PAIRS, p = i % PAIRS;
+    int kk = k;
+    const bool mir = k > NT / 2;
+    if (mir) kk = NT - k;
+    const int ca = col0 + 2 * p, cb = ca + 1;
+    float2 A = ca < ncols ? __ldg(Sp + (size_t)kk * ncols + ca) : make_float2(0.f, 0.f);
+    float2 B = cb < ncols ? __ldg(Sp + (size_t)kk * ncols + cb) : make_float2(0.f, 0.f);
+    if (mir) {
+      A.y = -A.y;
+      B.y = -B.y;
+    }
+    work[p * WP + fpos<NT>(k)] = make_float2(A.x - B.y, A.y + B.x);
+  }
+  __syncthreads();
+  team_fft<NT, true>(work, PAIRS, WP, 1, tw2, 2, tid, nthr);
+  const float scale = 1.0f / NT;
+  double acc[1] = {0.0};
+  for (int i = tid; i < COLS * NT; i += nthr) {
+    const int c = i / NT, n = i % NT;
+    if (col0 + c >= ncols) continue;
+    const float2 z = work[(c >> 1) * WP + n];
+    const float v = ((c & 1) ? z.y : z.x) * scale;
+    const size_t g = (size_t)(col0 + c) * NT + n;
+    x[g] = v;
+    if (ref) {
+      const float d = v - __ldg(ref + g);
+      acc[0] += (double)d * (double)d;
+    }
+  }
+  if (partials) block_reduce_store<1>(acc, partials);
+}
+
+
+template <typename K>
+static nlos_status set_smem_tp(K kernel, size_t bytes) {
+  NLOS_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return NLOS_OK;
+}
+
+template <int NT>
+nlos_status TpassOps<NT>::tfwd_rz(const Plan& P, const float* u, int ncols, float2* S, int pitch, cudaStream_t st) {
+  KTimer kt_(P, KC_TFWD, st);
+  auto kern = k_tfwd<NT, 0>;
+  const size_t sm = TP<NT>::smem_base;
+  NLOS_TRY(set_smem_tp(kern, sm));
+  Lin3 src{{u, nullptr, nullptr}, {1.f, 0.f, 0.f}, nullptr};
+  kern<<<div_up(ncols, TP<NT>::COLS), kTpassThreads, sm, st>>>(src, ncols, S, pitch, P.d_rz_i0, P.d_rz_w, nullptr,
+                                                               P.d_tw2t);
+  NLOS_LAUNCH_CHECK("k_tfwd<rz>");
+  return NLOS_OK;
+}
+
+template <int NT>
+nlos_status TpassOps<NT>::tfwd_rtt(const Plan& P, const Lin3& r, int ncols, float2* S, int pitch, cudaStream_t st) {
+  KTimer kt_(P, KC_TFWD, st);
+  auto kern = k_tfwd<NT, 1>;
+  const size_t sm = TP<NT>::smem_base;
+  NLOS_TRY(set_smem_tp(kern, sm));
+  kern<<<div_up(ncols, TP<NT>::COLS), kTpassThreads, sm, st>>>(r, ncols, S, pitch, nullptr, P.d_rt_w, P.d_rtt_start,
+                                                               P.d_tw2t);
+  NLOS_LAUNCH_CHECK("k_tfwd<rtt>");
+  return NLOS_OK;
+}
+
+template <int NT>
+nlos_status TpassOps<NT>::tinv_store(const Plan& P, const float2* S, int pitch, int ncols, float* out,
+                                     const int32_t* outmap, cudaStream_t st) {
+  KTimer kt_(P, KC_TINV, st);
+  auto kern = k_tinv<NT, 0>;
+  const size_t sm = TP<NT>::smem_base;
+  NLOS_TRY(set_smem_tp(kern, sm));
+  FitArgs fa{};
+  kern<<<div_up(ncols, TP<NT>::COLS), kTpassThreads, sm, st>>>(S, pitch, ncols, out, outmap, fa, P.d_rt_k0, P.d_rt_w,
+                                                               P.d_tw2t);
+  NLOS_LAUNCH_CHECK("k_tinv<store>");
+  return NLOS_OK;
+}
+
+template <int NT>
+nlos_status TpassOps<NT>::tinv_fit(const Plan& P, const float2* S, int pitch, int ncols, float* out,
+                                   const FitArgs& fa, int* nblocks, cudaStream_t st) {
+  KTimer kt_(P, KC_TINV, st);
+  auto kern = k_tinv<NT, 1>;
+  const size_t sm = TP<NT>::smem_base;
+  NLOS_TRY(set_smem_tp(kern, sm));
+  const int nb = div_up(ncols, TP<NT>::COLS);
+  if (nb > P.partial_blocks) return fail(NLOS_ERR_INVALID_ARG, "partials buffer too small");
+  *nblocks = nb;
+  kern<<<nb, kTpassThreads, sm, st>>>(S, pitch, ncols, out, nullptr, fa, P.d_rt_k0, P.d_rt_w, P.d_tw2t);
+  NLOS_LAUNCH_CHECK("k_tinv<fit>");
+  return NLOS_OK;
+}
+
+template <int NT>
+nlos_status TpassOps<NT>::tadj_store(const Plan& P, const float2* S, int pitch, int ncols, float* out,
+                                     cudaStream_t st) {
+  KTimer kt_(P, KC_TADJ, st);
+  auto kern = k_tadj<NT, 0>;
+  const size_t sm = TP<NT>::smem_base + sizeof(float) * TP<NT>::COLS * NT;
+  NLOS_TRY(set_smem_tp(kern, sm));
+  SolveRhs sr{};
+  kern<<<div_up(ncols, TP<NT>::COLS), kTpassThreads, sm, st>>>(S, pitch, ncols, out, sr, nullptr, P.d_rz_i0, P.d_rz_w,
+                                                               P.d_rzt_start, P.d_tw2t);
+  NLOS_LAUNCH_CHECK("k_tadj<store>");
+  return NLOS_OK;
+}
+
+template <int NT>
+nlos_status TpassOps<NT>::tadj_solve(const Plan& P, const float2* S, int pitch, int ncols, const SolveRhs& sr,
+                                     float2* Sp, cudaStream_t st) {
+  KTimer kt_(P, KC_TADJ, st);
+  auto kern = k_tadj<NT, 1>;
+  const size_t sm = TP<NT>::smem_base + sizeof(float) * TP<NT>::COLS * NT;
+  NLOS_TRY(set_smem_tp(kern, sm));
+  kern<<<div_up(ncols, TP<NT>::COLS), kTpassThreads, sm, st>>>(S, pitch, ncols, nullptr, sr, Sp, P.d_rz_i0, P.d_rz_w,
+                                                               P.d_rzt_start, P.d_tw2t);
+  NLOS_LAUNCH_CHECK("k_tadj<solve>");
+  return NLOS_OK;
+}
+
+template <int NT>
+nlos_status TpassOps<NT>::sfwd(const Plan& P, const float* x, int ncols, float2* Sp, cudaStream_t st) {
+  KTimer kt_(P, KC_SFWD, st);
+  auto kern = k_sfwd<NT>;
+  const size_t sm = sizeof(float2) * (2 * NT + TP<NT>::PAIRS * TP<NT>::WP);
+  NLOS_TRY(set_smem_tp(kern, sm));
+  kern<<<div_up(ncols, TP<NT>::COLS), kTpassThreads, sm, st>>>(x, ncols, Sp, P.d_tw2t);
+  NLOS_LAUNCH_CHECK("k_sfwd");
+  return NLOS_OK;
+}
+
+template <int NT>
+nlos_status TpassOps<NT>::sinv(const Plan& P, const float2* Sp, int ncols, float* x, const float* ref,
+                               double* partials, int* nblocks, cudaStream_t st) {
+  KTimer kt_(P, KC_SINV, st);
+  auto kern = k_sinv<NT>;
+  const size_t sm = sizeof(float2) * (2 * NT + TP<NT>::PAIRS * TP<NT>::WP);
+  NLOS_TRY(set_smem_tp(kern, sm));
+  const int nb = div_up(ncols, TP<NT>::COLS);
+  if (partials && nb > P.partial_blocks) return fail(NLOS_ERR_INVALID_ARG, "partials buffer too small");
+  if (nblocks) *nblocks = nb;
+  kern<<<nb, kTpassThreads, sm, st>>>(Sp, ncols, x, ref, partials, P.d_tw2t);
+  NLOS_LAUNCH_CHECK("k_sinv");
+  return NLOS_OK;
+}
+
+#endif  // NLOS_TPASS_IMPL
+
+}  // namespace nlos

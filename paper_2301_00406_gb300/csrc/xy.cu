@@ -1,0 +1,290 @@
+// FFT passes of the light-cone-transform operator A = R_t^{-1} H R_z (Eq. 3),
+// of its transpose, and of the periodic solve of Eq. 11.
+//
+// Data layout in HBM (row-major, t fastest): volumes and transients are
+// [nx][ny][nt] float32, i.e. one contiguous column of nt values per scan
+// point.  Spectra are stored transposed, [kt][col] complex64, so that the
+// lateral passes read whole kt planes.
+//
+// The zero-padded 3-D FFT of the convolution is factored into
+//  * a t-pass per column: real signal of length nt zero-padded to 2 nt.
+//    Two real columns a, b are packed as z = a + i b; the even and odd bins of
+//    the padded length-2nt DFT of z are two length-nt DFTs (of z and of
+//    z * exp(-i pi n / nt)), and the bins of a and b are separated with
+//    Hermitian symmetry.  Only kt in [0, nt] is kept.
+//  * a lateral pass per kt plane on a pair of CTAs in a thread-block cluster:
+//    CTA r handles the ky bins of parity r of the 2 ny-point padded DFT
+//    (again an ny-point DFT of a twisted row), runs the 2 nx-point padded
+//    transform along x as two nx-point DFTs per column, multiplies by the
+//    kernel spectrum, transforms back, and the pair sums its two halves of
+//    the result through distributed shared memory.
+// No padded array ever reaches HBM.
+#include <cooperative_groups.h>
+
+#include <type_traits>
+
+#include "fft.cuh"
+#include "passes.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace nlos {
+
+// ---------------------------------------------------------------------------
+// Lateral convolution per kt plane on a CTA pair (cluster of 2).
+// ---------------------------------------------------------------------------
+template <int N>
+struct CV {
+  static constexpr int P = N + 1;                 // odd row pitch of the plane
+  static constexpr int CH = N >= 16 ? 16 : N;     // columns per x-chunk
+  static constexpr int SP = 2 * CH + 1;           // pitch of the chunk scratch
+  static constexpr size_t smem = sizeof(float2) * (N * P + N * SP + 2 * N);
+};
+constexpr int kConvThreads = 512;
+
+template <int N>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kConvThreads)
+    k_conv(const float2* __restrict__ Sin, int in_pitch, const int32_t* __restrict__ in_cols, int in_n,
+           float2* __restrict__ Sout, int out_pitch, const int32_t* __restrict__ out_cols, int out_n,
+           const float2* __restrict__ H, int adj, const float2* __restrict__ twg) {
+  constexpr int P = CV<N>::P, CH = CV<N>::CH, SP = CV<N>::SP;
+  extern __shared__ float4 smem_f4[];
+  float2* plane = reinterpret_cast<float2*>(smem_f4);   // [N][P]
+  float2* scr = plane + N * P;                           // [N][SP]
+  float2* tw = scr + N * SP;                             // [2N]: exp(-2 pi i n / 2N)
+  cg::cluster_group cluster = cg::this_cluster();
+  const int r = (int)cluster.block_rank();
+  const int kt = blockIdx.x >> 1;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  for (int i = tid; i < 2 * N; i += nthr) tw[i] = __ldg(twg + i);
+  __syncthreads();
+
+  // 1. load the plane with the y-twist of parity r
+  const float2* src = Sin + (size_t)kt * in_pitch;
+  if (in_cols == nullptr) {
+    for (int i = tid; i < N * N; i += nthr) {
+      const int x = i / N, y = i % N;
+      float2 v = __ldg(src + i);
+      if (r) v = cmul(v, tw[y]);
+      plane[x * P + y] = v;
+    }
+  } else {
+    for (int i = tid; i < N * P; i += nthr) plane[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    for (int j = tid; j < in_n; j += nthr) {
+      const int col = __ldg(in_cols + j);
+      const int x = col / N, y = col % N;
+      float2 v = __ldg(src + j);
+      if (r) v = cmul(v, tw[y]);
+      plane[x * P + y] = v;
+    }
+  }
+  __syncthreads();
+
+  // 2. y-DFT of every row (ky' positions, permuted)
+  team_fft<N, false>(plane, N, P, 1, tw, 2, tid, nthr);
+
+  // 3. x-direction padded convolution, CH columns at a time
+  const float2* Hk = H + (size_t)kt * (N + 1) * (N + 1);
+  for (int c0 = 0; c0 < N; c0 += CH) {
+    for (int i = tid; i < N * CH; i += nthr) {
+      const int x = i / CH, j = i % CH;
+      const float2 v = plane[x * P + c0 + j];
+      scr[x * SP + j] = v;
+      scr[x * SP + CH + j] = cmul(v, tw[x]);
+    }
+    __syncthreads();
+    team_fft<N, false>(scr, 2 * CH, 1, SP, tw, 2, tid, nthr);
+    for (int i = tid; i < N * 2 * CH; i += nthr) {
+      const int xp = i / (2 * CH), t = i % (2 * CH);
+      const int ax = t / CH, j = t % CH;
+      int kx = 2 * kfreq<N>(xp) + ax;
+      int ky = 2 * kfreq<N>(c0 + j) + r;
+      if (kx > N) kx = 2 * N - kx;
+      if (ky > N) ky = 2 * N - ky;
+      const float2 h = __ldg(Hk + kx * (N + 1) + ky);
+      const float2 v = scr[xp * SP + t];
+      scr[xp * SP + t] = adj ? cmulc(v, h) : cmul(v, h);
+    }
+    __syncthreads();
+    team_fft<N, true>(scr, 2 * CH, 1, SP, tw, 2, tid, nthr);
+    for (int i = tid; i < N * CH; i += nthr) {
+      const int x = i / CH, j = i % CH;
+      plane[x * P + c0 + j] = cadd(scr[x * SP + j], cmulc(scr[x * SP + CH + j], tw[x]));
+    }
+    __syncthreads();
+  }
+
+  // 4. inverse y-DFT of every row (natural y order)
+  team_fft<N, true>(plane, N, P, 1, tw, 2, tid, nthr);
+
+  // 5. sum the two parities across the pair: out = s (O_0 + O_1 exp(+i pi y / N))
+  cluster.sync();
+  const float2* p0 = r == 0 ? plane : cluster.map_shared_rank(plane, 0);
+  const float2* p1 = r == 1 ? plane : cluster.map_shared_rank(plane, 1);
+  const float s = 1.0f / (4.0f * N * N);
+  float2* dst = Sout + (size_t)kt * out_pitch;
+  if (out_cols == nullptr) {
+    for (int i = tid + r * (N * N / 2); i < (r + 1) * (N * N / 2); i += nthr) {
+      const int x = i / N, y = i % N;
+      const float2 v = cadd(p0[x * P + y], cmulc(p1[x * P + y], tw[y]));
+      dst[i] = cscale(v, s);
+    }
+  } else {
+    const int half = (out_n + 1) / 2;
+    const int jb = r * half, je = r ? out_n : half;
+    for (int j = jb + tid; j < je; j += nthr) {
+      const int col = __ldg(out_cols + j);
+      const int x = col / N, y = col % N;
+      const float2 v = cadd(p0[x * P + y], cmulc(p1[x * P + y], tw[y]));
+      dst[j] = cscale(v, s);
+    }
+  }
+  cluster.sync();
+}
+
+// ---------------------------------------------------------------------------
+// Periodic lateral solve per kt' plane.
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(kConvThreads)
+    k_sxy(float2* __restrict__ Sp, int nt, const float* __restrict__ lamx, const float* __restrict__ lamt,
+          const DevScalars* __restrict__ sc, double c0_host, double c1, const float2* __restrict__ twg) {
+  constexpr int P = N + 1;
+  extern __shared__ float4 smem_f4[];
+  float2* plane = reinterpret_cast<float2*>(smem_f4);
+  float2* tw = plane + N * P;
+  const int kt = blockIdx.x;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  for (int i = tid; i < 2 * N; i += nthr) tw[i] = __ldg(twg + i);
+  float2* g = Sp + (size_t)kt * N * N;
+  for (int i = tid; i < N * N; i += nthr) plane[(i / N) * P + (i % N)] = g[i];
+  __syncthreads();
+  team_fft<N, false>(plane, N, P, 1, tw, 2, tid, nthr);   // rows (y)
+  team_fft<N, false>(plane, N, 1, P, tw, 2, tid, nthr);   // columns (x)
+  const float c0 = sc ? (float)sc->L : (float)c0_host;
+  const float lt = __ldg(lamt + kt);
+  const float s = 1.0f / (float)(N * N);
+  for (int i = tid; i < N * N; i += nthr) {
+    const int xp = i / N, yp = i % N;
+    const float den = c0 + (float)c1 * (__ldg(lamx + kfreq<N>(xp)) + __ldg(lamx + kfreq<N>(yp)) + lt);
+    plane[xp * P + yp] = cscale(plane[xp * P + yp], s / den);
+  }
+  __syncthreads();
+  team_fft<N, true>(plane, N, 1, P, tw, 2, tid, nthr);
+  team_fft<N, true>(plane, N, P, 1, tw, 2, tid, nthr);
+  for (int i = tid; i < N * N; i += nthr) g[i] = plane[(i / N) * P + (i % N)];
+}
+
+// ---------------------------------------------------------------------------
+// Cone-kernel spectrum: H(kx, ky, kt) for kx, ky in [0, N], kt in [0, nt], the
+// DFT of h over the (2N, 2N, 2nt) grid.  One CTA per (kt, parity quadrant).
+// Lateral tap (i, j) of h has two nonzero t-taps m0, m0 + 1 with weights hw.
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(kConvThreads)
+    k_kspec(float2* __restrict__ H, int nt, const int32_t* __restrict__ m0t, const float2* __restrict__ hw,
+            const float2* __restrict__ tw2t, const float2* __restrict__ twg) {
+  constexpr int P = N + 1;
+  extern __shared__ float4 smem_f4[];
+  float2* plane = reinterpret_cast<float2*>(smem_f4);
+  float2* tw = plane + N * P;
+  const int kt = blockIdx.x >> 2, ax = (blockIdx.x >> 1) & 1, ay = blockIdx.x & 1;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  for (int i = tid; i < 2 * N; i += nthr) tw[i] = __ldg(twg + i);
+  __syncthreads();
+  const int n2 = 2 * nt;
+  for (int i = tid; i < N * N; i += nthr) {
+    const int x = i / N, y = i % N;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int sx = 0; sx < 2; ++sx)
+      for (int sy = 0; sy < 2; ++sy) {
+        const int li = (x + sx * N) * (2 * N) + (y + sy * N);
+        const int m = __ldg(m0t + li);
+        const float2 w = __ldg(hw + li);
+        // G = w0 exp(-2 pi i m kt / 2nt) + w1 exp(-2 pi i (m + 1) kt / 2nt)
+        const long long ph0 = ((long long)m * kt) % n2;
+        const long long ph1 = ((long long)(m + 1) * kt) % n2;
+        float2 gv = cadd(cscale(__ldg(tw2t + ph0), w.x), cscale(__ldg(tw2t + ph1), w.y));
+        const float sgn = ((ax & sx) ^ (ay & sy)) ? -1.0f : 1.0f;
+        acc = cadd(acc, cscale(gv, sgn));
+      }
+    // twist exp(-i pi (ax x + ay y) / N)
+    float2 t = make_float2(1.f, 0.f);
+    if (ax) t = cmul(t, tw[x]);
+    if (ay) t = cmul(t, tw[y]);
+    plane[x * P + y] = cmul(acc, t);
+  }
+  __syncthreads();
+  team_fft<N, false>(plane, N, P, 1, tw, 2, tid, nthr);
+  team_fft<N, false>(plane, N, 1, P, tw, 2, tid, nthr);
+  for (int i = tid; i < N * N; i += nthr) {
+    const int xp = i / N, yp = i % N;
+    const int kx = 2 * kfreq<N>(xp) + ax, ky = 2 * kfreq<N>(yp) + ay;
+    if (kx <= N && ky <= N) H[((size_t)kt * (N + 1) + kx) * (N + 1) + ky] = plane[xp * P + yp];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers (runtime size -> template instance)
+// ---------------------------------------------------------------------------
+template <typename F>
+static nlos_status dispatch_n(int n, F&& f) {
+  switch (n) {
+    case 8: return f(std::integral_constant<int, 8>{});
+    case 16: return f(std::integral_constant<int, 16>{});
+    case 32: return f(std::integral_constant<int, 32>{});
+    case 64: return f(std::integral_constant<int, 64>{});
+    case 128: return f(std::integral_constant<int, 128>{});
+  }
+  return fail(NLOS_ERR_INVALID_ARG, "unsupported nx/ny");
+}
+
+template <typename K>
+static nlos_status set_smem(K kernel, size_t bytes) {
+  NLOS_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return NLOS_OK;
+}
+
+nlos_status launch_conv(const Plan& P, const float2* Sin, bool in_compact, float2* Sout, bool out_compact, bool adj,
+                        cudaStream_t st) {
+  KTimer kt_(P, KC_CONV, st);
+  return dispatch_n(P.nx, [&](auto nc) -> nlos_status {
+    constexpr int N = decltype(nc)::value;
+    auto kern = k_conv<N>;
+    NLOS_TRY(set_smem(kern, CV<N>::smem));
+    const int full = P.nx * P.ny;
+    kern<<<2 * (P.nt + 1), kConvThreads, CV<N>::smem, st>>>(
+        Sin, in_compact ? P.ncols : full, in_compact ? P.d_cols : nullptr, P.ncols, Sout,
+        out_compact ? P.ncols : full, out_compact ? P.d_cols : nullptr, P.ncols, P.d_H, adj ? 1 : 0, P.d_twx);
+    NLOS_LAUNCH_CHECK("k_conv");
+    return NLOS_OK;
+  });
+}
+
+nlos_status launch_sxy(const Plan& P, float2* Sp, const DevScalars* sc, double c0_host, double c1, cudaStream_t st) {
+  KTimer kt_(P, KC_SXY, st);
+  return dispatch_n(P.nx, [&](auto nc) -> nlos_status {
+    constexpr int N = decltype(nc)::value;
+    auto kern = k_sxy<N>;
+    const size_t sm = sizeof(float2) * (N * (N + 1) + 2 * N);
+    NLOS_TRY(set_smem(kern, sm));
+    kern<<<P.nt / 2 + 1, kConvThreads, sm, st>>>(Sp, P.nt, P.d_lamx, P.d_lamt, sc, c0_host, c1, P.d_twx);
+    NLOS_LAUNCH_CHECK("k_sxy");
+    return NLOS_OK;
+  });
+}
+
+nlos_status launch_kernel_spectrum(const Plan& P, const int32_t* m0, const float2* hw, cudaStream_t st) {
+  return dispatch_n(P.nx, [&](auto nc) -> nlos_status {
+    constexpr int N = decltype(nc)::value;
+    auto kern = k_kspec<N>;
+    const size_t sm = sizeof(float2) * (N * (N + 1) + 2 * N);
+    NLOS_TRY(set_smem(kern, sm));
+    kern<<<4 * (P.nt + 1), kConvThreads, sm, st>>>(P.d_H, P.nt, m0, hw, P.d_tw2t, P.d_twx);
+    NLOS_LAUNCH_CHECK("k_kspec");
+    return NLOS_OK;
+  });
+}
+
+}  // namespace nlos
