@@ -180,6 +180,29 @@ nlos_status nlos_reconstruct(nlos_plan plan, const nlos_params* params, const fl
                              float* u_out_dev, float* tau_out_dev, nlos_stats* stats_host,
                              void* stream);
 
+/* The periodic FFT solve of nlos_solve for callers that cannot allocate
+ * device memory when they solve: code running while its stream is being
+ * captured into a CUDA graph (allocations are refused during a capture),
+ * code whose device memory is owned by another allocator or capped by a
+ * fixed budget, and real-time loops that must stay off the driver's
+ * allocation path, which can synchronise the device.  The paper has no
+ * counterpart: this is a deployment variant of the solve above.
+ *
+ * No plan: pass the grid (nx == ny, powers of two, 8 <= nx <= 64,
+ * 16 <= nt <= 512), rhs_dev and x_dev ([nx][ny][nt] float32, may alias),
+ * c0 > 0 and c1 >= 0.  Nothing is allocated: the spectrum scratch is a
+ * static device array of 64 * 64 * 257 complex values (8 MiB) that every
+ * GPU loading the library holds until the process exits; larger grids
+ * return NLOS_ERR_INVALID_ARG (use nlos_solve).  The first call on a device
+ * (with that device current) looks up the array's device address and fills
+ * small twiddle tables; make that first call before any stream capture.
+ * All calls share the scratch: calls whose kernels overlap on the GPU
+ * (other streams or other host threads) race and must be serialised by the
+ * caller.  It keeps the last call's contents, but no call reads a value an
+ * earlier call left behind.  Queued on `stream`, no host synchronisation. */
+nlos_status nlos_solve_static(int32_t nx, int32_t ny, int32_t nt, const float* rhs_dev, float* x_dev, double c0,
+                              double c1, void* stream);
+
 /* Per-launch timing of a plan's kernels, for profiling.  When enabled, every
  * kernel the plan launches is bracketed by a pair of CUDA events recorded on
  * its launch stream.  nlos_timing_read synchronises the device, returns per

@@ -75,6 +75,8 @@ _SIGS = {
                                                ctypes.c_int32, ctypes.c_double, _P]),
     "nlos_reconstruct": (ctypes.c_int32, [_P, ctypes.POINTER(Params), _P, _P, _P,
                                           ctypes.POINTER(Stats), _P]),
+    "nlos_solve_static": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P,
+                                           ctypes.c_double, ctypes.c_double, _P]),
     "nlos_timing_enable": (ctypes.c_int32, [_P, ctypes.c_int32]),
     "nlos_timing_read": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32]),
 }
