@@ -12,6 +12,7 @@
 
 #include "passes.cuh"
 #include "stencil.cuh"
+#include "stencil_tiled.cuh"
 
 namespace nlos {
 
@@ -81,19 +82,41 @@ __global__ void __launch_bounds__(kStencilThreads)
   block_reduce_to<1>(acc, partials);
 }
 
-// Sum the first nb partials of term `term` in a fixed order (one thread).
-__device__ __forceinline__ double sum_partials(const double* p, int nb, int term) {
-  double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += p[(size_t)b * kMaxTerms + term];
-  return s;
+// Deterministic block-wide sums of per-block partials: thread i adds the
+// partials of blocks i, i + T, i + 2T, ... in order, then a fixed binary tree
+// combines the threads.  Every thread of the (single) block gets the result.
+constexpr int kSumThreads = 256;
+
+template <int NTERMS>
+__device__ __forceinline__ void sum_partials_block(const double* __restrict__ p, int nb, const int (&terms)[NTERMS],
+                                                   double (&out)[NTERMS]) {
+  __shared__ double red[NTERMS][kSumThreads];
+  double acc[NTERMS];
+#pragma unroll
+  for (int t = 0; t < NTERMS; ++t) acc[t] = 0.0;
+  for (int b = threadIdx.x; b < nb; b += kSumThreads)
+#pragma unroll
+    for (int t = 0; t < NTERMS; ++t) acc[t] += p[(size_t)b * kMaxTerms + terms[t]];
+#pragma unroll
+  for (int t = 0; t < NTERMS; ++t) red[t][threadIdx.x] = acc[t];
+  __syncthreads();
+  for (int w = kSumThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+#pragma unroll
+      for (int t = 0; t < NTERMS; ++t) red[t][threadIdx.x] += red[t][threadIdx.x + w];
+    __syncthreads();
+  }
+#pragma unroll
+  for (int t = 0; t < NTERMS; ++t) out[t] = red[t][0];
+  __syncthreads();
 }
 
-__global__ void k_sum_to(const double* __restrict__ p, int nb, int term, double* __restrict__ out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) *out = sum_partials(p, nb, term);
-}
-
-__global__ void k_sqrt_sum_to(const double* __restrict__ p, int nb, int term, double* __restrict__ out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) *out = sqrt(sum_partials(p, nb, term));
+__global__ void __launch_bounds__(kSumThreads) k_sum_to(const double* __restrict__ p, int nb, int term,
+                                                        double* __restrict__ out) {
+  const int terms[1] = {term};
+  double r[1];
+  sum_partials_block<1>(p, nb, terms, r);
+  if (threadIdx.x == 0) *out = r[0];
 }
 
 // Copy the sampled columns of a full [nx*ny][nt] array into compact form.
@@ -290,13 +313,17 @@ __global__ void k_add(const float* __restrict__ a, const float* __restrict__ b, 
 // Backtracking test of the linearised u-step: f is quadratic, so
 // f(u+) - f(ubar) - <grad f(ubar), d> = 1/2 ||A d||^2 and the rule
 // f(u+) <= f(ubar) + <grad f, d> + L/2 ||d||^2 is ||A d||^2 <= L ||d||^2.
-__global__ void k_test(DevScalars* sc, const double* __restrict__ pd, int nbd, const double* __restrict__ pf, int nbf,
-                       double eta, int max_bt, int force_accept) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__global__ void __launch_bounds__(kSumThreads)
+    k_test(DevScalars* sc, const double* __restrict__ pd, int nbd, const double* __restrict__ pf, int nbf, double eta,
+           int max_bt, int force_accept) {
+  const int t0[1] = {0};
+  const int t01[2] = {0, 1};
+  double d[1], f[2];
+  sum_partials_block<1>(pd, nbd, t0, d);
+  sum_partials_block<2>(pf, nbf, t01, f);
+  if (threadIdx.x != 0) return;
   if (sc->status != NLOS_OK) return;
-  const double dn2 = sum_partials(pd, nbd, 0);
-  const double r2 = sum_partials(pf, nbf, 0);
-  const double ad2 = sum_partials(pf, nbf, 1);
+  const double dn2 = d[0], r2 = f[0], ad2 = f[1];
   sc->test_lhs = ad2;
   sc->test_rhs = sc->L * dn2;
   const bool ok = ad2 <= sc->L * dn2;
@@ -318,19 +345,23 @@ __global__ void k_test(DevScalars* sc, const double* __restrict__ pd, int nbd, c
 
 // End of an iteration: energy, relative change, restart, bookkeeping.
 // model 1: E = f_fit + sum phi |grad u|; model 2: E from the post partials.
-__global__ void k_finalize(DevScalars* sc, const double* __restrict__ pp, int nb, int model, double lam_w,
-                           int restart, double eps_stop) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__global__ void __launch_bounds__(kSumThreads)
+    k_finalize(DevScalars* sc, const double* __restrict__ pp, int nb, int model, double lam_w, int restart,
+               double eps_stop) {
+  const int terms[7] = {0, 1, 2, 3, 4, 5, 6};
+  double v[7];
+  sum_partials_block<7>(pp, nb, terms, v);
+  if (threadIdx.x != 0) return;
   if (sc->status != NLOS_OK) return;
   double E, pres2;
   if (model == 1) {
-    E = sc->f_fit + sum_partials(pp, nb, 0);
-    pres2 = sum_partials(pp, nb, 1);
+    E = sc->f_fit + v[0];
+    pres2 = v[1];
   } else {
-    const double fit = 0.5 * sum_partials(pp, nb, 2);
-    E = fit + 0.5 * lam_w * sum_partials(pp, nb, 3) + sum_partials(pp, nb, 0) + sum_partials(pp, nb, 1);
+    const double fit = 0.5 * v[2];
+    E = fit + 0.5 * lam_w * v[3] + v[0] + v[1];
     sc->f_fit = fit;
-    pres2 = sum_partials(pp, nb, 4);
+    pres2 = v[4];
   }
   const double e = E != 0.0 ? fabs(sc->E_prev - E) / fabs(E) : 0.0;
   if (!isfinite(E)) sc->status = NLOS_ERR_DIVERGED;
@@ -347,12 +378,16 @@ __global__ void k_finalize(DevScalars* sc, const double* __restrict__ pp, int nb
   if (eps_stop > 0.0 && e <= eps_stop) sc->stop = 1;
 }
 
-__global__ void k_init_scalars(DevScalars* sc, double L0, const double* __restrict__ pe, int nb, double e_scale) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__global__ void __launch_bounds__(kSumThreads)
+    k_init_scalars(DevScalars* sc, double L0, const double* __restrict__ pe, int nb, double e_scale) {
+  const int t0[1] = {0};
+  double v[1];
+  sum_partials_block<1>(pe, nb, t0, v);
+  if (threadIdx.x != 0) return;
   memset(sc, 0, sizeof(DevScalars));
   sc->L = L0;
   sc->t = 1.0;
-  sc->E_prev = e_scale * sum_partials(pe, nb, 0);
+  sc->E_prev = e_scale * v[0];
   sc->status = NLOS_OK;
 }
 
@@ -500,7 +535,7 @@ static nlos_status host_sumsq(const Plan& P, const float* a, size_t n, double* o
   NLOS_LAUNCH_CHECK("k_sumsq");
   double* d_out = reinterpret_cast<double*>(P.d_scal);
   { KTimer kt_(P, KC_SMALL, st);
-  k_sum_to<<<1, 1, 0, st>>>(P.d_partials, kStencilBlocks, 0, d_out);
+  k_sum_to<<<1, kSumThreads, 0, st>>>(P.d_partials, kStencilBlocks, 0, d_out);
   }
   NLOS_LAUNCH_CHECK("k_sum_to");
   NLOS_CUDA(cudaMemcpyAsync(out, d_out, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -628,7 +663,7 @@ static nlos_status u_step(Plan& P, SolverState* s, const UStepArgs& a, bool host
     FitArgs fa{a.data, a.auk, a.aukm1, s->sc, s->pb};
     NLOS_TRY(launch_tinv_fit(P, Sfit, ncols, ncols, a.au_out, fa, &nbf, st));
     { KTimer kt_(P, KC_SMALL, st);
-    k_test<<<1, 1, 0, st>>>(s->sc, s->pa, nbd, s->pb, nbf, a.eta, a.max_bt, host_check ? 0 : 1);
+    k_test<<<1, kSumThreads, 0, st>>>(s->sc, s->pa, nbd, s->pb, nbf, a.eta, a.max_bt, host_check ? 0 : 1);
     }
     NLOS_LAUNCH_CHECK("k_test");
     if (!host_check) return NLOS_OK;
@@ -662,7 +697,7 @@ static nlos_status init_scalars(Plan& P, SolverState* s, double L0, const float*
   }
   NLOS_LAUNCH_CHECK("k_sumsq");
   { KTimer kt_(P, KC_SMALL, st);
-  k_init_scalars<<<1, 1, 0, st>>>(s->sc, L0, s->pc, kStencilBlocks, scale);
+  k_init_scalars<<<1, kSumThreads, 0, st>>>(s->sc, L0, s->pc, kStencilBlocks, scale);
   }
   NLOS_LAUNCH_CHECK("k_init_scalars");
   return NLOS_OK;
@@ -702,9 +737,17 @@ static nlos_status run_alg1(Plan& P, const nlos_params& p, const float* tau0, fl
   int cur = 0, prev = 1, nxt = 2;
   double L_host = L0;
   const float eps2 = (float)(p.eps_normal * p.eps_normal);
+  // halo-tiled stencils when the grid tiles evenly (TT = 128 along t, 8 rows in y)
+  const bool tiled = P.nt % kTT == 0 && P.ny % kTY == 0;
+  const int xb = std::min(16, P.nx);
+  const dim3 tgrid((P.nt / kTT) * (P.ny / kTY), P.nx / xb);
+  const int post_blocks = tiled ? (int)(tgrid.x * tgrid.y) : kStencilBlocks;
   for (int it = 0; it < p.iters; ++it) {
     { KTimer kt_(P, KC_PRE, st);
-    k_pre1<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->ub, s->lam, s->ph, s->reg, g, vi, (float)p.mu, V);
+    if (tiled)
+      k_pre1_tiled<<<tgrid, kTileThreads, 0, st>>>(s->ub, s->lam, s->ph, s->reg, g, xb, (float)p.mu, V);
+    else
+      k_pre1<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->ub, s->lam, s->ph, s->reg, g, vi, (float)p.mu, V);
     }
     NLOS_LAUNCH_CHECK("k_pre1");
     Lin3 r{{s->cache[cur], s->cache[prev], s->tau0c}, {0.f, 0.f, 0.f}, s->sc};
@@ -714,12 +757,17 @@ static nlos_status run_alg1(Plan& P, const nlos_params& p, const float* tau0, fl
     UStepArgs ua{s->reg, p.mu, true, s->tau0c, p.eta, p.max_backtracks, s->cache[nxt], s->cache[cur], s->cache[prev]};
     NLOS_TRY(u_step(P, s, ua, host_check, &L_host, st));
     { KTimer kt_(P, KC_POST, st);
-    k_post1<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->unew, s->uk, s->ub, s->lam, s->ph, s->ubn, s->sc, g, vi,
-                                                        (float)p.mu, (float)p.a, (float)p.b, p.phi, eps2, V, s->pc);
+    if (tiled)
+      k_post1_tiled<<<tgrid, kTileThreads, 0, st>>>(s->unew, s->uk, s->ub, s->lam, s->ph, s->ubn, s->sc, g, xb,
+                                                    (float)p.mu, (float)p.a, (float)p.b, p.phi, eps2, V, s->pc);
+    else
+      k_post1<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->unew, s->uk, s->ub, s->lam, s->ph, s->ubn, s->sc, g,
+                                                          vi, (float)p.mu, (float)p.a, (float)p.b, p.phi, eps2, V,
+                                                          s->pc);
     }
     NLOS_LAUNCH_CHECK("k_post1");
     { KTimer kt_(P, KC_SMALL, st);
-    k_finalize<<<1, 1, 0, st>>>(s->sc, s->pc, kStencilBlocks, 1, 0.0, restart, p.eps_stop);
+    k_finalize<<<1, kSumThreads, 0, st>>>(s->sc, s->pc, post_blocks, 1, 0.0, restart, p.eps_stop);
     }
     NLOS_LAUNCH_CHECK("k_finalize");
     swap_ptr(s->uk, s->unew);
@@ -790,7 +838,7 @@ static nlos_status run_alg2(Plan& P, const nlos_params& p, const float* tau0, fl
     }
     NLOS_LAUNCH_CHECK("k_post2");
     { KTimer kt_(P, KC_SMALL, st);
-    k_finalize<<<1, 1, 0, st>>>(s->sc, s->pc, kStencilBlocks, 2, p.lambda, restart, p.eps_stop);
+    k_finalize<<<1, kSumThreads, 0, st>>>(s->sc, s->pc, kStencilBlocks, 2, p.lambda, restart, p.eps_stop);
     }
     NLOS_LAUNCH_CHECK("k_finalize");
     swap_ptr(s->uk, s->unew);

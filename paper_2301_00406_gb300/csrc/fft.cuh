@@ -122,16 +122,17 @@ __device__ __forceinline__ int kfreq(int p) {
   return p / R2 + R1 * (p % R2);
 }
 
-// B transforms of length N: element n of transform b at buf[b * ts + n * es].
-// tw[j * tws] = exp(-2 pi i j / N) for j < N.  All threads of the block call
-// it; it ends with __syncthreads().
+// B transforms of length N (B a power of two): element n of transform b at
+// buf[b * ts + n * es].  tw[j * tws] = exp(-2 pi i j / N) for j < N.  All
+// threads of the block call it; it ends with __syncthreads().
 template <int N, bool INV>
 __device__ __forceinline__ void team_fft(float2* buf, int B, int ts, int es, const float2* tw, int tws,
                                          int tid, int nthr) {
   constexpr int R1 = FftPlan<N>::R1, R2 = FftPlan<N>::R2;
+  const int lb = __ffs(B) - 1;
   if (!INV) {
     for (int it = tid; it < B * R2; it += nthr) {
-      const int b = it % B, n2 = it / B;
+      const int b = it & (B - 1), n2 = it >> lb;
       float2* p = buf + b * ts + n2 * es;
       float2 a[R1];
 #pragma unroll
@@ -145,7 +146,7 @@ __device__ __forceinline__ void team_fft(float2* buf, int B, int ts, int es, con
     __syncthreads();
     if (R2 > 1) {
       for (int it = tid; it < B * R1; it += nthr) {
-        const int b = it % B, k1 = it / B;
+        const int b = it & (B - 1), k1 = it >> lb;
         float2* p = buf + b * ts + k1 * R2 * es;
         float2 a[R2];
 #pragma unroll
@@ -159,7 +160,7 @@ __device__ __forceinline__ void team_fft(float2* buf, int B, int ts, int es, con
   } else {
     if (R2 > 1) {
       for (int it = tid; it < B * R1; it += nthr) {
-        const int b = it % B, k1 = it / B;
+        const int b = it & (B - 1), k1 = it >> lb;
         float2* p = buf + b * ts + k1 * R2 * es;
         float2 a[R2];
 #pragma unroll
@@ -173,7 +174,7 @@ __device__ __forceinline__ void team_fft(float2* buf, int B, int ts, int es, con
       __syncthreads();
     }
     for (int it = tid; it < B * R2; it += nthr) {
-      const int b = it % B, n2 = it / B;
+      const int b = it & (B - 1), n2 = it >> lb;
       float2* p = buf + b * ts + n2 * es;
       float2 a[R1];
 #pragma unroll
@@ -183,6 +184,27 @@ __device__ __forceinline__ void team_fft(float2* buf, int B, int ts, int es, con
       for (int n1 = 0; n1 < R1; ++n1) p[n1 * R2 * es] = a[n1];
     }
     __syncthreads();
+  }
+}
+
+// Global -> shared staging with U independent loads in flight per thread:
+// item i is produced by ld(i) and consumed by st(i, value).  A plain
+// "load, store, next" loop keeps one load per thread in flight and is bound
+// by memory latency, not bandwidth.
+template <int U, typename T, typename LoadF, typename StoreF>
+__device__ __forceinline__ void batched_copy(int total, int tid, int nthr, LoadF ld, StoreF st) {
+  for (int base = tid; base < total; base += U * nthr) {
+    T v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = base + u * nthr;
+      if (i < total) v[u] = ld(i);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = base + u * nthr;
+      if (i < total) st(i, v[u]);
+    }
   }
 }
 

@@ -72,8 +72,8 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[NTERMS], double* 
 // kt = 2 k' + half of both columns of every pair to S.
 template <int NT>
 __device__ __forceinline__ void tfwd_post_store(const float2* work, int half, float2* S, int pitch, int col0,
-                                                int ncols, int tid, int nthr) {
-  constexpr int COLS = TP<NT>::COLS, WP = TP<NT>::WP;
+                                                int ncols, int COLS, int tid, int nthr) {
+  constexpr int WP = TP<NT>::WP;
   const int nk = half ? NT / 2 : NT / 2 + 1;
   for (int i = tid; i < nk * COLS; i += nthr) {
     const int kp = i / COLS, c = i % COLS, p = c >> 1;
@@ -95,33 +95,37 @@ __device__ __forceinline__ void tfwd_post_store(const float2* work, int half, fl
 // using Hermitian symmetry for kt > nt, packed as Z = X_a + i X_b.
 template <int NT>
 __device__ __forceinline__ void tinv_load(const float2* __restrict__ S, int pitch, int col0, int ncols, int half,
-                                          float2* work, int tid, int nthr) {
-  constexpr int PAIRS = TP<NT>::PAIRS, WP = TP<NT>::WP;
-  for (int i = tid; i < NT * PAIRS; i += nthr) {
-    const int kp = i / PAIRS, p = i % PAIRS;
-    int kt = 2 * kp + half;
-    bool mir = kt > NT;
-    if (mir) kt = 2 * NT - kt;
-    const int ca = col0 + 2 * p, cb = ca + 1;
-    float2 A = ca < ncols ? __ldg(S + (size_t)kt * pitch + ca) : make_float2(0.f, 0.f);
-    float2 B = cb < ncols ? __ldg(S + (size_t)kt * pitch + cb) : make_float2(0.f, 0.f);
-    if (mir) {
-      A.y = -A.y;
-      B.y = -B.y;
-    }
-    work[p * WP + fpos<NT>(kp)] = make_float2(A.x - B.y, A.y + B.x);
-  }
+                                          float2* work, int PAIRS, int tid, int nthr) {
+  constexpr int WP = TP<NT>::WP;
+  const int lp = __ffs(PAIRS) - 1;
+  batched_copy<8, float2>(
+      NT * PAIRS, tid, nthr,
+      [&](int i) {
+        const int kp = i >> lp, p = i & (PAIRS - 1);
+        int kt = 2 * kp + half;
+        const bool mir = kt > NT;
+        if (mir) kt = 2 * NT - kt;
+        const int ca = col0 + 2 * p, cb = ca + 1;
+        float2 A = ca < ncols ? __ldg(S + (size_t)kt * pitch + ca) : make_float2(0.f, 0.f);
+        float2 B = cb < ncols ? __ldg(S + (size_t)kt * pitch + cb) : make_float2(0.f, 0.f);
+        if (mir) {
+          A.y = -A.y;
+          B.y = -B.y;
+        }
+        return make_float2(A.x - B.y, A.y + B.x);
+      },
+      [&](int i, float2 z) { work[(i & (PAIRS - 1)) * WP + fpos<NT>(i >> lp)] = z; });
 }
 
 // Inverse padded t-FFT of the CTA's pairs: cbuf[c][n] = (1/(2nt)) * real signal
 // of column c at n in [0, nt).
 template <int NT>
 __device__ __forceinline__ void tinv_core(const float2* __restrict__ S, int pitch, int col0, int ncols,
-                                          float2* work, float* cbuf, const float2* tw2, int tid, int nthr) {
-  constexpr int PAIRS = TP<NT>::PAIRS, WP = TP<NT>::WP;
+                                          float2* work, float* cbuf, const float2* tw2, int PAIRS, int tid, int nthr) {
+  constexpr int WP = TP<NT>::WP;
   const float scale = 1.0f / (2.0f * NT);
   for (int half = 0; half < 2; ++half) {
-    tinv_load<NT>(S, pitch, col0, ncols, half, work, tid, nthr);
+    tinv_load<NT>(S, pitch, col0, ncols, half, work, PAIRS, tid, nthr);
     __syncthreads();
     team_fft<NT, true>(work, PAIRS, WP, 1, tw2, 2, tid, nthr);
     for (int i = tid; i < PAIRS * NT; i += nthr) {
@@ -149,12 +153,13 @@ __device__ __forceinline__ void tinv_core(const float2* __restrict__ S, int pitc
 template <int NT, int MODE>
 __global__ void __launch_bounds__(kTpassThreads)
     k_tfwd(Lin3 src, int ncols, float2* __restrict__ S, int pitch, const int32_t* __restrict__ i0t,
-           const float* __restrict__ wt3, const int32_t* __restrict__ tstart, const float2* __restrict__ tw2g) {
-  constexpr int COLS = TP<NT>::COLS, PAIRS = TP<NT>::PAIRS, WP = TP<NT>::WP;
+           const float* __restrict__ wt3, const int32_t* __restrict__ tstart, const float2* __restrict__ tw2g, int cols) {
+  const int COLS = cols, PAIRS = cols >> 1;
+  constexpr int WP = TP<NT>::WP;
   extern __shared__ float4 smem_f4[];
   float2* tw2 = reinterpret_cast<float2*>(smem_f4);
   float2* work = tw2 + 2 * NT;
-  float* cbuf = reinterpret_cast<float*>(work + PAIRS * WP);
+  float* cbuf = reinterpret_cast<float*>(work + ((PAIRS * WP + 1) & ~1));
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int col0 = blockIdx.x * COLS;
   for (int i = tid; i < 2 * NT; i += nthr) tw2[i] = __ldg(tw2g + i);
@@ -167,24 +172,27 @@ __global__ void __launch_bounds__(kTpassThreads)
     c1 = -b;
     c2 = -1.0f;
   }
-  for (int i = tid; i < COLS * NT / 4; i += nthr) {
-    const int c = (i * 4) / NT;
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (col0 + c < ncols) {
-      const size_t off = (size_t)col0 * NT / 4 + i;
-      const float4 a = __ldg(reinterpret_cast<const float4*>(src.p[0]) + off);
-      v = make_float4(c0 * a.x, c0 * a.y, c0 * a.z, c0 * a.w);
-      if (src.p[1]) {
-        const float4 q = __ldg(reinterpret_cast<const float4*>(src.p[1]) + off);
-        v.x += c1 * q.x; v.y += c1 * q.y; v.z += c1 * q.z; v.w += c1 * q.w;
-      }
-      if (src.p[2]) {
-        const float4 q = __ldg(reinterpret_cast<const float4*>(src.p[2]) + off);
-        v.x += c2 * q.x; v.y += c2 * q.y; v.z += c2 * q.z; v.w += c2 * q.w;
-      }
-    }
-    reinterpret_cast<float4*>(cbuf)[i] = v;
-  }
+  batched_copy<4, float4>(
+      COLS * NT / 4, tid, nthr,
+      [&](int i) {
+        const int c = (i * 4) / NT;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (col0 + c < ncols) {
+          const size_t off = (size_t)col0 * NT / 4 + i;
+          const float4 a = __ldg(reinterpret_cast<const float4*>(src.p[0]) + off);
+          v = make_float4(c0 * a.x, c0 * a.y, c0 * a.z, c0 * a.w);
+          if (src.p[1]) {
+            const float4 q = __ldg(reinterpret_cast<const float4*>(src.p[1]) + off);
+            v.x += c1 * q.x; v.y += c1 * q.y; v.z += c1 * q.z; v.w += c1 * q.w;
+          }
+          if (src.p[2]) {
+            const float4 q = __ldg(reinterpret_cast<const float4*>(src.p[2]) + off);
+            v.x += c2 * q.x; v.y += c2 * q.y; v.z += c2 * q.z; v.w += c2 * q.w;
+          }
+        }
+        return v;
+      },
+      [&](int i, float4 v) { reinterpret_cast<float4*>(cbuf)[i] = v; });
   __syncthreads();
 
   for (int half = 0; half < 2; ++half) {
@@ -225,7 +233,7 @@ __global__ void __launch_bounds__(kTpassThreads)
     }
     __syncthreads();
     team_fft<NT, false>(work, PAIRS, WP, 1, tw2, 2, tid, nthr);
-    tfwd_post_store<NT>(work, half, S, pitch, col0, ncols, tid, nthr);
+    tfwd_post_store<NT>(work, half, S, pitch, col0, ncols, COLS, tid, nthr);
     __syncthreads();
   }
 }
@@ -237,39 +245,47 @@ template <int NT, int EPI>
 __global__ void __launch_bounds__(kTpassThreads)
     k_tinv(const float2* __restrict__ S, int pitch, int ncols, float* __restrict__ out,
            const int32_t* __restrict__ outmap, FitArgs fa, const int32_t* __restrict__ k0t,
-           const float* __restrict__ wt3, const float2* __restrict__ tw2g) {
-  constexpr int COLS = TP<NT>::COLS, PAIRS = TP<NT>::PAIRS, WP = TP<NT>::WP;
+           const float* __restrict__ wt3, const float2* __restrict__ tw2g, int cols) {
+  const int COLS = cols, PAIRS = cols >> 1;
+  constexpr int WP = TP<NT>::WP;
   extern __shared__ float4 smem_f4[];
   float2* tw2 = reinterpret_cast<float2*>(smem_f4);
   float2* work = tw2 + 2 * NT;
-  float* cbuf = reinterpret_cast<float*>(work + PAIRS * WP);
+  float* cbuf = reinterpret_cast<float*>(work + ((PAIRS * WP + 1) & ~1));
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int col0 = blockIdx.x * COLS;
   for (int i = tid; i < 2 * NT; i += nthr) tw2[i] = __ldg(tw2g + i);
   __syncthreads();
-  tinv_core<NT>(S, pitch, col0, ncols, work, cbuf, tw2, tid, nthr);
+  tinv_core<NT>(S, pitch, col0, ncols, work, cbuf, tw2, PAIRS, tid, nthr);
 
   double acc[2] = {0.0, 0.0};
   float bp = 0.f;
   if (EPI == 1) bp = (float)fa.sc->beta_prev;
-  for (int i = tid; i < COLS * NT; i += nthr) {
-    const int c = i / NT, k = i % NT;
-    if (col0 + c >= ncols) continue;
-    const float* cc = cbuf + c * NT;
-    const int k0 = __ldg(k0t + k);
-    const float tau = __ldg(wt3 + 3 * k + 2) * (__ldg(wt3 + 3 * k) * cc[k0] + __ldg(wt3 + 3 * k + 1) * cc[k0 + 1]);
-    const int oc = outmap ? __ldg(outmap + col0 + c) : col0 + c;
-    const size_t o = (size_t)oc * NT + k;
-    out[o] = tau;
-    if (EPI == 1) {
-      const size_t g = (size_t)(col0 + c) * NT + k;
-      const float r = tau - __ldg(fa.data + g);
-      const float aub = (1.0f + bp) * __ldg(fa.auk + g) - bp * __ldg(fa.aukm1 + g);
-      const float d = tau - aub;
-      acc[0] += (double)r * (double)r;
-      acc[1] += (double)d * (double)d;
-    }
-  }
+  const int total = min(COLS, ncols - col0) * NT;
+  // ld: the data, A u^k and A u^{k-1} samples (fit epilogue only); st: resample,
+  // store and accumulate
+  batched_copy<4, float3>(
+      total, tid, nthr,
+      [&](int i) {
+        if (EPI != 1) return make_float3(0.f, 0.f, 0.f);
+        const size_t g = (size_t)col0 * NT + i;
+        return make_float3(__ldg(fa.data + g), __ldg(fa.auk + g), __ldg(fa.aukm1 + g));
+      },
+      [&](int i, float3 in) {
+        const int c = i / NT, k = i % NT;
+        const float* cc = cbuf + c * NT;
+        const int k0 = __ldg(k0t + k);
+        const float tau =
+            __ldg(wt3 + 3 * k + 2) * (__ldg(wt3 + 3 * k) * cc[k0] + __ldg(wt3 + 3 * k + 1) * cc[k0 + 1]);
+        const int oc = outmap ? __ldg(outmap + col0 + c) : col0 + c;
+        out[(size_t)oc * NT + k] = tau;
+        if (EPI == 1) {
+          const float r = tau - in.x;
+          const float d = tau - ((1.0f + bp) * in.y - bp * in.z);
+          acc[0] += (double)r * (double)r;
+          acc[1] += (double)d * (double)d;
+        }
+      });
   if (EPI == 1) block_reduce_store<2>(acc, fa.partials);
 }
 
@@ -279,8 +295,8 @@ __global__ void __launch_bounds__(kTpassThreads)
 // ---------------------------------------------------------------------------
 template <int NT>
 __device__ __forceinline__ void periodic_fwd_post(const float2* work, float2* Sp, int col0, int ncols, int pitch,
-                                                  int tid, int nthr) {
-  constexpr int COLS = TP<NT>::COLS, WP = TP<NT>::WP;
+                                                  int COLS, int tid, int nthr) {
+  constexpr int WP = TP<NT>::WP;
   for (int i = tid; i < (NT / 2 + 1) * COLS; i += nthr) {
     const int k = i / COLS, c = i % COLS, p = c >> 1;
     if (col0 + c >= ncols) continue;
@@ -299,18 +315,19 @@ template <int NT, int MODE>
 __global__ void __launch_bounds__(kTpassThreads)
     k_tadj(const float2* __restrict__ S, int pitch, int ncols, float* __restrict__ out, SolveRhs sr,
            float2* __restrict__ Sp, const int32_t* __restrict__ i0t, const float* __restrict__ wt3,
-           const int32_t* __restrict__ zstart, const float2* __restrict__ tw2g) {
-  constexpr int COLS = TP<NT>::COLS, PAIRS = TP<NT>::PAIRS, WP = TP<NT>::WP;
+           const int32_t* __restrict__ zstart, const float2* __restrict__ tw2g, int cols) {
+  const int COLS = cols, PAIRS = cols >> 1;
+  constexpr int WP = TP<NT>::WP;
   extern __shared__ float4 smem_f4[];
   float2* tw2 = reinterpret_cast<float2*>(smem_f4);
   float2* work = tw2 + 2 * NT;
-  float* cbuf = reinterpret_cast<float*>(work + PAIRS * WP);
+  float* cbuf = reinterpret_cast<float*>(work + ((PAIRS * WP + 1) & ~1));
   float* gbuf = cbuf + COLS * NT;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int col0 = blockIdx.x * COLS;
   for (int i = tid; i < 2 * NT; i += nthr) tw2[i] = __ldg(tw2g + i);
   __syncthreads();
-  tinv_core<NT>(S, pitch, col0, ncols, work, cbuf, tw2, tid, nthr);
+  tinv_core<NT>(S, pitch, col0, ncols, work, cbuf, tw2, PAIRS, tid, nthr);
 
   // g_i = sum_{j: i0_j = i} g_j w0_j c_j + sum_{j: i0_j = i - 1} g_j w1_j c_j
   for (int idx = tid; idx < COLS * NT; idx += nthr) {
@@ -336,90 +353,111 @@ __global__ void __launch_bounds__(kTpassThreads)
     return;
   }
   const float L = sr.sc ? (float)sr.sc->L : (float)sr.c0_host;
-  for (int i = tid; i < PAIRS * NT; i += nthr) {
-    const int p = i / NT, n = i % NT;
-    const int ca = col0 + 2 * p, cb = ca + 1;
-    float a = 0.f, b = 0.f;
-    if (ca < ncols) {
-      const size_t g = (size_t)ca * NT + n;
-      a = L * __ldg(sr.ubar + g) - gbuf[(2 * p) * NT + n] + __ldg(sr.reg + g);
-    }
-    if (cb < ncols) {
-      const size_t g = (size_t)cb * NT + n;
-      b = L * __ldg(sr.ubar + g) - gbuf[(2 * p + 1) * NT + n] + __ldg(sr.reg + g);
-    }
-    work[p * WP + n] = make_float2(a, b);
-  }
+  // ld: u-bar and reg of both columns of the pair; st: rhs = L u-bar - g + reg
+  batched_copy<8, float4>(
+      PAIRS * NT, tid, nthr,
+      [&](int i) {
+        const int p = i / NT, n = i % NT;
+        const int ca = col0 + 2 * p, cb = ca + 1;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (ca < ncols) {
+          const size_t g = (size_t)ca * NT + n;
+          v.x = __ldg(sr.ubar + g);
+          v.y = __ldg(sr.reg + g);
+        }
+        if (cb < ncols) {
+          const size_t g = (size_t)cb * NT + n;
+          v.z = __ldg(sr.ubar + g);
+          v.w = __ldg(sr.reg + g);
+        }
+        return v;
+      },
+      [&](int i, float4 v) {
+        const int p = i / NT, n = i % NT;
+        const int ca = col0 + 2 * p, cb = ca + 1;
+        const float a = ca < ncols ? L * v.x - gbuf[(2 * p) * NT + n] + v.y : 0.f;
+        const float b = cb < ncols ? L * v.z - gbuf[(2 * p + 1) * NT + n] + v.w : 0.f;
+        work[p * WP + n] = make_float2(a, b);
+      });
   __syncthreads();
   team_fft<NT, false>(work, PAIRS, WP, 1, tw2, 2, tid, nthr);
-  periodic_fwd_post<NT>(work, Sp, col0, ncols, ncols, tid, nthr);
+  periodic_fwd_post<NT>(work, Sp, col0, ncols, ncols, COLS, tid, nthr);
 }
 
 // Periodic real FFT of a field (rhs of a solve).
 template <int NT>
 __global__ void __launch_bounds__(kTpassThreads)
-    k_sfwd(const float* __restrict__ x, int ncols, float2* __restrict__ Sp, const float2* __restrict__ tw2g) {
-  constexpr int PAIRS = TP<NT>::PAIRS, WP = TP<NT>::WP, COLS = TP<NT>::COLS;
+    k_sfwd(const float* __restrict__ x, int ncols, float2* __restrict__ Sp, const float2* __restrict__ tw2g, int cols) {
+  const int COLS = cols, PAIRS = cols >> 1;
+  constexpr int WP = TP<NT>::WP;
   extern __shared__ float4 smem_f4[];
   float2* tw2 = reinterpret_cast<float2*>(smem_f4);
   float2* work = tw2 + 2 * NT;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int col0 = blockIdx.x * COLS;
   for (int i = tid; i < 2 * NT; i += nthr) tw2[i] = __ldg(tw2g + i);
-  for (int i = tid; i < PAIRS * NT; i += nthr) {
-    const int p = i / NT, n = i % NT;
-    const int ca = col0 + 2 * p, cb = ca + 1;
-    const float a = ca < ncols ? __ldg(x + (size_t)ca * NT + n) : 0.f;
-    const float b = cb < ncols ? __ldg(x + (size_t)cb * NT + n) : 0.f;
-    work[p * WP + n] = make_float2(a, b);
-  }
+  batched_copy<8, float2>(
+      PAIRS * NT, tid, nthr,
+      [&](int i) {
+        const int p = i / NT, n = i % NT;
+        const int ca = col0 + 2 * p, cb = ca + 1;
+        return make_float2(ca < ncols ? __ldg(x + (size_t)ca * NT + n) : 0.f,
+                           cb < ncols ? __ldg(x + (size_t)cb * NT + n) : 0.f);
+      },
+      [&](int i, float2 z) { work[(i / NT) * WP + i % NT] = z; });
   __syncthreads();
   team_fft<NT, false>(work, PAIRS, WP, 1, tw2, 2, tid, nthr);
-  periodic_fwd_post<NT>(work, Sp, col0, ncols, ncols, tid, nthr);
+  periodic_fwd_post<NT>(work, Sp, col0, ncols, ncols, COLS, tid, nthr);
 }
 
 // Periodic inverse real FFT to a field; optional partial sums of (x - ref)^2.
 template <int NT>
 __global__ void __launch_bounds__(kTpassThreads)
     k_sinv(const float2* __restrict__ Sp, int ncols, float* __restrict__ x, const float* __restrict__ ref,
-           double* __restrict__ partials, const float2* __restrict__ tw2g) {
-  constexpr int PAIRS = TP<NT>::PAIRS, WP = TP<NT>::WP, COLS = TP<NT>::COLS;
+           double* __restrict__ partials, const float2* __restrict__ tw2g, int cols) {
+  const int COLS = cols, PAIRS = cols >> 1;
+  constexpr int WP = TP<NT>::WP;
   extern __shared__ float4 smem_f4[];
   float2* tw2 = reinterpret_cast<float2*>(smem_f4);
   float2* work = tw2 + 2 * NT;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int col0 = blockIdx.x * COLS;
   for (int i = tid; i < 2 * NT; i += nthr) tw2[i] = __ldg(tw2g + i);
-  for (int i = tid; i < NT * PAIRS; i += nthr) {
-    const int k = i / PAIRS, p = i % PAIRS;
-    int kk = k;
-    const bool mir = k > NT / 2;
-    if (mir) kk = NT - k;
-    const int ca = col0 + 2 * p, cb = ca + 1;
-    float2 A = ca < ncols ? __ldg(Sp + (size_t)kk * ncols + ca) : make_float2(0.f, 0.f);
-    float2 B = cb < ncols ? __ldg(Sp + (size_t)kk * ncols + cb) : make_float2(0.f, 0.f);
-    if (mir) {
-      A.y = -A.y;
-      B.y = -B.y;
-    }
-    work[p * WP + fpos<NT>(k)] = make_float2(A.x - B.y, A.y + B.x);
-  }
+  const int lp = __ffs(PAIRS) - 1;
+  batched_copy<8, float2>(
+      NT * PAIRS, tid, nthr,
+      [&](int i) {
+        const int k = i >> lp, p = i & (PAIRS - 1);
+        int kk = k;
+        const bool mir = k > NT / 2;
+        if (mir) kk = NT - k;
+        const int ca = col0 + 2 * p, cb = ca + 1;
+        float2 A = ca < ncols ? __ldg(Sp + (size_t)kk * ncols + ca) : make_float2(0.f, 0.f);
+        float2 B = cb < ncols ? __ldg(Sp + (size_t)kk * ncols + cb) : make_float2(0.f, 0.f);
+        if (mir) {
+          A.y = -A.y;
+          B.y = -B.y;
+        }
+        return make_float2(A.x - B.y, A.y + B.x);
+      },
+      [&](int i, float2 z) { work[(i & (PAIRS - 1)) * WP + fpos<NT>(i >> lp)] = z; });
   __syncthreads();
   team_fft<NT, true>(work, PAIRS, WP, 1, tw2, 2, tid, nthr);
   const float scale = 1.0f / NT;
   double acc[1] = {0.0};
-  for (int i = tid; i < COLS * NT; i += nthr) {
-    const int c = i / NT, n = i % NT;
-    if (col0 + c >= ncols) continue;
-    const float2 z = work[(c >> 1) * WP + n];
-    const float v = ((c & 1) ? z.y : z.x) * scale;
-    const size_t g = (size_t)(col0 + c) * NT + n;
-    x[g] = v;
-    if (ref) {
-      const float d = v - __ldg(ref + g);
-      acc[0] += (double)d * (double)d;
-    }
-  }
+  const int total = min(COLS, ncols - col0) * NT;
+  batched_copy<8, float>(
+      total, tid, nthr, [&](int i) { return ref ? __ldg(ref + (size_t)col0 * NT + i) : 0.f; },
+      [&](int i, float rv) {
+        const int c = i / NT, n = i % NT;
+        const float2 z = work[(c >> 1) * WP + n];
+        const float v = ((c & 1) ? z.y : z.x) * scale;
+        x[(size_t)col0 * NT + i] = v;
+        if (ref) {
+          const float d = v - rv;
+          acc[0] += (double)d * (double)d;
+        }
+      });
   if (partials) block_reduce_store<1>(acc, partials);
 }
 
@@ -430,15 +468,37 @@ static nlos_status set_smem_tp(K kernel, size_t bytes) {
   return NLOS_OK;
 }
 
+// Launch shape of a t-pass: columns per CTA (fewer when there are few
+// columns, e.g. the sampled columns of A_D, so the grid still covers the
+// GPU), threads per CTA and dynamic shared memory (twiddles, the packed pair
+// transforms, `extra` real column buffers).
+struct TpShape {
+  int cols, threads, blocks;
+  size_t smem;
+};
+
+template <int NT>
+static TpShape tp_shape(int ncols, int extra) {
+  TpShape sh;
+  sh.cols = TP<NT>::COLS;
+  while (sh.cols > 2 && div_up(ncols, sh.cols) < 2 * 152) sh.cols >>= 1;
+  sh.threads = sh.cols >= 8 ? kTpassThreads : sh.cols == 4 ? 128 : 64;
+  sh.blocks = div_up(ncols, sh.cols);
+  // the work region is padded to an even number of float2 so the real column
+  // buffers after it stay 16-byte aligned (float4 accesses)
+  sh.smem = sizeof(float2) * (2 * NT + (((sh.cols / 2) * TP<NT>::WP + 1) & ~1)) +
+            sizeof(float) * extra * sh.cols * NT;
+  return sh;
+}
+
 template <int NT>
 nlos_status TpassOps<NT>::tfwd_rz(const Plan& P, const float* u, int ncols, float2* S, int pitch, cudaStream_t st) {
   KTimer kt_(P, KC_TFWD, st);
   auto kern = k_tfwd<NT, 0>;
-  const size_t sm = TP<NT>::smem_base;
-  NLOS_TRY(set_smem_tp(kern, sm));
+  const TpShape sh = tp_shape<NT>(ncols, 1);
+  NLOS_TRY(set_smem_tp(kern, sh.smem));
   Lin3 src{{u, nullptr, nullptr}, {1.f, 0.f, 0.f}, nullptr};
-  kern<<<div_up(ncols, TP<NT>::COLS), kTpassThreads, sm, st>>>(src, ncols, S, pitch, P.d_rz_i0, P.d_rz_w, nullptr,
-                                                               P.d_tw2t);
+  kern<<<sh.blocks, sh.threads, sh.smem, st>>>(src, ncols, S, pitch, P.d_rz_i0, P.d_rz_w, nullptr, P.d_tw2t, sh.cols);
   NLOS_LAUNCH_CHECK("k_tfwd<rz>");
   return NLOS_OK;
 }
@@ -447,10 +507,10 @@ template <int NT>
 nlos_status TpassOps<NT>::tfwd_rtt(const Plan& P, const Lin3& r, int ncols, float2* S, int pitch, cudaStream_t st) {
   KTimer kt_(P, KC_TFWD, st);
   auto kern = k_tfwd<NT, 1>;
-  const size_t sm = TP<NT>::smem_base;
-  NLOS_TRY(set_smem_tp(kern, sm));
-  kern<<<div_up(ncols, TP<NT>::COLS), kTpassThreads, sm, st>>>(r, ncols, S, pitch, nullptr, P.d_rt_w, P.d_rtt_start,
-                                                               P.d_tw2t);
+  const TpShape sh = tp_shape<NT>(ncols, 1);
+  NLOS_TRY(set_smem_tp(kern, sh.smem));
+  kern<<<sh.blocks, sh.threads, sh.smem, st>>>(r, ncols, S, pitch, nullptr, P.d_rt_w, P.d_rtt_start, P.d_tw2t,
+                                               sh.cols);
   NLOS_LAUNCH_CHECK("k_tfwd<rtt>");
   return NLOS_OK;
 }
@@ -460,11 +520,11 @@ nlos_status TpassOps<NT>::tinv_store(const Plan& P, const float2* S, int pitch, 
                                      const int32_t* outmap, cudaStream_t st) {
   KTimer kt_(P, KC_TINV, st);
   auto kern = k_tinv<NT, 0>;
-  const size_t sm = TP<NT>::smem_base;
-  NLOS_TRY(set_smem_tp(kern, sm));
+  const TpShape sh = tp_shape<NT>(ncols, 1);
+  NLOS_TRY(set_smem_tp(kern, sh.smem));
   FitArgs fa{};
-  kern<<<div_up(ncols, TP<NT>::COLS), kTpassThreads, sm, st>>>(S, pitch, ncols, out, outmap, fa, P.d_rt_k0, P.d_rt_w,
-                                                               P.d_tw2t);
+  kern<<<sh.blocks, sh.threads, sh.smem, st>>>(S, pitch, ncols, out, outmap, fa, P.d_rt_k0, P.d_rt_w, P.d_tw2t,
+                                               sh.cols);
   NLOS_LAUNCH_CHECK("k_tinv<store>");
   return NLOS_OK;
 }
@@ -474,12 +534,12 @@ nlos_status TpassOps<NT>::tinv_fit(const Plan& P, const float2* S, int pitch, in
                                    const FitArgs& fa, int* nblocks, cudaStream_t st) {
   KTimer kt_(P, KC_TINV, st);
   auto kern = k_tinv<NT, 1>;
-  const size_t sm = TP<NT>::smem_base;
-  NLOS_TRY(set_smem_tp(kern, sm));
-  const int nb = div_up(ncols, TP<NT>::COLS);
-  if (nb > P.partial_blocks) return fail(NLOS_ERR_INVALID_ARG, "partials buffer too small");
-  *nblocks = nb;
-  kern<<<nb, kTpassThreads, sm, st>>>(S, pitch, ncols, out, nullptr, fa, P.d_rt_k0, P.d_rt_w, P.d_tw2t);
+  const TpShape sh = tp_shape<NT>(ncols, 1);
+  NLOS_TRY(set_smem_tp(kern, sh.smem));
+  if (sh.blocks > P.partial_blocks) return fail(NLOS_ERR_INVALID_ARG, "partials buffer too small");
+  *nblocks = sh.blocks;
+  kern<<<sh.blocks, sh.threads, sh.smem, st>>>(S, pitch, ncols, out, nullptr, fa, P.d_rt_k0, P.d_rt_w, P.d_tw2t,
+                                               sh.cols);
   NLOS_LAUNCH_CHECK("k_tinv<fit>");
   return NLOS_OK;
 }
@@ -489,11 +549,11 @@ nlos_status TpassOps<NT>::tadj_store(const Plan& P, const float2* S, int pitch, 
                                      cudaStream_t st) {
   KTimer kt_(P, KC_TADJ, st);
   auto kern = k_tadj<NT, 0>;
-  const size_t sm = TP<NT>::smem_base + sizeof(float) * TP<NT>::COLS * NT;
-  NLOS_TRY(set_smem_tp(kern, sm));
+  const TpShape sh = tp_shape<NT>(ncols, 2);
+  NLOS_TRY(set_smem_tp(kern, sh.smem));
   SolveRhs sr{};
-  kern<<<div_up(ncols, TP<NT>::COLS), kTpassThreads, sm, st>>>(S, pitch, ncols, out, sr, nullptr, P.d_rz_i0, P.d_rz_w,
-                                                               P.d_rzt_start, P.d_tw2t);
+  kern<<<sh.blocks, sh.threads, sh.smem, st>>>(S, pitch, ncols, out, sr, nullptr, P.d_rz_i0, P.d_rz_w,
+                                               P.d_rzt_start, P.d_tw2t, sh.cols);
   NLOS_LAUNCH_CHECK("k_tadj<store>");
   return NLOS_OK;
 }
@@ -503,10 +563,10 @@ nlos_status TpassOps<NT>::tadj_solve(const Plan& P, const float2* S, int pitch, 
                                      float2* Sp, cudaStream_t st) {
   KTimer kt_(P, KC_TADJ, st);
   auto kern = k_tadj<NT, 1>;
-  const size_t sm = TP<NT>::smem_base + sizeof(float) * TP<NT>::COLS * NT;
-  NLOS_TRY(set_smem_tp(kern, sm));
-  kern<<<div_up(ncols, TP<NT>::COLS), kTpassThreads, sm, st>>>(S, pitch, ncols, nullptr, sr, Sp, P.d_rz_i0, P.d_rz_w,
-                                                               P.d_rzt_start, P.d_tw2t);
+  const TpShape sh = tp_shape<NT>(ncols, 2);
+  NLOS_TRY(set_smem_tp(kern, sh.smem));
+  kern<<<sh.blocks, sh.threads, sh.smem, st>>>(S, pitch, ncols, nullptr, sr, Sp, P.d_rz_i0, P.d_rz_w, P.d_rzt_start,
+                                               P.d_tw2t, sh.cols);
   NLOS_LAUNCH_CHECK("k_tadj<solve>");
   return NLOS_OK;
 }
@@ -515,9 +575,9 @@ template <int NT>
 nlos_status TpassOps<NT>::sfwd(const Plan& P, const float* x, int ncols, float2* Sp, cudaStream_t st) {
   KTimer kt_(P, KC_SFWD, st);
   auto kern = k_sfwd<NT>;
-  const size_t sm = sizeof(float2) * (2 * NT + TP<NT>::PAIRS * TP<NT>::WP);
-  NLOS_TRY(set_smem_tp(kern, sm));
-  kern<<<div_up(ncols, TP<NT>::COLS), kTpassThreads, sm, st>>>(x, ncols, Sp, P.d_tw2t);
+  const TpShape sh = tp_shape<NT>(ncols, 0);
+  NLOS_TRY(set_smem_tp(kern, sh.smem));
+  kern<<<sh.blocks, sh.threads, sh.smem, st>>>(x, ncols, Sp, P.d_tw2t, sh.cols);
   NLOS_LAUNCH_CHECK("k_sfwd");
   return NLOS_OK;
 }
@@ -527,12 +587,11 @@ nlos_status TpassOps<NT>::sinv(const Plan& P, const float2* Sp, int ncols, float
                                double* partials, int* nblocks, cudaStream_t st) {
   KTimer kt_(P, KC_SINV, st);
   auto kern = k_sinv<NT>;
-  const size_t sm = sizeof(float2) * (2 * NT + TP<NT>::PAIRS * TP<NT>::WP);
-  NLOS_TRY(set_smem_tp(kern, sm));
-  const int nb = div_up(ncols, TP<NT>::COLS);
-  if (partials && nb > P.partial_blocks) return fail(NLOS_ERR_INVALID_ARG, "partials buffer too small");
-  if (nblocks) *nblocks = nb;
-  kern<<<nb, kTpassThreads, sm, st>>>(Sp, ncols, x, ref, partials, P.d_tw2t);
+  const TpShape sh = tp_shape<NT>(ncols, 0);
+  NLOS_TRY(set_smem_tp(kern, sh.smem));
+  if (partials && sh.blocks > P.partial_blocks) return fail(NLOS_ERR_INVALID_ARG, "partials buffer too small");
+  if (nblocks) *nblocks = sh.blocks;
+  kern<<<sh.blocks, sh.threads, sh.smem, st>>>(Sp, ncols, x, ref, partials, P.d_tw2t, sh.cols);
   NLOS_LAUNCH_CHECK("k_sinv");
   return NLOS_OK;
 }

@@ -36,11 +36,91 @@ namespace nlos {
 template <int N>
 struct CV {
   static constexpr int P = N + 1;                 // odd row pitch of the plane
-  static constexpr int CH = N >= 16 ? 16 : N;     // columns per x-chunk
-  static constexpr int SP = 2 * CH + 1;           // pitch of the chunk scratch
+  static constexpr int CH = N >= 32 ? 32 : N;     // columns per x-chunk
+  static constexpr int SP = 2 * CH + 1;           // pitch of the chunk scratch (2 CH transforms)
   static constexpr size_t smem = sizeof(float2) * (N * P + N * SP + 2 * N);
 };
 constexpr int kConvThreads = 512;
+
+// x-direction padded convolution of CH plane columns starting at c0 (the
+// columns are ky' positions of the y-transformed plane; ky = 2 ky_nat + r).
+// For each column and each x-parity ax the 2N-point padded DFT bin
+// kx = 2 kx' + ax is the N-point DFT of the column twisted by
+// exp(-i pi ax x / N); after the multiply by H the two inverse transforms are
+// untwisted and summed back into the plane.  The split N = R1 R2 runs as
+//   A  (per column, ax, n2): R1-point DFT of the stride-R2 subsequence,
+//      twiddles, into the scratch;
+//   B  (per transform, k1): R2-point DFT, multiply by H, inverse R2-point DFT
+//      and inverse twiddles, all in registers;
+//   A' (per column, n2): inverse R1-point DFTs of both parities, untwist,
+//      sum, back into the plane.
+template <int N>
+__device__ __forceinline__ void xconv_chunk(float2* __restrict__ plane, float2* __restrict__ scr, int c0, int r,
+                                            const float2* __restrict__ Hk, int adj, const float2* __restrict__ tw,
+                                            int tid, int nthr) {
+  constexpr int R1 = FftPlan<N>::R1, R2 = FftPlan<N>::R2, P = CV<N>::P, CH = CV<N>::CH, SP = CV<N>::SP;
+  // A: forward first step of both parities
+  for (int it = tid; it < 2 * CH * R2; it += nthr) {
+    const int t = it % (2 * CH), n2 = it / (2 * CH);
+    const int ax = t / CH, j = t % CH;
+    float2 a[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) {
+      const int x = R2 * n1 + n2;
+      float2 v = plane[x * P + c0 + j];
+      if (ax) v = cmul(v, tw[x]);
+      a[n1] = v;
+    }
+    dft_reg<R1, false>(a);
+#pragma unroll
+    for (int k1 = 1; k1 < R1; ++k1) a[k1] = cmul(a[k1], tw[2 * ((n2 * k1) & (N - 1))]);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) scr[(R2 * k1 + n2) * SP + t] = a[k1];
+  }
+  __syncthreads();
+  // B: second step, kernel multiply, inverse second step
+  for (int it = tid; it < 2 * CH * R1; it += nthr) {
+    const int t = it % (2 * CH), k1 = it / (2 * CH);
+    const int ax = t / CH, j = t % CH;
+    float2 b[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) b[n2] = scr[(R2 * k1 + n2) * SP + t];
+    dft_reg<R2, false>(b);
+    int ky = 2 * kfreq<N>(c0 + j) + r;
+    if (ky > N) ky = 2 * N - ky;
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      int kx = 2 * (k1 + R1 * k2) + ax;
+      if (kx > N) kx = 2 * N - kx;
+      const float2 h = __ldg(Hk + kx * (N + 1) + ky);
+      b[k2] = adj ? cmulc(b[k2], h) : cmul(b[k2], h);
+    }
+    dft_reg<R2, true>(b);
+#pragma unroll
+    for (int n2 = 1; n2 < R2; ++n2) b[n2] = cmulc(b[n2], tw[2 * ((n2 * k1) & (N - 1))]);
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) scr[(R2 * k1 + n2) * SP + t] = b[n2];
+  }
+  __syncthreads();
+  // A': inverse first step of both parities, untwist, sum into the plane
+  for (int it = tid; it < CH * R2; it += nthr) {
+    const int j = it % CH, n2 = it / CH;
+    float2 e[R1], o[R1];
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      e[k1] = scr[(R2 * k1 + n2) * SP + j];
+      o[k1] = scr[(R2 * k1 + n2) * SP + CH + j];
+    }
+    dft_reg<R1, true>(e);
+    dft_reg<R1, true>(o);
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) {
+      const int x = R2 * n1 + n2;
+      plane[x * P + c0 + j] = cadd(e[n1], cmulc(o[n1], tw[x]));
+    }
+  }
+  __syncthreads();
+}
 
 template <int N>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kConvThreads)
@@ -62,22 +142,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kConvThreads)
   // 1. load the plane with the y-twist of parity r
   const float2* src = Sin + (size_t)kt * in_pitch;
   if (in_cols == nullptr) {
-    for (int i = tid; i < N * N; i += nthr) {
-      const int x = i / N, y = i % N;
-      float2 v = __ldg(src + i);
-      if (r) v = cmul(v, tw[y]);
-      plane[x * P + y] = v;
-    }
+    batched_copy<8, float2>(
+        N * N, tid, nthr, [&](int i) { return __ldg(src + i); },
+        [&](int i, float2 v) {
+          const int x = i / N, y = i % N;
+          plane[x * P + y] = r ? cmul(v, tw[y]) : v;
+        });
   } else {
     for (int i = tid; i < N * P; i += nthr) plane[i] = make_float2(0.f, 0.f);
     __syncthreads();
-    for (int j = tid; j < in_n; j += nthr) {
-      const int col = __ldg(in_cols + j);
-      const int x = col / N, y = col % N;
-      float2 v = __ldg(src + j);
-      if (r) v = cmul(v, tw[y]);
-      plane[x * P + y] = v;
-    }
+    batched_copy<4, float2>(
+        in_n, tid, nthr, [&](int j) { return __ldg(src + j); },
+        [&](int j, float2 v) {
+          const int col = __ldg(in_cols + j);
+          const int x = col / N, y = col % N;
+          plane[x * P + y] = r ? cmul(v, tw[y]) : v;
+        });
   }
   __syncthreads();
 
@@ -86,34 +166,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kConvThreads)
 
   // 3. x-direction padded convolution, CH columns at a time
   const float2* Hk = H + (size_t)kt * (N + 1) * (N + 1);
-  for (int c0 = 0; c0 < N; c0 += CH) {
-    for (int i = tid; i < N * CH; i += nthr) {
-      const int x = i / CH, j = i % CH;
-      const float2 v = plane[x * P + c0 + j];
-      scr[x * SP + j] = v;
-      scr[x * SP + CH + j] = cmul(v, tw[x]);
-    }
-    __syncthreads();
-    team_fft<N, false>(scr, 2 * CH, 1, SP, tw, 2, tid, nthr);
-    for (int i = tid; i < N * 2 * CH; i += nthr) {
-      const int xp = i / (2 * CH), t = i % (2 * CH);
-      const int ax = t / CH, j = t % CH;
-      int kx = 2 * kfreq<N>(xp) + ax;
-      int ky = 2 * kfreq<N>(c0 + j) + r;
-      if (kx > N) kx = 2 * N - kx;
-      if (ky > N) ky = 2 * N - ky;
-      const float2 h = __ldg(Hk + kx * (N + 1) + ky);
-      const float2 v = scr[xp * SP + t];
-      scr[xp * SP + t] = adj ? cmulc(v, h) : cmul(v, h);
-    }
-    __syncthreads();
-    team_fft<N, true>(scr, 2 * CH, 1, SP, tw, 2, tid, nthr);
-    for (int i = tid; i < N * CH; i += nthr) {
-      const int x = i / CH, j = i % CH;
-      plane[x * P + c0 + j] = cadd(scr[x * SP + j], cmulc(scr[x * SP + CH + j], tw[x]));
-    }
-    __syncthreads();
-  }
+  for (int c0 = 0; c0 < N; c0 += CH) xconv_chunk<N>(plane, scr, c0, r, Hk, adj, tw, tid, nthr);
 
   // 4. inverse y-DFT of every row (natural y order)
   team_fft<N, true>(plane, N, P, 1, tw, 2, tid, nthr);
@@ -125,20 +178,33 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kConvThreads)
   const float s = 1.0f / (4.0f * N * N);
   float2* dst = Sout + (size_t)kt * out_pitch;
   if (out_cols == nullptr) {
-    for (int i = tid + r * (N * N / 2); i < (r + 1) * (N * N / 2); i += nthr) {
-      const int x = i / N, y = i % N;
-      const float2 v = cadd(p0[x * P + y], cmulc(p1[x * P + y], tw[y]));
-      dst[i] = cscale(v, s);
-    }
+    const int i0 = r * (N * N / 2);
+    batched_copy<8, float4>(
+        N * N / 2, tid, nthr,
+        [&](int ii) {
+          const int i = i0 + ii, x = i / N, y = i % N;
+          const float2 a = p0[x * P + y], b = p1[x * P + y];
+          return make_float4(a.x, a.y, b.x, b.y);
+        },
+        [&](int ii, float4 v) {
+          const int i = i0 + ii, y = i % N;
+          dst[i] = cscale(cadd(make_float2(v.x, v.y), cmulc(make_float2(v.z, v.w), tw[y])), s);
+        });
   } else {
     const int half = (out_n + 1) / 2;
     const int jb = r * half, je = r ? out_n : half;
-    for (int j = jb + tid; j < je; j += nthr) {
-      const int col = __ldg(out_cols + j);
-      const int x = col / N, y = col % N;
-      const float2 v = cadd(p0[x * P + y], cmulc(p1[x * P + y], tw[y]));
-      dst[j] = cscale(v, s);
-    }
+    batched_copy<4, float4>(
+        je - jb, tid, nthr,
+        [&](int jj) {
+          const int col = __ldg(out_cols + jb + jj);
+          const int x = col / N, y = col % N;
+          const float2 a = p0[x * P + y], b = p1[x * P + y];
+          return make_float4(a.x, a.y, b.x, b.y);
+        },
+        [&](int jj, float4 v) {
+          const int y = __ldg(out_cols + jb + jj) % N;
+          dst[jb + jj] = cscale(cadd(make_float2(v.x, v.y), cmulc(make_float2(v.z, v.w), tw[y])), s);
+        });
   }
   cluster.sync();
 }
@@ -146,6 +212,57 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kConvThreads)
 // ---------------------------------------------------------------------------
 // Periodic lateral solve per kt' plane.
 // ---------------------------------------------------------------------------
+// Column (x) pass of the periodic solve: forward first step, then per
+// (column, k1) the second step, the division by c0 + c1 lambda(k) and the
+// inverse second step in registers, then the inverse first step.
+template <int N>
+__device__ __forceinline__ void xsolve_pass(float2* __restrict__ plane, float c0, float c1, float lt,
+                                            const float* __restrict__ lamx, const float2* __restrict__ tw, int tid,
+                                            int nthr) {
+  constexpr int R1 = FftPlan<N>::R1, R2 = FftPlan<N>::R2, P = N + 1;
+  for (int it = tid; it < N * R2; it += nthr) {
+    const int j = it % N, n2 = it / N;
+    float2 a[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) a[n1] = plane[(R2 * n1 + n2) * P + j];
+    dft_reg<R1, false>(a);
+#pragma unroll
+    for (int k1 = 1; k1 < R1; ++k1) a[k1] = cmul(a[k1], tw[2 * ((n2 * k1) & (N - 1))]);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) plane[(R2 * k1 + n2) * P + j] = a[k1];
+  }
+  __syncthreads();
+  for (int it = tid; it < N * R1; it += nthr) {
+    const int j = it % N, k1 = it / N;
+    float2 b[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) b[n2] = plane[(R2 * k1 + n2) * P + j];
+    dft_reg<R2, false>(b);
+    const float ly = __ldg(lamx + kfreq<N>(j)) + lt;
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      const float den = c0 + c1 * (__ldg(lamx + k1 + R1 * k2) + ly);
+      b[k2] = cscale(b[k2], 1.0f / den);
+    }
+    dft_reg<R2, true>(b);
+#pragma unroll
+    for (int n2 = 1; n2 < R2; ++n2) b[n2] = cmulc(b[n2], tw[2 * ((n2 * k1) & (N - 1))]);
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) plane[(R2 * k1 + n2) * P + j] = b[n2];
+  }
+  __syncthreads();
+  for (int it = tid; it < N * R2; it += nthr) {
+    const int j = it % N, n2 = it / N;
+    float2 a[R1];
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) a[k1] = plane[(R2 * k1 + n2) * P + j];
+    dft_reg<R1, true>(a);
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) plane[(R2 * n1 + n2) * P + j] = a[n1];
+  }
+  __syncthreads();
+}
+
 template <int N>
 __global__ void __launch_bounds__(kConvThreads)
     k_sxy(float2* __restrict__ Sp, int nt, const float* __restrict__ lamx, const float* __restrict__ lamt,
@@ -158,20 +275,14 @@ __global__ void __launch_bounds__(kConvThreads)
   const int tid = threadIdx.x, nthr = blockDim.x;
   for (int i = tid; i < 2 * N; i += nthr) tw[i] = __ldg(twg + i);
   float2* g = Sp + (size_t)kt * N * N;
-  for (int i = tid; i < N * N; i += nthr) plane[(i / N) * P + (i % N)] = g[i];
+  const float s = 1.0f / (float)(N * N);
+  batched_copy<8, float2>(
+      N * N, tid, nthr, [&](int i) { return g[i]; },
+      [&](int i, float2 v) { plane[(i / N) * P + (i % N)] = cscale(v, s); });
   __syncthreads();
   team_fft<N, false>(plane, N, P, 1, tw, 2, tid, nthr);   // rows (y)
-  team_fft<N, false>(plane, N, 1, P, tw, 2, tid, nthr);   // columns (x)
   const float c0 = sc ? (float)sc->L : (float)c0_host;
-  const float lt = __ldg(lamt + kt);
-  const float s = 1.0f / (float)(N * N);
-  for (int i = tid; i < N * N; i += nthr) {
-    const int xp = i / N, yp = i % N;
-    const float den = c0 + (float)c1 * (__ldg(lamx + kfreq<N>(xp)) + __ldg(lamx + kfreq<N>(yp)) + lt);
-    plane[xp * P + yp] = cscale(plane[xp * P + yp], s / den);
-  }
-  __syncthreads();
-  team_fft<N, true>(plane, N, 1, P, tw, 2, tid, nthr);
+  xsolve_pass<N>(plane, c0, (float)c1, __ldg(lamt + kt), lamx, tw, tid, nthr);
   team_fft<N, true>(plane, N, P, 1, tw, 2, tid, nthr);
   for (int i = tid; i < N * N; i += nthr) g[i] = plane[(i / N) * P + (i % N)];
 }
