@@ -180,6 +180,49 @@ nlos_status nlos_reconstruct(nlos_plan plan, const nlos_params* params, const fl
                              float* u_out_dev, float* tau_out_dev, nlos_stats* stats_host,
                              void* stream);
 
+/* Reconstruct n independent scenes at once.  plans[i] must be n distinct
+ * plans (each owns its scratch; a plan appearing twice is rejected);
+ * params[i], tau0[i] (device), u_out[i] (device) and tau_out[i] (device,
+ * nullable array or entries) as for nlos_reconstruct.  Each scene runs on an
+ * internal stream forked from `stream` and joined back to it; their
+ * iterations are enqueued round-robin so the scenes' kernels overlap on the
+ * GPU.  A scene's result does not depend on the other scenes of the batch.
+ * Synchronises before returning; stats (nullable) receives n entries.  This
+ * is the batched execution of the benchmark spec's batching workload; the paper
+ * reconstructs one scene at a time. */
+nlos_status nlos_reconstruct_batch(const nlos_plan* plans, const nlos_params* params, const float* const* tau0,
+                                   float* const* u_out, float* const* tau_out, int32_t n, nlos_stats* stats,
+                                   void* stream);
+
+/* Serving.  A server owns a worker thread on the current device that admits
+ * submitted reconstruction jobs in arrival order while fewer than max_slots
+ * run and the device memory they need fits hbm_budget_bytes, keeps each
+ * running job's state resident on the device, and advances all running jobs
+ * together (continuous batching: a job submitted while others run joins them
+ * as soon as a slot and memory free up).  A job that can never fit the budget
+ * fails with NLOS_ERR_OOM.  nlos_submit copies tau0_host (full grid
+ * [nx][ny][nt]) and the geometry (mask included) and returns at once;
+ * u_out_host must stay valid until the job is reported done, when the result
+ * has been written there.  nlos_poll returns NLOS_OK (done, *out filled),
+ * NLOS_ERR_NOT_READY, or the job's error; nlos_wait blocks up to timeout_s.
+ * nlos_job_times gives the seconds from submit to start and from submit to
+ * completion of a finished job.  nlos_server_info fills 8 counters: queued,
+ * running, completed, failed, peak running, device bytes in use, peak bytes,
+ * budget.  nlos_server_destroy stops accepting jobs, cancels queued ones if
+ * cancel_pending != 0 (they end with NLOS_ERR_TIMEOUT), waits at most
+ * timeout_s for the rest, joins the worker and frees everything; it returns
+ * NLOS_ERR_TIMEOUT if jobs were still unfinished at the deadline (queued ones
+ * are then cancelled; running ones are finished by the worker before it
+ * exits).  Submit, poll, wait, job_times and info are thread-safe. */
+nlos_status nlos_server_create(size_t hbm_budget_bytes, int32_t max_slots, nlos_server* out);
+nlos_status nlos_submit(nlos_server server, const nlos_geometry* geom, const nlos_params* params,
+                        const float* tau0_host, float* u_out_host, uint64_t* job_id);
+nlos_status nlos_poll(nlos_server server, uint64_t job_id, nlos_stats* out);
+nlos_status nlos_wait(nlos_server server, uint64_t job_id, double timeout_s, nlos_stats* out);
+nlos_status nlos_job_times(nlos_server server, uint64_t job_id, double* queued_s, double* total_s);
+nlos_status nlos_server_info(nlos_server server, int64_t* counters8);
+nlos_status nlos_server_destroy(nlos_server server, int32_t cancel_pending, double timeout_s);
+
 /* The periodic FFT solve of nlos_solve for callers that cannot allocate
  * device memory when they solve: code running while its stream is being
  * captured into a CUDA graph (allocations are refused during a capture),

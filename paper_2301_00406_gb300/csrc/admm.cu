@@ -703,165 +703,194 @@ static nlos_status init_scalars(Plan& P, SolverState* s, double L0, const float*
   return NLOS_OK;
 }
 
-static nlos_status finish(Plan& P, SolverState* s, float* u_out, float* tau_out, nlos_stats* stats, cudaStream_t st) {
-  const size_t F = s->V * sizeof(float);
-  NLOS_CUDA(cudaMemcpyAsync(u_out, s->uk, F, cudaMemcpyDeviceToDevice, st));
-  if (tau_out && s->model == 2) NLOS_CUDA(cudaMemcpyAsync(tau_out, s->tk, F, cudaMemcpyDeviceToDevice, st));
-  NLOS_TRY(read_scalars(s, st));
-  fill_stats(*s->h_sc, stats);
-  if (s->h_sc->status != NLOS_OK) return fail(s->h_sc->status, "reconstruction stopped: non-finite energy or backtracking gave up");
+// ---------------------------------------------------------------------------
+// One reconstruction as a state machine: init, one enqueued iteration per
+// step, an asynchronous finish and the collection of the statistics.  A
+// single reconstruction runs the steps back to back; the batch and the
+// server interleave the steps of many jobs on their own streams.
+// ---------------------------------------------------------------------------
+nlos_status job_init(JobRun& j) {
+  Plan& P = *j.P;
+  const nlos_params& p = j.p;
+  cudaStream_t st = j.st;
+  NLOS_TRY(get_solver(P, p.model, &j.s));
+  SolverState* s = j.s;
+  const size_t V = s->V;
+  NLOS_TRY(plan_norm2(P, p.model == 1, st, &j.norm2));
+  j.L0 = p.L0 > 0.0 ? p.L0 : 2.0 * j.norm2;
+  j.L_host = j.L0;
+  j.restart = p.restart < 0 ? (p.model == 2 ? 1 : 0) : p.restart;
+  j.it = 0;
+  j.cur = 0;
+  j.prev = 1;
+  j.nxt = 2;
+  j.done = p.iters == 0;
+  if (p.model == 1) {
+    const size_t C = (size_t)P.ncols * P.nt;
+    NLOS_TRY(zero(s->uk, V, st));
+    NLOS_TRY(zero(s->ub, V, st));
+    NLOS_TRY(zero(s->lam, 3 * V, st));
+    for (int i = 0; i < 3; ++i) NLOS_TRY(zero(s->cache[i], C, st));
+    NLOS_TRY(fill(s->ph, phi_zero(p.a, p.b, p.phi), V, st));
+    NLOS_TRY(gather_columns(P, j.tau0, s->tau0c, st));
+    NLOS_TRY(init_scalars(P, s, j.L0, s->tau0c, C, 0.5, st));
+  } else {
+    for (float* f : {s->uk, s->ub, s->tk, s->tb, s->lam3}) NLOS_TRY(zero(f, V, st));
+    NLOS_TRY(zero(s->lam, 3 * V, st));
+    NLOS_TRY(zero(s->lam2, 3 * V, st));
+    for (int i = 0; i < 3; ++i) NLOS_TRY(zero(s->cache[i], V, st));
+    NLOS_TRY(fill(s->ph, phi_zero(p.a_u, p.b_u, p.phi), V, st));
+    NLOS_TRY(fill(s->pht, phi_zero(p.a_tau, p.b_tau, p.phi), V, st));
+    // E(0, 0) = lambda/2 ||tau0||^2 over the sampled columns
+    NLOS_TRY(gather_columns(P, j.tau0, s->tmp, st));
+    NLOS_TRY(init_scalars(P, s, j.L0, s->tmp, (size_t)P.ncols * P.nt, 0.5 * p.lambda, st));
+  }
   return NLOS_OK;
 }
 
-static nlos_status run_alg1(Plan& P, const nlos_params& p, const float* tau0, float* u_out, nlos_stats* stats,
-                            cudaStream_t st) {
-  SolverState* s = nullptr;
-  NLOS_TRY(get_solver(P, 1, &s));
+bool job_async(const JobRun& j) { return j.p.eps_stop <= 0.0 && j.L0 >= 1.5 * j.norm2; }
+
+static nlos_status step_alg1(JobRun& j) {
+  Plan& P = *j.P;
+  SolverState* s = j.s;
+  const nlos_params& p = j.p;
+  cudaStream_t st = j.st;
   const size_t V = s->V;
-  const size_t C = (size_t)P.ncols * P.nt;
   const Vox g = make_vox(P.nx, P.ny, P.nt);
   const VoxIter vi{ilog2i(P.nt), ilog2i(P.ny)};
-  double norm2 = 0.0;
-  NLOS_TRY(plan_norm2(P, true, st, &norm2));
-  const double L0 = p.L0 > 0.0 ? p.L0 : 2.0 * norm2;
-  const int restart = p.restart < 0 ? 0 : p.restart;
-
-  NLOS_TRY(zero(s->uk, V, st));
-  NLOS_TRY(zero(s->ub, V, st));
-  NLOS_TRY(zero(s->lam, 3 * V, st));
-  for (int i = 0; i < 3; ++i) NLOS_TRY(zero(s->cache[i], C, st));
-  NLOS_TRY(fill(s->ph, phi_zero(p.a, p.b, p.phi), V, st));
-  NLOS_TRY(gather_columns(P, tau0, s->tau0c, st));
-  NLOS_TRY(init_scalars(P, s, L0, s->tau0c, C, 0.5, st));
-
-  int cur = 0, prev = 1, nxt = 2;
-  double L_host = L0;
   const float eps2 = (float)(p.eps_normal * p.eps_normal);
   // halo-tiled stencils when the grid tiles evenly (TT = 128 along t, 8 rows in y)
   const bool tiled = P.nt % kTT == 0 && P.ny % kTY == 0;
   const int xb = std::min(16, P.nx);
   const dim3 tgrid((P.nt / kTT) * (P.ny / kTY), P.nx / xb);
   const int post_blocks = tiled ? (int)(tgrid.x * tgrid.y) : kStencilBlocks;
-  for (int it = 0; it < p.iters; ++it) {
-    { KTimer kt_(P, KC_PRE, st);
-    if (tiled)
-      k_pre1_tiled<<<tgrid, kTileThreads, 0, st>>>(s->ub, s->lam, s->ph, s->reg, g, xb, (float)p.mu, V);
-    else
-      k_pre1<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->ub, s->lam, s->ph, s->reg, g, vi, (float)p.mu, V);
-    }
-    NLOS_LAUNCH_CHECK("k_pre1");
-    Lin3 r{{s->cache[cur], s->cache[prev], s->tau0c}, {0.f, 0.f, 0.f}, s->sc};
-    NLOS_TRY(launch_tfwd_rtt(P, r, P.ncols, P.d_Sc, P.ncols, st));
-    NLOS_TRY(launch_conv(P, P.d_Sc, true, P.d_S, false, true, st));
-    const bool host_check = L_host < 1.5 * norm2;
-    UStepArgs ua{s->reg, p.mu, true, s->tau0c, p.eta, p.max_backtracks, s->cache[nxt], s->cache[cur], s->cache[prev]};
-    NLOS_TRY(u_step(P, s, ua, host_check, &L_host, st));
-    { KTimer kt_(P, KC_POST, st);
-    if (tiled)
-      k_post1_tiled<<<tgrid, kTileThreads, 0, st>>>(s->unew, s->uk, s->ub, s->lam, s->ph, s->ubn, s->sc, g, xb,
-                                                    (float)p.mu, (float)p.a, (float)p.b, p.phi, eps2, V, s->pc);
-    else
-      k_post1<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->unew, s->uk, s->ub, s->lam, s->ph, s->ubn, s->sc, g,
-                                                          vi, (float)p.mu, (float)p.a, (float)p.b, p.phi, eps2, V,
-                                                          s->pc);
-    }
-    NLOS_LAUNCH_CHECK("k_post1");
-    { KTimer kt_(P, KC_SMALL, st);
-    k_finalize<<<1, kSumThreads, 0, st>>>(s->sc, s->pc, post_blocks, 1, 0.0, restart, p.eps_stop);
-    }
-    NLOS_LAUNCH_CHECK("k_finalize");
-    swap_ptr(s->uk, s->unew);
-    swap_ptr(s->ub, s->ubn);
-    const int t = prev;
-    prev = cur;
-    cur = nxt;
-    nxt = t;
-    if (p.eps_stop > 0.0) {
-      NLOS_TRY(read_scalars(s, st));
-      if (s->h_sc->stop || s->h_sc->status != NLOS_OK) break;
-    }
+  { KTimer kt_(P, KC_PRE, st);
+  if (tiled)
+    k_pre1_tiled<<<tgrid, kTileThreads, 0, st>>>(s->ub, s->lam, s->ph, s->reg, g, xb, (float)p.mu, V);
+  else
+    k_pre1<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->ub, s->lam, s->ph, s->reg, g, vi, (float)p.mu, V);
   }
-  return finish(P, s, u_out, nullptr, stats, st);
+  NLOS_LAUNCH_CHECK("k_pre1");
+  Lin3 r{{s->cache[j.cur], s->cache[j.prev], s->tau0c}, {0.f, 0.f, 0.f}, s->sc};
+  NLOS_TRY(launch_tfwd_rtt(P, r, P.ncols, P.d_Sc, P.ncols, st));
+  NLOS_TRY(launch_conv(P, P.d_Sc, true, P.d_S, false, true, st));
+  const bool host_check = j.L_host < 1.5 * j.norm2;
+  UStepArgs ua{s->reg, p.mu, true, s->tau0c, p.eta, p.max_backtracks, s->cache[j.nxt], s->cache[j.cur],
+               s->cache[j.prev]};
+  NLOS_TRY(u_step(P, s, ua, host_check, &j.L_host, st));
+  { KTimer kt_(P, KC_POST, st);
+  if (tiled)
+    k_post1_tiled<<<tgrid, kTileThreads, 0, st>>>(s->unew, s->uk, s->ub, s->lam, s->ph, s->ubn, s->sc, g, xb,
+                                                  (float)p.mu, (float)p.a, (float)p.b, p.phi, eps2, V, s->pc);
+  else
+    k_post1<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->unew, s->uk, s->ub, s->lam, s->ph, s->ubn, s->sc, g, vi,
+                                                        (float)p.mu, (float)p.a, (float)p.b, p.phi, eps2, V, s->pc);
+  }
+  NLOS_LAUNCH_CHECK("k_post1");
+  { KTimer kt_(P, KC_SMALL, st);
+  k_finalize<<<1, kSumThreads, 0, st>>>(s->sc, s->pc, post_blocks, 1, 0.0, j.restart, p.eps_stop);
+  }
+  NLOS_LAUNCH_CHECK("k_finalize");
+  swap_ptr(s->uk, s->unew);
+  swap_ptr(s->ub, s->ubn);
+  return NLOS_OK;
 }
 
-static nlos_status run_alg2(Plan& P, const nlos_params& p, const float* tau0, float* u_out, float* tau_out,
-                            nlos_stats* stats, cudaStream_t st) {
-  SolverState* s = nullptr;
-  NLOS_TRY(get_solver(P, 2, &s));
+static nlos_status step_alg2(JobRun& j) {
+  Plan& P = *j.P;
+  SolverState* s = j.s;
+  const nlos_params& p = j.p;
+  cudaStream_t st = j.st;
   const size_t V = s->V;
   const Vox g = make_vox(P.nx, P.ny, P.nt);
   const VoxIter vi{ilog2i(P.nt), ilog2i(P.ny)};
   const int full = P.nx * P.ny;
-  double norm2 = 0.0;
-  NLOS_TRY(plan_norm2(P, false, st, &norm2));
-  const double L0 = p.L0 > 0.0 ? p.L0 : 2.0 * norm2;
-  const int restart = p.restart < 0 ? 1 : p.restart;
   const int32_t* colpos = P.full_mask ? nullptr : P.d_colpos;
-
-  for (float* f : {s->uk, s->ub, s->tk, s->tb, s->lam3}) NLOS_TRY(zero(f, V, st));
-  NLOS_TRY(zero(s->lam, 3 * V, st));
-  NLOS_TRY(zero(s->lam2, 3 * V, st));
-  for (int i = 0; i < 3; ++i) NLOS_TRY(zero(s->cache[i], V, st));
-  NLOS_TRY(fill(s->ph, phi_zero(p.a_u, p.b_u, p.phi), V, st));
-  NLOS_TRY(fill(s->pht, phi_zero(p.a_tau, p.b_tau, p.phi), V, st));
-  // E(0, 0) = lambda/2 ||tau0||^2 over the sampled columns
-  NLOS_TRY(gather_columns(P, tau0, s->tmp, st));
-  NLOS_TRY(init_scalars(P, s, L0, s->tmp, (size_t)P.ncols * P.nt, 0.5 * p.lambda, st));
-
   Alg2Coef c{(float)p.mu1, (float)p.mu2, (float)p.mu3, (float)p.lambda, (float)p.a_u, (float)p.b_u,
              (float)p.a_tau, (float)p.b_tau, p.phi, (float)(p.eps_normal * p.eps_normal)};
-  int cur = 0, prev = 1, nxt = 2;
-  double L_host = L0;
-  for (int it = 0; it < p.iters; ++it) {
-    { KTimer kt_(P, KC_PRE, st);
-    k_pre2<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->ub, s->tb, s->lam, s->lam2, s->lam3, s->ph, s->pht, tau0,
-                                                       colpos, s->reg, s->regt, g, vi, c, V);
-    }
-    NLOS_LAUNCH_CHECK("k_pre2");
-    Lin3 r{{s->cache[cur], s->cache[prev], s->tb}, {0.f, 0.f, 0.f}, s->sc};
-    NLOS_TRY(launch_tfwd_rtt(P, r, full, P.d_S, full, st));
-    NLOS_TRY(launch_conv(P, P.d_S, false, P.d_S, false, true, st));
-    const bool host_check = L_host < 1.5 * norm2;
-    UStepArgs ua{s->reg, p.mu1, false, s->tb, p.eta, p.max_backtracks, s->cache[nxt], s->cache[cur], s->cache[prev]};
-    NLOS_TRY(u_step(P, s, ua, host_check, &L_host, st));
-    { KTimer kt_(P, KC_SMALL, st);
-    k_add<<<elem_grid(V), 256, 0, st>>>(s->cache[nxt], s->regt, s->tmp, V);
-    }
-    NLOS_LAUNCH_CHECK("k_add");
-    NLOS_TRY(launch_sfwd(P, s->tmp, full, P.d_Sp, st));
-    NLOS_TRY(launch_sxy(P, P.d_Sp, nullptr, 1.0 + p.mu3, p.mu2, st));
-    NLOS_TRY(launch_sinv(P, P.d_Sp, full, s->tnew, nullptr, nullptr, nullptr, st));
-    { KTimer kt_(P, KC_POST, st);
-    k_post2<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->unew, s->uk, s->ub, s->tnew, s->tk, s->tb, s->lam, s->lam2,
-                                                        s->lam3, s->ph, s->pht, s->ubn, s->tbn, s->cache[nxt], tau0,
-                                                        colpos, s->sc, g, vi, c, V, s->pc);
-    }
-    NLOS_LAUNCH_CHECK("k_post2");
-    { KTimer kt_(P, KC_SMALL, st);
-    k_finalize<<<1, kSumThreads, 0, st>>>(s->sc, s->pc, kStencilBlocks, 2, p.lambda, restart, p.eps_stop);
-    }
-    NLOS_LAUNCH_CHECK("k_finalize");
-    swap_ptr(s->uk, s->unew);
-    swap_ptr(s->ub, s->ubn);
-    swap_ptr(s->tk, s->tnew);
-    swap_ptr(s->tb, s->tbn);
-    const int t = prev;
-    prev = cur;
-    cur = nxt;
-    nxt = t;
-    if (p.eps_stop > 0.0) {
-      NLOS_TRY(read_scalars(s, st));
-      if (s->h_sc->stop || s->h_sc->status != NLOS_OK) break;
-    }
+  { KTimer kt_(P, KC_PRE, st);
+  k_pre2<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->ub, s->tb, s->lam, s->lam2, s->lam3, s->ph, s->pht, j.tau0,
+                                                     colpos, s->reg, s->regt, g, vi, c, V);
   }
-  return finish(P, s, u_out, tau_out, stats, st);
+  NLOS_LAUNCH_CHECK("k_pre2");
+  Lin3 r{{s->cache[j.cur], s->cache[j.prev], s->tb}, {0.f, 0.f, 0.f}, s->sc};
+  NLOS_TRY(launch_tfwd_rtt(P, r, full, P.d_S, full, st));
+  NLOS_TRY(launch_conv(P, P.d_S, false, P.d_S, false, true, st));
+  const bool host_check = j.L_host < 1.5 * j.norm2;
+  UStepArgs ua{s->reg, p.mu1, false, s->tb, p.eta, p.max_backtracks, s->cache[j.nxt], s->cache[j.cur],
+               s->cache[j.prev]};
+  NLOS_TRY(u_step(P, s, ua, host_check, &j.L_host, st));
+  { KTimer kt_(P, KC_SMALL, st);
+  k_add<<<elem_grid(V), 256, 0, st>>>(s->cache[j.nxt], s->regt, s->tmp, V);
+  }
+  NLOS_LAUNCH_CHECK("k_add");
+  NLOS_TRY(launch_sfwd(P, s->tmp, full, P.d_Sp, st));
+  NLOS_TRY(launch_sxy(P, P.d_Sp, nullptr, 1.0 + p.mu3, p.mu2, st));
+  NLOS_TRY(launch_sinv(P, P.d_Sp, full, s->tnew, nullptr, nullptr, nullptr, st));
+  { KTimer kt_(P, KC_POST, st);
+  k_post2<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->unew, s->uk, s->ub, s->tnew, s->tk, s->tb, s->lam, s->lam2,
+                                                      s->lam3, s->ph, s->pht, s->ubn, s->tbn, s->cache[j.nxt], j.tau0,
+                                                      colpos, s->sc, g, vi, c, V, s->pc);
+  }
+  NLOS_LAUNCH_CHECK("k_post2");
+  { KTimer kt_(P, KC_SMALL, st);
+  k_finalize<<<1, kSumThreads, 0, st>>>(s->sc, s->pc, kStencilBlocks, 2, p.lambda, j.restart, p.eps_stop);
+  }
+  NLOS_LAUNCH_CHECK("k_finalize");
+  swap_ptr(s->uk, s->unew);
+  swap_ptr(s->ub, s->ubn);
+  swap_ptr(s->tk, s->tnew);
+  swap_ptr(s->tb, s->tbn);
+  return NLOS_OK;
+}
+
+nlos_status job_step(JobRun& j) {
+  if (j.done) return NLOS_OK;
+  NLOS_TRY(j.p.model == 1 ? step_alg1(j) : step_alg2(j));
+  const int t = j.prev;
+  j.prev = j.cur;
+  j.cur = j.nxt;
+  j.nxt = t;
+  j.it += 1;
+  if (j.it >= j.p.iters) j.done = true;
+  if (j.p.eps_stop > 0.0 && !j.done) {
+    NLOS_TRY(read_scalars(j.s, j.st));
+    if (j.s->h_sc->stop || j.s->h_sc->status != NLOS_OK) j.done = true;
+  }
+  return NLOS_OK;
+}
+
+nlos_status job_finish(JobRun& j) {
+  SolverState* s = j.s;
+  const size_t F = s->V * sizeof(float);
+  NLOS_CUDA(cudaMemcpyAsync(j.u_out, s->uk, F, cudaMemcpyDeviceToDevice, j.st));
+  if (j.tau_out && s->model == 2) NLOS_CUDA(cudaMemcpyAsync(j.tau_out, s->tk, F, cudaMemcpyDeviceToDevice, j.st));
+  NLOS_CUDA(cudaMemcpyAsync(s->h_sc, s->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, j.st));
+  return NLOS_OK;
+}
+
+nlos_status job_collect(JobRun& j, nlos_stats* stats) {
+  fill_stats(*j.s->h_sc, stats);
+  if (j.s->h_sc->status != NLOS_OK)
+    return fail(j.s->h_sc->status, "reconstruction stopped: non-finite energy or backtracking gave up");
+  return NLOS_OK;
 }
 
 nlos_status reconstruct(Plan& P, const nlos_params& p, const float* tau0, float* u_out, float* tau_out,
                         nlos_stats* stats, cudaStream_t st) {
-  if (p.model == 1) return run_alg1(P, p, tau0, u_out, stats, st);
-  if (p.model == 2) return run_alg2(P, p, tau0, u_out, tau_out, stats, st);
-  return fail(NLOS_ERR_INVALID_ARG, "params->model must be 1 or 2");
+  if (p.model != 1 && p.model != 2) return fail(NLOS_ERR_INVALID_ARG, "params->model must be 1 or 2");
+  JobRun j;
+  j.P = &P;
+  j.p = p;
+  j.tau0 = tau0;
+  j.u_out = u_out;
+  j.tau_out = tau_out;
+  j.st = st;
+  NLOS_TRY(job_init(j));
+  while (!j.done) NLOS_TRY(job_step(j));
+  NLOS_TRY(job_finish(j));
+  NLOS_CUDA(cudaStreamSynchronize(st));
+  return job_collect(j, stats);
 }
 
 }  // namespace nlos

@@ -5,7 +5,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/nlos.h"
@@ -129,6 +131,7 @@ struct Plan {
 
   double norm2_masked = -1.0, norm2_full = -1.0;
   SolverState* solver[3] = {nullptr, nullptr, nullptr};
+  bool owns_tables = true;  // false for a per-job workspace clone (tables and H shared)
 
   // optional per-launch timing (nlos_timing_enable): event pairs recorded
   // around every kernel launch on the launch stream, harvested on read.
@@ -177,7 +180,54 @@ nlos_status reconstruct(Plan& P, const nlos_params& p, const float* tau0, float*
                         nlos_stats* stats, cudaStream_t st);
 void free_solver(SolverState* s);
 
+// Per-job workspace: a copy of `base` that shares its read-only device tables
+// and kernel spectrum but owns fresh scratch spectra and solver state, so
+// several jobs of one geometry can run concurrently (plan.cu).
+Plan* plan_clone_workspace(const Plan& base, nlos_status* status);
+void plan_release(Plan* P);
+// Bytes of device memory a workspace clone plus the solver state of `model`
+// occupy (the shared tables excluded), and of the shared tables alone.
+size_t workspace_bytes(const Plan& P, int model);
+size_t shared_table_bytes(const Plan& P);
+nlos_status create_plan_internal(const nlos_geometry* g, cudaStream_t st, Plan** out);
+
+// One reconstruction as a sequence of enqueued steps (admm.cu).
+struct JobRun {
+  Plan* P = nullptr;
+  SolverState* s = nullptr;
+  nlos_params p{};
+  const float* tau0 = nullptr;  // device, full grid
+  float* u_out = nullptr;       // device
+  float* tau_out = nullptr;     // device, nullable (model 2)
+  cudaStream_t st = nullptr;
+  double norm2 = 0.0, L0 = 0.0, L_host = 0.0;
+  int restart = 0;
+  int it = 0;
+  int cur = 0, prev = 1, nxt = 2;  // rotation of the cached A u iterates
+  bool done = false;
+};
+// Allocates the solver state on first use, computes (once per plan) the
+// operator norm with a host synchronisation, and enqueues the initial state.
+nlos_status job_init(JobRun& j);
+// Enqueues one iteration.  Needs the host only while the backtracking rule can
+// still reject (L < 1.5 ||A_D||^2) or when eps_stop > 0.
+nlos_status job_step(JobRun& j);
+bool job_async(const JobRun& j);
+// Enqueues the copies of the result and of the scalar block to the host.
+nlos_status job_finish(JobRun& j);
+// After the job's stream has completed: statistics and final status.
+nlos_status job_collect(JobRun& j, nlos_stats* stats);
+
 // Launch configuration helpers
 inline int div_up(int a, int b) { return (a + b - 1) / b; }
+
+// Raise a kernel's dynamic shared-memory limit once per (device, kernel):
+// the attribute call is not repeated on every launch (nor during a stream
+// capture once the kernel has been launched before).
+nlos_status ensure_smem_attr(const void* kernel, size_t bytes);
+template <typename K>
+inline nlos_status ensure_smem(K kernel, size_t bytes) {
+  return ensure_smem_attr(reinterpret_cast<const void*>(kernel), bytes);
+}
 
 }  // namespace nlos

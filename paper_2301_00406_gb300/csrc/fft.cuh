@@ -99,36 +99,124 @@ __device__ __forceinline__ void dft_reg(float2 (&a)[R]) {
   for (int i = 0; i < R; ++i) a[i] = t[i];
 }
 
-// Factorisation N = R1 * R2 used for each transform length.
+// Factorisation N = R1 * R2 (* R3) used for each transform length.  Lengths
+// up to 128 use two steps (the lateral passes rely on that); longer ones use
+// three balanced steps so every step keeps all threads busy with small
+// register DFTs.
 template <int N> struct FftPlan;
-template <> struct FftPlan<8>    { static constexpr int R1 = 4,  R2 = 2; };
-template <> struct FftPlan<16>   { static constexpr int R1 = 4,  R2 = 4; };
-template <> struct FftPlan<32>   { static constexpr int R1 = 8,  R2 = 4; };
-template <> struct FftPlan<64>   { static constexpr int R1 = 8,  R2 = 8; };
-template <> struct FftPlan<128>  { static constexpr int R1 = 16, R2 = 8; };
-template <> struct FftPlan<256>  { static constexpr int R1 = 16, R2 = 16; };
-template <> struct FftPlan<512>  { static constexpr int R1 = 32, R2 = 16; };
-template <> struct FftPlan<1024> { static constexpr int R1 = 32, R2 = 32; };
+template <> struct FftPlan<8>    { static constexpr int R1 = 4,  R2 = 2, R3 = 1; };
+template <> struct FftPlan<16>   { static constexpr int R1 = 4,  R2 = 4, R3 = 1; };
+template <> struct FftPlan<32>   { static constexpr int R1 = 8,  R2 = 4, R3 = 1; };
+template <> struct FftPlan<64>   { static constexpr int R1 = 8,  R2 = 8, R3 = 1; };
+template <> struct FftPlan<128>  { static constexpr int R1 = 16, R2 = 8, R3 = 1; };
+template <> struct FftPlan<256>  { static constexpr int R1 = 8,  R2 = 8, R3 = 4; };
+template <> struct FftPlan<512>  { static constexpr int R1 = 8,  R2 = 8, R3 = 8; };
+template <> struct FftPlan<1024> { static constexpr int R1 = 16, R2 = 8, R3 = 8; };
 
-// Position in the forward output of natural frequency k, and the inverse map.
+// Position in the forward output of natural frequency k, and the inverse map:
+// position k1 R2 R3 + k2 R3 + k3 holds frequency k1 + R1 (k2 + R2 k3).
 template <int N>
 __device__ __forceinline__ int fpos(int k) {
-  constexpr int R1 = FftPlan<N>::R1, R2 = FftPlan<N>::R2;
-  return (k % R1) * R2 + k / R1;
+  constexpr int R1 = FftPlan<N>::R1, R2 = FftPlan<N>::R2, R3 = FftPlan<N>::R3;
+  const int k1 = k % R1, kk = k / R1;
+  return k1 * (R2 * R3) + (kk % R2) * R3 + kk / R2;
 }
 template <int N>
 __device__ __forceinline__ int kfreq(int p) {
-  constexpr int R1 = FftPlan<N>::R1, R2 = FftPlan<N>::R2;
-  return p / R2 + R1 * (p % R2);
+  constexpr int R1 = FftPlan<N>::R1, R2 = FftPlan<N>::R2, R3 = FftPlan<N>::R3;
+  const int k1 = p / (R2 * R3), rem = p % (R2 * R3);
+  return k1 + R1 * (rem / R3 + R2 * (rem % R3));
 }
 
 // B transforms of length N (B a power of two): element n of transform b at
 // buf[b * ts + n * es].  tw[j * tws] = exp(-2 pi i j / N) for j < N.  All
 // threads of the block call it; it ends with __syncthreads().
+// Three-step version (R3 > 1): N = R1 M, M = R2 R3.
+//   step 1 (b, n23): R1-point DFT over n1 of x[n1 M + n23], twiddle w_N^(n23 k1);
+//   step 2 (b, k1, n3): R2-point DFT over n2 of y[k1 M + n2 R3 + n3],
+//          twiddle w_M^(n3 k2) = w_N^(R1 n3 k2);
+//   step 3 (b, k1, k2): R3-point DFT over the contiguous n3.
+// The inverse runs the steps backwards with conjugate twiddles.
+template <int N, bool INV>
+__device__ __forceinline__ void team_fft3(float2* buf, int B, int ts, int es, const float2* tw, int tws, int tid,
+                                          int nthr) {
+  constexpr int R1 = FftPlan<N>::R1, R2 = FftPlan<N>::R2, R3 = FftPlan<N>::R3, M = R2 * R3;
+  const int lb = __ffs(B) - 1;
+  auto step1 = [&]() {
+    for (int it = tid; it < B * M; it += nthr) {
+      const int b = it & (B - 1), n23 = it >> lb;
+      float2* p = buf + b * ts + n23 * es;
+      float2 a[R1];
+#pragma unroll
+      for (int n = 0; n < R1; ++n) a[n] = p[n * M * es];
+      if (!INV) {
+        dft_reg<R1, false>(a);
+#pragma unroll
+        for (int k = 1; k < R1; ++k) a[k] = cmul(a[k], tw[((n23 * k) & (N - 1)) * tws]);
+      } else {
+#pragma unroll
+        for (int k = 1; k < R1; ++k) a[k] = cmulc(a[k], tw[((n23 * k) & (N - 1)) * tws]);
+        dft_reg<R1, true>(a);
+      }
+#pragma unroll
+      for (int n = 0; n < R1; ++n) p[n * M * es] = a[n];
+    }
+    __syncthreads();
+  };
+  auto step2 = [&]() {
+    for (int it = tid; it < B * R1 * R3; it += nthr) {
+      const int b = it & (B - 1), r = it >> lb;
+      const int n3 = r % R3, k1 = r / R3;
+      float2* p = buf + b * ts + (k1 * M + n3) * es;
+      float2 a[R2];
+#pragma unroll
+      for (int n = 0; n < R2; ++n) a[n] = p[n * R3 * es];
+      if (!INV) {
+        dft_reg<R2, false>(a);
+#pragma unroll
+        for (int k = 1; k < R2; ++k) a[k] = cmul(a[k], tw[((R1 * n3 * k) & (N - 1)) * tws]);
+      } else {
+#pragma unroll
+        for (int k = 1; k < R2; ++k) a[k] = cmulc(a[k], tw[((R1 * n3 * k) & (N - 1)) * tws]);
+        dft_reg<R2, true>(a);
+      }
+#pragma unroll
+      for (int n = 0; n < R2; ++n) p[n * R3 * es] = a[n];
+    }
+    __syncthreads();
+  };
+  auto step3 = [&]() {
+    for (int it = tid; it < B * R1 * R2; it += nthr) {
+      const int b = it & (B - 1), r = it >> lb;
+      float2* p = buf + b * ts + r * R3 * es;
+      float2 a[R3];
+#pragma unroll
+      for (int n = 0; n < R3; ++n) a[n] = p[n * es];
+      dft_reg<R3, INV>(a);
+#pragma unroll
+      for (int n = 0; n < R3; ++n) p[n * es] = a[n];
+    }
+    __syncthreads();
+  };
+  if (!INV) {
+    step1();
+    step2();
+    step3();
+  } else {
+    step3();
+    step2();
+    step1();
+  }
+}
+
 template <int N, bool INV>
 __device__ __forceinline__ void team_fft(float2* buf, int B, int ts, int es, const float2* tw, int tws,
                                          int tid, int nthr) {
   constexpr int R1 = FftPlan<N>::R1, R2 = FftPlan<N>::R2;
+  if constexpr (FftPlan<N>::R3 > 1) {
+    team_fft3<N, INV>(buf, B, ts, es, tw, tws, tid, nthr);
+    return;
+  }
   const int lb = __ffs(B) - 1;
   if (!INV) {
     for (int it = tid; it < B * R2; it += nthr) {

@@ -48,6 +48,20 @@ KTimer::~KTimer() {
   if (on) cudaEventRecord(P.ev[2 * slot + 1], st);
 }
 
+nlos_status ensure_smem_attr(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, size_t> done[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& have = done[dev][kernel];
+  if (bytes <= have) return NLOS_OK;
+  NLOS_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  have = bytes;
+  return NLOS_OK;
+}
+
 static const double kC = 299792458.0;  // speed of light, m/s
 static const double kPi = 3.14159265358979323846;
 
@@ -135,17 +149,84 @@ static std::vector<float> lap_eigs(int n) {
   return l;
 }
 
+static void free_workspace(Plan* P) {
+  for (int m = 0; m < 3; ++m) {
+    free_solver(P->solver[m]);
+    P->solver[m] = nullptr;
+  }
+  void* ws[] = {P->d_S, P->d_S2, P->d_Sc, P->d_Sp, P->d_tmpc, P->d_partials, P->d_scal};
+  for (void* p : ws)
+    if (p) cudaFree(p);
+  for (cudaEvent_t e : P->ev) cudaEventDestroy(e);
+  P->ev.clear();
+}
+
 static void destroy_plan(Plan* P) {
   if (!P) return;
   cudaDeviceSynchronize();
-  for (int m = 0; m < 3; ++m) free_solver(P->solver[m]);
-  void* ptrs[] = {P->d_rz_i0, P->d_rz_w, P->d_rzt_start, P->d_rt_k0, P->d_rt_w, P->d_rtt_start, P->d_cols,
-                  P->d_colpos, P->d_tw2t, P->d_twt, P->d_twx, P->d_twy, P->d_lamx, P->d_lamy, P->d_lamt,
-                  P->d_H, P->d_S, P->d_S2, P->d_Sc, P->d_Sp, P->d_tmpc, P->d_partials, P->d_scal};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
-  for (cudaEvent_t e : P->ev) cudaEventDestroy(e);
+  free_workspace(P);
+  if (P->owns_tables) {
+    void* ptrs[] = {P->d_rz_i0, P->d_rz_w, P->d_rzt_start, P->d_rt_k0, P->d_rt_w, P->d_rtt_start, P->d_cols,
+                    P->d_colpos, P->d_tw2t, P->d_twt, P->d_twx, P->d_twy, P->d_lamx, P->d_lamy, P->d_lamt,
+                    P->d_H};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+  }
   delete P;
+}
+
+static nlos_status alloc_workspace(Plan* P) {
+  const size_t full = (size_t)P->nx * P->ny;
+  const size_t S = (size_t)(P->nt + 1) * full;
+  nlos_status s = dalloc(&P->d_S, S);
+  if (s == NLOS_OK) s = dalloc(&P->d_S2, S);
+  if (s == NLOS_OK) s = dalloc(&P->d_Sc, (size_t)(P->nt + 1) * P->ncols);
+  if (s == NLOS_OK) s = dalloc(&P->d_Sp, (size_t)(P->nt / 2 + 1) * full);
+  if (s == NLOS_OK) s = dalloc(&P->d_tmpc, (size_t)P->ncols * P->nt);
+  P->partial_blocks = 4096;
+  if (s == NLOS_OK) s = dalloc(&P->d_partials, (size_t)P->partial_blocks * kMaxTerms);
+  if (s == NLOS_OK) s = dalloc(&P->d_scal, 1);
+  return s;
+}
+
+Plan* plan_clone_workspace(const Plan& base, nlos_status* status) {
+  Plan* P = new Plan(base);
+  P->owns_tables = false;
+  for (int m = 0; m < 3; ++m) P->solver[m] = nullptr;
+  P->d_S = P->d_S2 = P->d_Sc = P->d_Sp = nullptr;
+  P->d_tmpc = nullptr;
+  P->d_partials = nullptr;
+  P->d_scal = nullptr;
+  P->timing = false;
+  P->ev.clear();
+  P->ev_cat.clear();
+  P->ev_used = 0;
+  nlos_status s = alloc_workspace(P);
+  if (s != NLOS_OK) {
+    destroy_plan(P);
+    *status = s;
+    return nullptr;
+  }
+  *status = NLOS_OK;
+  return P;
+}
+
+void plan_release(Plan* P) { destroy_plan(P); }
+
+size_t shared_table_bytes(const Plan& P) {
+  return sizeof(float2) * (size_t)(P.nt + 1) * (P.nx + 1) * (P.ny + 1) + 64 * (size_t)P.nt + 16 * (size_t)P.nx * P.ny;
+}
+
+size_t workspace_bytes(const Plan& P, int model) {
+  const size_t full = (size_t)P.nx * P.ny, V = full * P.nt, F = V * sizeof(float);
+  const size_t C = (size_t)P.ncols * P.nt * sizeof(float);
+  size_t b = sizeof(float2) * ((size_t)(P.nt + 1) * full * 2 + (size_t)(P.nt + 1) * P.ncols +
+                               (size_t)(P.nt / 2 + 1) * full) +
+             C + sizeof(double) * 4096 * kMaxTerms + 4096;
+  const size_t partials = 3 * sizeof(double) * kMaxTerms * 4096;
+  if (model == 1) b += 9 * F + 4 * C + partials;
+  if (model == 2) b += 21 * F + partials;
+  return b;
 }
 
 static nlos_status validate_geometry(const nlos_geometry* g) {
@@ -228,16 +309,8 @@ static nlos_status create_plan(const nlos_geometry* g, cudaStream_t st, Plan** o
   UP(d_lamy, ly);
   UP(d_lamt, lt);
 #undef UP
-  const size_t S = (size_t)(nt + 1) * full;
   if (s == NLOS_OK) s = dalloc(&P->d_H, (size_t)(nt + 1) * (nx + 1) * (ny + 1));
-  if (s == NLOS_OK) s = dalloc(&P->d_S, S);
-  if (s == NLOS_OK) s = dalloc(&P->d_S2, S);
-  if (s == NLOS_OK) s = dalloc(&P->d_Sc, (size_t)(nt + 1) * P->ncols);
-  if (s == NLOS_OK) s = dalloc(&P->d_Sp, (size_t)(nt / 2 + 1) * full);
-  if (s == NLOS_OK) s = dalloc(&P->d_tmpc, (size_t)P->ncols * nt);
-  P->partial_blocks = 4096;
-  if (s == NLOS_OK) s = dalloc(&P->d_partials, (size_t)P->partial_blocks * kMaxTerms);
-  if (s == NLOS_OK) s = dalloc(&P->d_scal, 1);
+  if (s == NLOS_OK) s = alloc_workspace(P);
   if (s != NLOS_OK) {
     destroy_plan(P);
     return s;
@@ -291,6 +364,10 @@ static nlos_status create_plan(const nlos_geometry* g, cudaStream_t st, Plan** o
   }
   *out = P;
   return NLOS_OK;
+}
+
+nlos_status create_plan_internal(const nlos_geometry* g, cudaStream_t st, Plan** out) {
+  return create_plan(g, st, out);
 }
 
 static nlos_status check_plan(nlos_plan plan) {

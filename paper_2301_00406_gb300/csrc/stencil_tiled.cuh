@@ -45,7 +45,7 @@ __device__ __forceinline__ void stage_plane(float* __restrict__ tile, int H, int
 
 // Tiled k_pre1: reg = -mu sum_d (q_d(c) - q_d(c - e_d)), q = v + Lam/mu,
 // v = shrink(grad ubar - Lam/mu, phi/mu).
-__global__ void __launch_bounds__(kTileThreads)
+__global__ void __launch_bounds__(kTileThreads, 4)
     k_pre1_tiled(const float* __restrict__ ub, const float* __restrict__ lam, const float* __restrict__ ph,
                  float* __restrict__ reg, Vox g, int xb, float mu, size_t V) {
   __shared__ float U[2][kUH * kUW];     // ubar planes x and x+1 over [y0-1, y0+TY] x [t0-1, t0+TT]
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kTileThreads)
 
 // Tiled k_post1: Lam += mu (v - grad u+), phi = phi(kappa(u+)),
 // ubar' = u+ + beta (u+ - u^k); partials 0 = sum phi |grad u+|, 1 = |v - grad u+|^2.
-__global__ void __launch_bounds__(kTileThreads)
+__global__ void __launch_bounds__(kTileThreads, 3)
     k_post1_tiled(const float* __restrict__ unew, const float* __restrict__ uk, const float* __restrict__ ub,
                   float* __restrict__ lam, float* __restrict__ ph, float* __restrict__ ubn,
                   const DevScalars* __restrict__ sc, Vox g, int xb, float mu, float a, float b, int kind, float eps2,

@@ -464,8 +464,7 @@ __global__ void __launch_bounds__(kTpassThreads)
 
 template <typename K>
 static nlos_status set_smem_tp(K kernel, size_t bytes) {
-  NLOS_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  return NLOS_OK;
+  return ensure_smem(kernel, bytes);
 }
 
 // Launch shape of a t-pass: columns per CTA (fewer when there are few

@@ -353,8 +353,7 @@ static nlos_status dispatch_n(int n, F&& f) {
 
 template <typename K>
 static nlos_status set_smem(K kernel, size_t bytes) {
-  NLOS_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  return NLOS_OK;
+  return ensure_smem(kernel, bytes);
 }
 
 nlos_status launch_conv(const Plan& P, const float2* Sin, bool in_compact, float2* Sout, bool out_compact, bool adj,

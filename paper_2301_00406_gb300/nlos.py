@@ -77,6 +77,17 @@ _SIGS = {
                                           ctypes.POINTER(Stats), _P]),
     "nlos_solve_static": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P,
                                            ctypes.c_double, ctypes.c_double, _P]),
+    "nlos_reconstruct_batch": (ctypes.c_int32, [_P, ctypes.POINTER(Params), _P, _P, _P, ctypes.c_int32,
+                                                ctypes.POINTER(Stats), _P]),
+    "nlos_server_create": (ctypes.c_int32, [ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(_P)]),
+    "nlos_submit": (ctypes.c_int32, [_P, ctypes.POINTER(Geometry), ctypes.POINTER(Params), _P, _P,
+                                     ctypes.POINTER(ctypes.c_uint64)]),
+    "nlos_poll": (ctypes.c_int32, [_P, ctypes.c_uint64, ctypes.POINTER(Stats)]),
+    "nlos_wait": (ctypes.c_int32, [_P, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(Stats)]),
+    "nlos_job_times": (ctypes.c_int32, [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double)]),
+    "nlos_server_info": (ctypes.c_int32, [_P, _P]),
+    "nlos_server_destroy": (ctypes.c_int32, [_P, ctypes.c_int32, ctypes.c_double]),
     "nlos_timing_enable": (ctypes.c_int32, [_P, ctypes.c_int32]),
     "nlos_timing_read": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32]),
 }
@@ -204,6 +215,82 @@ class Plan:
                                          ctypes.byref(st), stream)
         check(status)
         return st.as_dict()
+
+
+def reconstruct_batch(plans, params, tau0_ptrs, u_ptrs, tau_out_ptrs=None, stream=0):
+    """nlos_reconstruct_batch over lists of plans / params / device pointers; returns per-scene stats."""
+    n = len(plans)
+    hs = (_P * n)(*[p.handle for p in plans])
+    ps = (Params * n)(*params)
+    t0 = (_P * n)(*tau0_ptrs)
+    uo = (_P * n)(*u_ptrs)
+    to = (_P * n)(*tau_out_ptrs) if tau_out_ptrs is not None else None
+    st = (Stats * n)()
+    check(load().nlos_reconstruct_batch(hs, ps, t0, uo, to, n, st, stream))
+    return [s.as_dict() for s in st]
+
+
+class Server:
+    """nlos_server: asynchronous, continuously batched reconstructions from host buffers."""
+
+    INFO = ["queued", "running", "completed", "failed", "peak_running", "bytes_in_use", "bytes_peak", "budget"]
+
+    def __init__(self, hbm_budget_bytes, max_slots):
+        h = _P()
+        check(load().nlos_server_create(int(hbm_budget_bytes), int(max_slots), ctypes.byref(h)))
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, nx, ny, nt, bin_width_s, params, tau0, u_out, wall_width_m=1.0, radiometry="compensated",
+               mask=None):
+        """tau0: float32 C-contiguous numpy array (copied at submit); u_out: float32 numpy array written when done."""
+        g, keep = _geometry(nx, ny, nt, bin_width_s, wall_width_m, radiometry, mask)
+        tau0 = np.ascontiguousarray(tau0, dtype=np.float32)
+        assert u_out.dtype == np.float32 and u_out.flags["C_CONTIGUOUS"] and u_out.size == tau0.size
+        jid = ctypes.c_uint64()
+        check(load().nlos_submit(self.handle, ctypes.byref(g), ctypes.byref(params), tau0.ctypes.data,
+                                 u_out.ctypes.data, ctypes.byref(jid)))
+        self._keep[jid.value] = u_out   # the caller's buffer must outlive the job
+        return jid.value
+
+    def poll(self, job_id):
+        st = Stats()
+        s = load().nlos_poll(self.handle, job_id, ctypes.byref(st))
+        if s == -5:
+            return None
+        check(s)
+        return st.as_dict()
+
+    def wait(self, job_id, timeout_s=60.0):
+        st = Stats()
+        s = load().nlos_wait(self.handle, job_id, timeout_s, ctypes.byref(st))
+        if s == -5:
+            return None
+        check(s)
+        self._keep.pop(job_id, None)
+        return st.as_dict()
+
+    def job_times(self, job_id):
+        q, t = ctypes.c_double(), ctypes.c_double()
+        check(load().nlos_job_times(self.handle, job_id, ctypes.byref(q), ctypes.byref(t)))
+        return q.value, t.value
+
+    def info(self):
+        out = np.zeros(8, np.int64)
+        check(load().nlos_server_info(self.handle, out.ctypes.data))
+        return dict(zip(self.INFO, out.tolist()))
+
+    def close(self, cancel_pending=False, timeout_s=120.0):
+        if getattr(self, "handle", None):
+            s = load().nlos_server_destroy(self.handle, int(cancel_pending), timeout_s)
+            self.handle = None
+            check(s)
+
+    def __del__(self):
+        try:
+            self.close(cancel_pending=True, timeout_s=10.0)
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------------------
