@@ -44,6 +44,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ops", action="store_true",
                     help="only apply the forward and adjoint operators --steps times (for profiler captures)")
+    ap.add_argument("--workload", default="headline", choices=["headline", "batch16", "serve"],
+                    help="headline: one 128x128x512 scene; batch16: 16 mixed scenes batched vs one by one; "
+                         "serve: Poisson-arrival stream through the server")
+    ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
+    ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrivals per second")
+    ap.add_argument("--budget-gb", type=float, default=0.0, help="serve: HBM budget (0 = 80 percent of free)")
     return ap.parse_args()
 
 
@@ -372,8 +378,147 @@ def run_ops(args):
     return {"ops": args.steps, "checksum": float(u.double().sum().item())}
 
 
+# ---------------------------------------------------------------------------
+# batching (16 mixed scenes) and serving (Poisson arrivals)
+# ---------------------------------------------------------------------------
+BATCH16 = [(32, 256, 32e-12)] * 6 + [(64, 512, 16e-12)] * 6 + [(128, 512, 16e-12)] * 4
+
+
+def _scene_inputs(nlos, n, nt, bw, mask, seed, model):
+    import torch
+    plan = nlos.Plan(n, n, nt, bw, mask=mask)
+    vol = synth.scene_patches(n, n, nt, seed) if model == 2 else synth.scene_planes_glyph(n, n, nt, seed)
+    sig = nlos.forward_t(plan, torch.tensor(vol, dtype=torch.float32, device="cuda"), apply_mask=True).cpu().numpy()
+    tau0 = synth.poisson_measurement(sig, mask, 50.0, 2.0, seed + 1000).astype(np.float32)
+    return plan, tau0
+
+
+def _params(nlos, model, iters):
+    cfg = synth.CONFIGS["headline_128x128x512"]
+    p = nlos.params_default(model)
+    if model == 1:
+        p.a, p.b, p.mu = cfg["a"], cfg["b"], cfg["mu"]
+    p.iters = iters
+    return p
+
+
+def run_batch16(args):
+    """16 scenes of mixed size, random 25 % masks, models alternating, 50 iterations:
+    one nlos_reconstruct_batch call vs 16 nlos_reconstruct calls in sequence."""
+    import torch
+    from paper_2301_00406_gb300 import nlos
+    iters = 50
+    plans, params, taus, outs = [], [], [], []
+    for i, (n, nt, bw) in enumerate(BATCH16):
+        model = 1 if i % 2 == 0 else 2
+        mask = synth.random_mask(n, n, 0.25, 500 + i)
+        plan, tau0 = _scene_inputs(nlos, n, nt, bw, mask, i, model)
+        plans.append(plan)
+        params.append(_params(nlos, model, iters))
+        taus.append(torch.tensor(tau0, device="cuda"))
+        outs.append(torch.empty_like(taus[-1]))
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def sequential():
+        for pl, pa, t, o in zip(plans, params, taus, outs):
+            pl.reconstruct(pa, t.data_ptr(), o.data_ptr(), 0, stream)
+
+    def batched():
+        nlos.reconstruct_batch(plans, params, [t.data_ptr() for t in taus], [o.data_ptr() for o in outs],
+                               stream=stream)
+
+    for f in (sequential, batched):        # warm-up (plans compute their norms here)
+        f()
+    torch.cuda.synchronize()
+    times = {}
+    for name, f in (("sequential", sequential), ("batched", batched)):
+        reps = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            f()
+            torch.cuda.synchronize()
+            reps.append(time.perf_counter() - t0)
+        times[name] = statistics.median(reps)
+    seq = [o.clone() for o in outs]
+    batched()
+    torch.cuda.synchronize()
+    same = all(torch.equal(a, b) for a, b in zip(seq, outs))
+    total_iters = iters * len(BATCH16)
+    return {"metric": "batched reconstructions/s (16 mixed scenes, 50 iterations each)",
+            "value": round(len(BATCH16) / times["batched"], 3), "unit": "recon/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch16_mixed", "scenes": "6x 32x32x256, 6x 64x64x512, 4x 128x128x512",
+                       "masks": "random 25 %", "models": "alternating 1/2", "iters": iters},
+            "batched_s": round(times["batched"], 4), "sequential_s": round(times["sequential"], 4),
+            "speedup_vs_sequential": round(times["sequential"] / times["batched"], 3),
+            "batched_iter_per_s": round(total_iters / times["batched"], 1),
+            "results_identical_to_sequential": bool(same)}
+
+
+def run_serve(args):
+    """Poisson arrivals (mean --rate per second) for --duration seconds through nlos_server."""
+    import torch
+    from paper_2301_00406_gb300 import nlos
+    rng = np.random.default_rng(7)
+    grids = [(64, 512, 16e-12), (128, 512, 16e-12)]
+    samplings = [8, 16, 32]          # sampled points per side
+    pool = {}
+    for n, nt, bw in grids:          # a few seeded measurements per (grid, sampling, model)
+        for side in samplings:
+            mask = synth.stride_mask(n, n, n // side)
+            for model in (1, 2):
+                plan, tau0 = _scene_inputs(nlos, n, nt, bw, mask, len(pool), model)
+                plan.close()
+                pool[(n, nt, bw, side, model)] = (mask, tau0)
+    free, total = torch.cuda.mem_get_info()
+    budget = int(args.budget_gb * (1 << 30)) if args.budget_gb > 0 else int(0.8 * free)
+    srv = nlos.Server(hbm_budget_bytes=budget, max_slots=64)
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=int(args.rate * args.duration * 2)))
+    arrivals = arrivals[arrivals < args.duration]
+    keys = list(pool.keys())
+    choice = rng.integers(0, len(keys), size=len(arrivals))
+    jobs = []
+    t_start = time.perf_counter()
+    for t_arr, ci in zip(arrivals, choice):
+        while time.perf_counter() - t_start < t_arr:
+            time.sleep(0.0005)
+        n, nt, bw, side, model = keys[ci]
+        mask, tau0 = pool[keys[ci]]
+        out = np.empty_like(tau0)
+        jid = srv.submit(n, n, nt, bw, _params(nlos, model, 50), tau0, out, mask=mask)
+        jobs.append((jid, out, keys[ci]))
+    lat, queued = [], []
+    for jid, _, _ in jobs:
+        st = srv.wait(jid, timeout_s=600.0)
+        assert st is not None and st["status"] == 0
+        q, tot = srv.job_times(jid)
+        lat.append(tot)
+        queued.append(q)
+    t_end = time.perf_counter()
+    info = srv.info()
+    srv.close()
+    lat = np.array(lat)
+    return {"metric": "served reconstruction latency p50/p99 (Poisson arrivals)",
+            "value": round(float(np.percentile(lat, 50)), 4), "unit": "s", "higher_is_better": False,
+            "p50_s": round(float(np.percentile(lat, 50)), 4), "p99_s": round(float(np.percentile(lat, 99)), 4),
+            "mean_queue_s": round(float(np.mean(queued)), 4), "jobs": len(jobs),
+            "throughput_jobs_per_s": round(len(jobs) / (t_end - t_start), 3),
+            "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serve_poisson", "rate_per_s": args.rate, "duration_s": args.duration,
+                       "grids": "64x64x512, 128x128x512 (16 ps)", "sampling": "8x8, 16x16, 32x32 strides",
+                       "models": "1 or 2 at random", "iters": 50, "budget_bytes": budget},
+            "server": info}
+
+
 def main():
     args = parse()
+    if args.workload == "batch16":
+        print(json.dumps(run_batch16(args)))
+        return
+    if args.workload == "serve":
+        print(json.dumps(run_serve(args)))
+        return
     if args.ops:
         print(json.dumps(run_ops(args)))
         return
