@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrivals per second")
     ap.add_argument("--budget-gb", type=float, default=0.0, help="serve: HBM budget (0 = 80 percent of free)")
+    ap.add_argument("--slots", type=int, default=8, help="serve: jobs running at once")
     return ap.parse_args()
 
 
@@ -473,7 +474,7 @@ def run_serve(args):
                 pool[(n, nt, bw, side, model)] = (mask, tau0)
     free, total = torch.cuda.mem_get_info()
     budget = int(args.budget_gb * (1 << 30)) if args.budget_gb > 0 else int(0.8 * free)
-    srv = nlos.Server(hbm_budget_bytes=budget, max_slots=64)
+    srv = nlos.Server(hbm_budget_bytes=budget, max_slots=args.slots)
     arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=int(args.rate * args.duration * 2)))
     arrivals = arrivals[arrivals < args.duration]
     keys = list(pool.keys())
@@ -507,7 +508,7 @@ def run_serve(args):
             "n_gpus": 1, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "serve_poisson", "rate_per_s": args.rate, "duration_s": args.duration,
                        "grids": "64x64x512, 128x128x512 (16 ps)", "sampling": "8x8, 16x16, 32x32 strides",
-                       "models": "1 or 2 at random", "iters": 50, "budget_bytes": budget},
+                       "models": "1 or 2 at random", "iters": 50, "budget_bytes": budget, "slots": args.slots},
             "server": info}
 
 

@@ -301,6 +301,28 @@ __global__ void __launch_bounds__(kStencilThreads)
   block_reduce_to<7>(acc, partials);
 }
 
+// Algorithm 2, elementwise part of the post step: Lambda_3 += mu3 (f - tau+),
+// partials 0 = (A u+ - tau+)^2, 1 = M (tau+ - tau0)^2, 2 = (f - tau+)^2.
+__global__ void __launch_bounds__(kStencilThreads)
+    k_lam3(const float* __restrict__ tnew, const float* __restrict__ tb, const float* __restrict__ au,
+           const float* __restrict__ tau0, float* __restrict__ lam3, const int32_t* __restrict__ colpos, Vox g,
+           VoxIter vi, float lam_w, float mu3, size_t V, double* __restrict__ partials) {
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V; i += (size_t)gridDim.x * blockDim.x) {
+    int x, y, t;
+    vi.decode(i, g, x, y, t);
+    const float m = colpos ? (__ldg(colpos + x * g.ny + y) >= 0 ? 1.0f : 0.0f) : 1.0f;
+    const float t0 = __ldg(tau0 + i), tn = __ldg(tnew + i), l3 = lam3[i];
+    const float f = (lam_w * m * t0 + mu3 * __ldg(tb + i) - l3) / (lam_w * m + mu3);
+    lam3[i] = l3 + mu3 * (f - tn);
+    const float r = __ldg(au + i) - tn, sres = m * (tn - t0), fr = f - tn;
+    acc[0] += (double)r * r;
+    acc[1] += (double)sres * sres;
+    acc[2] += (double)fr * fr;
+  }
+  block_reduce_to<3>(acc, partials);
+}
+
 // rhs of the tau-solve: x = A u+ + regt (used as the input of the periodic FFT)
 __global__ void k_add(const float* __restrict__ a, const float* __restrict__ b, float* __restrict__ o, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -374,6 +396,38 @@ __global__ void __launch_bounds__(kSumThreads)
   sc->e = e;
   sc->E_prev = E;
   sc->primal_res = sqrt(pres2);
+  sc->iter += 1;
+  if (eps_stop > 0.0 && e <= eps_stop) sc->stop = 1;
+}
+
+// End of an Algorithm-2 iteration from the partials of the split post step
+// (u: phi|grad u|, |v - grad u|^2; tau: phi|grad tau|, |w - grad tau|^2;
+// elementwise: (A u - tau)^2, M (tau - tau0)^2, (f - tau)^2).
+__global__ void __launch_bounds__(kSumThreads)
+    k_finalize2(DevScalars* sc, const double* __restrict__ pu, int nbu, const double* __restrict__ pt, int nbt,
+                const double* __restrict__ p3, int nb3, double lam_w, int restart, double eps_stop) {
+  const int t01[2] = {0, 1};
+  const int t012[3] = {0, 1, 2};
+  double u[2], t[2], e3[3];
+  sum_partials_block<2>(pu, nbu, t01, u);
+  sum_partials_block<2>(pt, nbt, t01, t);
+  sum_partials_block<3>(p3, nb3, t012, e3);
+  if (threadIdx.x != 0) return;
+  if (sc->status != NLOS_OK) return;
+  const double fit = 0.5 * e3[0];
+  const double E = fit + 0.5 * lam_w * e3[1] + u[0] + t[0];
+  sc->f_fit = fit;
+  const double e = E != 0.0 ? fabs(sc->E_prev - E) / fabs(E) : 0.0;
+  if (!isfinite(E)) sc->status = NLOS_ERR_DIVERGED;
+  if (restart && E > sc->E_prev) {
+    sc->t = 1.0;
+    sc->restarts += 1;
+  }
+  sc->beta_prev = sc->beta;
+  sc->E = E;
+  sc->e = e;
+  sc->E_prev = E;
+  sc->primal_res = sqrt(u[1]);
   sc->iter += 1;
   if (eps_stop > 0.0 && e <= eps_stop) sc->stop = 1;
 }
@@ -626,6 +680,13 @@ static void swap_ptr(T*& a, T*& b) {
   b = t;
 }
 
+nlos_status prepare_stencils() {
+  NLOS_TRY(ensure_smem(k_pre1_pipe<false>, kPre1PipeSmem));
+  NLOS_TRY(ensure_smem(k_pre1_pipe<true>, kPre1PipeSmem));
+  NLOS_TRY(ensure_smem(k_post1_pipe, kPost1PipeSmem));
+  return NLOS_OK;
+}
+
 // One linearised u-step with the backtracking loop (shared by both
 // algorithms): the adjoint end + solve rhs (the adjoint spectrum is in d_S),
 // the lateral solve, the periodic inverse (u+ and ||u+ - ubar||^2), the
@@ -759,14 +820,16 @@ static nlos_status step_alg1(JobRun& j) {
   const Vox g = make_vox(P.nx, P.ny, P.nt);
   const VoxIter vi{ilog2i(P.nt), ilog2i(P.ny)};
   const float eps2 = (float)(p.eps_normal * p.eps_normal);
-  // halo-tiled stencils when the grid tiles evenly (TT = 128 along t, 8 rows in y)
-  const bool tiled = P.nt % kTT == 0 && P.ny % kTY == 0;
-  const int xb = std::min(16, P.nx);
-  const dim3 tgrid((P.nt / kTT) * (P.ny / kTY), P.nx / xb);
-  const int post_blocks = tiled ? (int)(tgrid.x * tgrid.y) : kStencilBlocks;
+  // pipelined halo-tiled stencils when the grid tiles evenly (TT = 128 along
+  // t, 8 rows in y, 4 planes in x); the plain per-voxel kernels otherwise
+  const bool tiled = P.nt % kTT == 0 && P.ny % kTY == 0 && P.nx % kPipeXB == 0;
+  const int ntiles = (P.nt / kTT) * (P.ny / kTY) * (P.nx / kPipeXB);
+  const int pre_grid = std::min(ntiles, 152 * 3), post_grid = std::min(ntiles, 152 * 2);
+  const int post_blocks = tiled ? post_grid : kStencilBlocks;
   { KTimer kt_(P, KC_PRE, st);
   if (tiled)
-    k_pre1_tiled<<<tgrid, kTileThreads, 0, st>>>(s->ub, s->lam, s->ph, s->reg, g, xb, (float)p.mu, V);
+    k_pre1_pipe<false><<<pre_grid, kTileThreads, kPre1PipeSmem, st>>>(s->ub, s->lam, s->ph, s->reg, g, ntiles,
+                                                                      (float)p.mu, V, FTerm{});
   else
     k_pre1<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->ub, s->lam, s->ph, s->reg, g, vi, (float)p.mu, V);
   }
@@ -780,8 +843,9 @@ static nlos_status step_alg1(JobRun& j) {
   NLOS_TRY(u_step(P, s, ua, host_check, &j.L_host, st));
   { KTimer kt_(P, KC_POST, st);
   if (tiled)
-    k_post1_tiled<<<tgrid, kTileThreads, 0, st>>>(s->unew, s->uk, s->ub, s->lam, s->ph, s->ubn, s->sc, g, xb,
-                                                  (float)p.mu, (float)p.a, (float)p.b, p.phi, eps2, V, s->pc);
+    k_post1_pipe<<<post_grid, kTileThreads, kPost1PipeSmem, st>>>(s->unew, s->uk, s->ub, s->lam, s->ph, s->ubn,
+                                                                  s->sc, g, ntiles, (float)p.mu, (float)p.a,
+                                                                  (float)p.b, p.phi, eps2, V, s->pc);
   else
     k_post1<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->unew, s->uk, s->ub, s->lam, s->ph, s->ubn, s->sc, g, vi,
                                                         (float)p.mu, (float)p.a, (float)p.b, p.phi, eps2, V, s->pc);
@@ -808,9 +872,20 @@ static nlos_status step_alg2(JobRun& j) {
   const int32_t* colpos = P.full_mask ? nullptr : P.d_colpos;
   Alg2Coef c{(float)p.mu1, (float)p.mu2, (float)p.mu3, (float)p.lambda, (float)p.a_u, (float)p.b_u,
              (float)p.a_tau, (float)p.b_tau, p.phi, (float)(p.eps_normal * p.eps_normal)};
+  const bool tiled = P.nt % kTT == 0 && P.ny % kTY == 0 && P.nx % kPipeXB == 0;
+  const int ntiles = (P.nt / kTT) * (P.ny / kTY) * (P.nx / kPipeXB);
+  const int pre_grid = std::min(ntiles, 152 * 3), post_grid = std::min(ntiles, 152 * 2);
   { KTimer kt_(P, KC_PRE, st);
-  k_pre2<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->ub, s->tb, s->lam, s->lam2, s->lam3, s->ph, s->pht, j.tau0,
-                                                     colpos, s->reg, s->regt, g, vi, c, V);
+  if (tiled) {
+    k_pre1_pipe<false><<<pre_grid, kTileThreads, kPre1PipeSmem, st>>>(s->ub, s->lam, s->ph, s->reg, g, ntiles,
+                                                                      (float)p.mu1, V, FTerm{});
+    const FTerm ft{j.tau0, s->lam3, colpos, (float)p.lambda, (float)p.mu3};
+    k_pre1_pipe<true><<<pre_grid, kTileThreads, kPre1PipeSmem, st>>>(s->tb, s->lam2, s->pht, s->regt, g, ntiles,
+                                                                     (float)p.mu2, V, ft);
+  } else {
+    k_pre2<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->ub, s->tb, s->lam, s->lam2, s->lam3, s->ph, s->pht,
+                                                       j.tau0, colpos, s->reg, s->regt, g, vi, c, V);
+  }
   }
   NLOS_LAUNCH_CHECK("k_pre2");
   Lin3 r{{s->cache[j.cur], s->cache[j.prev], s->tb}, {0.f, 0.f, 0.f}, s->sc};
@@ -827,16 +902,37 @@ static nlos_status step_alg2(JobRun& j) {
   NLOS_TRY(launch_sfwd(P, s->tmp, full, P.d_Sp, st));
   NLOS_TRY(launch_sxy(P, P.d_Sp, nullptr, 1.0 + p.mu3, p.mu2, st));
   NLOS_TRY(launch_sinv(P, P.d_Sp, full, s->tnew, nullptr, nullptr, nullptr, st));
-  { KTimer kt_(P, KC_POST, st);
-  k_post2<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->unew, s->uk, s->ub, s->tnew, s->tk, s->tb, s->lam, s->lam2,
-                                                      s->lam3, s->ph, s->pht, s->ubn, s->tbn, s->cache[j.nxt], j.tau0,
-                                                      colpos, s->sc, g, vi, c, V, s->pc);
+  if (tiled) {
+    // u and tau halves of the post step, then the elementwise Lambda_3 part;
+    // the u-step partial buffers (pa, pb) are free again at this point
+    { KTimer kt_(P, KC_POST, st);
+    k_lam3<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->tnew, s->tb, s->cache[j.nxt], j.tau0, s->lam3, colpos, g,
+                                                       vi, (float)p.lambda, (float)p.mu3, V, s->pb);
+    k_post1_pipe<<<post_grid, kTileThreads, kPost1PipeSmem, st>>>(s->unew, s->uk, s->ub, s->lam, s->ph, s->ubn,
+                                                                  s->sc, g, ntiles, (float)p.mu1, (float)p.a_u,
+                                                                  (float)p.b_u, p.phi, c.eps2, V, s->pc);
+    k_post1_pipe<<<post_grid, kTileThreads, kPost1PipeSmem, st>>>(s->tnew, s->tk, s->tb, s->lam2, s->pht, s->tbn,
+                                                                  s->sc, g, ntiles, (float)p.mu2, (float)p.a_tau,
+                                                                  (float)p.b_tau, p.phi, c.eps2, V, s->pa);
+    }
+    NLOS_LAUNCH_CHECK("k_post2");
+    { KTimer kt_(P, KC_SMALL, st);
+    k_finalize2<<<1, kSumThreads, 0, st>>>(s->sc, s->pc, post_grid, s->pa, post_grid, s->pb, kStencilBlocks,
+                                           p.lambda, j.restart, p.eps_stop);
+    }
+    NLOS_LAUNCH_CHECK("k_finalize2");
+  } else {
+    { KTimer kt_(P, KC_POST, st);
+    k_post2<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->unew, s->uk, s->ub, s->tnew, s->tk, s->tb, s->lam,
+                                                        s->lam2, s->lam3, s->ph, s->pht, s->ubn, s->tbn,
+                                                        s->cache[j.nxt], j.tau0, colpos, s->sc, g, vi, c, V, s->pc);
+    }
+    NLOS_LAUNCH_CHECK("k_post2");
+    { KTimer kt_(P, KC_SMALL, st);
+    k_finalize<<<1, kSumThreads, 0, st>>>(s->sc, s->pc, kStencilBlocks, 2, p.lambda, j.restart, p.eps_stop);
+    }
+    NLOS_LAUNCH_CHECK("k_finalize");
   }
-  NLOS_LAUNCH_CHECK("k_post2");
-  { KTimer kt_(P, KC_SMALL, st);
-  k_finalize<<<1, kSumThreads, 0, st>>>(s->sc, s->pc, kStencilBlocks, 2, p.lambda, j.restart, p.eps_stop);
-  }
-  NLOS_LAUNCH_CHECK("k_finalize");
   swap_ptr(s->uk, s->unew);
   swap_ptr(s->ub, s->ubn);
   swap_ptr(s->tk, s->tnew);
@@ -876,6 +972,59 @@ nlos_status job_collect(JobRun& j, nlos_stats* stats) {
   return NLOS_OK;
 }
 
+void free_graphs(Plan* P) {
+  for (auto& g : P->graphs) cudaGraphExecDestroy(g.exec);
+  P->graphs.clear();
+  if (P->capture_stream) cudaStreamDestroy(P->capture_stream);
+  P->capture_stream = nullptr;
+}
+
+nlos_status job_enqueue_graph(JobRun& j, cudaStream_t launch, bool* used) {
+  *used = false;
+  Plan& P = *j.P;
+  const nlos_params& p = j.p;
+  if (P.timing) return NLOS_OK;
+  // everything that may synchronise happens before the capture
+  NLOS_TRY(get_solver(P, p.model, &j.s));
+  NLOS_TRY(plan_norm2(P, p.model == 1, launch, &j.norm2));
+  const double L0 = p.L0 > 0.0 ? p.L0 : 2.0 * j.norm2;
+  if (p.eps_stop > 0.0 || L0 < 1.5 * j.norm2 || p.iters <= 0) return NLOS_OK;
+  for (auto& g : P.graphs)
+    if (std::memcmp(&g.p, &p, sizeof(nlos_params)) == 0 && g.tau0 == j.tau0 && g.u_out == j.u_out &&
+        g.tau_out == j.tau_out) {
+      NLOS_CUDA(cudaGraphLaunch(g.exec, launch));
+      *used = true;
+      return NLOS_OK;
+    }
+  if (!P.capture_stream) NLOS_CUDA(cudaStreamCreateWithFlags(&P.capture_stream, cudaStreamNonBlocking));
+  JobRun c = j;
+  c.st = P.capture_stream;
+  NLOS_CUDA(cudaStreamBeginCapture(c.st, cudaStreamCaptureModeThreadLocal));
+  nlos_status s = job_init(c);
+  while (s == NLOS_OK && !c.done) s = job_step(c);
+  if (s == NLOS_OK) s = job_finish(c);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c.st, &graph);
+  if (s != NLOS_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  if (P.graphs.size() >= 4) {
+    cudaGraphExecDestroy(P.graphs.front().exec);
+    P.graphs.erase(P.graphs.begin());
+  }
+  P.graphs.push_back(Plan::GraphEntry{p, j.tau0, j.u_out, j.tau_out, exec});
+  NLOS_CUDA(cudaGraphLaunch(exec, launch));
+  j.s = c.s;
+  *used = true;
+  return NLOS_OK;
+}
+
 nlos_status reconstruct(Plan& P, const nlos_params& p, const float* tau0, float* u_out, float* tau_out,
                         nlos_stats* stats, cudaStream_t st) {
   if (p.model != 1 && p.model != 2) return fail(NLOS_ERR_INVALID_ARG, "params->model must be 1 or 2");
@@ -886,9 +1035,13 @@ nlos_status reconstruct(Plan& P, const nlos_params& p, const float* tau0, float*
   j.u_out = u_out;
   j.tau_out = tau_out;
   j.st = st;
-  NLOS_TRY(job_init(j));
-  while (!j.done) NLOS_TRY(job_step(j));
-  NLOS_TRY(job_finish(j));
+  bool graphed = false;
+  NLOS_TRY(job_enqueue_graph(j, st, &graphed));
+  if (!graphed) {
+    NLOS_TRY(job_init(j));
+    while (!j.done) NLOS_TRY(job_step(j));
+    NLOS_TRY(job_finish(j));
+  }
   NLOS_CUDA(cudaStreamSynchronize(st));
   return job_collect(j, stats);
 }

@@ -118,6 +118,15 @@ struct Plan {
   float* d_lamy = nullptr;       // [ny]
   float* d_lamt = nullptr;       // [nt]
   float2* d_H = nullptr;         // [(nt+1)][(nx+1)][(ny+1)] cone-kernel spectrum
+  // device forms of the resampling, weights pre-multiplied (FP64 -> float):
+  // forward taps {w0*g, w1*g, i0 (int bits), 0} per output bin, and the
+  // transposes as CSR rows of {weight, input index (int bits)}
+  float4* d_rz_f4 = nullptr;     // [nt]  R_z
+  float4* d_rt_f4 = nullptr;     // [nt]  R_t^{-1}
+  int32_t* d_rzT_ptr = nullptr;  // [nt+1]
+  float2* d_rzT_ent = nullptr;   // [<= 2 nt]
+  int32_t* d_rtT_ptr = nullptr;  // [nt+1]
+  float2* d_rtT_ent = nullptr;   // [<= 2 nt]
 
   // scratch owned by the plan
   float2* d_S = nullptr;         // [(nt+1)][nx][ny] padded t-spectrum (adjoint side)
@@ -132,6 +141,18 @@ struct Plan {
   double norm2_masked = -1.0, norm2_full = -1.0;
   SolverState* solver[3] = {nullptr, nullptr, nullptr};
   bool owns_tables = true;  // false for a per-job workspace clone (tables and H shared)
+
+  // CUDA graphs of whole reconstructions (init, iterations, finish), keyed by
+  // the parameters and the caller's buffers; replayed with one launch.
+  struct GraphEntry {
+    nlos_params p;
+    const float* tau0;
+    float* u_out;
+    float* tau_out;
+    cudaGraphExec_t exec;
+  };
+  std::vector<GraphEntry> graphs;
+  cudaStream_t capture_stream = nullptr;
 
   // optional per-launch timing (nlos_timing_enable): event pairs recorded
   // around every kernel launch on the launch stream, harvested on read.
@@ -190,6 +211,8 @@ void plan_release(Plan* P);
 size_t workspace_bytes(const Plan& P, int model);
 size_t shared_table_bytes(const Plan& P);
 nlos_status create_plan_internal(const nlos_geometry* g, cudaStream_t st, Plan** out);
+// Pre-set the shared-memory limits of the stencil kernels (admm.cu).
+nlos_status prepare_stencils();
 
 // One reconstruction as a sequence of enqueued steps (admm.cu).
 struct JobRun {
@@ -217,6 +240,13 @@ bool job_async(const JobRun& j);
 nlos_status job_finish(JobRun& j);
 // After the job's stream has completed: statistics and final status.
 nlos_status job_collect(JobRun& j, nlos_stats* stats);
+// Enqueue the whole reconstruction of j on `launch` as one CUDA-graph launch
+// (captured on first use for these parameters and buffers, then cached in the
+// plan).  Sets *used = false, enqueuing nothing, when the run needs host
+// decisions (backtracking that can reject, relative-energy stop) or the
+// plan's kernels are being timed.
+nlos_status job_enqueue_graph(JobRun& j, cudaStream_t launch, bool* used);
+void free_graphs(Plan* P);
 
 // Launch configuration helpers
 inline int div_up(int a, int b) { return (a + b - 1) / b; }

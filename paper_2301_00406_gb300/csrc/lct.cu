@@ -1,5 +1,5 @@
 // Runtime dispatch of the t-pass launchers to their per-size instances
-// (tpass_*.cu) and the shared-memory size query.
+// (tpass_*.cu).
 #include <type_traits>
 
 #include "tpass.cuh"
@@ -14,13 +14,6 @@ extern template struct TpassOps<256>;
 extern template struct TpassOps<512>;
 extern template struct TpassOps<1024>;
 
-size_t tpass_smem_bytes(int nt, int variant) {
-  const int cols = nt >= 1024 ? 8 : 16;
-  size_t b = sizeof(float2) * (2 * nt + (cols / 2) * (nt + 1)) + sizeof(float) * cols * nt;
-  if (variant == 1) b += sizeof(float) * cols * nt;  // adjoint end keeps g separately
-  return b;
-}
-
 #define NLOS_DISPATCH_NT(nt, call)                                  \
   switch (nt) {                                                      \
     case 16: return TpassOps<16>::call;                              \
@@ -32,6 +25,8 @@ size_t tpass_smem_bytes(int nt, int variant) {
     case 1024: return TpassOps<1024>::call;                          \
   }                                                                  \
   return fail(NLOS_ERR_INVALID_ARG, "unsupported nt")
+
+nlos_status prepare_tpass(int nt) { NLOS_DISPATCH_NT(nt, prepare()); }
 
 nlos_status launch_tfwd_rz(const Plan& P, const float* u, int ncols, float2* S, int pitch, cudaStream_t st) {
   NLOS_DISPATCH_NT(P.nt, tfwd_rz(P, u, ncols, S, pitch, st));

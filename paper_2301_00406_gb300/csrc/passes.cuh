@@ -64,7 +64,8 @@ nlos_status launch_sxy(const Plan& P, float2* Sp, const DevScalars* sc, double c
 // Cone-kernel spectrum of the plan (plan time).
 nlos_status launch_kernel_spectrum(const Plan& P, const int32_t* m0, const float2* hw, cudaStream_t st);
 
-// Shared-memory sizes (for attribute setup).
-size_t tpass_smem_bytes(int nt, int variant);
+// Pre-set the shared-memory attributes of every kernel for these sizes.
+nlos_status prepare_tpass(int nt);
+nlos_status prepare_xy(int n);
 
 }  // namespace nlos

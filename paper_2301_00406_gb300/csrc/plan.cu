@@ -103,6 +103,36 @@ static void build_tables(Plan& P) {
   }
 }
 
+// Device forms of a two-tap resampling out_k = s_k (w0_k in[i0_k] + w1_k in[i0_k + 1]):
+// forward taps with pre-multiplied weights, and the transpose as CSR rows.
+static void device_taps(const std::vector<int32_t>& i0, const std::vector<float>& w3, int n,
+                        std::vector<float4>* fwd, std::vector<int32_t>* ptr, std::vector<float2>* ent) {
+  fwd->resize(n);
+  std::vector<std::vector<std::pair<int, double>>> rows(n);
+  for (int k = 0; k < n; ++k) {
+    const double a = (double)w3[3 * k] * w3[3 * k + 2], b = (double)w3[3 * k + 1] * w3[3 * k + 2];
+    int32_t bits;
+    std::memcpy(&bits, &i0[k], sizeof(bits));
+    float fb;
+    std::memcpy(&fb, &bits, sizeof(fb));
+    (*fwd)[k] = make_float4((float)a, (float)b, fb, 0.f);
+    if (a != 0.0) rows[i0[k]].push_back({k, a});
+    if (b != 0.0) rows[i0[k] + 1].push_back({k, b});
+  }
+  ptr->assign(n + 1, 0);
+  ent->clear();
+  for (int i = 0; i < n; ++i) {
+    (*ptr)[i] = (int32_t)ent->size();
+    for (auto& e : rows[i]) {
+      float fi;
+      int32_t idx = e.first;
+      std::memcpy(&fi, &idx, sizeof(fi));
+      ent->push_back(make_float2((float)e.second, fi));
+    }
+  }
+  (*ptr)[n] = (int32_t)ent->size();
+}
+
 // start[i] = first index j with tab[j] >= i (tab non-decreasing), i in [0, n].
 static std::vector<int32_t> starts_of(const std::vector<int32_t>& tab, int n) {
   std::vector<int32_t> s(n + 1);
@@ -150,6 +180,7 @@ static std::vector<float> lap_eigs(int n) {
 }
 
 static void free_workspace(Plan* P) {
+  free_graphs(P);
   for (int m = 0; m < 3; ++m) {
     free_solver(P->solver[m]);
     P->solver[m] = nullptr;
@@ -168,7 +199,7 @@ static void destroy_plan(Plan* P) {
   if (P->owns_tables) {
     void* ptrs[] = {P->d_rz_i0, P->d_rz_w, P->d_rzt_start, P->d_rt_k0, P->d_rt_w, P->d_rtt_start, P->d_cols,
                     P->d_colpos, P->d_tw2t, P->d_twt, P->d_twx, P->d_twy, P->d_lamx, P->d_lamy, P->d_lamt,
-                    P->d_H};
+                    P->d_H, P->d_rz_f4, P->d_rt_f4, P->d_rzT_ptr, P->d_rzT_ent, P->d_rtT_ptr, P->d_rtT_ent};
     for (void* p : ptrs)
       if (p) cudaFree(p);
   }
@@ -201,6 +232,8 @@ Plan* plan_clone_workspace(const Plan& base, nlos_status* status) {
   P->ev.clear();
   P->ev_cat.clear();
   P->ev_used = 0;
+  P->graphs.clear();
+  P->capture_stream = nullptr;
   nlos_status s = alloc_workspace(P);
   if (s != NLOS_OK) {
     destroy_plan(P);
@@ -308,6 +341,19 @@ static nlos_status create_plan(const nlos_geometry* g, cudaStream_t st, Plan** o
   UP(d_lamx, lx);
   UP(d_lamy, ly);
   UP(d_lamt, lt);
+  std::vector<float4> rzf, rtf;
+  std::vector<int32_t> rzp, rtp;
+  std::vector<float2> rze, rte;
+  device_taps(P->h_rz_i0, P->h_rz_w, nt, &rzf, &rzp, &rze);
+  device_taps(P->h_rt_k0, P->h_rt_w, nt, &rtf, &rtp, &rte);
+  rze.resize(2 * nt, make_float2(0.f, 0.f));   // kernels stage a fixed 2 nt entries
+  rte.resize(2 * nt, make_float2(0.f, 0.f));
+  UP(d_rz_f4, rzf);
+  UP(d_rt_f4, rtf);
+  UP(d_rzT_ptr, rzp);
+  UP(d_rzT_ent, rze);
+  UP(d_rtT_ptr, rtp);
+  UP(d_rtT_ent, rte);
 #undef UP
   if (s == NLOS_OK) s = dalloc(&P->d_H, (size_t)(nt + 1) * (nx + 1) * (ny + 1));
   if (s == NLOS_OK) s = alloc_workspace(P);
@@ -348,6 +394,9 @@ static nlos_status create_plan(const nlos_geometry* g, cudaStream_t st, Plan** o
   float2* d_hw = nullptr;
   s = upload(&d_m0, m0.data(), m0.size());
   if (s == NLOS_OK) s = upload(&d_hw, hw.data(), hw.size());
+  if (s == NLOS_OK) s = prepare_tpass(nt);
+  if (s == NLOS_OK) s = prepare_xy(nx);
+  if (s == NLOS_OK) s = prepare_stencils();
   if (s == NLOS_OK) {
     KTimer kt_(*P, KC_KSPEC, st);
     s = launch_kernel_spectrum(*P, d_m0, d_hw, st);

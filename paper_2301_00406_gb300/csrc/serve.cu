@@ -53,9 +53,17 @@ static nlos_status reconstruct_batch(Plan** plans, const nlos_params* params, co
     j.u_out = u_out[i];
     j.tau_out = tau_out ? tau_out[i] : nullptr;
     j.st = streams[i];
-    if (st == NLOS_OK) st = job_init(j);
   }
-  // round robin: one enqueued iteration of every unfinished job per round
+  // whole reconstructions as graph launches where possible; the rest are
+  // stepped round robin, one enqueued iteration of every unfinished job per round
+  std::vector<char> graphed(n, 0);
+  for (int i = 0; i < n && st == NLOS_OK; ++i) {
+    bool used = false;
+    st = job_enqueue_graph(jobs[i], streams[i], &used);
+    graphed[i] = used;
+    if (st == NLOS_OK && !used) st = job_init(jobs[i]);
+    if (used) jobs[i].done = true;
+  }
   bool left = st == NLOS_OK;
   while (left && st == NLOS_OK) {
     left = false;
@@ -65,7 +73,8 @@ static nlos_status reconstruct_batch(Plan** plans, const nlos_params* params, co
       left = left || !jobs[i].done;
     }
   }
-  for (int i = 0; i < n && st == NLOS_OK; ++i) st = job_finish(jobs[i]);
+  for (int i = 0; i < n && st == NLOS_OK; ++i)
+    if (!graphed[i]) st = job_finish(jobs[i]);
   // join: the caller's stream waits for every job
   for (int i = 0; i < n; ++i) {
     if (!streams[i]) continue;
@@ -139,6 +148,7 @@ struct Job {
   JobCtx* ctx = nullptr;
   JobRun run;
   bool finishing = false;
+  bool graphed = false;  // the whole run was enqueued as one graph launch
 };
 
 struct BaseEntry {
@@ -305,7 +315,13 @@ static nlos_status start_job(Server* S, Job* jb, BaseEntry* base) {
   r.u_out = c->d_u;
   r.tau_out = nullptr;
   r.st = c->st;
-  NLOS_TRY(job_init(r));
+  bool used = false;
+  NLOS_TRY(job_enqueue_graph(r, c->st, &used));
+  jb->graphed = used;
+  if (used)
+    r.done = true;
+  else
+    NLOS_TRY(job_init(r));
   jb->t_start = Clock::now();
   return NLOS_OK;
 }
@@ -392,7 +408,7 @@ static void worker_main(Server* S) {
       }
       if (s == NLOS_OK && jb->run.done) {
         JobCtx* c = jb->ctx;
-        s = job_finish(jb->run);
+        if (!jb->graphed) s = job_finish(jb->run);
         const size_t F = (size_t)c->ws->nx * c->ws->ny * c->ws->nt * sizeof(float);
         if (s == NLOS_OK && cudaMemcpyAsync(c->h_u, c->d_u, F, cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
           s = fail(NLOS_ERR_CUDA, "server: result copy");

@@ -25,6 +25,9 @@ struct TpassOps {
   static nlos_status sfwd(const Plan& P, const float* x, int ncols, float2* Sp, cudaStream_t st);
   static nlos_status sinv(const Plan& P, const float2* Sp, int ncols, float* x, const float* ref, double* partials,
                           int* nblocks, cudaStream_t st);
+  // Raise every t-pass kernel's shared-memory limit to its largest launch
+  // shape (so no attribute call happens later, e.g. during a stream capture).
+  static nlos_status prepare();
 };
 
 #ifdef NLOS_TPASS_IMPL
@@ -37,9 +40,44 @@ struct TP {
   static constexpr int COLS = NT >= 1024 ? 8 : 16;  // columns per CTA
   static constexpr int PAIRS = COLS / 2;
   static constexpr int WP = NT + 1;                 // odd pitch of a work transform
-  static constexpr size_t smem_base = sizeof(float2) * (2 * NT + PAIRS * WP) + sizeof(float) * COLS * NT;
 };
 constexpr int kTpassThreads = 256;
+
+// Shared-memory table region (float4 slots): forward taps use nt slots; a CSR
+// transpose uses ceil((nt + 1) / 4) slots of row pointers then nt slots of
+// {weight, index} pairs.
+template <int NT>
+struct TabLayout {
+  static constexpr int PTR4 = (NT + 4) / 4;
+  static constexpr int SLOTS = NT + PTR4;
+};
+
+template <int NT>
+__device__ __forceinline__ void stage_fwd_taps(float4* tab, const float4* __restrict__ g, int tid, int nthr) {
+  for (int i = tid; i < NT; i += nthr) tab[i] = __ldg(g + i);
+}
+template <int NT>
+__device__ __forceinline__ void stage_csr(float4* tab, const int32_t* __restrict__ ptr, const float2* __restrict__ ent,
+                                          int tid, int nthr) {
+  int* p = reinterpret_cast<int*>(tab);
+  float2* e = reinterpret_cast<float2*>(tab + TabLayout<NT>::PTR4);
+  for (int i = tid; i <= NT; i += nthr) p[i] = __ldg(ptr + i);
+  for (int i = tid; i < 2 * NT; i += nthr) e[i] = __ldg(ent + i);
+}
+// sum over the CSR row n of w * x[index]
+template <int NT>
+__device__ __forceinline__ float2 csr_row2(const float4* tab, int n, const float* xa, const float* xb) {
+  const int* p = reinterpret_cast<const int*>(tab);
+  const float2* e = reinterpret_cast<const float2*>(tab + TabLayout<NT>::PTR4);
+  float a = 0.f, b = 0.f;
+  for (int q = p[n]; q < p[n + 1]; ++q) {
+    const float2 w = e[q];
+    const int k = __float_as_int(w.y);
+    a += w.x * xa[k];
+    b += w.x * xb[k];
+  }
+  return make_float2(a, b);
+}
 
 
 // Block-wide FP64 reduction of NTERMS values; thread 0 writes partials[blockIdx.x * kMaxTerms + t].
@@ -152,17 +190,23 @@ __device__ __forceinline__ void tinv_core(const float2* __restrict__ S, int pitc
 // ---------------------------------------------------------------------------
 template <int NT, int MODE>
 __global__ void __launch_bounds__(kTpassThreads)
-    k_tfwd(Lin3 src, int ncols, float2* __restrict__ S, int pitch, const int32_t* __restrict__ i0t,
-           const float* __restrict__ wt3, const int32_t* __restrict__ tstart, const float2* __restrict__ tw2g, int cols) {
+    k_tfwd(Lin3 src, int ncols, float2* __restrict__ S, int pitch, const float4* __restrict__ ftab,
+           const int32_t* __restrict__ tptr, const float2* __restrict__ tent, const float2* __restrict__ tw2g,
+           int cols) {
   const int COLS = cols, PAIRS = cols >> 1;
   constexpr int WP = TP<NT>::WP;
   extern __shared__ float4 smem_f4[];
   float2* tw2 = reinterpret_cast<float2*>(smem_f4);
-  float2* work = tw2 + 2 * NT;
+  float4* tab = reinterpret_cast<float4*>(tw2 + 2 * NT);
+  float2* work = reinterpret_cast<float2*>(tab + TabLayout<NT>::SLOTS);
   float* cbuf = reinterpret_cast<float*>(work + ((PAIRS * WP + 1) & ~1));
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int col0 = blockIdx.x * COLS;
   for (int i = tid; i < 2 * NT; i += nthr) tw2[i] = __ldg(tw2g + i);
+  if (MODE == 0)
+    stage_fwd_taps<NT>(tab, ftab, tid, nthr);
+  else
+    stage_csr<NT>(tab, tptr, tent, tid, nthr);
 
   // stage the CTA's input columns in shared memory
   float c0 = src.c[0], c1 = src.c[1], c2 = src.c[2];
@@ -200,34 +244,16 @@ __global__ void __launch_bounds__(kTpassThreads)
       const int p = i / NT, n = i % NT;
       const float* ca = cbuf + (2 * p) * NT;
       const float* cb = ca + NT;
-      float a, b;
+      float2 z;
       if (MODE == 0) {
-        // u~_n = g_n (w0_n u[i0_n] + w1_n u[i0_n + 1])
-        const int i0 = __ldg(i0t + n);
-        const float w0 = __ldg(wt3 + 3 * n), w1 = __ldg(wt3 + 3 * n + 1), g = __ldg(wt3 + 3 * n + 2);
-        a = g * (w0 * ca[i0] + w1 * ca[i0 + 1]);
-        b = g * (w0 * cb[i0] + w1 * cb[i0 + 1]);
+        // u~_n = (w0 g)_n u[i0_n] + (w1 g)_n u[i0_n + 1]
+        const float4 t = tab[n];
+        const int i0 = __float_as_int(t.z);
+        z = make_float2(t.x * ca[i0] + t.y * ca[i0 + 1], t.x * cb[i0] + t.y * cb[i0 + 1]);
       } else {
-        // c_n = sum over t-bins k with k0_k = n of wt_k w0_k r_k
-        //     + sum over t-bins k with k0_k = n - 1 of wt_k w1_k r_k
-        a = 0.f;
-        b = 0.f;
-        const int s0 = __ldg(tstart + n), s1 = __ldg(tstart + n + 1);
-        for (int k = s0; k < s1; ++k) {
-          const float w = __ldg(wt3 + 3 * k) * __ldg(wt3 + 3 * k + 2);
-          a += w * ca[k];
-          b += w * cb[k];
-        }
-        if (n > 0) {
-          const int sm = __ldg(tstart + n - 1);
-          for (int k = sm; k < s0; ++k) {
-            const float w = __ldg(wt3 + 3 * k + 1) * __ldg(wt3 + 3 * k + 2);
-            a += w * ca[k];
-            b += w * cb[k];
-          }
-        }
+        // c_n = sum over the t-bins k that interpolate v-bin n of (w wt)_k r_k
+        z = csr_row2<NT>(tab, n, ca, cb);
       }
-      float2 z = make_float2(a, b);
       if (half) z = cmul(z, tw2[n]);
       work[p * WP + n] = z;
     }
@@ -244,17 +270,19 @@ __global__ void __launch_bounds__(kTpassThreads)
 template <int NT, int EPI>
 __global__ void __launch_bounds__(kTpassThreads)
     k_tinv(const float2* __restrict__ S, int pitch, int ncols, float* __restrict__ out,
-           const int32_t* __restrict__ outmap, FitArgs fa, const int32_t* __restrict__ k0t,
-           const float* __restrict__ wt3, const float2* __restrict__ tw2g, int cols) {
+           const int32_t* __restrict__ outmap, FitArgs fa, const float4* __restrict__ ftab,
+           const float2* __restrict__ tw2g, int cols) {
   const int COLS = cols, PAIRS = cols >> 1;
   constexpr int WP = TP<NT>::WP;
   extern __shared__ float4 smem_f4[];
   float2* tw2 = reinterpret_cast<float2*>(smem_f4);
-  float2* work = tw2 + 2 * NT;
+  float4* tab = reinterpret_cast<float4*>(tw2 + 2 * NT);
+  float2* work = reinterpret_cast<float2*>(tab + TabLayout<NT>::SLOTS);
   float* cbuf = reinterpret_cast<float*>(work + ((PAIRS * WP + 1) & ~1));
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int col0 = blockIdx.x * COLS;
   for (int i = tid; i < 2 * NT; i += nthr) tw2[i] = __ldg(tw2g + i);
+  stage_fwd_taps<NT>(tab, ftab, tid, nthr);
   __syncthreads();
   tinv_core<NT>(S, pitch, col0, ncols, work, cbuf, tw2, PAIRS, tid, nthr);
 
@@ -274,9 +302,9 @@ __global__ void __launch_bounds__(kTpassThreads)
       [&](int i, float3 in) {
         const int c = i / NT, k = i % NT;
         const float* cc = cbuf + c * NT;
-        const int k0 = __ldg(k0t + k);
-        const float tau =
-            __ldg(wt3 + 3 * k + 2) * (__ldg(wt3 + 3 * k) * cc[k0] + __ldg(wt3 + 3 * k + 1) * cc[k0 + 1]);
+        const float4 t = tab[k];
+        const int k0 = __float_as_int(t.z);
+        const float tau = t.x * cc[k0] + t.y * cc[k0 + 1];
         const int oc = outmap ? __ldg(outmap + col0 + c) : col0 + c;
         out[(size_t)oc * NT + k] = tau;
         if (EPI == 1) {
@@ -314,41 +342,31 @@ __device__ __forceinline__ void periodic_fwd_post(const float2* work, float2* Sp
 template <int NT, int MODE>
 __global__ void __launch_bounds__(kTpassThreads)
     k_tadj(const float2* __restrict__ S, int pitch, int ncols, float* __restrict__ out, SolveRhs sr,
-           float2* __restrict__ Sp, const int32_t* __restrict__ i0t, const float* __restrict__ wt3,
-           const int32_t* __restrict__ zstart, const float2* __restrict__ tw2g, int cols) {
+           float2* __restrict__ Sp, const int32_t* __restrict__ tptr, const float2* __restrict__ tent,
+           const float2* __restrict__ tw2g, int cols) {
   const int COLS = cols, PAIRS = cols >> 1;
   constexpr int WP = TP<NT>::WP;
   extern __shared__ float4 smem_f4[];
   float2* tw2 = reinterpret_cast<float2*>(smem_f4);
-  float2* work = tw2 + 2 * NT;
+  float4* tab = reinterpret_cast<float4*>(tw2 + 2 * NT);
+  float2* work = reinterpret_cast<float2*>(tab + TabLayout<NT>::SLOTS);
   float* cbuf = reinterpret_cast<float*>(work + ((PAIRS * WP + 1) & ~1));
-  float* gbuf = cbuf + COLS * NT;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int col0 = blockIdx.x * COLS;
   for (int i = tid; i < 2 * NT; i += nthr) tw2[i] = __ldg(tw2g + i);
+  stage_csr<NT>(tab, tptr, tent, tid, nthr);
   __syncthreads();
   tinv_core<NT>(S, pitch, col0, ncols, work, cbuf, tw2, PAIRS, tid, nthr);
 
-  // g_i = sum_{j: i0_j = i} g_j w0_j c_j + sum_{j: i0_j = i - 1} g_j w1_j c_j
-  for (int idx = tid; idx < COLS * NT; idx += nthr) {
-    const int c = idx / NT, i = idx % NT;
-    const float* cc = cbuf + c * NT;
-    float acc = 0.f;
-    const int s0 = __ldg(zstart + i), s1 = __ldg(zstart + i + 1);
-    for (int j = s0; j < s1; ++j) acc += __ldg(wt3 + 3 * j) * __ldg(wt3 + 3 * j + 2) * cc[j];
-    if (i > 0) {
-      const int sm = __ldg(zstart + i - 1);
-      for (int j = sm; j < s0; ++j) acc += __ldg(wt3 + 3 * j + 1) * __ldg(wt3 + 3 * j + 2) * cc[j];
-    }
-    gbuf[idx] = acc;
-  }
-  __syncthreads();
-
+  // g_i = sum over the v-bins j whose R_z taps touch rho-bin i of (w g)_j c_j,
+  // gathered straight into the output (MODE 0) or into the solve rhs (MODE 1)
   if (MODE == 0) {
-    for (int i = tid; i < COLS * NT / 4; i += nthr) {
-      const int c = (i * 4) / NT;
-      if (col0 + c < ncols)
-        reinterpret_cast<float4*>(out)[(size_t)col0 * NT / 4 + i] = reinterpret_cast<const float4*>(gbuf)[i];
+    for (int idx = tid; idx < PAIRS * NT; idx += nthr) {
+      const int p = idx / NT, i = idx % NT;
+      const int ca = col0 + 2 * p, cb = ca + 1;
+      const float2 v = csr_row2<NT>(tab, i, cbuf + (2 * p) * NT, cbuf + (2 * p + 1) * NT);
+      if (ca < ncols) out[(size_t)ca * NT + i] = v.x;
+      if (cb < ncols) out[(size_t)cb * NT + i] = v.y;
     }
     return;
   }
@@ -375,8 +393,9 @@ __global__ void __launch_bounds__(kTpassThreads)
       [&](int i, float4 v) {
         const int p = i / NT, n = i % NT;
         const int ca = col0 + 2 * p, cb = ca + 1;
-        const float a = ca < ncols ? L * v.x - gbuf[(2 * p) * NT + n] + v.y : 0.f;
-        const float b = cb < ncols ? L * v.z - gbuf[(2 * p + 1) * NT + n] + v.w : 0.f;
+        const float2 gv = csr_row2<NT>(tab, n, cbuf + (2 * p) * NT, cbuf + (2 * p + 1) * NT);
+        const float a = ca < ncols ? L * v.x - gv.x + v.y : 0.f;
+        const float b = cb < ncols ? L * v.z - gv.y + v.w : 0.f;
         work[p * WP + n] = make_float2(a, b);
       });
   __syncthreads();
@@ -477,7 +496,7 @@ struct TpShape {
 };
 
 template <int NT>
-static TpShape tp_shape(int ncols, int extra) {
+static TpShape tp_shape(int ncols, int extra, bool tab = true) {
   TpShape sh;
   sh.cols = TP<NT>::COLS;
   while (sh.cols > 2 && div_up(ncols, sh.cols) < 2 * 152) sh.cols >>= 1;
@@ -486,7 +505,7 @@ static TpShape tp_shape(int ncols, int extra) {
   // the work region is padded to an even number of float2 so the real column
   // buffers after it stay 16-byte aligned (float4 accesses)
   sh.smem = sizeof(float2) * (2 * NT + (((sh.cols / 2) * TP<NT>::WP + 1) & ~1)) +
-            sizeof(float) * extra * sh.cols * NT;
+            (tab ? sizeof(float4) * TabLayout<NT>::SLOTS : 0) + sizeof(float) * extra * sh.cols * NT;
   return sh;
 }
 
@@ -497,7 +516,8 @@ nlos_status TpassOps<NT>::tfwd_rz(const Plan& P, const float* u, int ncols, floa
   const TpShape sh = tp_shape<NT>(ncols, 1);
   NLOS_TRY(set_smem_tp(kern, sh.smem));
   Lin3 src{{u, nullptr, nullptr}, {1.f, 0.f, 0.f}, nullptr};
-  kern<<<sh.blocks, sh.threads, sh.smem, st>>>(src, ncols, S, pitch, P.d_rz_i0, P.d_rz_w, nullptr, P.d_tw2t, sh.cols);
+  kern<<<sh.blocks, sh.threads, sh.smem, st>>>(src, ncols, S, pitch, P.d_rz_f4, nullptr, nullptr, P.d_tw2t,
+                                               sh.cols);
   NLOS_LAUNCH_CHECK("k_tfwd<rz>");
   return NLOS_OK;
 }
@@ -508,7 +528,7 @@ nlos_status TpassOps<NT>::tfwd_rtt(const Plan& P, const Lin3& r, int ncols, floa
   auto kern = k_tfwd<NT, 1>;
   const TpShape sh = tp_shape<NT>(ncols, 1);
   NLOS_TRY(set_smem_tp(kern, sh.smem));
-  kern<<<sh.blocks, sh.threads, sh.smem, st>>>(r, ncols, S, pitch, nullptr, P.d_rt_w, P.d_rtt_start, P.d_tw2t,
+  kern<<<sh.blocks, sh.threads, sh.smem, st>>>(r, ncols, S, pitch, nullptr, P.d_rtT_ptr, P.d_rtT_ent, P.d_tw2t,
                                                sh.cols);
   NLOS_LAUNCH_CHECK("k_tfwd<rtt>");
   return NLOS_OK;
@@ -522,8 +542,7 @@ nlos_status TpassOps<NT>::tinv_store(const Plan& P, const float2* S, int pitch, 
   const TpShape sh = tp_shape<NT>(ncols, 1);
   NLOS_TRY(set_smem_tp(kern, sh.smem));
   FitArgs fa{};
-  kern<<<sh.blocks, sh.threads, sh.smem, st>>>(S, pitch, ncols, out, outmap, fa, P.d_rt_k0, P.d_rt_w, P.d_tw2t,
-                                               sh.cols);
+  kern<<<sh.blocks, sh.threads, sh.smem, st>>>(S, pitch, ncols, out, outmap, fa, P.d_rt_f4, P.d_tw2t, sh.cols);
   NLOS_LAUNCH_CHECK("k_tinv<store>");
   return NLOS_OK;
 }
@@ -537,8 +556,7 @@ nlos_status TpassOps<NT>::tinv_fit(const Plan& P, const float2* S, int pitch, in
   NLOS_TRY(set_smem_tp(kern, sh.smem));
   if (sh.blocks > P.partial_blocks) return fail(NLOS_ERR_INVALID_ARG, "partials buffer too small");
   *nblocks = sh.blocks;
-  kern<<<sh.blocks, sh.threads, sh.smem, st>>>(S, pitch, ncols, out, nullptr, fa, P.d_rt_k0, P.d_rt_w, P.d_tw2t,
-                                               sh.cols);
+  kern<<<sh.blocks, sh.threads, sh.smem, st>>>(S, pitch, ncols, out, nullptr, fa, P.d_rt_f4, P.d_tw2t, sh.cols);
   NLOS_LAUNCH_CHECK("k_tinv<fit>");
   return NLOS_OK;
 }
@@ -548,11 +566,11 @@ nlos_status TpassOps<NT>::tadj_store(const Plan& P, const float2* S, int pitch, 
                                      cudaStream_t st) {
   KTimer kt_(P, KC_TADJ, st);
   auto kern = k_tadj<NT, 0>;
-  const TpShape sh = tp_shape<NT>(ncols, 2);
+  const TpShape sh = tp_shape<NT>(ncols, 1);
   NLOS_TRY(set_smem_tp(kern, sh.smem));
   SolveRhs sr{};
-  kern<<<sh.blocks, sh.threads, sh.smem, st>>>(S, pitch, ncols, out, sr, nullptr, P.d_rz_i0, P.d_rz_w,
-                                               P.d_rzt_start, P.d_tw2t, sh.cols);
+  kern<<<sh.blocks, sh.threads, sh.smem, st>>>(S, pitch, ncols, out, sr, nullptr, P.d_rzT_ptr, P.d_rzT_ent,
+                                               P.d_tw2t, sh.cols);
   NLOS_LAUNCH_CHECK("k_tadj<store>");
   return NLOS_OK;
 }
@@ -562,9 +580,9 @@ nlos_status TpassOps<NT>::tadj_solve(const Plan& P, const float2* S, int pitch, 
                                      float2* Sp, cudaStream_t st) {
   KTimer kt_(P, KC_TADJ, st);
   auto kern = k_tadj<NT, 1>;
-  const TpShape sh = tp_shape<NT>(ncols, 2);
+  const TpShape sh = tp_shape<NT>(ncols, 1);
   NLOS_TRY(set_smem_tp(kern, sh.smem));
-  kern<<<sh.blocks, sh.threads, sh.smem, st>>>(S, pitch, ncols, nullptr, sr, Sp, P.d_rz_i0, P.d_rz_w, P.d_rzt_start,
+  kern<<<sh.blocks, sh.threads, sh.smem, st>>>(S, pitch, ncols, nullptr, sr, Sp, P.d_rzT_ptr, P.d_rzT_ent,
                                                P.d_tw2t, sh.cols);
   NLOS_LAUNCH_CHECK("k_tadj<solve>");
   return NLOS_OK;
@@ -574,7 +592,7 @@ template <int NT>
 nlos_status TpassOps<NT>::sfwd(const Plan& P, const float* x, int ncols, float2* Sp, cudaStream_t st) {
   KTimer kt_(P, KC_SFWD, st);
   auto kern = k_sfwd<NT>;
-  const TpShape sh = tp_shape<NT>(ncols, 0);
+  const TpShape sh = tp_shape<NT>(ncols, 0, false);
   NLOS_TRY(set_smem_tp(kern, sh.smem));
   kern<<<sh.blocks, sh.threads, sh.smem, st>>>(x, ncols, Sp, P.d_tw2t, sh.cols);
   NLOS_LAUNCH_CHECK("k_sfwd");
@@ -586,12 +604,26 @@ nlos_status TpassOps<NT>::sinv(const Plan& P, const float2* Sp, int ncols, float
                                double* partials, int* nblocks, cudaStream_t st) {
   KTimer kt_(P, KC_SINV, st);
   auto kern = k_sinv<NT>;
-  const TpShape sh = tp_shape<NT>(ncols, 0);
+  const TpShape sh = tp_shape<NT>(ncols, 0, false);
   NLOS_TRY(set_smem_tp(kern, sh.smem));
   if (partials && sh.blocks > P.partial_blocks) return fail(NLOS_ERR_INVALID_ARG, "partials buffer too small");
   if (nblocks) *nblocks = sh.blocks;
   kern<<<sh.blocks, sh.threads, sh.smem, st>>>(Sp, ncols, x, ref, partials, P.d_tw2t, sh.cols);
   NLOS_LAUNCH_CHECK("k_sinv");
+  return NLOS_OK;
+}
+
+template <int NT>
+nlos_status TpassOps<NT>::prepare() {
+  const TpShape s1 = tp_shape<NT>(1 << 30, 1), s2 = s1, s0 = tp_shape<NT>(1 << 30, 0, false);
+  NLOS_TRY(set_smem_tp(k_tfwd<NT, 0>, s1.smem));
+  NLOS_TRY(set_smem_tp(k_tfwd<NT, 1>, s1.smem));
+  NLOS_TRY(set_smem_tp(k_tinv<NT, 0>, s1.smem));
+  NLOS_TRY(set_smem_tp(k_tinv<NT, 1>, s1.smem));
+  NLOS_TRY(set_smem_tp(k_tadj<NT, 0>, s2.smem));
+  NLOS_TRY(set_smem_tp(k_tadj<NT, 1>, s2.smem));
+  NLOS_TRY(set_smem_tp(k_sfwd<NT>, s0.smem));
+  NLOS_TRY(set_smem_tp(k_sinv<NT>, s0.smem));
   return NLOS_OK;
 }
 
