@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnlos.so")
-SOURCES = ["lct.cu", "xy.cu", "tpass_small.cu", "tpass_256.cu", "tpass_512.cu", "tpass_1024.cu", "admm.cu", "plan.cu", "static_solve.cu", "serve.cu"]
+SOURCES = ["lct.cu", "xy.cu", "conv4.cu", "tpass_small.cu", "tpass_256.cu", "tpass_512.cu", "tpass_1024.cu", "admm.cu", "plan.cu", "static_solve.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

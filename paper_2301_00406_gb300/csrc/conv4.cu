@@ -1,0 +1,490 @@
+// Lateral convolution of the light-cone transform (the H of Eq. 3 applied to
+// every kt plane of the t-transformed volume) for N = nx = ny in {32, 64, 128}:
+// a cluster of four CTAs per kt plane, two CTAs resident per SM.
+//
+// The plane (N x N complex, zero-padded to 2N x 2N by the convolution) is
+// split by lateral frequency: CTA q of the cluster owns the padded y bins
+// ky = 4 k + q, k in [0, M), M = N / 2.  Because the input occupies only the
+// first N of the 2N padded samples, those bins are an M-point DFT of the row
+// folded once,
+//     Y[4 k + q] = DFT_M( w^(q n) (row[n] + (-i)^q row[n + M]) )[k],
+//     w = exp(-2 pi i / 2N),
+// and the same fold by x parity p = kx mod 4 turns the padded 2N-point
+// transform along x of each column into four M-point transforms.  After the
+// multiply by H and the inverse transforms, the four parities (and, for y,
+// the four CTAs) recombine as
+//     out[n] = sum_p w^(-p n) I_p[n],  out[n + M] = sum_p i^p w^(-p n) I_p[n].
+// Every M-point transform runs as two register DFTs (8 x R2, R2 = M / 8) with
+// one exchange through shared memory.
+//
+// Phases of one CTA (q = rank in the cluster):
+//  1. stage rows [q N/4, (q+1) N/4) of the input plane in shared memory;
+//  2. y transform of all N rows (rows read from the four CTAs' staging
+//     buffers through distributed shared memory) -> plane[x][k], k < M;
+//  3. x convolution, one warp per column: fold by the four x parities,
+//     forward M-point transforms, multiply by H, inverse, recombine across
+//     the parity lanes with warp shuffles, back into the column;
+//  4. inverse y transform of every row, untwisted by w^(-q n);
+//  5. CTA q sums the four CTAs' results for its rows and writes them.
+// Only cluster barriers separate the CTA-wide phases; inside a phase each
+// warp owns whole rows or columns and synchronises with __syncwarp.
+//
+// The multiply reads H(kx, ky) as H(ky, kx): the cone kernel depends on
+// (i dx)^2 + (j dy)^2 with dx = dy (nx = ny over one wall width), so its
+// spectrum is symmetric in the two lateral frequencies, and the transposed
+// lookup makes the 32 lanes of a warp read 32 consecutive kx.
+#include <cooperative_groups.h>
+
+#include <type_traits>
+
+#include "fft.cuh"
+#include "passes.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace nlos {
+
+template <int N>
+struct C4 {
+  static constexpr int M = N / 2;            // points per folded transform
+  static constexpr int R2 = M / 8;           // second-step radix (first step is 8)
+  static constexpr int RW = 32 / R2;         // rows per warp in the y phases
+  static constexpr int CW = 8 / R2;          // columns per warp in the x phase
+  static constexpr int ROWS = N / 4;         // input rows staged per CTA
+  static constexpr int SP = N + R2;          // stage row pitch (float2)
+  static constexpr int SPX = N == 128 ? 72 : N == 64 ? 40 : 18;  // x scratch pitch per (column, parity)
+  static constexpr int WSCR = CW * 4 * SPX;  // x scratch per warp (float2)
+  static constexpr int WARPS = 8, THREADS = 256;
+  static constexpr int REGION = ROWS * SP > WARPS * WSCR ? ROWS * SP : WARPS * WSCR;
+  static constexpr size_t smem = sizeof(float2) * (N * M + REGION + 2 * N) + sizeof(int) * 2 * N;
+};
+
+// Row swizzle of the plane: element (x, k) lives at x M + (k ^ swz(x)), swz
+// linear over GF(2) in the bits of x.  The coefficients make every access
+// pattern of the three phases hit distinct banks.
+template <int N>
+__host__ __device__ constexpr int swc(int bit) {
+  return N == 128 ? (bit == 0 ? 8 : bit == 1 ? 1 : bit == 2 ? 2 : bit == 6 ? 4 : 0)
+         : N == 64 ? (bit == 0 ? 8 : bit == 1 ? 15 : bit == 2 ? 10 : bit == 3 ? 8 : bit == 4 ? 3 : bit == 5 ? 14 : 0)
+                   : (bit == 0 ? 8 : bit == 1 ? 3 : bit == 2 ? 12 : bit == 3 ? 11 : bit == 4 ? 15 : 0);
+}
+template <int N>
+__host__ __device__ __forceinline__ constexpr int swz(int x) {
+  int v = 0;
+#pragma unroll
+  for (int b = 0; (1 << b) < N; ++b)
+    if ((x >> b) & 1) v ^= swc<N>(b);
+  return v;
+}
+// In-row position of the intermediate value (n2, k1) between the two steps
+// of a y transform, and within a (column, parity) slot of the x scratch.
+__device__ __forceinline__ constexpr int ipos(int n2, int k1) { return 8 * n2 + (k1 ^ (n2 & 7)); }
+
+// v * (-i)^p and v * i^p for a runtime p in [0, 4)
+__device__ __forceinline__ float2 rot_mi(float2 v, int p) {
+  const float2 r = (p & 1) ? make_float2(v.y, -v.x) : v;
+  return (p & 2) ? make_float2(-r.x, -r.y) : r;
+}
+__device__ __forceinline__ float2 rot_i(float2 v, int p) {
+  const float2 r = (p & 1) ? make_float2(-v.y, v.x) : v;
+  return (p & 2) ? make_float2(-r.x, -r.y) : r;
+}
+// index of the padded frequency k in [0, 2N) within the stored [0, N] half
+template <int N>
+__device__ __forceinline__ int fold_k(int k) {
+  return k <= N ? k : 2 * N - k;
+}
+
+// Phase 2: forward y transform of every row for bins ky = 4 k + Q.
+template <int N, int Q>
+__device__ __forceinline__ void c4_yfwd(float2* __restrict__ plane, const float2* const (&stage)[4],
+                                        const float2* __restrict__ tw, const int* __restrict__ rowin, int warp,
+                                        int lane) {
+  using C = C4<N>;
+  constexpr int M = C::M, R2 = C::R2, RW = C::RW, SP = C::SP, ROWS = C::ROWS;
+  const int rsub = lane / R2, n2 = lane % R2;
+  // inter-step twiddles w^(n2 (Q + 4 k1)), k1 = 0..7 (the fold twist w^(Q n2) merged in)
+  float2 twa[8];
+  {
+    const float2 st = tw[(4 * n2) & (2 * N - 1)];
+    twa[0] = tw[(Q * n2) & (2 * N - 1)];
+#pragma unroll
+    for (int k1 = 1; k1 < 8; ++k1) twa[k1] = cmul(twa[k1 - 1], st);
+  }
+  for (int it = warp; it < N / RW; it += C::WARPS) {
+    {
+      const int x = it * RW + rsub;
+      if (rowin[x]) {
+        const int o = x / ROWS;
+        const float2* row = (o == 0 ? stage[0] : o == 1 ? stage[1] : o == 2 ? stage[2] : stage[3]) + (x % ROWS) * SP;
+        float2 a[8];
+#pragma unroll
+        for (int n1 = 0; n1 < 8; ++n1) {
+          const float2 u = row[n2 + R2 * n1], v = row[n2 + R2 * n1 + M];
+          // (-i)^Q v and the fold twist w^(Q R2 n1) = exp(-2 pi i Q n1 / 32)
+          const float2 r = Q == 0 ? v : Q == 1 ? make_float2(v.y, -v.x) : Q == 2 ? make_float2(-v.x, -v.y)
+                                                                             : make_float2(-v.y, v.x);
+          a[n1] = twmul64<false>(cadd(u, r), (2 * Q * n1) & 63);
+        }
+        dft_reg<8, false>(a);
+        float2* prow = plane + x * M;
+        const int s = swz<N>(x);
+#pragma unroll
+        for (int k1 = 0; k1 < 8; ++k1) prow[ipos(n2, k1) ^ s] = cmul(a[k1], twa[k1]);
+      }
+    }
+    __syncwarp();
+    // second step: item (row rs, k1); 8 / R2 items per lane
+    float2 b[8 / R2][R2];
+#pragma unroll
+    for (int j = 0; j < 8 / R2; ++j) {
+      const int i = lane + 32 * j, xx = it * RW + i / 8, k1 = i % 8;
+      if (rowin[xx]) {
+        const float2* pr = plane + xx * M;
+        const int ss = swz<N>(xx);
+#pragma unroll
+        for (int m = 0; m < R2; ++m) b[j][m] = pr[ipos(m, k1) ^ ss];
+        dft_reg<R2, false>(b[j]);
+      } else {
+#pragma unroll
+        for (int m = 0; m < R2; ++m) b[j][m] = make_float2(0.f, 0.f);
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 8 / R2; ++j) {
+      const int i = lane + 32 * j, xx = it * RW + i / 8, k1 = i % 8;
+      float2* pr = plane + xx * M;
+      const int ss = swz<N>(xx);
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) pr[(k1 + 8 * k2) ^ ss] = b[j][k2];
+    }
+    __syncwarp();
+  }
+}
+
+// Phase 4: inverse y transform of every row, times w^(-Q n) (n < M).
+template <int N, int Q>
+__device__ __forceinline__ void c4_yinv(float2* __restrict__ plane, const float2* __restrict__ tw,
+                                        const int* __restrict__ rowout, int warp, int lane) {
+  using C = C4<N>;
+  constexpr int M = C::M, R2 = C::R2, RW = C::RW;
+  const int rsub = lane / R2, n2 = lane % R2;
+  const int k1l = lane % 8;
+  // w^(-m (4 k1 + Q)), m < R2, for this lane's k1
+  float2 twi[R2];
+  {
+    const float2 st = cconj(tw[(4 * k1l + Q) & (2 * N - 1)]);
+    twi[0] = make_float2(1.f, 0.f);
+#pragma unroll
+    for (int m = 1; m < R2; ++m) twi[m] = cmul(twi[m - 1], st);
+  }
+  for (int it = warp; it < N / RW; it += C::WARPS) {
+    float2 b[8 / R2][R2];
+#pragma unroll
+    for (int j = 0; j < 8 / R2; ++j) {
+      const int i = lane + 32 * j, xx = it * RW + i / 8, k1 = i % 8;
+      if (rowout[xx]) {
+        const float2* pr = plane + xx * M;
+        const int ss = swz<N>(xx);
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) b[j][k2] = pr[(k1 + 8 * k2) ^ ss];
+        dft_reg<R2, true>(b[j]);
+#pragma unroll
+        for (int m = 1; m < R2; ++m) b[j][m] = cmul(b[j][m], twi[m]);
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 8 / R2; ++j) {
+      const int i = lane + 32 * j, xx = it * RW + i / 8, k1 = i % 8;
+      if (rowout[xx]) {
+        float2* pr = plane + xx * M;
+        const int ss = swz<N>(xx);
+#pragma unroll
+        for (int m = 0; m < R2; ++m) pr[ipos(m, k1) ^ ss] = b[j][m];
+      }
+    }
+    __syncwarp();
+    const int x = it * RW + rsub;
+    float2 e[8];
+    const bool live = rowout[x] != 0;
+    float2* prow = plane + x * M;
+    const int s = swz<N>(x);
+    if (live) {
+#pragma unroll
+      for (int k1 = 0; k1 < 8; ++k1) e[k1] = prow[ipos(n2, k1) ^ s];
+      dft_reg<8, true>(e);
+    }
+    __syncwarp();
+    if (live) {
+#pragma unroll
+      for (int n1 = 0; n1 < 8; ++n1) prow[(n2 + R2 * n1) ^ s] = twmul64<true>(e[n1], (2 * Q * n1) & 63);
+    }
+    __syncwarp();
+  }
+}
+
+// Phase 3: x convolution of the CTA's M columns (ky = 4 c + q).
+template <int N>
+__device__ __forceinline__ void c4_xconv(float2* __restrict__ plane, float2* __restrict__ scr,
+                                         const float2* __restrict__ tw, const float2* __restrict__ Hk, int q, int adj,
+                                         int warp, int lane) {
+  using C = C4<N>;
+  constexpr int M = C::M, R2 = C::R2, CW = C::CW, SPX = C::SPX;
+  const int cs = lane / (4 * R2), p = (lane / R2) % 4, n2 = lane % R2;
+  const int pB = (lane / 8) % 4, k1B = lane % 8;   // step-B item of this lane
+  // fold twist exp(-2 pi i p n1 / 32), n1 = 0..7
+  float2 w32[8];
+  {
+    const float2 st = tw[p * (2 * N / 32)];
+    w32[0] = make_float2(1.f, 0.f);
+#pragma unroll
+    for (int n1 = 1; n1 < 8; ++n1) w32[n1] = cmul(w32[n1 - 1], st);
+  }
+  // inter-step twiddles w^(n2 (p + 4 k1))
+  float2 twa[8];
+  {
+    const float2 st = tw[(4 * n2) & (2 * N - 1)];
+    twa[0] = tw[(p * n2) & (2 * N - 1)];
+#pragma unroll
+    for (int k1 = 1; k1 < 8; ++k1) twa[k1] = cmul(twa[k1 - 1], st);
+  }
+  // inverse inter-step twiddles w^(-m (4 k1 + p)) for the step-B item
+  float2 twb[R2];
+  {
+    const float2 st = cconj(tw[(4 * k1B + pB) & (2 * N - 1)]);
+    twb[0] = make_float2(1.f, 0.f);
+#pragma unroll
+    for (int m = 1; m < R2; ++m) twb[m] = cmul(twb[m - 1], st);
+  }
+  const int sn2 = swz<N>(n2);
+  float2* myscr = scr + (cs * 4 + p) * SPX;
+  for (int cb = warp * CW; cb < M; cb += C::WARPS * CW) {
+    const int c = cb + cs;
+    // A: fold, first step, twiddles -> scratch
+    {
+      float2 a[8];
+#pragma unroll
+      for (int n1 = 0; n1 < 8; ++n1) {
+        const int r0 = n2 + R2 * n1;
+        const float2 u = plane[r0 * M + (c ^ sn2 ^ swz<N>(R2 * n1))];
+        const float2 v = plane[(r0 + M) * M + (c ^ sn2 ^ swz<N>(R2 * n1) ^ swz<N>(M))];
+        a[n1] = cmul(cadd(u, rot_mi(v, p)), w32[n1]);
+      }
+      dft_reg<8, false>(a);
+#pragma unroll
+      for (int k1 = 0; k1 < 8; ++k1) myscr[ipos(n2, k1)] = cmul(a[k1], twa[k1]);
+    }
+    __syncwarp();
+    // B: second step, multiply by H, inverse second step, inverse twiddles
+#pragma unroll
+    for (int j = 0; j < CW; ++j) {
+      const int cc = cb + j;
+      const int ky = fold_k<N>(4 * cc + q);
+      const float2* hrow = Hk + ky * (N + 1);
+      float2* s = scr + (j * 4 + pB) * SPX;
+      float2 h[R2];
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) h[k2] = __ldg(hrow + fold_k<N>(4 * (k1B + 8 * k2) + pB));
+      float2 b[R2];
+#pragma unroll
+      for (int m = 0; m < R2; ++m) b[m] = s[ipos(m, k1B)];
+      dft_reg<R2, false>(b);
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) b[k2] = adj ? cmulc(b[k2], h[k2]) : cmul(b[k2], h[k2]);
+      dft_reg<R2, true>(b);
+#pragma unroll
+      for (int m = 0; m < R2; ++m) s[ipos(m, k1B)] = m == 0 ? b[0] : cmul(b[m], twb[m]);
+    }
+    __syncwarp();
+    // A': inverse first step, untwist, recombine the four parities
+    {
+      float2 e[8];
+#pragma unroll
+      for (int k1 = 0; k1 < 8; ++k1) e[k1] = myscr[ipos(n2, k1)];
+      dft_reg<8, true>(e);
+      // v_p[n] = w^(-p n) I_p[n]; the w^(-p n2) part is already applied in B
+      float2 keep[8];
+#pragma unroll
+      for (int n1 = 0; n1 < 8; ++n1) {
+        const float2 v = cmulc(e[n1], w32[n1]);
+        const float2 v1 = rot_i(v, p);        // contribution to out[n + M]
+        const float2 send = (p & 1) ? v : v1;  // the half this lane gives away
+        const float2 mine = (p & 1) ? v1 : v;
+        const float2 got = make_float2(__shfl_xor_sync(0xffffffffu, send.x, R2),
+                                       __shfl_xor_sync(0xffffffffu, send.y, R2));
+        keep[n1] = cadd(mine, got);
+      }
+      const int h = p & 1, hi = p >> 1;
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const float2 send = hi ? keep[jj] : keep[4 + jj];
+        const float2 mine = hi ? keep[4 + jj] : keep[jj];
+        const float2 got = make_float2(__shfl_xor_sync(0xffffffffu, send.x, 2 * R2),
+                                       __shfl_xor_sync(0xffffffffu, send.y, 2 * R2));
+        const int x = n2 + R2 * (4 * hi + jj) + M * h;
+        plane[x * M + (c ^ swz<N>(x))] = cadd(mine, got);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <int N>
+__global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(256, 2)
+    k_conv4(const float2* __restrict__ Sin, int in_pitch, const int32_t* __restrict__ in_cols, int in_n,
+            float2* __restrict__ Sout, int out_pitch, const int32_t* __restrict__ out_cols, int out_n,
+            const float2* __restrict__ H, int adj, const float2* __restrict__ twg) {
+  using C = C4<N>;
+  constexpr int M = C::M, ROWS = C::ROWS, SP = C::SP;
+  extern __shared__ float4 smem_f4[];
+  float2* plane = reinterpret_cast<float2*>(smem_f4);  // [N][M], swizzled rows
+  float2* region = plane + N * M;                      // stage [ROWS][SP]; later the x scratch
+  float2* tw = region + C::REGION;                     // [2N]: exp(-2 pi i e / 2N)
+  int* rowin = reinterpret_cast<int*>(tw + 2 * N);     // rows holding input samples
+  int* rowout = rowin + N;                             // rows holding output samples
+  cg::cluster_group cluster = cg::this_cluster();
+  const int q = (int)cluster.block_rank();
+  const int kt = blockIdx.x >> 2;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int x0 = q * ROWS;
+
+  for (int i = tid; i < 2 * N; i += C::THREADS) tw[i] = __ldg(twg + i);
+  for (int i = tid; i < N; i += C::THREADS) {
+    rowin[i] = in_cols ? 0 : 1;
+    rowout[i] = out_cols ? 0 : 1;
+  }
+  __syncthreads();
+  if (in_cols)
+    for (int j = tid; j < in_n; j += C::THREADS) rowin[__ldg(in_cols + j) / N] = 1;
+  if (out_cols)
+    for (int j = tid; j < out_n; j += C::THREADS) rowout[__ldg(out_cols + j) / N] = 1;
+
+  // 1. stage this CTA's quarter of the input rows
+  const float2* src = Sin + (size_t)kt * in_pitch;
+  if (in_cols == nullptr) {
+    const float4* s4 = reinterpret_cast<const float4*>(src + (size_t)x0 * N);
+    batched_copy<8, float4>(
+        ROWS * N / 2, tid, C::THREADS, [&](int i) { return __ldg(s4 + i); },
+        [&](int i, float4 v) {
+          const int r = i / (N / 2), c2 = i % (N / 2);
+          *reinterpret_cast<float4*>(region + r * SP + 2 * c2) = v;
+        });
+  } else {
+    for (int i = tid; i < ROWS * SP; i += C::THREADS) region[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    batched_copy<4, float2>(
+        in_n, tid, C::THREADS, [&](int j) { return __ldg(src + j); },
+        [&](int j, float2 v) {
+          const int col = __ldg(in_cols + j), x = col / N;
+          if (x >= x0 && x < x0 + ROWS) region[(x - x0) * SP + col % N] = v;
+        });
+  }
+  cluster.sync();
+
+  // 2. forward y transform (rows read from the four staging buffers)
+  const float2* stage[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) stage[r] = cluster.map_shared_rank(region, r);
+  switch (q) {
+    case 0: c4_yfwd<N, 0>(plane, stage, tw, rowin, warp, lane); break;
+    case 1: c4_yfwd<N, 1>(plane, stage, tw, rowin, warp, lane); break;
+    case 2: c4_yfwd<N, 2>(plane, stage, tw, rowin, warp, lane); break;
+    default: c4_yfwd<N, 3>(plane, stage, tw, rowin, warp, lane); break;
+  }
+  cluster.sync();  // plane complete; no CTA reads the staging buffers any more
+
+  // 3. x convolution
+  const float2* Hk = H + (size_t)kt * (N + 1) * (N + 1);
+  c4_xconv<N>(plane, region + warp * C::WSCR, tw, Hk, q, adj, warp, lane);
+  __syncthreads();
+
+  // 4. inverse y transform
+  switch (q) {
+    case 0: c4_yinv<N, 0>(plane, tw, rowout, warp, lane); break;
+    case 1: c4_yinv<N, 1>(plane, tw, rowout, warp, lane); break;
+    case 2: c4_yinv<N, 2>(plane, tw, rowout, warp, lane); break;
+    default: c4_yinv<N, 3>(plane, tw, rowout, warp, lane); break;
+  }
+  cluster.sync();
+
+  // 5. out[x][n + M h] = s sum_r i^(r h) P_r[x][n] over the four CTAs' planes
+  const float2* pr[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) pr[r] = cluster.map_shared_rank(plane, r);
+  const float s = 1.0f / (4.0f * N * N);
+  float2* dst = Sout + (size_t)kt * out_pitch;
+  if (out_cols == nullptr) {
+    constexpr int ITEMS = ROWS * M;
+    for (int i = tid; i < ITEMS; i += C::THREADS) {
+      const int x = x0 + i / M, n = i % M;
+      const int a = x * M + (n ^ swz<N>(x));
+      const float2 v0 = pr[0][a], v1 = pr[1][a], v2 = pr[2][a], v3 = pr[3][a];
+      const float2 e02 = cadd(v0, v2), d02 = csub(v0, v2);
+      const float2 e13 = cadd(v1, v3), d13 = csub(v1, v3);
+      // h = 0: v0 + v1 + v2 + v3; h = 1: v0 + i v1 - v2 - i v3
+      dst[x * N + n] = cscale(cadd(e02, e13), s);
+      dst[x * N + n + M] = cscale(make_float2(d02.x - d13.y, d02.y + d13.x), s);
+    }
+  } else {
+    for (int j = tid; j < out_n; j += C::THREADS) {
+      const int col = __ldg(out_cols + j), x = col / N;
+      if (x < x0 || x >= x0 + ROWS) continue;
+      const int y = col % N, n = y % M, h = y / M;
+      const int a = x * M + (n ^ swz<N>(x));
+      const float2 v0 = pr[0][a], v1 = pr[1][a], v2 = pr[2][a], v3 = pr[3][a];
+      float2 o;
+      if (h == 0) {
+        o = cadd(cadd(v0, v2), cadd(v1, v3));
+      } else {
+        const float2 d02 = csub(v0, v2), d13 = csub(v1, v3);
+        o = make_float2(d02.x - d13.y, d02.y + d13.x);
+      }
+      dst[j] = cscale(o, s);
+    }
+  }
+  cluster.sync();  // keep this CTA's plane alive until the others have read it
+}
+
+size_t conv4_smem_bytes(int n) {
+  switch (n) {
+    case 32: return C4<32>::smem;
+    case 64: return C4<64>::smem;
+    case 128: return C4<128>::smem;
+  }
+  return 0;
+}
+
+nlos_status prepare_conv4(int n) {
+  switch (n) {
+    case 32: return ensure_smem(k_conv4<32>, C4<32>::smem);
+    case 64: return ensure_smem(k_conv4<64>, C4<64>::smem);
+    case 128: return ensure_smem(k_conv4<128>, C4<128>::smem);
+  }
+  return NLOS_OK;
+}
+
+nlos_status launch_conv4(const Plan& P, const float2* Sin, bool in_compact, float2* Sout, bool out_compact, bool adj,
+                         cudaStream_t st) {
+  const int full = P.nx * P.ny;
+  const int in_pitch = in_compact ? P.ncols : full, out_pitch = out_compact ? P.ncols : full;
+  if (!in_compact && (reinterpret_cast<uintptr_t>(Sin) & 15) != 0)
+    return fail(NLOS_ERR_INVALID_ARG, "conv4: input spectrum must be 16-byte aligned");
+  auto go = [&](auto kern, size_t smem) -> nlos_status {
+    NLOS_TRY(ensure_smem(kern, smem));
+    kern<<<4 * (P.nt + 1), 256, smem, st>>>(Sin, in_pitch, in_compact ? P.d_cols : nullptr, P.ncols, Sout,
+                                            out_pitch, out_compact ? P.d_cols : nullptr, P.ncols, P.d_H,
+                                            adj ? 1 : 0, P.d_twx);
+    NLOS_LAUNCH_CHECK("k_conv4");
+    return NLOS_OK;
+  };
+  switch (P.nx) {
+    case 32: return go(k_conv4<32>, C4<32>::smem);
+    case 64: return go(k_conv4<64>, C4<64>::smem);
+    case 128: return go(k_conv4<128>, C4<128>::smem);
+  }
+  return fail(NLOS_ERR_INVALID_ARG, "conv4: unsupported nx");
+}
+
+}  // namespace nlos

@@ -58,6 +58,11 @@ nlos_status launch_sinv(const Plan& P, const float2* Sp, int ncols, float* x, co
 // (the plan's sampled columns) with plane pitch ncols.
 nlos_status launch_conv(const Plan& P, const float2* Sin, bool in_compact, float2* Sout, bool out_compact,
                         bool adj, cudaStream_t st);
+// Four-CTA-cluster lateral convolution for nx in {32, 64, 128} (conv4.cu);
+// launch_conv dispatches to it.
+nlos_status launch_conv4(const Plan& P, const float2* Sin, bool in_compact, float2* Sout, bool out_compact,
+                         bool adj, cudaStream_t st);
+nlos_status prepare_conv4(int n);
 // Periodic lateral solve per kt plane: divide by c0 + c1 (lx + ly + lt).
 nlos_status launch_sxy(const Plan& P, float2* Sp, const DevScalars* sc, double c0_host, double c1,
                        cudaStream_t st);

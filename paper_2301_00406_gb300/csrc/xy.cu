@@ -359,7 +359,10 @@ static nlos_status set_smem(K kernel, size_t bytes) {
 nlos_status prepare_xy(int n) {
   return dispatch_n(n, [&](auto nc) -> nlos_status {
     constexpr int N = decltype(nc)::value;
-    NLOS_TRY(set_smem(k_conv<N>, CV<N>::smem));
+    if (N >= 32)
+      NLOS_TRY(prepare_conv4(N));
+    else
+      NLOS_TRY(set_smem(k_conv<N>, CV<N>::smem));
     NLOS_TRY(set_smem(k_sxy<N>, sizeof(float2) * (N * (N + 1) + 2 * N)));
     NLOS_TRY(set_smem(k_kspec<N>, sizeof(float2) * (N * (N + 1) + 2 * N)));
     return NLOS_OK;
@@ -369,6 +372,7 @@ nlos_status prepare_xy(int n) {
 nlos_status launch_conv(const Plan& P, const float2* Sin, bool in_compact, float2* Sout, bool out_compact, bool adj,
                         cudaStream_t st) {
   KTimer kt_(P, KC_CONV, st);
+  if (P.nx >= 32) return launch_conv4(P, Sin, in_compact, Sout, out_compact, adj, st);
   return dispatch_n(P.nx, [&](auto nc) -> nlos_status {
     constexpr int N = decltype(nc)::value;
     auto kern = k_conv<N>;

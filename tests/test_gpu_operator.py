@@ -28,6 +28,8 @@ CASES = [
     (16, 1024, "compensated", "random"),   # nt = 1024 path (8 columns per CTA)
     (32, 128, "compensated", "ragged"),    # sampled count not a multiple of 16
     (64, 512, "compensated", "stride2"),
+    (64, 256, "compensated", "random"),    # four-CTA lateral pass, scattered sampled rows
+    (128, 64, "compensated", "ragged"),    # four-CTA lateral pass at N = 128, ragged sample list
 ]
 
 
@@ -129,6 +131,19 @@ def test_forward_full_size_sampled_columns(nlos):
     vol = synth.scene_patches(n, n, nt, 0)
     got = host(nlos.forward_t(plan, dev(vol), apply_mask=True))
     want = lct.Operator(g, mask).forward_d(vol)
+    assert rel_l2(got, want) < TOL
+
+
+def test_adjoint_full_size_sampled_columns(nlos):
+    # 128 x 128 x 512: A_D^T of a measurement on the 32 x 32 sampled grid
+    n, nt, bw = 128, 512, 16e-12
+    g = lct.Geometry(n, n, nt, bw)
+    mask = synth.stride_mask(n, n, 4)
+    plan = nlos.Plan(n, n, nt, bw, mask=mask)
+    rng = np.random.default_rng(11)
+    tau = (rng.random((n, n, nt)) * mask[:, :, None]).astype(np.float32)
+    got = host(nlos.adjoint_t(plan, dev(tau), apply_mask=True))
+    want = lct.Operator(g, mask).adjoint_d(tau.astype(np.float64))
     assert rel_l2(got, want) < TOL
 
 
