@@ -74,12 +74,14 @@ __global__ void k_scale(float* __restrict__ a, const double* __restrict__ s, siz
 // partials[b][0] = sum a^2 (optionally only over columns with colpos >= 0)
 __global__ void __launch_bounds__(kStencilThreads)
     k_sumsq(const float* __restrict__ a, size_t n, double* __restrict__ partials) {
-  double acc[1] = {0.0};
+  ChunkAcc<1> ca;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double v = __ldg(a + i);
-    acc[0] += v * v;
+    const float v = __ldg(a + i);
+    ca.add(0, v * v);
+    ca.step();
   }
-  block_reduce_to<1>(acc, partials);
+  ca.flush();
+  block_reduce_to<1>(ca.tot, partials);
 }
 
 // Deterministic block-wide sums of per-block partials: thread i adds the
@@ -175,7 +177,7 @@ __global__ void __launch_bounds__(kStencilThreads)
             Vox g, VoxIter vi, float mu, float a, float b, int kind, float eps2, size_t V, double* __restrict__ partials) {
   const float inv_mu = 1.0f / mu;
   const float beta = (float)sc->beta;
-  double acc[2] = {0.0, 0.0};
+  ChunkAcc<2> ca;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V; i += (size_t)gridDim.x * blockDim.x) {
     int x, y, t;
     vi.decode(i, g, x, y, t);
@@ -190,10 +192,12 @@ __global__ void __launch_bounds__(kStencilThreads)
     ph[i] = pn;
     const float un = __ldg(unew + i);
     ubn[i] = un + beta * (un - __ldg(uk + i));
-    acc[0] += (double)pn * (double)sqrtf(gu.x * gu.x + gu.y * gu.y + gu.z * gu.z);
-    acc[1] += (double)d.x * d.x + (double)d.y * d.y + (double)d.z * d.z;
+    ca.add(0, pn * sqrtf(gu.x * gu.x + gu.y * gu.y + gu.z * gu.z));
+    ca.add(1, d.x * d.x + d.y * d.y + d.z * d.z);
+    ca.step();
   }
-  block_reduce_to<2>(acc, partials);
+  ca.flush();
+  block_reduce_to<2>(ca.tot, partials);
 }
 
 // ---------------------------------------------------------------------------
@@ -260,7 +264,7 @@ __global__ void __launch_bounds__(kStencilThreads)
             VoxIter vi, Alg2Coef c, size_t V, double* __restrict__ partials) {
   const float im1 = 1.0f / c.mu1, im2 = 1.0f / c.mu2;
   const float beta = (float)sc->beta;
-  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  ChunkAcc<7> ca;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V; i += (size_t)gridDim.x * blockDim.x) {
     int x, y, t;
     vi.decode(i, g, x, y, t);
@@ -290,15 +294,17 @@ __global__ void __launch_bounds__(kStencilThreads)
     tbn[i] = tn + beta * (tn - __ldg(tk + i));
     const float r = __ldg(au + i) - tn;
     const float s = m * (tn - t0);
-    acc[0] += (double)pu * (double)sqrtf(gu.x * gu.x + gu.y * gu.y + gu.z * gu.z);
-    acc[1] += (double)pt * (double)sqrtf(gt.x * gt.x + gt.y * gt.y + gt.z * gt.z);
-    acc[2] += (double)r * r;
-    acc[3] += (double)s * s;
-    acc[4] += (double)dv.x * dv.x + (double)dv.y * dv.y + (double)dv.z * dv.z;
-    acc[5] += (double)dw.x * dw.x + (double)dw.y * dw.y + (double)dw.z * dw.z;
-    acc[6] += (double)(f - tn) * (f - tn);
+    ca.add(0, pu * sqrtf(gu.x * gu.x + gu.y * gu.y + gu.z * gu.z));
+    ca.add(1, pt * sqrtf(gt.x * gt.x + gt.y * gt.y + gt.z * gt.z));
+    ca.add(2, r * r);
+    ca.add(3, s * s);
+    ca.add(4, dv.x * dv.x + dv.y * dv.y + dv.z * dv.z);
+    ca.add(5, dw.x * dw.x + dw.y * dw.y + dw.z * dw.z);
+    ca.add(6, (f - tn) * (f - tn));
+    ca.step();
   }
-  block_reduce_to<7>(acc, partials);
+  ca.flush();
+  block_reduce_to<7>(ca.tot, partials);
 }
 
 // Algorithm 2, elementwise part of the post step: Lambda_3 += mu3 (f - tau+),
@@ -307,7 +313,7 @@ __global__ void __launch_bounds__(kStencilThreads)
     k_lam3(const float* __restrict__ tnew, const float* __restrict__ tb, const float* __restrict__ au,
            const float* __restrict__ tau0, float* __restrict__ lam3, const int32_t* __restrict__ colpos, Vox g,
            VoxIter vi, float lam_w, float mu3, size_t V, double* __restrict__ partials) {
-  double acc[3] = {0.0, 0.0, 0.0};
+  ChunkAcc<3> ca;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V; i += (size_t)gridDim.x * blockDim.x) {
     int x, y, t;
     vi.decode(i, g, x, y, t);
@@ -316,11 +322,13 @@ __global__ void __launch_bounds__(kStencilThreads)
     const float f = (lam_w * m * t0 + mu3 * __ldg(tb + i) - l3) / (lam_w * m + mu3);
     lam3[i] = l3 + mu3 * (f - tn);
     const float r = __ldg(au + i) - tn, sres = m * (tn - t0), fr = f - tn;
-    acc[0] += (double)r * r;
-    acc[1] += (double)sres * sres;
-    acc[2] += (double)fr * fr;
+    ca.add(0, r * r);
+    ca.add(1, sres * sres);
+    ca.add(2, fr * fr);
+    ca.step();
   }
-  block_reduce_to<3>(acc, partials);
+  ca.flush();
+  block_reduce_to<3>(ca.tot, partials);
 }
 
 // rhs of the tau-solve: x = A u+ + regt (used as the input of the periodic FFT)

@@ -83,6 +83,39 @@ struct DevScalars {
 // Number of FP64 partial-sum slots per block used by the reductions.
 constexpr int kMaxTerms = 8;
 
+// Per-thread accumulation of T sums: FP32 partial sums over chunks of at most
+// kChunk terms, each chunk added to an FP64 total in a fixed order.  FP64
+// arithmetic runs at a small fraction of the FP32 rate on this GPU, so an FP64
+// add per term would dominate an otherwise bandwidth-bound epilogue; a float
+// sum of 16 terms adds at most about 1e-6 relative rounding per chunk.
+template <int T>
+struct ChunkAcc {
+  static constexpr int kChunk = 16;
+  double tot[T];
+  float cur[T];
+  int n;
+  __device__ __forceinline__ ChunkAcc() : n(0) {
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+      tot[t] = 0.0;
+      cur[t] = 0.f;
+    }
+  }
+  __device__ __forceinline__ void add(int t, float v) { cur[t] += v; }
+  __device__ __forceinline__ void flush() {
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+      tot[t] += (double)cur[t];
+      cur[t] = 0.f;
+    }
+    n = 0;
+  }
+  // call once per term group (after the add()s of one element)
+  __device__ __forceinline__ void step() {
+    if (++n == kChunk) flush();
+  }
+};
+
 // ---------------------------------------------------------------------------
 // Plan
 // ---------------------------------------------------------------------------

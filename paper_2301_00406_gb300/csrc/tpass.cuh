@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(kTpassThreads)
   __syncthreads();
   tinv_core<NT>(S, pitch, col0, ncols, work, cbuf, tw2, PAIRS, tid, nthr);
 
-  double acc[2] = {0.0, 0.0};
+  ChunkAcc<2> ca;
   float bp = 0.f;
   if (EPI == 1) bp = (float)fa.sc->beta_prev;
   const int total = min(COLS, ncols - col0) * NT;
@@ -310,11 +310,15 @@ __global__ void __launch_bounds__(kTpassThreads)
         if (EPI == 1) {
           const float r = tau - in.x;
           const float d = tau - ((1.0f + bp) * in.y - bp * in.z);
-          acc[0] += (double)r * (double)r;
-          acc[1] += (double)d * (double)d;
+          ca.add(0, r * r);
+          ca.add(1, d * d);
+          ca.step();
         }
       });
-  if (EPI == 1) block_reduce_store<2>(acc, fa.partials);
+  if (EPI == 1) {
+    ca.flush();
+    block_reduce_store<2>(ca.tot, fa.partials);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -463,7 +467,7 @@ __global__ void __launch_bounds__(kTpassThreads)
   __syncthreads();
   team_fft<NT, true>(work, PAIRS, WP, 1, tw2, 2, tid, nthr);
   const float scale = 1.0f / NT;
-  double acc[1] = {0.0};
+  ChunkAcc<1> ca;
   const int total = min(COLS, ncols - col0) * NT;
   batched_copy<8, float>(
       total, tid, nthr, [&](int i) { return ref ? __ldg(ref + (size_t)col0 * NT + i) : 0.f; },
@@ -474,10 +478,14 @@ __global__ void __launch_bounds__(kTpassThreads)
         x[(size_t)col0 * NT + i] = v;
         if (ref) {
           const float d = v - rv;
-          acc[0] += (double)d * (double)d;
+          ca.add(0, d * d);
+          ca.step();
         }
       });
-  if (partials) block_reduce_store<1>(acc, partials);
+  if (partials) {
+    ca.flush();
+    block_reduce_store<1>(ca.tot, partials);
+  }
 }
 
 
