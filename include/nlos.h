@@ -88,6 +88,10 @@ typedef struct {
   double eps_normal;     /* regulariser of |grad u| in the normal field                     */
   int32_t restart;       /* FISTA restart on energy increase: 0 off, 1 on, -1 model default
                             (off for model 1, on for model 2)                              */
+  int32_t warm_start_iters; /* model 2 only: first run this many Algorithm-1 iterations
+                            (a, b, mu, default L0, no restart) and start Algorithm 2 from
+                            their u (the remark after Algorithm 2; tau starts at 0);
+                            0 = start from u = 0.  Ignored for model 1; < 0 is an error. */
 } nlos_params;
 
 /* Per-reconstruction statistics (host struct, filled after the run). */
@@ -114,7 +118,8 @@ int32_t nlos_version(void);
  * settings of Sec. 5.2.1 (a = 9e-5, b = 2e-5, mu = 0.1; lambda = 235,
  * a_tau = 4e-4, b_tau = 3e-2, a_u = 2e-4, b_u = 4.5e-4), mu1..3 = 1, 800, 2 and
  * T_max = 200 / 300 (Sec. 5.1), eps_stop = 0, L0 = 0 (= 2||A_D||^2), eta = 2,
- * max_backtracks = 30, eps_normal = 1e-6, restart = -1.  Host only. */
+ * max_backtracks = 30, eps_normal = 1e-6, restart = -1, warm_start_iters = 0.
+ * Host only. */
 nlos_status nlos_params_default(int32_t model, nlos_params* out);
 
 /* Create a plan for one geometry (Sec. 2, Eq. 3): builds the R_z and R_t^{-1}

@@ -440,17 +440,39 @@ __global__ void __launch_bounds__(kSumThreads)
   if (eps_stop > 0.0 && e <= eps_stop) sc->stop = 1;
 }
 
+// Initial scalar block; E_prev = s0 sum(pe0) + s1 sum(pe1) + s2 sum(pe2) over
+// the nb block partials of each (pe1, pe2 nullable).
 __global__ void __launch_bounds__(kSumThreads)
-    k_init_scalars(DevScalars* sc, double L0, const double* __restrict__ pe, int nb, double e_scale) {
+    k_init_scalars(DevScalars* sc, double L0, int nb, const double* __restrict__ pe0, double s0,
+                   const double* __restrict__ pe1, double s1, const double* __restrict__ pe2, double s2) {
   const int t0[1] = {0};
-  double v[1];
-  sum_partials_block<1>(pe, nb, t0, v);
+  double v0[1], v1[1] = {0.0}, v2[1] = {0.0};
+  sum_partials_block<1>(pe0, nb, t0, v0);
+  if (pe1) sum_partials_block<1>(pe1, nb, t0, v1);
+  if (pe2) sum_partials_block<1>(pe2, nb, t0, v2);
   if (threadIdx.x != 0) return;
   memset(sc, 0, sizeof(DevScalars));
   sc->L = L0;
   sc->t = 1.0;
-  sc->E_prev = e_scale * v[0];
+  sc->E_prev = s0 * v0[0] + s1 * v1[0] + s2 * v2[0];
   sc->status = NLOS_OK;
+}
+
+// partials[b][0] = sum phi |grad u| (forward differences, periodic): the
+// curvature-weighted TV term of the energy at a given u.
+__global__ void __launch_bounds__(kStencilThreads)
+    k_tv_weighted(const float* __restrict__ u, const float* __restrict__ ph, Vox g, VoxIter vi, size_t V,
+                  double* __restrict__ partials) {
+  ChunkAcc<1> ca;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V; i += (size_t)gridDim.x * blockDim.x) {
+    int x, y, t;
+    vi.decode(i, g, x, y, t);
+    const float3 gu = grad_at(u, g, x, y, t);
+    ca.add(0, __ldg(ph + i) * sqrtf(gu.x * gu.x + gu.y * gu.y + gu.z * gu.z));
+    ca.step();
+  }
+  ca.flush();
+  block_reduce_to<1>(ca.tot, partials);
 }
 
 // ---------------------------------------------------------------------------
@@ -759,14 +781,30 @@ static float phi_zero(double a, double b, int kind) {
   return kind == NLOS_PHI_TRV ? (float)std::sqrt(a) : (float)a;
 }
 
+// E_prev = scale * sum(sumsq_src^2) (+ 1/2 ||A u0||^2 + sum phi |grad u0| when
+// `au0` is given: the energy of a warm-started Algorithm 2 at (u0, tau = 0)).
 static nlos_status init_scalars(Plan& P, SolverState* s, double L0, const float* sumsq_src, size_t n, double scale,
-                                cudaStream_t st) {
+                                cudaStream_t st, const float* au0 = nullptr, const float* u0 = nullptr,
+                                const float* ph0 = nullptr) {
   { KTimer kt_(P, KC_SMALL, st);
   k_sumsq<<<kStencilBlocks, kStencilThreads, 0, st>>>(sumsq_src, n, s->pc);
   }
   NLOS_LAUNCH_CHECK("k_sumsq");
+  if (au0) {
+    const Vox g = make_vox(P.nx, P.ny, P.nt);
+    const VoxIter vi{ilog2i(P.nt), ilog2i(P.ny)};
+    { KTimer kt_(P, KC_SMALL, st);
+    k_sumsq<<<kStencilBlocks, kStencilThreads, 0, st>>>(au0, s->V, s->pa);
+    }
+    NLOS_LAUNCH_CHECK("k_sumsq");
+    { KTimer kt_(P, KC_SMALL, st);
+    k_tv_weighted<<<kStencilBlocks, kStencilThreads, 0, st>>>(u0, ph0, g, vi, s->V, s->pb);
+    }
+    NLOS_LAUNCH_CHECK("k_tv_weighted");
+  }
   { KTimer kt_(P, KC_SMALL, st);
-  k_init_scalars<<<1, kSumThreads, 0, st>>>(s->sc, L0, s->pc, kStencilBlocks, scale);
+  k_init_scalars<<<1, kSumThreads, 0, st>>>(s->sc, L0, kStencilBlocks, s->pc, scale, au0 ? s->pa : nullptr, 0.5,
+                                            au0 ? s->pb : nullptr, 1.0);
   }
   NLOS_LAUNCH_CHECK("k_init_scalars");
   return NLOS_OK;
@@ -778,7 +816,8 @@ static nlos_status init_scalars(Plan& P, SolverState* s, double L0, const float*
 // single reconstruction runs the steps back to back; the batch and the
 // server interleave the steps of many jobs on their own streams.
 // ---------------------------------------------------------------------------
-nlos_status job_init(JobRun& j) {
+// Initial state of the run j.p (u0 = u_init for model 2 when given, else 0).
+static nlos_status init_run(JobRun& j, const float* u_init) {
   Plan& P = *j.P;
   const nlos_params& p = j.p;
   cudaStream_t st = j.st;
@@ -804,17 +843,55 @@ nlos_status job_init(JobRun& j) {
     NLOS_TRY(gather_columns(P, j.tau0, s->tau0c, st));
     NLOS_TRY(init_scalars(P, s, j.L0, s->tau0c, C, 0.5, st));
   } else {
-    for (float* f : {s->uk, s->ub, s->tk, s->tb, s->lam3}) NLOS_TRY(zero(f, V, st));
+    for (float* f : {s->tk, s->tb, s->lam3}) NLOS_TRY(zero(f, V, st));
     NLOS_TRY(zero(s->lam, 3 * V, st));
     NLOS_TRY(zero(s->lam2, 3 * V, st));
-    for (int i = 0; i < 3; ++i) NLOS_TRY(zero(s->cache[i], V, st));
-    NLOS_TRY(fill(s->ph, phi_zero(p.a_u, p.b_u, p.phi), V, st));
+    if (u_init) {
+      // warm start: u0 = u-bar0 = u_init, cached A u0 (u-bar0 = u0, so A u^{-1} = A u0),
+      // phi_u = phi(kappa(u0))
+      NLOS_CUDA(cudaMemcpyAsync(s->uk, u_init, V * sizeof(float), cudaMemcpyDeviceToDevice, st));
+      NLOS_CUDA(cudaMemcpyAsync(s->ub, u_init, V * sizeof(float), cudaMemcpyDeviceToDevice, st));
+      NLOS_TRY(apply_forward(P, s->uk, s->cache[j.cur], false, st));
+      NLOS_CUDA(cudaMemcpyAsync(s->cache[j.prev], s->cache[j.cur], V * sizeof(float), cudaMemcpyDeviceToDevice,
+                                st));
+      NLOS_TRY(zero(s->cache[j.nxt], V, st));
+      NLOS_TRY(apply_curvature_weight(P, s->uk, s->ph, p.a_u, p.b_u, p.phi, p.eps_normal, st));
+    } else {
+      NLOS_TRY(zero(s->uk, V, st));
+      NLOS_TRY(zero(s->ub, V, st));
+      for (int i = 0; i < 3; ++i) NLOS_TRY(zero(s->cache[i], V, st));
+      NLOS_TRY(fill(s->ph, phi_zero(p.a_u, p.b_u, p.phi), V, st));
+    }
     NLOS_TRY(fill(s->pht, phi_zero(p.a_tau, p.b_tau, p.phi), V, st));
-    // E(0, 0) = lambda/2 ||tau0||^2 over the sampled columns
+    // E(u0, 0) = lambda/2 ||tau0||^2 over the sampled columns (+ 1/2 ||A u0||^2
+    // + sum phi_u |grad u0| for a warm start)
     NLOS_TRY(gather_columns(P, j.tau0, s->tmp, st));
-    NLOS_TRY(init_scalars(P, s, j.L0, s->tmp, (size_t)P.ncols * P.nt, 0.5 * p.lambda, st));
+    NLOS_TRY(init_scalars(P, s, j.L0, s->tmp, (size_t)P.ncols * P.nt, 0.5 * p.lambda, st,
+                          u_init ? s->cache[j.cur] : nullptr, s->uk, s->ph));
   }
   return NLOS_OK;
+}
+
+// Parameters of the Algorithm-1 warm stage of model-2 parameters p.
+static nlos_params warm_params(const nlos_params& p) {
+  nlos_params w = p;
+  w.model = 1;
+  w.iters = p.warm_start_iters;
+  w.eps_stop = 0.0;
+  w.L0 = 0.0;
+  w.restart = 0;
+  w.warm_start_iters = 0;
+  return w;
+}
+
+nlos_status job_init(JobRun& j) {
+  j.phase = 0;
+  if (j.p.model == 2 && j.p.warm_start_iters > 0) {
+    j.main_p = j.p;
+    j.p = warm_params(j.main_p);
+    j.phase = 1;
+  }
+  return init_run(j, nullptr);
 }
 
 bool job_async(const JobRun& j) { return j.p.eps_stop <= 0.0 && j.L0 >= 1.5 * j.norm2; }
@@ -961,6 +1038,13 @@ nlos_status job_step(JobRun& j) {
     NLOS_TRY(read_scalars(j.s, j.st));
     if (j.s->h_sc->stop || j.s->h_sc->status != NLOS_OK) j.done = true;
   }
+  if (j.done && j.phase == 1) {
+    // warm stage finished: Algorithm 2 from the Algorithm-1 result
+    const float* u_warm = j.s->uk;
+    j.p = j.main_p;
+    j.phase = 2;
+    NLOS_TRY(init_run(j, u_warm));
+  }
   return NLOS_OK;
 }
 
@@ -992,9 +1076,15 @@ nlos_status job_enqueue_graph(JobRun& j, cudaStream_t launch, bool* used) {
   Plan& P = *j.P;
   const nlos_params& p = j.p;
   if (P.timing) return NLOS_OK;
-  // everything that may synchronise happens before the capture
+  // everything that may synchronise or allocate happens before the capture
   NLOS_TRY(get_solver(P, p.model, &j.s));
   NLOS_TRY(plan_norm2(P, p.model == 1, launch, &j.norm2));
+  if (p.model == 2 && p.warm_start_iters > 0) {
+    SolverState* s1 = nullptr;
+    double n1 = 0.0;
+    NLOS_TRY(get_solver(P, 1, &s1));
+    NLOS_TRY(plan_norm2(P, true, launch, &n1));
+  }
   const double L0 = p.L0 > 0.0 ? p.L0 : 2.0 * j.norm2;
   if (p.eps_stop > 0.0 || L0 < 1.5 * j.norm2 || p.iters <= 0) return NLOS_OK;
   for (auto& g : P.graphs)

@@ -241,6 +241,8 @@ Plan* plan_clone_workspace(const Plan& base, nlos_status* status);
 void plan_release(Plan* P);
 // Bytes of device memory a workspace clone plus the solver state of `model`
 // occupy (the shared tables excluded), and of the shared tables alone.
+// Device bytes of a workspace clone plus the solver state of `model` (1, 2,
+// or 3 = both, a model-2 run with an Algorithm-1 warm stage).
 size_t workspace_bytes(const Plan& P, int model);
 size_t shared_table_bytes(const Plan& P);
 nlos_status create_plan_internal(const nlos_geometry* g, cudaStream_t st, Plan** out);
@@ -261,6 +263,11 @@ struct JobRun {
   int it = 0;
   int cur = 0, prev = 1, nxt = 2;  // rotation of the cached A u iterates
   bool done = false;
+  // Algorithm-1 warm stage of a model-2 run: while phase == 1, p holds the
+  // warm-stage parameters and main_p the run's own; job_step switches to
+  // Algorithm 2 (phase 2) when the warm stage is done.
+  int phase = 0;
+  nlos_params main_p{};
 };
 // Allocates the solver state on first use, computes (once per plan) the
 // operator norm with a host synchronisation, and enqueues the initial state.

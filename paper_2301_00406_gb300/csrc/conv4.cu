@@ -18,9 +18,11 @@
 // one exchange through shared memory.
 //
 // Phases of one CTA (q = rank in the cluster):
-//  1. stage rows [q N/4, (q+1) N/4) of the input plane in shared memory;
-//  2. y transform of all N rows (rows read from the four CTAs' staging
-//     buffers through distributed shared memory) -> plane[x][k], k < M;
+//  1. compact input only: scatter the sampled values of rows
+//     [q N/4, (q+1) N/4) into a zeroed staging buffer;
+//  2. y transform of all N rows (a dense input plane read from global
+//     memory, a compact one from the four CTAs' staging buffers through
+//     distributed shared memory) -> plane[x][k], k < M;
 //  3. x convolution, one warp per column: fold by the four x parities,
 //     forward M-point transforms, multiply by H, inverse, recombine across
 //     the parity lanes with warp shuffles, back into the column;
@@ -98,8 +100,8 @@ __device__ __forceinline__ int fold_k(int k) {
 // Phase 2: forward y transform of every row for bins ky = 4 k + Q.
 template <int N, int Q>
 __device__ __forceinline__ void c4_yfwd(float2* __restrict__ plane, const float2* const (&stage)[4],
-                                        const float2* __restrict__ tw, const int* __restrict__ rowin, int warp,
-                                        int lane) {
+                                        const float2* __restrict__ gsrc, const float2* __restrict__ tw,
+                                        const int* __restrict__ rowin, int warp, int lane) {
   using C = C4<N>;
   constexpr int M = C::M, R2 = C::R2, RW = C::RW, SP = C::SP, ROWS = C::ROWS;
   const int rsub = lane / R2, n2 = lane % R2;
@@ -111,16 +113,48 @@ __device__ __forceinline__ void c4_yfwd(float2* __restrict__ plane, const float2
 #pragma unroll
     for (int k1 = 1; k1 < 8; ++k1) twa[k1] = cmul(twa[k1 - 1], st);
   }
+  // Rows come from global memory (gsrc, a dense plane) or from the four
+  // CTAs' staging buffers (distributed shared memory); either way the next
+  // row group's 16 values per lane are fetched while the current one computes.
+  float2 pu[8], pv[8];
+  auto fetch = [&](int it) {
+    const int x = it * RW + rsub;
+    if (it < N / RW && rowin[x]) {
+      if (gsrc) {
+        const float2* row = gsrc + x * N;
+#pragma unroll
+        for (int n1 = 0; n1 < 8; ++n1) {
+          pu[n1] = __ldg(row + n2 + R2 * n1);
+          pv[n1] = __ldg(row + n2 + R2 * n1 + M);
+        }
+      } else {
+        const int o = x / ROWS;
+        const float2* row =
+            (o == 0 ? stage[0] : o == 1 ? stage[1] : o == 2 ? stage[2] : stage[3]) + (x % ROWS) * SP;
+#pragma unroll
+        for (int n1 = 0; n1 < 8; ++n1) {
+          pu[n1] = row[n2 + R2 * n1];
+          pv[n1] = row[n2 + R2 * n1 + M];
+        }
+      }
+    }
+  };
+  fetch(warp);
   for (int it = warp; it < N / RW; it += C::WARPS) {
     {
       const int x = it * RW + rsub;
+      float2 cu[8], cv[8];
+#pragma unroll
+      for (int n1 = 0; n1 < 8; ++n1) {
+        cu[n1] = pu[n1];
+        cv[n1] = pv[n1];
+      }
+      fetch(it + C::WARPS);
       if (rowin[x]) {
-        const int o = x / ROWS;
-        const float2* row = (o == 0 ? stage[0] : o == 1 ? stage[1] : o == 2 ? stage[2] : stage[3]) + (x % ROWS) * SP;
         float2 a[8];
 #pragma unroll
         for (int n1 = 0; n1 < 8; ++n1) {
-          const float2 u = row[n2 + R2 * n1], v = row[n2 + R2 * n1 + M];
+          const float2 u = cu[n1], v = cv[n1];
           // (-i)^Q v and the fold twist w^(Q R2 n1) = exp(-2 pi i Q n1 / 32)
           const float2 r = Q == 0 ? v : Q == 1 ? make_float2(v.y, -v.x) : Q == 2 ? make_float2(-v.x, -v.y)
                                                                              : make_float2(-v.y, v.x);
@@ -260,8 +294,24 @@ __device__ __forceinline__ void c4_xconv(float2* __restrict__ plane, float2* __r
   }
   const int sn2 = swz<N>(n2);
   float2* myscr = scr + (cs * 4 + p) * SPX;
+  // H of this lane's step-B items (CW columns x R2 bins), fetched before step A
+  // so the global-load latency overlaps it; conjugated for the adjoint
+  auto fetch_h = [&](int cb, float2 (&h)[CW][R2]) {
+#pragma unroll
+    for (int j = 0; j < CW; ++j) {
+      const float2* hrow = Hk + fold_k<N>(4 * (cb + j) + q) * (N + 1);
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) {
+        float2 v = __ldg(hrow + fold_k<N>(4 * (k1B + 8 * k2) + pB));
+        if (adj) v.y = -v.y;
+        h[j][k2] = v;
+      }
+    }
+  };
   for (int cb = warp * CW; cb < M; cb += C::WARPS * CW) {
     const int c = cb + cs;
+    float2 hv[CW][R2];
+    fetch_h(cb, hv);
     // A: fold, first step, twiddles -> scratch
     {
       float2 a[8];
@@ -280,19 +330,13 @@ __device__ __forceinline__ void c4_xconv(float2* __restrict__ plane, float2* __r
     // B: second step, multiply by H, inverse second step, inverse twiddles
 #pragma unroll
     for (int j = 0; j < CW; ++j) {
-      const int cc = cb + j;
-      const int ky = fold_k<N>(4 * cc + q);
-      const float2* hrow = Hk + ky * (N + 1);
       float2* s = scr + (j * 4 + pB) * SPX;
-      float2 h[R2];
-#pragma unroll
-      for (int k2 = 0; k2 < R2; ++k2) h[k2] = __ldg(hrow + fold_k<N>(4 * (k1B + 8 * k2) + pB));
       float2 b[R2];
 #pragma unroll
       for (int m = 0; m < R2; ++m) b[m] = s[ipos(m, k1B)];
       dft_reg<R2, false>(b);
 #pragma unroll
-      for (int k2 = 0; k2 < R2; ++k2) b[k2] = adj ? cmulc(b[k2], h[k2]) : cmul(b[k2], h[k2]);
+      for (int k2 = 0; k2 < R2; ++k2) b[k2] = cmul(b[k2], hv[j][k2]);
       dft_reg<R2, true>(b);
 #pragma unroll
       for (int m = 0; m < R2; ++m) s[ipos(m, k1B)] = m == 0 ? b[0] : cmul(b[m], twb[m]);
@@ -361,16 +405,19 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(256, 2)
   if (out_cols)
     for (int j = tid; j < out_n; j += C::THREADS) rowout[__ldg(out_cols + j) / N] = 1;
 
-  // 1. stage this CTA's quarter of the input rows
+  // 1-2. forward y transform.  A dense input plane is read straight from
+  // global memory (each row by the four CTAs, the three later reads mostly
+  // L2 hits); a compact one (sampled columns) is first scattered, a quarter
+  // of the rows per CTA, into the staging buffers and read from there
+  // through distributed shared memory.
   const float2* src = Sin + (size_t)kt * in_pitch;
+  const float2* stage[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) stage[r] = cluster.map_shared_rank(region, r);
+  const float2* gsrc = nullptr;
   if (in_cols == nullptr) {
-    const float4* s4 = reinterpret_cast<const float4*>(src + (size_t)x0 * N);
-    batched_copy<8, float4>(
-        ROWS * N / 2, tid, C::THREADS, [&](int i) { return __ldg(s4 + i); },
-        [&](int i, float4 v) {
-          const int r = i / (N / 2), c2 = i % (N / 2);
-          *reinterpret_cast<float4*>(region + r * SP + 2 * c2) = v;
-        });
+    gsrc = src;
+    __syncthreads();
   } else {
     for (int i = tid; i < ROWS * SP; i += C::THREADS) region[i] = make_float2(0.f, 0.f);
     __syncthreads();
@@ -380,20 +427,18 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(256, 2)
           const int col = __ldg(in_cols + j), x = col / N;
           if (x >= x0 && x < x0 + ROWS) region[(x - x0) * SP + col % N] = v;
         });
+    cluster.sync();
   }
-  cluster.sync();
-
-  // 2. forward y transform (rows read from the four staging buffers)
-  const float2* stage[4];
-#pragma unroll
-  for (int r = 0; r < 4; ++r) stage[r] = cluster.map_shared_rank(region, r);
   switch (q) {
-    case 0: c4_yfwd<N, 0>(plane, stage, tw, rowin, warp, lane); break;
-    case 1: c4_yfwd<N, 1>(plane, stage, tw, rowin, warp, lane); break;
-    case 2: c4_yfwd<N, 2>(plane, stage, tw, rowin, warp, lane); break;
-    default: c4_yfwd<N, 3>(plane, stage, tw, rowin, warp, lane); break;
+    case 0: c4_yfwd<N, 0>(plane, stage, gsrc, tw, rowin, warp, lane); break;
+    case 1: c4_yfwd<N, 1>(plane, stage, gsrc, tw, rowin, warp, lane); break;
+    case 2: c4_yfwd<N, 2>(plane, stage, gsrc, tw, rowin, warp, lane); break;
+    default: c4_yfwd<N, 3>(plane, stage, gsrc, tw, rowin, warp, lane); break;
   }
-  cluster.sync();  // plane complete; no CTA reads the staging buffers any more
+  if (in_cols == nullptr)
+    __syncthreads();  // plane complete
+  else
+    cluster.sync();   // plane complete; no CTA reads the staging buffers any more
 
   // 3. x convolution
   const float2* Hk = H + (size_t)kt * (N + 1) * (N + 1);
@@ -416,16 +461,32 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(256, 2)
   const float s = 1.0f / (4.0f * N * N);
   float2* dst = Sout + (size_t)kt * out_pitch;
   if (out_cols == nullptr) {
-    constexpr int ITEMS = ROWS * M;
-    for (int i = tid; i < ITEMS; i += C::THREADS) {
-      const int x = x0 + i / M, n = i % M;
-      const int a = x * M + (n ^ swz<N>(x));
-      const float2 v0 = pr[0][a], v1 = pr[1][a], v2 = pr[2][a], v3 = pr[3][a];
-      const float2 e02 = cadd(v0, v2), d02 = csub(v0, v2);
-      const float2 e13 = cadd(v1, v3), d13 = csub(v1, v3);
-      // h = 0: v0 + v1 + v2 + v3; h = 1: v0 + i v1 - v2 - i v3
-      dst[x * N + n] = cscale(cadd(e02, e13), s);
-      dst[x * N + n + M] = cscale(make_float2(d02.x - d13.y, d02.y + d13.x), s);
+    constexpr int ITEMS = ROWS * M, U = 4;
+    static_assert(ITEMS % (U * C::THREADS) == 0 || ITEMS < U * C::THREADS, "combine unroll");
+    for (int i0 = tid; i0 < ITEMS; i0 += U * C::THREADS) {
+      float2 v[U][4];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u * C::THREADS;
+        if (i < ITEMS) {
+          const int x = x0 + i / M, n = i % M;
+          const int a = x * M + (n ^ swz<N>(x));
+#pragma unroll
+          for (int r = 0; r < 4; ++r) v[u][r] = pr[r][a];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u * C::THREADS;
+        if (i < ITEMS) {
+          const int x = x0 + i / M, n = i % M;
+          const float2 e02 = cadd(v[u][0], v[u][2]), d02 = csub(v[u][0], v[u][2]);
+          const float2 e13 = cadd(v[u][1], v[u][3]), d13 = csub(v[u][1], v[u][3]);
+          // h = 0: v0 + v1 + v2 + v3; h = 1: v0 + i v1 - v2 - i v3
+          dst[x * N + n] = cscale(cadd(e02, e13), s);
+          dst[x * N + n + M] = cscale(make_float2(d02.x - d13.y, d02.y + d13.x), s);
+        }
+      }
     }
   } else {
     for (int j = tid; j < out_n; j += C::THREADS) {
@@ -469,8 +530,8 @@ nlos_status launch_conv4(const Plan& P, const float2* Sin, bool in_compact, floa
                          cudaStream_t st) {
   const int full = P.nx * P.ny;
   const int in_pitch = in_compact ? P.ncols : full, out_pitch = out_compact ? P.ncols : full;
-  if (!in_compact && (reinterpret_cast<uintptr_t>(Sin) & 15) != 0)
-    return fail(NLOS_ERR_INVALID_ARG, "conv4: input spectrum must be 16-byte aligned");
+  if ((reinterpret_cast<uintptr_t>(Sin) & 7) != 0 || (reinterpret_cast<uintptr_t>(Sout) & 7) != 0)
+    return fail(NLOS_ERR_INVALID_ARG, "conv4: spectra must be 8-byte aligned");
   auto go = [&](auto kern, size_t smem) -> nlos_status {
     NLOS_TRY(ensure_smem(kern, smem));
     kern<<<4 * (P.nt + 1), 256, smem, st>>>(Sin, in_pitch, in_compact ? P.d_cols : nullptr, P.ncols, Sout,

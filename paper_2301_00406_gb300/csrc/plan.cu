@@ -257,8 +257,8 @@ size_t workspace_bytes(const Plan& P, int model) {
                                (size_t)(P.nt / 2 + 1) * full) +
              C + sizeof(double) * 4096 * kMaxTerms + 4096;
   const size_t partials = 3 * sizeof(double) * kMaxTerms * 4096;
-  if (model == 1) b += 9 * F + 4 * C + partials;
-  if (model == 2) b += 21 * F + partials;
+  if (model == 1 || model == 3) b += 9 * F + 4 * C + partials;
+  if (model == 2 || model == 3) b += 21 * F + partials;
   return b;
 }
 
@@ -480,6 +480,7 @@ nlos_status nlos_params_default(int32_t model, nlos_params* out) {
   out->max_backtracks = 30;
   out->eps_normal = 1e-6;
   out->restart = -1;
+  out->warm_start_iters = 0;
   return NLOS_OK;
 }
 
@@ -583,9 +584,10 @@ nlos_status nlos_reconstruct(nlos_plan plan, const nlos_params* params, const fl
     if (!params || !tau0_dev || !u_out_dev || !aligned16(tau0_dev) || !aligned16(u_out_dev))
       return fail(NLOS_ERR_INVALID_ARG, "nlos_reconstruct: null or non-16-byte-aligned pointer");
     const nlos_params& p = *params;
-    if (p.iters < 0 || !(p.eta > 1.0) || p.max_backtracks < 0 || p.phi < 0 || p.phi > 2 || !(p.eps_normal >= 0.0))
+    if (p.iters < 0 || !(p.eta > 1.0) || p.max_backtracks < 0 || p.phi < 0 || p.phi > 2 || !(p.eps_normal >= 0.0) ||
+        p.warm_start_iters < 0)
       return fail(NLOS_ERR_INVALID_ARG, "nlos_reconstruct: invalid iteration parameters");
-    if (p.model == 1 && !(p.mu > 0.0)) return fail(NLOS_ERR_INVALID_ARG, "mu must be > 0");
+    if ((p.model == 1 || p.warm_start_iters > 0) && !(p.mu > 0.0)) return fail(NLOS_ERR_INVALID_ARG, "mu must be > 0");
     if (p.model == 2 && !(p.mu1 > 0.0 && p.mu2 > 0.0 && p.mu3 > 0.0 && p.lambda >= 0.0))
       return fail(NLOS_ERR_INVALID_ARG, "mu1, mu2, mu3 must be > 0 and lambda >= 0");
     if (stats_host) std::memset(stats_host, 0, sizeof(*stats_host));

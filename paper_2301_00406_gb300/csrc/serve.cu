@@ -214,6 +214,10 @@ static void free_ctx(JobCtx* c) {
   delete c;
 }
 
+// Solver state a job needs: its model, or 3 for a model-2 job with an
+// Algorithm-1 warm stage (both solver states live in its workspace).
+static int ctx_kind(const nlos_params& p) { return p.model == 2 && p.warm_start_iters > 0 ? 3 : p.model; }
+
 static size_t ctx_bytes(const Plan& base, int model) {
   const size_t F = (size_t)base.nx * base.ny * base.nt * sizeof(float);
   return workspace_bytes(base, model) + 2 * F;
@@ -233,7 +237,8 @@ static nlos_status get_base(Server* S, const GeomKey& key, int model, BaseEntry*
     it = S->bases.emplace(key, e).first;
   }
   double n2 = 0.0;
-  NLOS_TRY(plan_norm2(*it->second.plan, model == 1, S->setup_stream, &n2));
+  if (model != 2) NLOS_TRY(plan_norm2(*it->second.plan, true, S->setup_stream, &n2));
+  if (model != 1) NLOS_TRY(plan_norm2(*it->second.plan, false, S->setup_stream, &n2));
   *out = &it->second;
   return NLOS_OK;
 }
@@ -248,7 +253,7 @@ static void release_idle(Server* S, size_t need) {
 }
 
 static nlos_status acquire_ctx(Server* S, Job* jb, BaseEntry* base, JobCtx** out) {
-  const auto k = std::make_pair(jb->key, jb->params.model);
+  const auto k = std::make_pair(jb->key, ctx_kind(jb->params));
   auto it = S->idle.find(k);
   if (it != S->idle.end()) {
     *out = it->second;
@@ -257,8 +262,8 @@ static nlos_status acquire_ctx(Server* S, Job* jb, BaseEntry* base, JobCtx** out
   }
   JobCtx* c = new JobCtx();
   c->key = jb->key;
-  c->model = jb->params.model;
-  c->bytes = ctx_bytes(*base->plan, jb->params.model);
+  c->model = ctx_kind(jb->params);
+  c->bytes = ctx_bytes(*base->plan, c->model);
   const size_t F = (size_t)base->plan->nx * base->plan->ny * base->plan->nt * sizeof(float);
   nlos_status s = NLOS_OK;
   c->ws = plan_clone_workspace(*base->plan, &s);
@@ -356,16 +361,16 @@ static void worker_main(Server* S) {
     while (!S->pending.empty() && (int)S->active.size() < S->max_slots) {
       Job* jb = S->pending.front();
       BaseEntry* base = nullptr;
-      nlos_status s = get_base(S, jb->key, jb->params.model, &base);
+      nlos_status s = get_base(S, jb->key, ctx_kind(jb->params), &base);
       if (s != NLOS_OK) {
         S->pending.pop_front();
         finish_job(S, jb, JOB_FAILED, s);
         progressed = true;
         continue;
       }
-      const auto k = std::make_pair(jb->key, jb->params.model);
+      const auto k = std::make_pair(jb->key, ctx_kind(jb->params));
       const bool recycled = S->idle.count(k) > 0;
-      const size_t need = recycled ? 0 : ctx_bytes(*base->plan, jb->params.model);
+      const size_t need = recycled ? 0 : ctx_bytes(*base->plan, k.second);
       if (S->used + need > S->budget) release_idle(S, need);
       if (S->used + need > S->budget) {
         if (S->active.empty()) {  // can never fit: fail instead of waiting forever
@@ -481,6 +486,8 @@ nlos_status nlos_reconstruct_batch(const nlos_plan* plans, const nlos_params* pa
       if (P[i]->device != dev) return fail(NLOS_ERR_INVALID_ARG, "nlos_reconstruct_batch: plan on another device");
       if (params[i].model != 1 && params[i].model != 2)
         return fail(NLOS_ERR_INVALID_ARG, "nlos_reconstruct_batch: model must be 1 or 2");
+      if (params[i].warm_start_iters < 0)
+        return fail(NLOS_ERR_INVALID_ARG, "nlos_reconstruct_batch: warm_start_iters < 0");
       for (int k = 0; k < i; ++k)
         if (P[k] == P[i]) return fail(NLOS_ERR_INVALID_ARG, "nlos_reconstruct_batch: a plan appears twice");
     }
@@ -515,6 +522,7 @@ nlos_status nlos_submit(nlos_server server, const nlos_geometry* geom, const nlo
     int32_t n = 0;
     NLOS_TRY(nlos_geometry_tables(geom, nullptr, nullptr, nullptr, nullptr, nullptr, &n));
     if (params->model != 1 && params->model != 2) return fail(NLOS_ERR_INVALID_ARG, "nlos_submit: model");
+    if (params->warm_start_iters < 0) return fail(NLOS_ERR_INVALID_ARG, "nlos_submit: warm_start_iters < 0");
     Server& S = server->impl;
     auto jb = std::make_unique<Job>();
     jb->key = make_key(*geom);

@@ -106,6 +106,21 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[NTERMS], double* 
   }
 }
 
+// The two columns (ca, ca + 1) of a pair from spectrum row `row`: one
+// 16-byte load when both exist and the pair is 16-byte aligned (even pitch
+// and even ca, base from cudaMalloc), else one or two 8-byte loads.
+__device__ __forceinline__ void load_pair(const float2* __restrict__ row, int ca, int ncols, bool even_pitch,
+                                          float2& A, float2& B) {
+  if (even_pitch && ca + 1 < ncols) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(row + ca));
+    A = make_float2(v.x, v.y);
+    B = make_float2(v.z, v.w);
+  } else {
+    A = ca < ncols ? __ldg(row + ca) : make_float2(0.f, 0.f);
+    B = ca + 1 < ncols ? __ldg(row + ca + 1) : make_float2(0.f, 0.f);
+  }
+}
+
 // Post-processing of the padded forward t-FFT of packed pairs: writes bins
 // kt = 2 k' + half of both columns of every pair to S.
 template <int NT>
@@ -113,8 +128,9 @@ __device__ __forceinline__ void tfwd_post_store(const float2* work, int half, fl
                                                 int ncols, int COLS, int tid, int nthr) {
   constexpr int WP = TP<NT>::WP;
   const int nk = half ? NT / 2 : NT / 2 + 1;
+  const int lc = __ffs(COLS) - 1;  // COLS is a power of two
   for (int i = tid; i < nk * COLS; i += nthr) {
-    const int kp = i / COLS, c = i % COLS, p = c >> 1;
+    const int kp = i >> lc, c = i & (COLS - 1), p = c >> 1;
     if (col0 + c >= ncols) continue;
     const int m = half ? (NT - 1 - kp) : ((NT - kp) & (NT - 1));
     const float2 za = work[p * WP + fpos<NT>(kp)];
@@ -143,9 +159,9 @@ __device__ __forceinline__ void tinv_load(const float2* __restrict__ S, int pitc
         int kt = 2 * kp + half;
         const bool mir = kt > NT;
         if (mir) kt = 2 * NT - kt;
-        const int ca = col0 + 2 * p, cb = ca + 1;
-        float2 A = ca < ncols ? __ldg(S + (size_t)kt * pitch + ca) : make_float2(0.f, 0.f);
-        float2 B = cb < ncols ? __ldg(S + (size_t)kt * pitch + cb) : make_float2(0.f, 0.f);
+        const int ca = col0 + 2 * p;
+        float2 A, B;
+        load_pair(S + (size_t)kt * pitch, ca, ncols, (pitch & 1) == 0, A, B);
         if (mir) {
           A.y = -A.y;
           B.y = -B.y;
@@ -329,8 +345,9 @@ template <int NT>
 __device__ __forceinline__ void periodic_fwd_post(const float2* work, float2* Sp, int col0, int ncols, int pitch,
                                                   int COLS, int tid, int nthr) {
   constexpr int WP = TP<NT>::WP;
+  const int lc = __ffs(COLS) - 1;  // COLS is a power of two
   for (int i = tid; i < (NT / 2 + 1) * COLS; i += nthr) {
-    const int k = i / COLS, c = i % COLS, p = c >> 1;
+    const int k = i >> lc, c = i & (COLS - 1), p = c >> 1;
     if (col0 + c >= ncols) continue;
     const float2 za = work[p * WP + fpos<NT>(k)];
     const float2 zb = work[p * WP + fpos<NT>((NT - k) & (NT - 1))];
@@ -454,9 +471,9 @@ __global__ void __launch_bounds__(kTpassThreads)
         int kk = k;
         const bool mir = k > NT / 2;
         if (mir) kk = NT - k;
-        const int ca = col0 + 2 * p, cb = ca + 1;
-        float2 A = ca < ncols ? __ldg(Sp + (size_t)kk * ncols + ca) : make_float2(0.f, 0.f);
-        float2 B = cb < ncols ? __ldg(Sp + (size_t)kk * ncols + cb) : make_float2(0.f, 0.f);
+        const int ca = col0 + 2 * p;
+        float2 A, B;
+        load_pair(Sp + (size_t)kk * ncols, ca, ncols, (ncols & 1) == 0, A, B);
         if (mir) {
           A.y = -A.y;
           B.y = -B.y;

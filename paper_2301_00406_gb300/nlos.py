@@ -19,6 +19,8 @@ STATUS_NAMES = {0: "NLOS_OK", -1: "NLOS_ERR_INVALID_ARG", -2: "NLOS_ERR_OOM", -3
                 -4: "NLOS_ERR_BUSY", -5: "NLOS_ERR_NOT_READY", -6: "NLOS_ERR_TIMEOUT",
                 -7: "NLOS_ERR_DIVERGED"}
 RADIOMETRY = {"compensated": 0, "raw": 1}
+# curvature weights phi(kappa) (NLOS_PHI_*): a + b kappa^2, a + b |kappa|, sqrt(a + b kappa^2)
+PHI_TSC, PHI_TAC, PHI_TRV = 0, 1, 2
 PHI = {"tsc": 0, "tac": 1, "trv": 2}
 
 
@@ -36,7 +38,8 @@ class Params(ctypes.Structure):
                 ("mu1", ctypes.c_double), ("mu2", ctypes.c_double), ("mu3", ctypes.c_double),
                 ("iters", ctypes.c_int32), ("eps_stop", ctypes.c_double), ("L0", ctypes.c_double),
                 ("eta", ctypes.c_double), ("max_backtracks", ctypes.c_int32),
-                ("eps_normal", ctypes.c_double), ("restart", ctypes.c_int32)]
+                ("eps_normal", ctypes.c_double), ("restart", ctypes.c_int32),
+                ("warm_start_iters", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

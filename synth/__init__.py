@@ -102,6 +102,39 @@ def poisson_measurement(signal, mask, peak, background, seed):
     return y / ymax if ymax > 0 else y
 
 
+def _lcg_uniforms(seed, n):
+    """n numbers in [0, 1) from a 64-bit linear congruential sequence (integer
+    arithmetic only, so identical on every platform and numpy version)."""
+    x = (int(seed) * 6364136223846793005 + 1442695040888963407) % (1 << 64)
+    out = []
+    for _ in range(n):
+        x = (x * 6364136223846793005 + 1442695040888963407) % (1 << 64)
+        out.append((x >> 11) / float(1 << 53))
+    return out
+
+
+def pulse_transients(nx, ny, nt, mask, seed, width_bins=1.5, floor=0.02):
+    """Seeded synthetic transients without random sampling: every sampled
+    column holds a main return at a depth that varies smoothly across the
+    wall (0.35-0.75 of the range), a weaker second return behind it on part
+    of the wall, and a constant floor; normalised to max 1, zero off the mask.
+    Built from closed-form functions and integer-generated phases only, so
+    both sides of a comparison can regenerate it on any machine."""
+    u = _lcg_uniforms(seed, 6)
+    x = (np.arange(nx) + 0.5)[:, None] / nx
+    y = (np.arange(ny) + 0.5)[None, :] / ny
+    d1 = nt * (0.55 + 0.15 * np.sin(2 * np.pi * (x + u[0])) * np.cos(2 * np.pi * (y + u[1])))
+    d2 = d1 + nt * (0.08 + 0.04 * u[2])
+    a1 = 0.6 + 0.4 * np.cos(np.pi * (x - u[3])) ** 2
+    a2 = 0.35 * (np.sin(2 * np.pi * (x + y + u[4])) > 0.2 * (2 * u[5] - 1))
+    t = np.arange(nt)[None, None, :]
+    sig = (a1[:, :, None] * np.exp(-0.5 * ((t - d1[:, :, None]) / width_bins) ** 2)
+           + a2[:, :, None] * np.exp(-0.5 * ((t - d2[:, :, None]) / width_bins) ** 2) + floor)
+    sig *= np.asarray(mask, dtype=np.float64)[:, :, None]
+    m = float(np.max(sig))
+    return sig / m if m > 0 else sig
+
+
 # Workloads used by the tests and the bench (sizes and parameters of the
 # paper's experiments; see the design notes for the recipe).
 CONFIGS = {
@@ -117,6 +150,9 @@ CONFIGS = {
                                  model=1, iters=50, a=9e-5, b=2e-5, mu=0.1,
                                  lam=235.0, a_u=2e-4, b_u=4.5e-4,
                                  a_tau=4e-4, b_tau=3e-2, mu1=1.0, mu2=800.0, mu3=2.0),
+    # precision case: 8 ps bins over the same 1.2288 m range, 32x32 sampled
+    "c4_alg1_128x128x1024": dict(nx=128, ny=128, nt=1024, bin_width_s=8e-12, stride=4,
+                                 scene="pulses", model=1, iters=12, a=9e-5, b=2e-5, mu=0.1),
 }
 
 

@@ -1,0 +1,59 @@
+"""The bench's multi-rank path on CPU: two gloo ranks (replicas) each time
+their own work; the job's time is the slowest rank's and its throughput is
+the units of all ranks over that time."""
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, times, out):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    import torch.distributed as dist
+
+    import bench
+    r, w, _ = bench.dist_env()
+    dist.init_process_group("gloo", rank=r, world_size=w)
+    try:
+        t_max = bench.max_over_ranks(times[r], w, "cpu")
+        out.put((r, t_max, bench.job_rate(50, w, t_max)))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_report_slowest_time_and_total_units():
+    torch = pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    times = [40.0, 55.0]           # ms per rank
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, times, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    got = sorted(q.get(timeout=10) for _ in range(2))
+    for r, t_max, rate in got:
+        assert t_max == 55.0
+        assert rate == pytest.approx(2 * 50 / 0.055)
+
+
+def test_single_rank_needs_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(12.5, 1, "cpu") == 12.5
+    assert bench.job_rate(50, 1, 100.0) == pytest.approx(500.0)

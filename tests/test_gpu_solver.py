@@ -111,3 +111,59 @@ def test_alg2_parity(nlos, n, nt, iters):
     assert eu < tol and et < tol, (eu, et)
     assert st["restarts"] == sum(h["restart"])
     assert abs(st["energy"] - h["E"][-1]) <= 1e-3 * abs(h["E"][-1])
+
+
+def test_alg2_warm_start_parity(nlos):
+    # the remark after Algorithm 2: u starts from W Algorithm-1 iterations, tau from 0
+    n, nt, W, iters = 16, 64, 6, 12
+    cfg, g, mask, vol, tau0 = scene(2, n, nt, seed=2)
+    c1 = synth.CONFIGS["c1_alg1_32x32x256"]
+    op = lct.Operator(g, mask)
+    n2, _ = lct.power_norm2(op, masked=False)
+    plan = nlos.Plan(n, n, nt, cfg["bin_width_s"], mask=mask)
+    p = alg2_params(nlos, cfg, iters, 2 * n2)
+    p.a, p.b, p.mu = c1["a"], c1["b"], c1["mu"]
+    p.warm_start_iters = W
+    u_gpu, tau_gpu, st = nlos.reconstruct_t(plan, p, dev(tau0), want_tau=True)
+    u_w, _ = admm.alg1(tau0, mask, g, c1["a"], c1["b"], c1["mu"], W, op=op)
+    u_ref, tau_ref, h = admm.alg2(tau0, mask, g, cfg["a_u"], cfg["b_u"], cfg["a_tau"], cfg["b_tau"], cfg["lam"],
+                                  cfg["mu1"], cfg["mu2"], cfg["mu3"], iters, L0=2 * n2, op=op, u_init=u_w)
+    eu, et = rel_l2(host(u_gpu), u_ref), rel_l2(host(tau_gpu), tau_ref)
+    assert eu < 1e-3 and et < 1e-3, (eu, et)
+    assert st["iters_done"] == iters and st["status"] == 0
+    assert st["restarts"] == sum(h["restart"])
+    assert abs(st["energy"] - h["E"][-1]) <= 1e-3 * abs(h["E"][-1])
+    # and it differs from the cold start
+    p.warm_start_iters = 0
+    u_cold, _ = nlos.reconstruct_t(plan, p, dev(tau0))
+    assert rel_l2(host(u_cold), u_ref) > 1e-2
+
+
+@pytest.mark.parametrize("kind", ["tac", "trv"])
+def test_alg1_phi_variant_parity(nlos, kind):
+    # phi = a + b |kappa| (TAC) and sqrt(a + b kappa^2) (TRV), Sec. 3
+    n, nt, iters = 16, 64, 10
+    cfg, g, mask, vol, tau0 = scene(1, n, nt, seed=5)
+    op = lct.Operator(g, mask)
+    n2, _ = lct.power_norm2(op)
+    plan = nlos.Plan(n, n, nt, cfg["bin_width_s"], mask=mask)
+    p = alg1_params(nlos, cfg, iters, 2 * n2)
+    p.phi = {"tac": nlos.PHI_TAC, "trv": nlos.PHI_TRV}[kind]
+    u_gpu, st = nlos.reconstruct_t(plan, p, dev(tau0))
+    u_ref, h = admm.alg1(tau0, mask, g, cfg["a"], cfg["b"], cfg["mu"], iters, L0=2 * n2, op=op, phi_kind=kind)
+    assert rel_l2(host(u_gpu), u_ref) < 1e-3
+    assert abs(st["energy"] - h["E"][-1]) <= 1e-3 * abs(h["E"][-1])
+
+
+def test_alg2_phi_variant_parity(nlos):
+    n, nt, iters = 16, 64, 10
+    cfg, g, mask, vol, tau0 = scene(2, n, nt, seed=6)
+    op = lct.Operator(g, mask)
+    n2, _ = lct.power_norm2(op, masked=False)
+    plan = nlos.Plan(n, n, nt, cfg["bin_width_s"], mask=mask)
+    p = alg2_params(nlos, cfg, iters, 2 * n2)
+    p.phi = nlos.PHI_TAC
+    u_gpu, tau_gpu, st = nlos.reconstruct_t(plan, p, dev(tau0), want_tau=True)
+    u_ref, tau_ref, h = admm.alg2(tau0, mask, g, cfg["a_u"], cfg["b_u"], cfg["a_tau"], cfg["b_tau"], cfg["lam"],
+                                  cfg["mu1"], cfg["mu2"], cfg["mu3"], iters, L0=2 * n2, op=op, phi_kind="tac")
+    assert rel_l2(host(u_gpu), u_ref) < 1e-3 and rel_l2(host(tau_gpu), tau_ref) < 1e-3
