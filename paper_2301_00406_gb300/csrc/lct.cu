@@ -1,5 +1,10 @@
 // Runtime dispatch of the t-pass launchers to their per-size instances
-// (tpass_*.cu).
+// (tpass_*.cu), and the launch-shape tuner of the t-passes.
+#include <functional>
+#include <map>
+#include <vector>
+#include <mutex>
+#include <tuple>
 #include <type_traits>
 
 #include "tpass.cuh"
@@ -55,6 +60,113 @@ nlos_status launch_sfwd(const Plan& P, const float* x, int ncols, float2* Sp, cu
 nlos_status launch_sinv(const Plan& P, const float2* Sp, int ncols, float* x, const float* ref, double* partials,
                         int* nblocks, cudaStream_t st) {
   NLOS_DISPATCH_NT(P.nt, sinv(P, Sp, ncols, x, ref, partials, nblocks, st));
+}
+
+}  // namespace nlos
+
+namespace nlos {
+
+// ---------------------------------------------------------------------------
+// t-pass launch-shape tuning
+// ---------------------------------------------------------------------------
+namespace {
+std::mutex g_tp_mu;
+std::map<std::tuple<int, int, int>, int> g_tp_cols;  // (kind, nt, ncols) -> columns per CTA
+thread_local int g_tp_force = 0;                       // candidate under test (tuner only)
+}  // namespace
+
+int tp_cols_for(int kind, int nt, int ncols) {
+  if (g_tp_force) return g_tp_force;
+  std::lock_guard<std::mutex> lock(g_tp_mu);
+  auto it = g_tp_cols.find(std::make_tuple(kind, nt, ncols));
+  return it == g_tp_cols.end() ? 0 : it->second;
+}
+
+// Times every column count for each t-pass kind the plan launches and keeps
+// the fastest.  Inputs are the plan's scratch buffers with whatever they hold
+// (the kernels' addressing depends only on the tables and the shape, so any
+// contents are safe); nothing outside the plan is written.
+nlos_status autotune_tpass(Plan& P, cudaStream_t st) {
+  const int nt = P.nt, full = P.nx * P.ny;
+  const size_t V = (size_t)full * nt;
+  float* f1 = reinterpret_cast<float*>(P.d_S2);  // 2 (nt + 1) full floats: two fields
+  float* f2 = f1 + V;
+  float* f3 = reinterpret_cast<float*>(P.d_Sp);  // (nt + 2) full floats: one field
+  DevScalars* dsc = nullptr;
+  NLOS_CUDA(cudaMalloc(&dsc, sizeof(DevScalars)));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  nlos_status status = NLOS_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+      cudaMemsetAsync(dsc, 0, sizeof(DevScalars), st) != cudaSuccess)
+    status = fail(NLOS_ERR_CUDA, "autotune: setup");
+  int nb = 0;
+  struct Case {
+    int kind, ncols;
+    bool partials;
+    std::function<nlos_status()> run;
+  };
+  const int nc = P.ncols;  // compact launches; captured by value below
+  const Lin3 r_full{{f3, nullptr, nullptr}, {1.f, 0.f, 0.f}, nullptr};
+  const Lin3 r_comp{{P.d_tmpc, nullptr, nullptr}, {1.f, 0.f, 0.f}, nullptr};
+  const SolveRhs sr{f1, f2, nullptr, 1.0};
+  const FitArgs fa_full{f1, f2, f1, dsc, P.d_partials};
+  const FitArgs fa_comp{P.d_tmpc, P.d_tmpc, P.d_tmpc, dsc, P.d_partials};
+  std::vector<Case> cases = {
+      {TPK_TFWD_RZ, full, false, [&] { return launch_tfwd_rz(P, f3, full, P.d_S, full, st); }},
+      {TPK_TFWD_RTT, full, false, [&] { return launch_tfwd_rtt(P, r_full, full, P.d_S, full, st); }},
+      {TPK_TINV_STORE, full, false, [&] { return launch_tinv_store(P, P.d_S, full, full, f3, nullptr, st); }},
+      {TPK_TINV_FIT, full, true, [&] { return launch_tinv_fit(P, P.d_S, full, full, f3, fa_full, &nb, st); }},
+      {TPK_TADJ_STORE, full, false, [&] { return launch_tadj_store(P, P.d_S, full, full, f1, st); }},
+      {TPK_TADJ_SOLVE, full, false, [&] { return launch_tadj_solve(P, P.d_S, full, full, sr, P.d_Sp, st); }},
+      {TPK_SFWD, full, false, [&] { return launch_sfwd(P, f1, full, P.d_Sp, st); }},
+      {TPK_SINV, full, true, [&] { return launch_sinv(P, P.d_Sp, full, f1, f2, P.d_partials, &nb, st); }},
+  };
+  if (nc < full) {
+    cases.push_back({TPK_TFWD_RTT, nc, false, [&, nc] { return launch_tfwd_rtt(P, r_comp, nc, P.d_Sc, nc, st); }});
+    cases.push_back(
+        {TPK_TINV_FIT, nc, true, [&, nc] { return launch_tinv_fit(P, P.d_Sc, nc, nc, f1, fa_comp, &nb, st); }});
+    cases.push_back(
+        {TPK_TINV_STORE, nc, false, [&, nc] { return launch_tinv_store(P, P.d_Sc, nc, nc, f1, nullptr, st); }});
+  }
+  const int max_cols = nt >= 1024 ? 8 : 16;
+  for (const Case& c : cases) {
+    if (status != NLOS_OK) break;
+    {
+      std::lock_guard<std::mutex> lock(g_tp_mu);
+      if (g_tp_cols.count(std::make_tuple(c.kind, nt, c.ncols))) continue;
+    }
+    int best = 0;
+    float best_ms = 0.f;
+    for (int cols = max_cols; cols >= 2 && status == NLOS_OK; cols >>= 1) {
+      if (c.partials && (c.ncols + cols - 1) / cols > P.partial_blocks) continue;
+      g_tp_force = cols;
+      float t = 0.f;
+      status = c.run();  // warm-up
+      for (int rep = 0; rep < 3 && status == NLOS_OK; ++rep) {
+        float ms = 0.f;
+        if (cudaEventRecord(e0, st) != cudaSuccess) status = fail(NLOS_ERR_CUDA, "autotune: event");
+        if (status == NLOS_OK) status = c.run();
+        if (status == NLOS_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                                  cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+          status = fail(NLOS_ERR_CUDA, "autotune: timing");
+        if (rep == 0 || ms < t) t = ms;
+      }
+      g_tp_force = 0;
+      if (status == NLOS_OK && (best == 0 || t < best_ms)) {
+        best = cols;
+        best_ms = t;
+      }
+    }
+    if (status == NLOS_OK && best) {
+      std::lock_guard<std::mutex> lock(g_tp_mu);
+      g_tp_cols.emplace(std::make_tuple(c.kind, nt, c.ncols), best);  // first plan of this key decides
+    }
+  }
+  g_tp_force = 0;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(dsc);
+  return status;
 }
 
 }  // namespace nlos

@@ -69,6 +69,18 @@ nlos_status launch_sxy(const Plan& P, float2* Sp, const DevScalars* sc, double c
 // Cone-kernel spectrum of the plan (plan time).
 nlos_status launch_kernel_spectrum(const Plan& P, const int32_t* m0, const float2* hw, cudaStream_t st);
 
+// Launch-shape tuning of the t-passes.  Every t-pass kind picks its columns
+// per CTA (16, 8, 4 or 2) by timing at plan creation (autotune_tpass, on the
+// plan's own scratch buffers); the choice is cached for the whole process
+// per (kind, nt, launch column count), so all plans of a geometry launch the
+// same shapes and their block-partial reductions sum in the same order.
+enum TpKind {
+  TPK_TFWD_RZ, TPK_TFWD_RTT, TPK_TINV_STORE, TPK_TINV_FIT, TPK_TADJ_STORE, TPK_TADJ_SOLVE, TPK_SFWD, TPK_SINV
+};
+// Tuned columns per CTA for a launch, or 0 (use the default rule).
+int tp_cols_for(int kind, int nt, int ncols);
+nlos_status autotune_tpass(Plan& P, cudaStream_t st);
+
 // Pre-set the shared-memory attributes of every kernel for these sizes.
 nlos_status prepare_tpass(int nt);
 nlos_status prepare_xy(int n);

@@ -397,6 +397,7 @@ static nlos_status create_plan(const nlos_geometry* g, cudaStream_t st, Plan** o
   if (s == NLOS_OK) s = prepare_tpass(nt);
   if (s == NLOS_OK) s = prepare_xy(nx);
   if (s == NLOS_OK) s = prepare_stencils();
+  if (s == NLOS_OK) s = autotune_tpass(*P, st);
   if (s == NLOS_OK) {
     KTimer kt_(*P, KC_KSPEC, st);
     s = launch_kernel_spectrum(*P, d_m0, d_hw, st);

@@ -37,7 +37,7 @@ struct TpassOps {
 // ---------------------------------------------------------------------------
 template <int NT>
 struct TP {
-  static constexpr int COLS = NT >= 1024 ? 8 : 16;  // columns per CTA
+  static constexpr int COLS = NT >= 1024 ? 8 : 16;  // columns per CTA (heuristic default)
   static constexpr int PAIRS = COLS / 2;
   static constexpr int WP = NT + 1;                 // odd pitch of a work transform
 };
@@ -521,10 +521,15 @@ struct TpShape {
 };
 
 template <int NT>
-static TpShape tp_shape(int ncols, int extra, bool tab = true) {
+static TpShape tp_shape(int ncols, int extra, bool tab, int kind) {
   TpShape sh;
-  sh.cols = TP<NT>::COLS;
-  while (sh.cols > 2 && div_up(ncols, sh.cols) < 2 * 152) sh.cols >>= 1;
+  const int tuned = kind >= 0 ? tp_cols_for(kind, NT, ncols) : 0;
+  if (tuned >= 2 && tuned <= TP<NT>::COLS) {
+    sh.cols = tuned;
+  } else {
+    sh.cols = TP<NT>::COLS;
+    while (sh.cols > 2 && div_up(ncols, sh.cols) < 2 * 152) sh.cols >>= 1;
+  }
   sh.threads = sh.cols >= 8 ? kTpassThreads : sh.cols == 4 ? 128 : 64;
   sh.blocks = div_up(ncols, sh.cols);
   // the work region is padded to an even number of float2 so the real column
@@ -538,7 +543,7 @@ template <int NT>
 nlos_status TpassOps<NT>::tfwd_rz(const Plan& P, const float* u, int ncols, float2* S, int pitch, cudaStream_t st) {
   KTimer kt_(P, KC_TFWD, st);
   auto kern = k_tfwd<NT, 0>;
-  const TpShape sh = tp_shape<NT>(ncols, 1);
+  const TpShape sh = tp_shape<NT>(ncols, 1, true, TPK_TFWD_RZ);
   NLOS_TRY(set_smem_tp(kern, sh.smem));
   Lin3 src{{u, nullptr, nullptr}, {1.f, 0.f, 0.f}, nullptr};
   kern<<<sh.blocks, sh.threads, sh.smem, st>>>(src, ncols, S, pitch, P.d_rz_f4, nullptr, nullptr, P.d_tw2t,
@@ -551,7 +556,7 @@ template <int NT>
 nlos_status TpassOps<NT>::tfwd_rtt(const Plan& P, const Lin3& r, int ncols, float2* S, int pitch, cudaStream_t st) {
   KTimer kt_(P, KC_TFWD, st);
   auto kern = k_tfwd<NT, 1>;
-  const TpShape sh = tp_shape<NT>(ncols, 1);
+  const TpShape sh = tp_shape<NT>(ncols, 1, true, TPK_TFWD_RTT);
   NLOS_TRY(set_smem_tp(kern, sh.smem));
   kern<<<sh.blocks, sh.threads, sh.smem, st>>>(r, ncols, S, pitch, nullptr, P.d_rtT_ptr, P.d_rtT_ent, P.d_tw2t,
                                                sh.cols);
@@ -564,7 +569,7 @@ nlos_status TpassOps<NT>::tinv_store(const Plan& P, const float2* S, int pitch, 
                                      const int32_t* outmap, cudaStream_t st) {
   KTimer kt_(P, KC_TINV, st);
   auto kern = k_tinv<NT, 0>;
-  const TpShape sh = tp_shape<NT>(ncols, 1);
+  const TpShape sh = tp_shape<NT>(ncols, 1, true, TPK_TINV_STORE);
   NLOS_TRY(set_smem_tp(kern, sh.smem));
   FitArgs fa{};
   kern<<<sh.blocks, sh.threads, sh.smem, st>>>(S, pitch, ncols, out, outmap, fa, P.d_rt_f4, P.d_tw2t, sh.cols);
@@ -577,7 +582,7 @@ nlos_status TpassOps<NT>::tinv_fit(const Plan& P, const float2* S, int pitch, in
                                    const FitArgs& fa, int* nblocks, cudaStream_t st) {
   KTimer kt_(P, KC_TINV, st);
   auto kern = k_tinv<NT, 1>;
-  const TpShape sh = tp_shape<NT>(ncols, 1);
+  const TpShape sh = tp_shape<NT>(ncols, 1, true, TPK_TINV_FIT);
   NLOS_TRY(set_smem_tp(kern, sh.smem));
   if (sh.blocks > P.partial_blocks) return fail(NLOS_ERR_INVALID_ARG, "partials buffer too small");
   *nblocks = sh.blocks;
@@ -591,7 +596,7 @@ nlos_status TpassOps<NT>::tadj_store(const Plan& P, const float2* S, int pitch, 
                                      cudaStream_t st) {
   KTimer kt_(P, KC_TADJ, st);
   auto kern = k_tadj<NT, 0>;
-  const TpShape sh = tp_shape<NT>(ncols, 1);
+  const TpShape sh = tp_shape<NT>(ncols, 1, true, TPK_TADJ_STORE);
   NLOS_TRY(set_smem_tp(kern, sh.smem));
   SolveRhs sr{};
   kern<<<sh.blocks, sh.threads, sh.smem, st>>>(S, pitch, ncols, out, sr, nullptr, P.d_rzT_ptr, P.d_rzT_ent,
@@ -605,7 +610,7 @@ nlos_status TpassOps<NT>::tadj_solve(const Plan& P, const float2* S, int pitch, 
                                      float2* Sp, cudaStream_t st) {
   KTimer kt_(P, KC_TADJ, st);
   auto kern = k_tadj<NT, 1>;
-  const TpShape sh = tp_shape<NT>(ncols, 1);
+  const TpShape sh = tp_shape<NT>(ncols, 1, true, TPK_TADJ_SOLVE);
   NLOS_TRY(set_smem_tp(kern, sh.smem));
   kern<<<sh.blocks, sh.threads, sh.smem, st>>>(S, pitch, ncols, nullptr, sr, Sp, P.d_rzT_ptr, P.d_rzT_ent,
                                                P.d_tw2t, sh.cols);
@@ -617,7 +622,7 @@ template <int NT>
 nlos_status TpassOps<NT>::sfwd(const Plan& P, const float* x, int ncols, float2* Sp, cudaStream_t st) {
   KTimer kt_(P, KC_SFWD, st);
   auto kern = k_sfwd<NT>;
-  const TpShape sh = tp_shape<NT>(ncols, 0, false);
+  const TpShape sh = tp_shape<NT>(ncols, 0, false, TPK_SFWD);
   NLOS_TRY(set_smem_tp(kern, sh.smem));
   kern<<<sh.blocks, sh.threads, sh.smem, st>>>(x, ncols, Sp, P.d_tw2t, sh.cols);
   NLOS_LAUNCH_CHECK("k_sfwd");
@@ -629,7 +634,7 @@ nlos_status TpassOps<NT>::sinv(const Plan& P, const float2* Sp, int ncols, float
                                double* partials, int* nblocks, cudaStream_t st) {
   KTimer kt_(P, KC_SINV, st);
   auto kern = k_sinv<NT>;
-  const TpShape sh = tp_shape<NT>(ncols, 0, false);
+  const TpShape sh = tp_shape<NT>(ncols, 0, false, TPK_SINV);
   NLOS_TRY(set_smem_tp(kern, sh.smem));
   if (partials && sh.blocks > P.partial_blocks) return fail(NLOS_ERR_INVALID_ARG, "partials buffer too small");
   if (nblocks) *nblocks = sh.blocks;
@@ -640,7 +645,8 @@ nlos_status TpassOps<NT>::sinv(const Plan& P, const float2* Sp, int ncols, float
 
 template <int NT>
 nlos_status TpassOps<NT>::prepare() {
-  const TpShape s1 = tp_shape<NT>(1 << 30, 1), s2 = s1, s0 = tp_shape<NT>(1 << 30, 0, false);
+  // largest shapes: the default rule's column count for a huge launch
+  const TpShape s1 = tp_shape<NT>(1 << 30, 1, true, -1), s2 = s1, s0 = tp_shape<NT>(1 << 30, 0, false, -1);
   NLOS_TRY(set_smem_tp(k_tfwd<NT, 0>, s1.smem));
   NLOS_TRY(set_smem_tp(k_tfwd<NT, 1>, s1.smem));
   NLOS_TRY(set_smem_tp(k_tinv<NT, 0>, s1.smem));
