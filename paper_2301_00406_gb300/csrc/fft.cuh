@@ -128,27 +128,29 @@ __device__ __forceinline__ int kfreq(int p) {
   return k1 + R1 * (rem / R3 + R2 * (rem % R3));
 }
 
-// B transforms of length N (B a power of two): element n of transform b at
-// buf[b * ts + n * es].  tw[j * tws] = exp(-2 pi i j / N) for j < N.  All
-// threads of the block call it; it ends with __syncthreads().
+// B transforms of length N (B a power of two) in shared memory; element e of
+// transform b lives at buf[addr(b, e)] (addr: any bijective layout, e.g. a
+// strided plane or a bank-swizzled one).  tw[j * tws] = exp(-2 pi i j / N)
+// for j < N.  All threads of the block call these; they end with
+// __syncthreads().
+//
 // Three-step version (R3 > 1): N = R1 M, M = R2 R3.
 //   step 1 (b, n23): R1-point DFT over n1 of x[n1 M + n23], twiddle w_N^(n23 k1);
 //   step 2 (b, k1, n3): R2-point DFT over n2 of y[k1 M + n2 R3 + n3],
 //          twiddle w_M^(n3 k2) = w_N^(R1 n3 k2);
 //   step 3 (b, k1, k2): R3-point DFT over the contiguous n3.
 // The inverse runs the steps backwards with conjugate twiddles.
-template <int N, bool INV>
-__device__ __forceinline__ void team_fft3(float2* buf, int B, int ts, int es, const float2* tw, int tws, int tid,
-                                          int nthr) {
+template <int N, bool INV, typename Addr>
+__device__ __forceinline__ void team_fft3a(float2* buf, int B, const Addr& addr, const float2* tw, int tws, int tid,
+                                           int nthr) {
   constexpr int R1 = FftPlan<N>::R1, R2 = FftPlan<N>::R2, R3 = FftPlan<N>::R3, M = R2 * R3;
   const int lb = __ffs(B) - 1;
   auto step1 = [&]() {
     for (int it = tid; it < B * M; it += nthr) {
       const int b = it & (B - 1), n23 = it >> lb;
-      float2* p = buf + b * ts + n23 * es;
       float2 a[R1];
 #pragma unroll
-      for (int n = 0; n < R1; ++n) a[n] = p[n * M * es];
+      for (int n = 0; n < R1; ++n) a[n] = buf[addr(b, n * M + n23)];
       if (!INV) {
         dft_reg<R1, false>(a);
 #pragma unroll
@@ -159,7 +161,7 @@ __device__ __forceinline__ void team_fft3(float2* buf, int B, int ts, int es, co
         dft_reg<R1, true>(a);
       }
 #pragma unroll
-      for (int n = 0; n < R1; ++n) p[n * M * es] = a[n];
+      for (int n = 0; n < R1; ++n) buf[addr(b, n * M + n23)] = a[n];
     }
     __syncthreads();
   };
@@ -167,10 +169,10 @@ __device__ __forceinline__ void team_fft3(float2* buf, int B, int ts, int es, co
     for (int it = tid; it < B * R1 * R3; it += nthr) {
       const int b = it & (B - 1), r = it >> lb;
       const int n3 = r % R3, k1 = r / R3;
-      float2* p = buf + b * ts + (k1 * M + n3) * es;
+      const int e0 = k1 * M + n3;
       float2 a[R2];
 #pragma unroll
-      for (int n = 0; n < R2; ++n) a[n] = p[n * R3 * es];
+      for (int n = 0; n < R2; ++n) a[n] = buf[addr(b, e0 + n * R3)];
       if (!INV) {
         dft_reg<R2, false>(a);
 #pragma unroll
@@ -181,20 +183,20 @@ __device__ __forceinline__ void team_fft3(float2* buf, int B, int ts, int es, co
         dft_reg<R2, true>(a);
       }
 #pragma unroll
-      for (int n = 0; n < R2; ++n) p[n * R3 * es] = a[n];
+      for (int n = 0; n < R2; ++n) buf[addr(b, e0 + n * R3)] = a[n];
     }
     __syncthreads();
   };
   auto step3 = [&]() {
     for (int it = tid; it < B * R1 * R2; it += nthr) {
       const int b = it & (B - 1), r = it >> lb;
-      float2* p = buf + b * ts + r * R3 * es;
+      const int e0 = r * R3;
       float2 a[R3];
 #pragma unroll
-      for (int n = 0; n < R3; ++n) a[n] = p[n * es];
+      for (int n = 0; n < R3; ++n) a[n] = buf[addr(b, e0 + n)];
       dft_reg<R3, INV>(a);
 #pragma unroll
-      for (int n = 0; n < R3; ++n) p[n * es] = a[n];
+      for (int n = 0; n < R3; ++n) buf[addr(b, e0 + n)] = a[n];
     }
     __syncthreads();
   };
@@ -209,39 +211,38 @@ __device__ __forceinline__ void team_fft3(float2* buf, int B, int ts, int es, co
   }
 }
 
-template <int N, bool INV>
-__device__ __forceinline__ void team_fft(float2* buf, int B, int ts, int es, const float2* tw, int tws,
-                                         int tid, int nthr) {
+// Two-step version (R3 = 1; dispatches to the three-step one otherwise).
+template <int N, bool INV, typename Addr>
+__device__ __forceinline__ void team_fft_a(float2* buf, int B, const Addr& addr, const float2* tw, int tws, int tid,
+                                           int nthr) {
   constexpr int R1 = FftPlan<N>::R1, R2 = FftPlan<N>::R2;
   if constexpr (FftPlan<N>::R3 > 1) {
-    team_fft3<N, INV>(buf, B, ts, es, tw, tws, tid, nthr);
+    team_fft3a<N, INV>(buf, B, addr, tw, tws, tid, nthr);
     return;
   }
   const int lb = __ffs(B) - 1;
   if (!INV) {
     for (int it = tid; it < B * R2; it += nthr) {
       const int b = it & (B - 1), n2 = it >> lb;
-      float2* p = buf + b * ts + n2 * es;
       float2 a[R1];
 #pragma unroll
-      for (int n1 = 0; n1 < R1; ++n1) a[n1] = p[n1 * R2 * es];
+      for (int n1 = 0; n1 < R1; ++n1) a[n1] = buf[addr(b, n1 * R2 + n2)];
       dft_reg<R1, false>(a);
 #pragma unroll
       for (int k1 = 1; k1 < R1; ++k1) a[k1] = cmul(a[k1], tw[((n2 * k1) & (N - 1)) * tws]);
 #pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1) p[k1 * R2 * es] = a[k1];
+      for (int k1 = 0; k1 < R1; ++k1) buf[addr(b, k1 * R2 + n2)] = a[k1];
     }
     __syncthreads();
     if (R2 > 1) {
       for (int it = tid; it < B * R1; it += nthr) {
         const int b = it & (B - 1), k1 = it >> lb;
-        float2* p = buf + b * ts + k1 * R2 * es;
         float2 a[R2];
 #pragma unroll
-        for (int n2 = 0; n2 < R2; ++n2) a[n2] = p[n2 * es];
+        for (int n2 = 0; n2 < R2; ++n2) a[n2] = buf[addr(b, k1 * R2 + n2)];
         dft_reg<R2, false>(a);
 #pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) p[k2 * es] = a[k2];
+        for (int k2 = 0; k2 < R2; ++k2) buf[addr(b, k1 * R2 + k2)] = a[k2];
       }
       __syncthreads();
     }
@@ -249,30 +250,39 @@ __device__ __forceinline__ void team_fft(float2* buf, int B, int ts, int es, con
     if (R2 > 1) {
       for (int it = tid; it < B * R1; it += nthr) {
         const int b = it & (B - 1), k1 = it >> lb;
-        float2* p = buf + b * ts + k1 * R2 * es;
         float2 a[R2];
 #pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) a[k2] = p[k2 * es];
+        for (int k2 = 0; k2 < R2; ++k2) a[k2] = buf[addr(b, k1 * R2 + k2)];
         dft_reg<R2, true>(a);
 #pragma unroll
         for (int n2 = 1; n2 < R2; ++n2) a[n2] = cmulc(a[n2], tw[((n2 * k1) & (N - 1)) * tws]);
 #pragma unroll
-        for (int n2 = 0; n2 < R2; ++n2) p[n2 * es] = a[n2];
+        for (int n2 = 0; n2 < R2; ++n2) buf[addr(b, k1 * R2 + n2)] = a[n2];
       }
       __syncthreads();
     }
     for (int it = tid; it < B * R2; it += nthr) {
       const int b = it & (B - 1), n2 = it >> lb;
-      float2* p = buf + b * ts + n2 * es;
       float2 a[R1];
 #pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1) a[k1] = p[k1 * R2 * es];
+      for (int k1 = 0; k1 < R1; ++k1) a[k1] = buf[addr(b, k1 * R2 + n2)];
       dft_reg<R1, true>(a);
 #pragma unroll
-      for (int n1 = 0; n1 < R1; ++n1) p[n1 * R2 * es] = a[n1];
+      for (int n1 = 0; n1 < R1; ++n1) buf[addr(b, n1 * R2 + n2)] = a[n1];
     }
     __syncthreads();
   }
+}
+
+// Strided layout: element e of transform b at buf[b * ts + e * es].
+struct StridedAddr {
+  int ts, es;
+  __device__ __forceinline__ int operator()(int b, int e) const { return b * ts + e * es; }
+};
+template <int N, bool INV>
+__device__ __forceinline__ void team_fft(float2* buf, int B, int ts, int es, const float2* tw, int tws, int tid,
+                                         int nthr) {
+  team_fft_a<N, INV>(buf, B, StridedAddr{ts, es}, tw, tws, tid, nthr);
 }
 
 // Global -> shared staging with U independent loads in flight per thread:

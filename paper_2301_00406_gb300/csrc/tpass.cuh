@@ -39,7 +39,51 @@ template <int NT>
 struct TP {
   static constexpr int COLS = NT >= 1024 ? 8 : 16;  // columns per CTA (heuristic default)
   static constexpr int PAIRS = COLS / 2;
-  static constexpr int WP = NT + 1;                 // odd pitch of a work transform
+};
+
+// Shared-memory layout of the packed pair transforms ("work"): element e of
+// transform p sits at p * pitch + swz(e), where swz XORs a linear function of
+// e's bits 4 and up into its low four bits (the float2 bank slot) and the
+// pitch NT + pad depends on the number of transforms per CTA.  The constants
+// come from a bank model of the access patterns of the shared-memory FFT steps
+// (lanes over transforms and over stride-R positions): with them a warp's
+// accesses need at most two wavefronts per half-warp where the plain odd pitch
+// needed up to eight.
+template <int NT>
+struct WLay;
+#define NLOS_WLAY(NTV, NBV, C0, C1, C2, C3, C4, C5, P1V, P2V, P4V, P8V)                                          \
+  template <>                                                                                                      \
+  struct WLay<NTV> {                                                                                               \
+    static constexpr int NB = NBV, P1 = P1V, P2 = P2V, P4 = P4V, P8 = P8V;                                        \
+    __host__ __device__ static constexpr int L(int i) {                                                            \
+      return i == 0 ? C0 : i == 1 ? C1 : i == 2 ? C2 : i == 3 ? C3 : i == 4 ? C4 : C5;                             \
+    }                                                                                                              \
+  };
+NLOS_WLAY(16, 0, 0, 0, 0, 0, 0, 0, 2, 6, 5, 6)
+NLOS_WLAY(32, 1, 1, 0, 0, 0, 0, 0, 1, 6, 3, 6)
+NLOS_WLAY(64, 2, 2, 4, 0, 0, 0, 0, 1, 8, 12, 2)
+NLOS_WLAY(128, 3, 7, 12, 6, 0, 0, 0, 0, 8, 2, 6)
+NLOS_WLAY(256, 4, 3, 13, 11, 4, 0, 0, 12, 8, 3, 6)
+NLOS_WLAY(512, 5, 13, 6, 10, 2, 3, 0, 2, 8, 4, 2)
+NLOS_WLAY(1024, 6, 10, 13, 11, 12, 4, 9, 4, 8, 12, 6)
+#undef NLOS_WLAY
+
+template <int NT>
+__host__ __device__ constexpr int work_pitch(int pairs) {
+  return NT + (pairs >= 8 ? WLay<NT>::P8 : pairs == 4 ? WLay<NT>::P4 : pairs == 2 ? WLay<NT>::P2 : WLay<NT>::P1);
+}
+template <int NT>
+__device__ __forceinline__ int work_swz(int e) {
+  int v = e;
+#pragma unroll
+  for (int i = 0; i < WLay<NT>::NB; ++i)
+    if ((e >> (4 + i)) & 1) v ^= WLay<NT>::L(i);
+  return v;
+}
+template <int NT>
+struct WorkAddr {
+  int pitch;
+  __device__ __forceinline__ int operator()(int p, int e) const { return p * pitch + work_swz<NT>(e); }
 };
 constexpr int kTpassThreads = 256;
 
@@ -126,15 +170,15 @@ __device__ __forceinline__ void load_pair(const float2* __restrict__ row, int ca
 template <int NT>
 __device__ __forceinline__ void tfwd_post_store(const float2* work, int half, float2* S, int pitch, int col0,
                                                 int ncols, int COLS, int tid, int nthr) {
-  constexpr int WP = TP<NT>::WP;
+  const WorkAddr<NT> wa{work_pitch<NT>(COLS >> 1)};
   const int nk = half ? NT / 2 : NT / 2 + 1;
   const int lc = __ffs(COLS) - 1;  // COLS is a power of two
   for (int i = tid; i < nk * COLS; i += nthr) {
     const int kp = i >> lc, c = i & (COLS - 1), p = c >> 1;
     if (col0 + c >= ncols) continue;
     const int m = half ? (NT - 1 - kp) : ((NT - kp) & (NT - 1));
-    const float2 za = work[p * WP + fpos<NT>(kp)];
-    const float2 zb = work[p * WP + fpos<NT>(m)];
+    const float2 za = work[wa(p, fpos<NT>(kp))];
+    const float2 zb = work[wa(p, fpos<NT>(m))];
     float2 x;
     if ((c & 1) == 0)
       x = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
@@ -150,7 +194,7 @@ __device__ __forceinline__ void tfwd_post_store(const float2* work, int half, fl
 template <int NT>
 __device__ __forceinline__ void tinv_load(const float2* __restrict__ S, int pitch, int col0, int ncols, int half,
                                           float2* work, int PAIRS, int tid, int nthr) {
-  constexpr int WP = TP<NT>::WP;
+  const WorkAddr<NT> wa{work_pitch<NT>(PAIRS)};
   const int lp = __ffs(PAIRS) - 1;
   batched_copy<8, float2>(
       NT * PAIRS, tid, nthr,
@@ -168,7 +212,7 @@ __device__ __forceinline__ void tinv_load(const float2* __restrict__ S, int pitc
         }
         return make_float2(A.x - B.y, A.y + B.x);
       },
-      [&](int i, float2 z) { work[(i & (PAIRS - 1)) * WP + fpos<NT>(i >> lp)] = z; });
+      [&](int i, float2 z) { work[wa(i & (PAIRS - 1), fpos<NT>(i >> lp))] = z; });
 }
 
 // Inverse padded t-FFT of the CTA's pairs: cbuf[c][n] = (1/(2nt)) * real signal
@@ -176,15 +220,15 @@ __device__ __forceinline__ void tinv_load(const float2* __restrict__ S, int pitc
 template <int NT>
 __device__ __forceinline__ void tinv_core(const float2* __restrict__ S, int pitch, int col0, int ncols,
                                           float2* work, float* cbuf, const float2* tw2, int PAIRS, int tid, int nthr) {
-  constexpr int WP = TP<NT>::WP;
+  const WorkAddr<NT> wa{work_pitch<NT>(PAIRS)};
   const float scale = 1.0f / (2.0f * NT);
   for (int half = 0; half < 2; ++half) {
     tinv_load<NT>(S, pitch, col0, ncols, half, work, PAIRS, tid, nthr);
     __syncthreads();
-    team_fft<NT, true>(work, PAIRS, WP, 1, tw2, 2, tid, nthr);
+    team_fft_a<NT, true>(work, PAIRS, wa, tw2, 2, tid, nthr);
     for (int i = tid; i < PAIRS * NT; i += nthr) {
       const int p = i / NT, n = i % NT;
-      float2 z = work[p * WP + n];
+      float2 z = work[wa(p, n)];
       if (half) z = cmulc(z, tw2[n]);
       float* ca = cbuf + (2 * p) * NT;
       float* cb = ca + NT;
@@ -210,12 +254,12 @@ __global__ void __launch_bounds__(kTpassThreads)
            const int32_t* __restrict__ tptr, const float2* __restrict__ tent, const float2* __restrict__ tw2g,
            int cols) {
   const int COLS = cols, PAIRS = cols >> 1;
-  constexpr int WP = TP<NT>::WP;
+  const WorkAddr<NT> wa{work_pitch<NT>(PAIRS)};
   extern __shared__ float4 smem_f4[];
   float2* tw2 = reinterpret_cast<float2*>(smem_f4);
   float4* tab = reinterpret_cast<float4*>(tw2 + 2 * NT);
   float2* work = reinterpret_cast<float2*>(tab + TabLayout<NT>::SLOTS);
-  float* cbuf = reinterpret_cast<float*>(work + ((PAIRS * WP + 1) & ~1));
+  float* cbuf = reinterpret_cast<float*>(work + ((PAIRS * wa.pitch + 1) & ~1));
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int col0 = blockIdx.x * COLS;
   for (int i = tid; i < 2 * NT; i += nthr) tw2[i] = __ldg(tw2g + i);
@@ -271,10 +315,10 @@ __global__ void __launch_bounds__(kTpassThreads)
         z = csr_row2<NT>(tab, n, ca, cb);
       }
       if (half) z = cmul(z, tw2[n]);
-      work[p * WP + n] = z;
+      work[wa(p, n)] = z;
     }
     __syncthreads();
-    team_fft<NT, false>(work, PAIRS, WP, 1, tw2, 2, tid, nthr);
+    team_fft_a<NT, false>(work, PAIRS, wa, tw2, 2, tid, nthr);
     tfwd_post_store<NT>(work, half, S, pitch, col0, ncols, COLS, tid, nthr);
     __syncthreads();
   }
@@ -289,12 +333,12 @@ __global__ void __launch_bounds__(kTpassThreads)
            const int32_t* __restrict__ outmap, FitArgs fa, const float4* __restrict__ ftab,
            const float2* __restrict__ tw2g, int cols) {
   const int COLS = cols, PAIRS = cols >> 1;
-  constexpr int WP = TP<NT>::WP;
+  const WorkAddr<NT> wa{work_pitch<NT>(PAIRS)};
   extern __shared__ float4 smem_f4[];
   float2* tw2 = reinterpret_cast<float2*>(smem_f4);
   float4* tab = reinterpret_cast<float4*>(tw2 + 2 * NT);
   float2* work = reinterpret_cast<float2*>(tab + TabLayout<NT>::SLOTS);
-  float* cbuf = reinterpret_cast<float*>(work + ((PAIRS * WP + 1) & ~1));
+  float* cbuf = reinterpret_cast<float*>(work + ((PAIRS * wa.pitch + 1) & ~1));
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int col0 = blockIdx.x * COLS;
   for (int i = tid; i < 2 * NT; i += nthr) tw2[i] = __ldg(tw2g + i);
@@ -344,13 +388,13 @@ __global__ void __launch_bounds__(kTpassThreads)
 template <int NT>
 __device__ __forceinline__ void periodic_fwd_post(const float2* work, float2* Sp, int col0, int ncols, int pitch,
                                                   int COLS, int tid, int nthr) {
-  constexpr int WP = TP<NT>::WP;
+  const WorkAddr<NT> wa{work_pitch<NT>(COLS >> 1)};
   const int lc = __ffs(COLS) - 1;  // COLS is a power of two
   for (int i = tid; i < (NT / 2 + 1) * COLS; i += nthr) {
     const int k = i >> lc, c = i & (COLS - 1), p = c >> 1;
     if (col0 + c >= ncols) continue;
-    const float2 za = work[p * WP + fpos<NT>(k)];
-    const float2 zb = work[p * WP + fpos<NT>((NT - k) & (NT - 1))];
+    const float2 za = work[wa(p, fpos<NT>(k))];
+    const float2 zb = work[wa(p, fpos<NT>((NT - k) & (NT - 1)))];
     float2 x;
     if ((c & 1) == 0)
       x = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
@@ -366,12 +410,12 @@ __global__ void __launch_bounds__(kTpassThreads)
            float2* __restrict__ Sp, const int32_t* __restrict__ tptr, const float2* __restrict__ tent,
            const float2* __restrict__ tw2g, int cols) {
   const int COLS = cols, PAIRS = cols >> 1;
-  constexpr int WP = TP<NT>::WP;
+  const WorkAddr<NT> wa{work_pitch<NT>(PAIRS)};
   extern __shared__ float4 smem_f4[];
   float2* tw2 = reinterpret_cast<float2*>(smem_f4);
   float4* tab = reinterpret_cast<float4*>(tw2 + 2 * NT);
   float2* work = reinterpret_cast<float2*>(tab + TabLayout<NT>::SLOTS);
-  float* cbuf = reinterpret_cast<float*>(work + ((PAIRS * WP + 1) & ~1));
+  float* cbuf = reinterpret_cast<float*>(work + ((PAIRS * wa.pitch + 1) & ~1));
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int col0 = blockIdx.x * COLS;
   for (int i = tid; i < 2 * NT; i += nthr) tw2[i] = __ldg(tw2g + i);
@@ -417,10 +461,10 @@ __global__ void __launch_bounds__(kTpassThreads)
         const float2 gv = csr_row2<NT>(tab, n, cbuf + (2 * p) * NT, cbuf + (2 * p + 1) * NT);
         const float a = ca < ncols ? L * v.x - gv.x + v.y : 0.f;
         const float b = cb < ncols ? L * v.z - gv.y + v.w : 0.f;
-        work[p * WP + n] = make_float2(a, b);
+        work[wa(p, n)] = make_float2(a, b);
       });
   __syncthreads();
-  team_fft<NT, false>(work, PAIRS, WP, 1, tw2, 2, tid, nthr);
+  team_fft_a<NT, false>(work, PAIRS, wa, tw2, 2, tid, nthr);
   periodic_fwd_post<NT>(work, Sp, col0, ncols, ncols, COLS, tid, nthr);
 }
 
@@ -429,7 +473,7 @@ template <int NT>
 __global__ void __launch_bounds__(kTpassThreads)
     k_sfwd(const float* __restrict__ x, int ncols, float2* __restrict__ Sp, const float2* __restrict__ tw2g, int cols) {
   const int COLS = cols, PAIRS = cols >> 1;
-  constexpr int WP = TP<NT>::WP;
+  const WorkAddr<NT> wa{work_pitch<NT>(PAIRS)};
   extern __shared__ float4 smem_f4[];
   float2* tw2 = reinterpret_cast<float2*>(smem_f4);
   float2* work = tw2 + 2 * NT;
@@ -444,9 +488,9 @@ __global__ void __launch_bounds__(kTpassThreads)
         return make_float2(ca < ncols ? __ldg(x + (size_t)ca * NT + n) : 0.f,
                            cb < ncols ? __ldg(x + (size_t)cb * NT + n) : 0.f);
       },
-      [&](int i, float2 z) { work[(i / NT) * WP + i % NT] = z; });
+      [&](int i, float2 z) { work[wa(i / NT, i % NT)] = z; });
   __syncthreads();
-  team_fft<NT, false>(work, PAIRS, WP, 1, tw2, 2, tid, nthr);
+  team_fft_a<NT, false>(work, PAIRS, wa, tw2, 2, tid, nthr);
   periodic_fwd_post<NT>(work, Sp, col0, ncols, ncols, COLS, tid, nthr);
 }
 
@@ -456,7 +500,7 @@ __global__ void __launch_bounds__(kTpassThreads)
     k_sinv(const float2* __restrict__ Sp, int ncols, float* __restrict__ x, const float* __restrict__ ref,
            double* __restrict__ partials, const float2* __restrict__ tw2g, int cols) {
   const int COLS = cols, PAIRS = cols >> 1;
-  constexpr int WP = TP<NT>::WP;
+  const WorkAddr<NT> wa{work_pitch<NT>(PAIRS)};
   extern __shared__ float4 smem_f4[];
   float2* tw2 = reinterpret_cast<float2*>(smem_f4);
   float2* work = tw2 + 2 * NT;
@@ -480,9 +524,9 @@ __global__ void __launch_bounds__(kTpassThreads)
         }
         return make_float2(A.x - B.y, A.y + B.x);
       },
-      [&](int i, float2 z) { work[(i & (PAIRS - 1)) * WP + fpos<NT>(i >> lp)] = z; });
+      [&](int i, float2 z) { work[wa(i & (PAIRS - 1), fpos<NT>(i >> lp))] = z; });
   __syncthreads();
-  team_fft<NT, true>(work, PAIRS, WP, 1, tw2, 2, tid, nthr);
+  team_fft_a<NT, true>(work, PAIRS, wa, tw2, 2, tid, nthr);
   const float scale = 1.0f / NT;
   ChunkAcc<1> ca;
   const int total = min(COLS, ncols - col0) * NT;
@@ -490,7 +534,7 @@ __global__ void __launch_bounds__(kTpassThreads)
       total, tid, nthr, [&](int i) { return ref ? __ldg(ref + (size_t)col0 * NT + i) : 0.f; },
       [&](int i, float rv) {
         const int c = i / NT, n = i % NT;
-        const float2 z = work[(c >> 1) * WP + n];
+        const float2 z = work[wa(c >> 1, n)];
         const float v = ((c & 1) ? z.y : z.x) * scale;
         x[(size_t)col0 * NT + i] = v;
         if (ref) {
@@ -534,7 +578,7 @@ static TpShape tp_shape(int ncols, int extra, bool tab, int kind) {
   sh.blocks = div_up(ncols, sh.cols);
   // the work region is padded to an even number of float2 so the real column
   // buffers after it stay 16-byte aligned (float4 accesses)
-  sh.smem = sizeof(float2) * (2 * NT + (((sh.cols / 2) * TP<NT>::WP + 1) & ~1)) +
+  sh.smem = sizeof(float2) * (2 * NT + (((sh.cols / 2) * work_pitch<NT>(sh.cols / 2) + 1) & ~1)) +
             (tab ? sizeof(float4) * TabLayout<NT>::SLOTS : 0) + sizeof(float) * extra * sh.cols * NT;
   return sh;
 }
