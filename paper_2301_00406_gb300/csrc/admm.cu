@@ -313,13 +313,15 @@ __global__ void __launch_bounds__(kStencilThreads)
     k_lam3(const float* __restrict__ tnew, const float* __restrict__ tb, const float* __restrict__ au,
            const float* __restrict__ tau0, float* __restrict__ lam3, const int32_t* __restrict__ colpos, Vox g,
            VoxIter vi, float lam_w, float mu3, size_t V, double* __restrict__ partials) {
+  const float inv_d1 = 1.0f / (lam_w + mu3), inv_d0 = 1.0f / mu3;  // lambda M + mu3, M = 1 or 0
   ChunkAcc<3> ca;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V; i += (size_t)gridDim.x * blockDim.x) {
     int x, y, t;
     vi.decode(i, g, x, y, t);
-    const float m = colpos ? (__ldg(colpos + x * g.ny + y) >= 0 ? 1.0f : 0.0f) : 1.0f;
+    const bool sampled = colpos ? __ldg(colpos + x * g.ny + y) >= 0 : true;
+    const float m = sampled ? 1.0f : 0.0f;
     const float t0 = __ldg(tau0 + i), tn = __ldg(tnew + i), l3 = lam3[i];
-    const float f = (lam_w * m * t0 + mu3 * __ldg(tb + i) - l3) / (lam_w * m + mu3);
+    const float f = (lam_w * m * t0 + mu3 * __ldg(tb + i) - l3) * (sampled ? inv_d1 : inv_d0);
     lam3[i] = l3 + mu3 * (f - tn);
     const float r = __ldg(au + i) - tn, sres = m * (tn - t0), fr = f - tn;
     ca.add(0, r * r);

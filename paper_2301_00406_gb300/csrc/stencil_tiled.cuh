@@ -253,6 +253,7 @@ __global__ void __launch_bounds__(kTileThreads, 3)
   const int iy = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const float inv_mu = 1.0f / mu;
   const float* lfields[4] = {lam, lam + V, lam + 2 * V, ph};
+  const float inv_d1 = 1.0f / (ft.lam_w + ft.mu3), inv_d0 = 1.0f / ft.mu3;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const TileIdx T = tile_of(tile, g);
     const int y = T.y0 + iy;
@@ -308,11 +309,13 @@ __global__ void __launch_bounds__(kTileThreads, 3)
         const size_t gi = g.idx(x, y, T.t0 + it);
         float out = -mu * div;
         if (FTERM) {
-          const float m = ft.colpos ? (__ldg(ft.colpos + x * g.ny + y) >= 0 ? 1.0f : 0.0f) : 1.0f;
+          // the denominator lambda M + mu3 takes two values: sampled or not
+          const bool sampled = ft.colpos ? __ldg(ft.colpos + x * g.ny + y) >= 0 : true;
+          const float m = sampled ? 1.0f : 0.0f;
           const float l3 = __ldg(ft.lam3 + gi);
           const float tb = Ux[(iy + 1) * kP + it + kC];
-          const float f = (ft.lam_w * m * __ldg(ft.tau0 + gi) + ft.mu3 * tb - l3) / (ft.lam_w * m + ft.mu3);
-          out += ft.mu3 * (f + l3 / ft.mu3);
+          const float f = (ft.lam_w * m * __ldg(ft.tau0 + gi) + ft.mu3 * tb - l3) * (sampled ? inv_d1 : inv_d0);
+          out += ft.mu3 * f + l3;
         }
         reg[gi] = out;
         qx_prev[j] = qx;
