@@ -78,6 +78,10 @@ __host__ __device__ __forceinline__ constexpr int swz(int x) {
     if ((x >> b) & 1) v ^= swc<N>(b);
   return v;
 }
+// swz is linear over GF(2): for x = a + b with disjoint bits, swz(x) =
+// swz(a) ^ swz(b).  The phases below split row indices into a lane-constant
+// part and an iteration (or compile-time) part and combine the two.
+
 // In-row position of the intermediate value (n2, k1) between the two steps
 // of a y transform, and within a (column, parity) slot of the x scratch.
 __device__ __forceinline__ constexpr int ipos(int n2, int k1) { return 8 * n2 + (k1 ^ (n2 & 7)); }
@@ -139,8 +143,15 @@ __device__ __forceinline__ void c4_yfwd(float2* __restrict__ plane, const float2
       }
     }
   };
+  // swizzles of the lane's row offsets within a row group (rsub, and the
+  // step-2 items' rows lane / 8 + 4 j)
+  const int s_rsub = swz<N>(rsub);
+  int s_item[8 / R2];
+#pragma unroll
+  for (int j = 0; j < 8 / R2; ++j) s_item[j] = swz<N>((lane + 32 * j) / 8);
   fetch(warp);
   for (int it = warp; it < N / RW; it += C::WARPS) {
+    const int s_it = swz<N>(it * RW);
     {
       const int x = it * RW + rsub;
       float2 cu[8], cv[8];
@@ -162,7 +173,7 @@ __device__ __forceinline__ void c4_yfwd(float2* __restrict__ plane, const float2
         }
         dft_reg<8, false>(a);
         float2* prow = plane + x * M;
-        const int s = swz<N>(x);
+        const int s = s_it ^ s_rsub;
 #pragma unroll
         for (int k1 = 0; k1 < 8; ++k1) prow[ipos(n2, k1) ^ s] = cmul(a[k1], twa[k1]);
       }
@@ -175,7 +186,7 @@ __device__ __forceinline__ void c4_yfwd(float2* __restrict__ plane, const float2
       const int i = lane + 32 * j, xx = it * RW + i / 8, k1 = i % 8;
       if (rowin[xx]) {
         const float2* pr = plane + xx * M;
-        const int ss = swz<N>(xx);
+        const int ss = s_it ^ s_item[j];
 #pragma unroll
         for (int m = 0; m < R2; ++m) b[j][m] = pr[ipos(m, k1) ^ ss];
         dft_reg<R2, false>(b[j]);
@@ -189,7 +200,7 @@ __device__ __forceinline__ void c4_yfwd(float2* __restrict__ plane, const float2
     for (int j = 0; j < 8 / R2; ++j) {
       const int i = lane + 32 * j, xx = it * RW + i / 8, k1 = i % 8;
       float2* pr = plane + xx * M;
-      const int ss = swz<N>(xx);
+      const int ss = s_it ^ s_item[j];
 #pragma unroll
       for (int k2 = 0; k2 < R2; ++k2) pr[(k1 + 8 * k2) ^ ss] = b[j][k2];
     }
@@ -213,14 +224,19 @@ __device__ __forceinline__ void c4_yinv(float2* __restrict__ plane, const float2
 #pragma unroll
     for (int m = 1; m < R2; ++m) twi[m] = cmul(twi[m - 1], st);
   }
+  const int s_rsub = swz<N>(rsub);
+  int s_item[8 / R2];
+#pragma unroll
+  for (int j = 0; j < 8 / R2; ++j) s_item[j] = swz<N>((lane + 32 * j) / 8);
   for (int it = warp; it < N / RW; it += C::WARPS) {
+    const int s_it = swz<N>(it * RW);
     float2 b[8 / R2][R2];
 #pragma unroll
     for (int j = 0; j < 8 / R2; ++j) {
       const int i = lane + 32 * j, xx = it * RW + i / 8, k1 = i % 8;
       if (rowout[xx]) {
         const float2* pr = plane + xx * M;
-        const int ss = swz<N>(xx);
+        const int ss = s_it ^ s_item[j];
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2) b[j][k2] = pr[(k1 + 8 * k2) ^ ss];
         dft_reg<R2, true>(b[j]);
@@ -234,7 +250,7 @@ __device__ __forceinline__ void c4_yinv(float2* __restrict__ plane, const float2
       const int i = lane + 32 * j, xx = it * RW + i / 8, k1 = i % 8;
       if (rowout[xx]) {
         float2* pr = plane + xx * M;
-        const int ss = swz<N>(xx);
+        const int ss = s_it ^ s_item[j];
 #pragma unroll
         for (int m = 0; m < R2; ++m) pr[ipos(m, k1) ^ ss] = b[j][m];
       }
@@ -244,7 +260,7 @@ __device__ __forceinline__ void c4_yinv(float2* __restrict__ plane, const float2
     float2 e[8];
     const bool live = rowout[x] != 0;
     float2* prow = plane + x * M;
-    const int s = swz<N>(x);
+    const int s = s_it ^ s_rsub;
     if (live) {
 #pragma unroll
       for (int k1 = 0; k1 < 8; ++k1) e[k1] = prow[ipos(n2, k1) ^ s];
@@ -361,6 +377,7 @@ __device__ __forceinline__ void c4_xconv(float2* __restrict__ plane, float2* __r
         keep[n1] = cadd(mine, got);
       }
       const int h = p & 1, hi = p >> 1;
+      const int s_out = sn2 ^ swz<N>(R2 * 4 * hi + M * h);  // row bits fixed per lane
 #pragma unroll
       for (int jj = 0; jj < 4; ++jj) {
         const float2 send = hi ? keep[jj] : keep[4 + jj];
@@ -368,7 +385,7 @@ __device__ __forceinline__ void c4_xconv(float2* __restrict__ plane, float2* __r
         const float2 got = make_float2(__shfl_xor_sync(0xffffffffu, send.x, 2 * R2),
                                        __shfl_xor_sync(0xffffffffu, send.y, 2 * R2));
         const int x = n2 + R2 * (4 * hi + jj) + M * h;
-        plane[x * M + (c ^ swz<N>(x))] = cadd(mine, got);
+        plane[x * M + (c ^ s_out ^ swz<N>(R2 * jj))] = cadd(mine, got);
       }
     }
     __syncwarp();
