@@ -217,12 +217,18 @@ def run_ours(args):
         p.iters = iters
         return plan.reconstruct(p, tau_ptr or tau0.data_ptr(), out_ptr or u_out.data_ptr(), 0, stream)
 
+    def prepare(iters, tau_ptr=None, out_ptr=None):
+        # capture the run's graph outside the timed region (no iterations run)
+        p.iters = iters
+        return plan.reconstruct_prepare(p, tau_ptr or tau0.data_ptr(), out_ptr or u_out.data_ptr(), 0, stream)
+
     def barrier():
         if world > 1:
             import torch.distributed as dist
             dist.barrier()
 
     recon(args.warmup)                       # warm-up (also computes ||A_D||^2 once)
+    graphed = prepare(args.steps)
     torch.cuda.synchronize()
 
     # timed region: K iterations of one reconstruction, inputs resident in HBM
@@ -253,6 +259,7 @@ def run_ours(args):
     tau0_pin = torch.tensor(tau0_h, dtype=torch.float32).pin_memory()
     u_pin = torch.empty_like(tau0_pin).pin_memory()
     tau_d = torch.empty_like(tau0)
+    prepare(args.steps, tau_d.data_ptr(), u_out.data_ptr())
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -275,6 +282,8 @@ def run_ours(args):
     plan.reconstruct(p2, tau0.data_ptr(), u_out.data_ptr(), tau_out.data_ptr(), stream)
     torch.cuda.synchronize()
     p2.iters = args.steps
+    plan.reconstruct_prepare(p2, tau0.data_ptr(), u_out.data_ptr(), tau_out.data_ptr(), stream)
+    torch.cuda.synchronize()
     a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a0.record()
     plan.reconstruct(p2, tau0.data_ptr(), u_out.data_ptr(), tau_out.data_ptr(), stream)
@@ -316,7 +325,8 @@ def run_ours(args):
         "config": {"workload": "alg1_128x128x512_16ps_32x32_sampled", "nx": nx, "ny": ny, "nt": nt,
                    "sampled_columns": ncols, "model": "object-domain curvature ADMM (Algorithm 1)",
                    "iters_per_reconstruction": args.steps, "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "working set ~0.7 GB > 129 MB L2; no flush needed"},
+                   "l2": "working set ~0.7 GB > 129 MB L2; no flush needed",
+                   "graph": "whole reconstruction captured before the timed region" if graphed else "no graph"},
         "clocks": clocks,
         "e2e": {"value": round(job_rate(args.steps, world, e2e_ms), 2), "unit": "iter/s",
                 "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": nbytes / args.steps,

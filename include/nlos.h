@@ -185,6 +185,20 @@ nlos_status nlos_reconstruct(nlos_plan plan, const nlos_params* params, const fl
                              float* u_out_dev, float* tau_out_dev, nlos_stats* stats_host,
                              void* stream);
 
+/* Prepare the reconstruction that nlos_reconstruct would run with exactly these
+ * arguments (same parameters and the same device pointers) without running it:
+ * allocate the solver state, compute the operator norm if the plan lacks it
+ * (host synchronisation on `stream`), and capture and cache the CUDA graph of
+ * the whole run (the plan keeps four).  A following nlos_reconstruct with the
+ * same arguments is then one graph launch with no capture work, e.g. inside
+ * a timed or latency-critical region.  *graphed (nullable) = 1 when a graph is
+ * cached, 0 when the run needs host decisions between iterations (eps_stop >
+ * 0, or L0 below 1.5 ||A_D||^2 so that backtracking can reject) and will run
+ * without one.  Argument rules and errors as nlos_reconstruct; nothing is
+ * written to u_out_dev or tau_out_dev. */
+nlos_status nlos_reconstruct_prepare(nlos_plan plan, const nlos_params* params, const float* tau0_dev,
+                                     float* u_out_dev, float* tau_out_dev, int32_t* graphed, void* stream);
+
 /* Reconstruct n independent scenes at once.  plans[i] must be n distinct
  * plans (each owns its scratch; a plan appearing twice is rejected);
  * params[i], tau0[i] (device), u_out[i] (device) and tau_out[i] (device,

@@ -1073,27 +1073,29 @@ void free_graphs(Plan* P) {
   P->capture_stream = nullptr;
 }
 
-nlos_status job_enqueue_graph(JobRun& j, cudaStream_t launch, bool* used) {
-  *used = false;
+// The cached graph of run j (same parameters and buffers), captured and
+// cached on first use; *exec = nullptr when the run needs host decisions
+// between iterations or the plan's kernels are being timed.
+static nlos_status job_graph(JobRun& j, cudaStream_t st, cudaGraphExec_t* exec) {
+  *exec = nullptr;
   Plan& P = *j.P;
   const nlos_params& p = j.p;
   if (P.timing) return NLOS_OK;
   // everything that may synchronise or allocate happens before the capture
   NLOS_TRY(get_solver(P, p.model, &j.s));
-  NLOS_TRY(plan_norm2(P, p.model == 1, launch, &j.norm2));
+  NLOS_TRY(plan_norm2(P, p.model == 1, st, &j.norm2));
   if (p.model == 2 && p.warm_start_iters > 0) {
     SolverState* s1 = nullptr;
     double n1 = 0.0;
     NLOS_TRY(get_solver(P, 1, &s1));
-    NLOS_TRY(plan_norm2(P, true, launch, &n1));
+    NLOS_TRY(plan_norm2(P, true, st, &n1));
   }
   const double L0 = p.L0 > 0.0 ? p.L0 : 2.0 * j.norm2;
   if (p.eps_stop > 0.0 || L0 < 1.5 * j.norm2 || p.iters <= 0) return NLOS_OK;
   for (auto& g : P.graphs)
     if (std::memcmp(&g.p, &p, sizeof(nlos_params)) == 0 && g.tau0 == j.tau0 && g.u_out == j.u_out &&
         g.tau_out == j.tau_out) {
-      NLOS_CUDA(cudaGraphLaunch(g.exec, launch));
-      *used = true;
+      *exec = g.exec;
       return NLOS_OK;
     }
   if (!P.capture_stream) NLOS_CUDA(cudaStreamCreateWithFlags(&P.capture_stream, cudaStreamNonBlocking));
@@ -1110,19 +1112,48 @@ nlos_status job_enqueue_graph(JobRun& j, cudaStream_t launch, bool* used) {
     return s;
   }
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-  cudaGraphExec_t exec = nullptr;
-  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphExec_t ge = nullptr;
+  e = cudaGraphInstantiate(&ge, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
   if (P.graphs.size() >= 4) {
     cudaGraphExecDestroy(P.graphs.front().exec);
     P.graphs.erase(P.graphs.begin());
   }
-  P.graphs.push_back(Plan::GraphEntry{p, j.tau0, j.u_out, j.tau_out, exec});
-  NLOS_CUDA(cudaGraphLaunch(exec, launch));
+  P.graphs.push_back(Plan::GraphEntry{p, j.tau0, j.u_out, j.tau_out, ge});
   j.s = c.s;
+  *exec = ge;
+  return NLOS_OK;
+}
+
+nlos_status job_enqueue_graph(JobRun& j, cudaStream_t launch, bool* used) {
+  *used = false;
+  cudaGraphExec_t exec = nullptr;
+  NLOS_TRY(job_graph(j, launch, &exec));
+  if (!exec) return NLOS_OK;
+  NLOS_CUDA(cudaGraphLaunch(exec, launch));
   *used = true;
   return NLOS_OK;
+}
+
+nlos_status job_prepare_graph(JobRun& j, cudaStream_t st, bool* ready) {
+  cudaGraphExec_t exec = nullptr;
+  NLOS_TRY(job_graph(j, st, &exec));
+  *ready = exec != nullptr;
+  return NLOS_OK;
+}
+
+nlos_status reconstruct_prepare(Plan& P, const nlos_params& p, const float* tau0, float* u_out, float* tau_out,
+                                bool* ready, cudaStream_t st) {
+  if (p.model != 1 && p.model != 2) return fail(NLOS_ERR_INVALID_ARG, "params->model must be 1 or 2");
+  JobRun j;
+  j.P = &P;
+  j.p = p;
+  j.tau0 = tau0;
+  j.u_out = u_out;
+  j.tau_out = tau_out;
+  j.st = st;
+  return job_prepare_graph(j, st, ready);
 }
 
 nlos_status reconstruct(Plan& P, const nlos_params& p, const float* tau0, float* u_out, float* tau_out,

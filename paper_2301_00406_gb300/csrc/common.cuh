@@ -286,6 +286,11 @@ nlos_status job_collect(JobRun& j, nlos_stats* stats);
 // decisions (backtracking that can reject, relative-energy stop) or the
 // plan's kernels are being timed.
 nlos_status job_enqueue_graph(JobRun& j, cudaStream_t launch, bool* used);
+// Captures and caches j's graph without launching it (*ready = false when the
+// run needs host decisions and would run without a graph).
+nlos_status job_prepare_graph(JobRun& j, cudaStream_t st, bool* ready);
+nlos_status reconstruct_prepare(Plan& P, const nlos_params& p, const float* tau0, float* u_out, float* tau_out,
+                                bool* ready, cudaStream_t st);
 void free_graphs(Plan* P);
 
 // Launch configuration helpers

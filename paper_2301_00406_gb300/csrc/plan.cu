@@ -597,6 +597,25 @@ nlos_status nlos_reconstruct(nlos_plan plan, const nlos_params* params, const fl
   })
 }
 
+nlos_status nlos_reconstruct_prepare(nlos_plan plan, const nlos_params* params, const float* tau0_dev,
+                                     float* u_out_dev, float* tau_out_dev, int32_t* graphed, void* stream) {
+  API_GUARD({
+    NLOS_TRY(check_plan(plan));
+    if (graphed) *graphed = 0;
+    if (!params || !tau0_dev || !u_out_dev || !aligned16(tau0_dev) || !aligned16(u_out_dev))
+      return fail(NLOS_ERR_INVALID_ARG, "nlos_reconstruct_prepare: null or non-16-byte-aligned pointer");
+    const nlos_params& p = *params;
+    if (p.iters < 0 || !(p.eta > 1.0) || p.max_backtracks < 0 || p.phi < 0 || p.phi > 2 || !(p.eps_normal >= 0.0) ||
+        p.warm_start_iters < 0)
+      return fail(NLOS_ERR_INVALID_ARG, "nlos_reconstruct_prepare: invalid iteration parameters");
+    bool ready = false;
+    NLOS_TRY(reconstruct_prepare(*reinterpret_cast<Plan*>(plan), p, tau0_dev, u_out_dev, tau_out_dev, &ready,
+                                 reinterpret_cast<cudaStream_t>(stream)));
+    if (graphed) *graphed = ready ? 1 : 0;
+    return NLOS_OK;
+  })
+}
+
 nlos_status nlos_timing_enable(nlos_plan plan, int32_t enable) {
   API_GUARD({
     if (!plan) return fail(NLOS_ERR_INVALID_ARG, "null plan");

@@ -78,6 +78,8 @@ _SIGS = {
                                                ctypes.c_int32, ctypes.c_double, _P]),
     "nlos_reconstruct": (ctypes.c_int32, [_P, ctypes.POINTER(Params), _P, _P, _P,
                                           ctypes.POINTER(Stats), _P]),
+    "nlos_reconstruct_prepare": (ctypes.c_int32, [_P, ctypes.POINTER(Params), _P, _P, _P,
+                                                  ctypes.POINTER(ctypes.c_int32), _P]),
     "nlos_solve_static": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P,
                                            ctypes.c_double, ctypes.c_double, _P]),
     "nlos_reconstruct_batch": (ctypes.c_int32, [_P, ctypes.POINTER(Params), _P, _P, _P, ctypes.c_int32,
@@ -211,6 +213,13 @@ class Plan:
 
     def curvature_weight(self, u_ptr, phi_ptr, a, b, phi_kind=0, eps=1e-6, stream=0):
         check(load().nlos_curvature_weight(self.handle, u_ptr, phi_ptr, a, b, phi_kind, eps, stream))
+
+    def reconstruct_prepare(self, params, tau0_ptr, u_ptr, tau_out_ptr=0, stream=0):
+        """Capture the graph reconstruct() would launch for these arguments; True when one is cached."""
+        g = ctypes.c_int32(0)
+        check(load().nlos_reconstruct_prepare(self.handle, ctypes.byref(params), tau0_ptr, u_ptr,
+                                              tau_out_ptr or None, ctypes.byref(g), stream))
+        return bool(g.value)
 
     def reconstruct(self, params, tau0_ptr, u_ptr, tau_out_ptr=0, stream=0):
         st = Stats()

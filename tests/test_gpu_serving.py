@@ -131,3 +131,19 @@ def test_destroy_cancels_queued_jobs(nlos):
     srv.close(cancel_pending=True, timeout_s=60.0)   # returns; no hang
     # ids are gone with the server; the point is that close() returned
     assert len(ids) == 6
+
+
+def test_reconstruct_prepare_then_run_matches_plain_run(nlos):
+    import torch
+    job = make_job(nlos, 3)
+    plan = nlos.Plan(job["n"], job["n"], job["nt"], job["bw"], mask=job["mask"])
+    tau0 = dev(job["tau0"])
+    u_plain = torch.empty_like(tau0)
+    st_plain = plan.reconstruct(job["params"], tau0.data_ptr(), u_plain.data_ptr())
+    u = torch.empty_like(tau0)
+    assert plan.reconstruct_prepare(job["params"], tau0.data_ptr(), u.data_ptr()) is True
+    st = plan.reconstruct(job["params"], tau0.data_ptr(), u.data_ptr())
+    assert torch.equal(u, u_plain) and st["energy"] == st_plain["energy"]
+    p = nlos.params_default(job["params"].model)
+    p.iters, p.eps_stop = 3, 1e-9                       # needs host decisions: no graph
+    assert plan.reconstruct_prepare(p, tau0.data_ptr(), u.data_ptr()) is False
