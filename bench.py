@@ -315,6 +315,20 @@ def run_ours(args):
         roof = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4), "traffic": None, "peak_source": f"hbm_gbs ({src})"}
     step_ms = t_ms / args.steps
+    # whole-iteration HBM model: compulsory bytes of one Algorithm-1 iteration
+    # (each state field read and written once, spectra written and read once,
+    # the kernel spectrum read by both lateral passes)
+    full = nx * ny
+    s_frac = ncols / full
+    F = full * nt * 4
+    S = (nt + 1) * full * 8
+    Sp = (nt // 2 + 1) * full * 8
+    K = (nt + 1) * (nx + 1) * (ny + 1) * 8
+    b_iter = (14 + s_frac) * F + 4 * S + 4 * s_frac * S + 4 * Sp + 2 * K
+    it_gbs = b_iter / (step_ms / 1e3) / 1e9
+    iter_roof = {"bytes_per_iter": round(b_iter), "achieved": round(it_gbs, 1), "peak": peaks["hbm_gbs"],
+                 "unit": "GB/s", "frac": round(it_gbs / peaks["hbm_gbs"], 4),
+                 "note": "model bytes (14+s)F + 4S + 4sS + 4S' + 2K over the measured iteration time"}
     kernels = {k: {"ms_per_step": round(v[0] / args.steps, 4), "launches_per_step": round(v[1] / args.steps, 2)}
                for k, v in kt.items() if v[1] > 0}
 
@@ -333,6 +347,7 @@ def run_ours(args):
                 "note": "one reconstruction of K iterations from pinned host tau0 to pinned host u"},
         "gpu_launches": launches,
         "roofline": roof,
+        "iteration_roofline": iter_roof,
         "kernels": kernels,
         "secondary": {"alg2_iter_per_s": round(args.steps / (alg2_ms / 1e3), 2),
                       "recon_per_s_at_50_iters": round(value / 50.0, 3),
