@@ -84,7 +84,8 @@ typedef struct {
   double eps_stop;       /* relative-energy stop of Algorithms 1/2; 0 = run all iters       */
   double L0;             /* initial L; <= 0 means 2 ||A_D||_2^2 (below Eq. 10)              */
   double eta;            /* backtracking growth factor for L (> 1)                          */
-  int32_t max_backtracks;/* rejections allowed in one iteration before NLOS_ERR_DIVERGED    */
+  int32_t max_backtracks;/* rejections allowed in one iteration before NLOS_ERR_DIVERGED;
+                            0..1000                                                        */
   double eps_normal;     /* regulariser of |grad u| in the normal field                     */
   int32_t restart;       /* FISTA restart on energy increase: 0 off, 1 on, -1 model default
                             (off for model 1, on for model 2)                              */
@@ -191,11 +192,13 @@ nlos_status nlos_reconstruct(nlos_plan plan, const nlos_params* params, const fl
  * (host synchronisation on `stream`), and capture and cache the CUDA graph of
  * the whole run (the plan keeps four).  A following nlos_reconstruct with the
  * same arguments is then one graph launch with no capture work, e.g. inside
- * a timed or latency-critical region.  *graphed (nullable) = 1 when a graph is
- * cached, 0 when the run needs host decisions between iterations (eps_stop >
- * 0, or L0 below 1.5 ||A_D||^2 so that backtracking can reject) and will run
- * without one.  Argument rules and errors as nlos_reconstruct; nothing is
- * written to u_out_dev or tau_out_dev. */
+ * a timed or latency-critical region.  Runs with a relative-energy stop
+ * (eps_stop > 0) or a backtracking rule that can reject (L0 below
+ * 1.5 ||A_D||^2) are graphs too: their iteration loop and backtracking loop
+ * are conditional graph nodes decided on the device, with no host round trip.
+ * *graphed (nullable) = 1 when a graph is cached, 0 when the run will not use
+ * one (kernel timing enabled, or iters = 0).  Argument rules and errors as
+ * nlos_reconstruct; nothing is written to u_out_dev or tau_out_dev. */
 nlos_status nlos_reconstruct_prepare(nlos_plan plan, const nlos_params* params, const float* tau0_dev,
                                      float* u_out_dev, float* tau_out_dev, int32_t* graphed, void* stream);
 

@@ -8,6 +8,7 @@
 // kernels, so no host synchronisation is needed per iteration unless the
 // backtracking rule can still reject a step (L below 1.5 ||A_D||^2).
 #include <cmath>
+#include <array>
 #include <cstring>
 
 #include "passes.cuh"
@@ -345,15 +346,19 @@ __global__ void k_add(const float* __restrict__ a, const float* __restrict__ b, 
 // Backtracking test of the linearised u-step: f is quadratic, so
 // f(u+) - f(ubar) - <grad f(ubar), d> = 1/2 ||A d||^2 and the rule
 // f(u+) <= f(ubar) + <grad f, d> + L/2 ||d||^2 is ||A d||^2 <= L ||d||^2.
+// With `set_redo` (inside a graph) it also sets the condition of the
+// backtracking loop node `redo`: 1 only after a rejection that leaves the
+// status OK, so the loop ends after at most max_bt + 1 trials.
 __global__ void __launch_bounds__(kSumThreads)
     k_test(DevScalars* sc, const double* __restrict__ pd, int nbd, const double* __restrict__ pf, int nbf, double eta,
-           int max_bt, int force_accept) {
+           int max_bt, int force_accept, cudaGraphConditionalHandle redo, int set_redo) {
   const int t0[1] = {0};
   const int t01[2] = {0, 1};
   double d[1], f[2];
   sum_partials_block<1>(pd, nbd, t0, d);
   sum_partials_block<2>(pf, nbf, t01, f);
   if (threadIdx.x != 0) return;
+  if (set_redo) cudaGraphSetConditional(redo, 0);
   if (sc->status != NLOS_OK) return;
   const double dn2 = d[0], r2 = f[0], ad2 = f[1];
   sc->test_lhs = ad2;
@@ -372,7 +377,35 @@ __global__ void __launch_bounds__(kSumThreads)
     sc->backtracks += 1;
     sc->rej_iter += 1;
     if (sc->rej_iter > max_bt) sc->status = NLOS_ERR_DIVERGED;
+    if (set_redo && sc->status == NLOS_OK) cudaGraphSetConditional(redo, 1);
   }
+}
+
+// Graph-resident iteration loop (one thread each).  Each trip of the loop
+// body runs one iteration out of a switch over the six pointer phases of the
+// solver state (the u / u-bar buffers alternate with period 2 and the cached
+// A u iterates rotate with period 3); `trips` counts the trips.
+__global__ void k_loop_begin(const DevScalars* sc, cudaGraphConditionalHandle phase) {
+  cudaGraphSetConditional(phase, (unsigned)(sc->trips % 6));
+}
+// End of a trip: continue while the status is OK, the relative-energy stop
+// has not fired and fewer than `iters` trips ran (the trip count alone bounds
+// the loop).
+__global__ void k_loop_end(DevScalars* sc, cudaGraphConditionalHandle cont, int iters) {
+  sc->trips += 1;
+  const bool go = sc->trips < iters && sc->status == NLOS_OK && !sc->stop;
+  cudaGraphSetConditional(cont, go ? 1u : 0u);
+}
+// o = a after an even number of trips, b after an odd number.
+__global__ void k_select_copy(float* __restrict__ o, const float* __restrict__ a, const float* __restrict__ b,
+                              size_t n, const DevScalars* sc) {
+  const float* src = (sc->trips & 1) ? b : a;
+  const bool al = ((reinterpret_cast<uintptr_t>(o) | reinterpret_cast<uintptr_t>(src)) & 15) == 0;
+  const size_t n4 = al ? n / 4 : 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x)
+    reinterpret_cast<float4*>(o)[i] = __ldg(reinterpret_cast<const float4*>(src) + i);
+  for (size_t i = 4 * n4 + blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    o[i] = __ldg(src + i);
 }
 
 // End of an iteration: energy, relative change, restart, bookkeeping.
@@ -735,28 +768,108 @@ struct UStepArgs {
   const float* aukm1;
 };
 
-static nlos_status u_step(Plan& P, SolverState* s, const UStepArgs& a, bool host_check, double* L_host,
-                          cudaStream_t st) {
+// Helpers for conditional nodes added during a stream capture.
+static nlos_status capture_graph_of(cudaStream_t st, cudaGraph_t* g) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  NLOS_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, g, nullptr, nullptr, nullptr));
+  if (cs != cudaStreamCaptureStatusActive) return fail(NLOS_ERR_CUDA, "stream is not capturing");
+  return NLOS_OK;
+}
+
+// A condition handle of the graph that st is capturing into.
+static nlos_status cond_handle(cudaStream_t st, unsigned dflt, unsigned flags, cudaGraphConditionalHandle* h) {
+  cudaGraph_t g = nullptr;
+  NLOS_TRY(capture_graph_of(st, &g));
+  NLOS_CUDA(cudaGraphConditionalHandleCreate(h, g, dflt, flags));
+  return NLOS_OK;
+}
+
+// Appends a conditional node (after everything captured on st so far) and
+// continues st's capture after it; bodies receives its `size` body graphs.
+static nlos_status add_cond_node(cudaStream_t st, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                                 unsigned size, cudaGraph_t* bodies) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* ed = nullptr;
+  size_t nd = 0;
+  NLOS_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &ed, &nd));
+  if (cs != cudaStreamCaptureStatusActive) return fail(NLOS_ERR_CUDA, "stream is not capturing");
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = type;
+  np.conditional.size = size;
+  cudaGraphNode_t node = nullptr;
+  NLOS_CUDA(cudaGraphAddNode(&node, g, deps, ed, nd, &np));
+  for (unsigned i = 0; i < size; ++i) bodies[i] = np.conditional.phGraph_out[i];
+  NLOS_CUDA(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return NLOS_OK;
+}
+
+// Captures fn(bs) into the (empty) body graph `body` on stream bs.
+template <typename Fn>
+static nlos_status capture_body(cudaStream_t bs, cudaGraph_t body, Fn&& fn) {
+  NLOS_CUDA(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  const nlos_status s = fn(bs);
+  cudaGraph_t out = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(bs, &out);
+  NLOS_TRY(s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture (conditional body)");
+  return NLOS_OK;
+}
+
+// One trial of the linearised u-step: solve for u+ at the current L, A u+
+// (sampled columns for model 1) and the partial sums of the test.
+static nlos_status u_trial(Plan& P, SolverState* s, const UStepArgs& a, int* nbd, int* nbf, cudaStream_t st) {
   const int full = P.nx * P.ny;
   const int ncols = a.compact ? P.ncols : full;
-  for (;;) {
-    SolveRhs sr{s->ub, a.reg, s->sc, 0.0};
-    NLOS_TRY(launch_tadj_solve(P, P.d_S, full, full, sr, P.d_Sp, st));
-    NLOS_TRY(launch_sxy(P, P.d_Sp, s->sc, 0.0, a.mu, st));
+  SolveRhs sr{s->ub, a.reg, s->sc, 0.0};
+  NLOS_TRY(launch_tadj_solve(P, P.d_S, full, full, sr, P.d_Sp, st));
+  NLOS_TRY(launch_sxy(P, P.d_Sp, s->sc, 0.0, a.mu, st));
+  NLOS_TRY(launch_sinv(P, P.d_Sp, full, s->unew, s->ub, s->pa, nbd, st));
+  NLOS_TRY(launch_tfwd_rz(P, s->unew, full, P.d_S2, full, st));
+  float2* Sfit = P.d_S2;
+  if (a.compact) {
+    NLOS_TRY(launch_conv(P, P.d_S2, false, P.d_Sc, true, false, st));
+    Sfit = P.d_Sc;
+  } else {
+    NLOS_TRY(launch_conv(P, P.d_S2, false, P.d_S2, false, false, st));
+  }
+  FitArgs fa{a.data, a.auk, a.aukm1, s->sc, s->pb};
+  NLOS_TRY(launch_tinv_fit(P, Sfit, ncols, ncols, a.au_out, fa, nbf, st));
+  return NLOS_OK;
+}
+
+// The u-step with its backtracking rule.  host_check: the rule can still
+// reject (L below 1.5 ||A_D||^2).  Then either the host reads the test after
+// every trial, or, while a graph-resident loop is captured (bt_stream set),
+// the trials repeat in a conditional loop node on the device.  Otherwise the
+// trial is accepted without a host round trip.
+static nlos_status u_step(Plan& P, SolverState* s, const UStepArgs& a, bool host_check, double* L_host,
+                          cudaStream_t bt_stream, cudaStream_t st) {
+  if (host_check && bt_stream) {
+    cudaGraphConditionalHandle redo = 0;
+    NLOS_TRY(cond_handle(st, 0, 0, &redo));
     int nbd = 0, nbf = 0;
-    NLOS_TRY(launch_sinv(P, P.d_Sp, full, s->unew, s->ub, s->pa, &nbd, st));
-    NLOS_TRY(launch_tfwd_rz(P, s->unew, full, P.d_S2, full, st));
-    float2* Sfit = P.d_S2;
-    if (a.compact) {
-      NLOS_TRY(launch_conv(P, P.d_S2, false, P.d_Sc, true, false, st));
-      Sfit = P.d_Sc;
-    } else {
-      NLOS_TRY(launch_conv(P, P.d_S2, false, P.d_S2, false, false, st));
-    }
-    FitArgs fa{a.data, a.auk, a.aukm1, s->sc, s->pb};
-    NLOS_TRY(launch_tinv_fit(P, Sfit, ncols, ncols, a.au_out, fa, &nbf, st));
+    NLOS_TRY(u_trial(P, s, a, &nbd, &nbf, st));
+    k_test<<<1, kSumThreads, 0, st>>>(s->sc, s->pa, nbd, s->pb, nbf, a.eta, a.max_bt, 0, redo, 1);
+    NLOS_LAUNCH_CHECK("k_test");
+    cudaGraph_t body = nullptr;
+    NLOS_TRY(add_cond_node(st, redo, cudaGraphCondTypeWhile, 1, &body));
+    return capture_body(bt_stream, body, [&](cudaStream_t bs) -> nlos_status {
+      int nbd2 = 0, nbf2 = 0;
+      NLOS_TRY(u_trial(P, s, a, &nbd2, &nbf2, bs));
+      k_test<<<1, kSumThreads, 0, bs>>>(s->sc, s->pa, nbd2, s->pb, nbf2, a.eta, a.max_bt, 0, redo, 1);
+      NLOS_LAUNCH_CHECK("k_test");
+      return NLOS_OK;
+    });
+  }
+  for (;;) {
+    int nbd = 0, nbf = 0;
+    NLOS_TRY(u_trial(P, s, a, &nbd, &nbf, st));
     { KTimer kt_(P, KC_SMALL, st);
-    k_test<<<1, kSumThreads, 0, st>>>(s->sc, s->pa, nbd, s->pb, nbf, a.eta, a.max_bt, host_check ? 0 : 1);
+    k_test<<<1, kSumThreads, 0, st>>>(s->sc, s->pa, nbd, s->pb, nbf, a.eta, a.max_bt, host_check ? 0 : 1, 0, 0);
     }
     NLOS_LAUNCH_CHECK("k_test");
     if (!host_check) return NLOS_OK;
@@ -927,7 +1040,7 @@ static nlos_status step_alg1(JobRun& j) {
   const bool host_check = j.L_host < 1.5 * j.norm2;
   UStepArgs ua{s->reg, p.mu, true, s->tau0c, p.eta, p.max_backtracks, s->cache[j.nxt], s->cache[j.cur],
                s->cache[j.prev]};
-  NLOS_TRY(u_step(P, s, ua, host_check, &j.L_host, st));
+  NLOS_TRY(u_step(P, s, ua, host_check, &j.L_host, j.bt_stream, st));
   { KTimer kt_(P, KC_POST, st);
   if (tiled)
     k_post1_pipe<<<post_grid, kTileThreads, kPost1PipeSmem, st>>>(s->unew, s->uk, s->ub, s->lam, s->ph, s->ubn,
@@ -981,7 +1094,7 @@ static nlos_status step_alg2(JobRun& j) {
   const bool host_check = j.L_host < 1.5 * j.norm2;
   UStepArgs ua{s->reg, p.mu1, false, s->tb, p.eta, p.max_backtracks, s->cache[j.nxt], s->cache[j.cur],
                s->cache[j.prev]};
-  NLOS_TRY(u_step(P, s, ua, host_check, &j.L_host, st));
+  NLOS_TRY(u_step(P, s, ua, host_check, &j.L_host, j.bt_stream, st));
   { KTimer kt_(P, KC_SMALL, st);
   k_add<<<elem_grid(V), 256, 0, st>>>(s->cache[j.nxt], s->regt, s->tmp, V);
   }
@@ -1027,13 +1140,19 @@ static nlos_status step_alg2(JobRun& j) {
   return NLOS_OK;
 }
 
-nlos_status job_step(JobRun& j) {
-  if (j.done) return NLOS_OK;
+// Enqueues one iteration and rotates the cached A u slots.
+static nlos_status step_once(JobRun& j) {
   NLOS_TRY(j.p.model == 1 ? step_alg1(j) : step_alg2(j));
   const int t = j.prev;
   j.prev = j.cur;
   j.cur = j.nxt;
   j.nxt = t;
+  return NLOS_OK;
+}
+
+nlos_status job_step(JobRun& j) {
+  if (j.done) return NLOS_OK;
+  NLOS_TRY(step_once(j));
   j.it += 1;
   if (j.it >= j.p.iters) j.done = true;
   if (j.p.eps_stop > 0.0 && !j.done) {
@@ -1071,11 +1190,77 @@ void free_graphs(Plan* P) {
   P->graphs.clear();
   if (P->capture_stream) cudaStreamDestroy(P->capture_stream);
   P->capture_stream = nullptr;
+  for (auto& b : P->body_stream) {
+    if (b) cudaStreamDestroy(b);
+    b = nullptr;
+  }
+}
+
+// Captures (on c.st, which is capturing) a run whose iteration count is
+// decided on the device: after the initial state (and the unrolled warm
+// stage of a warm-started model-2 run), a while node runs one iteration per
+// trip, chosen by a switch over the six pointer phases; k_loop_end stops it at
+// `iters` trips, at the relative-energy stop or on an error.  A backtracking
+// rule that can reject runs as a nested while node (u_step).  The result is
+// copied from the buffer that the trip count's parity selects.
+static nlos_status capture_looped(JobRun& c, cudaStream_t* bs) {
+  NLOS_TRY(job_init(c));
+  while (c.phase == 1) NLOS_TRY(job_step(c));  // warm stage: fixed count, no host decisions
+  SolverState* s = c.s;
+  if (c.p.iters <= 0) return job_finish(c);
+  const float* u0 = s->uk;
+  const float* u1 = s->unew;
+  const float* t0 = s->tk;
+  const float* t1 = s->tnew;
+  const JobRun start = c;
+  auto phase_ptrs = [s]() {
+    return std::array<const float*, 11>{s->uk, s->unew, s->ub, s->ubn, s->tk, s->tnew, s->tb, s->tbn,
+                                        s->cache[0], s->cache[1], s->cache[2]};
+  };
+  const auto ptrs_start = phase_ptrs();
+  cudaGraphConditionalHandle cont = 0;
+  NLOS_TRY(cond_handle(c.st, 1, cudaGraphCondAssignDefault, &cont));
+  cudaGraph_t loop_body = nullptr;
+  NLOS_TRY(add_cond_node(c.st, cont, cudaGraphCondTypeWhile, 1, &loop_body));
+  const cudaStream_t main_st = c.st;
+  NLOS_TRY(capture_body(bs[0], loop_body, [&](cudaStream_t ls) -> nlos_status {
+    cudaGraphConditionalHandle phase = 0;
+    NLOS_TRY(cond_handle(ls, 0, 0, &phase));
+    k_loop_begin<<<1, 1, 0, ls>>>(s->sc, phase);
+    NLOS_LAUNCH_CHECK("k_loop_begin");
+    cudaGraph_t bodies[6] = {};
+    NLOS_TRY(add_cond_node(ls, phase, cudaGraphCondTypeSwitch, 6, bodies));
+    for (int k = 0; k < 6; ++k) {
+      NLOS_TRY(capture_body(bs[1], bodies[k], [&](cudaStream_t ps) -> nlos_status {
+        c.st = ps;
+        c.bt_stream = bs[2];
+        const nlos_status r = step_once(c);
+        c.st = main_st;
+        c.bt_stream = nullptr;
+        return r;
+      }));
+    }
+    k_loop_end<<<1, 1, 0, ls>>>(s->sc, cont, c.p.iters);
+    NLOS_LAUNCH_CHECK("k_loop_end");
+    return NLOS_OK;
+  }));
+  // six iterations bring every rotated pointer back to its starting place
+  if (c.cur != start.cur || c.prev != start.prev || c.nxt != start.nxt || phase_ptrs() != ptrs_start)
+    return fail(NLOS_ERR_CUDA, "iteration pointer phases do not repeat after six iterations");
+  const size_t V = s->V;
+  k_select_copy<<<elem_grid(V), 256, 0, c.st>>>(c.u_out, u0, u1, V, s->sc);
+  NLOS_LAUNCH_CHECK("k_select_copy");
+  if (c.tau_out && s->model == 2) {
+    k_select_copy<<<elem_grid(V), 256, 0, c.st>>>(c.tau_out, t0, t1, V, s->sc);
+    NLOS_LAUNCH_CHECK("k_select_copy");
+  }
+  NLOS_CUDA(cudaMemcpyAsync(s->h_sc, s->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c.st));
+  return NLOS_OK;
 }
 
 // The cached graph of run j (same parameters and buffers), captured and
-// cached on first use; *exec = nullptr when the run needs host decisions
-// between iterations or the plan's kernels are being timed.
+// cached on first use; *exec = nullptr when the plan's kernels are being
+// timed or the run has no iterations.
 static nlos_status job_graph(JobRun& j, cudaStream_t st, cudaGraphExec_t* exec) {
   *exec = nullptr;
   Plan& P = *j.P;
@@ -1091,7 +1276,8 @@ static nlos_status job_graph(JobRun& j, cudaStream_t st, cudaGraphExec_t* exec) 
     NLOS_TRY(plan_norm2(P, true, st, &n1));
   }
   const double L0 = p.L0 > 0.0 ? p.L0 : 2.0 * j.norm2;
-  if (p.eps_stop > 0.0 || L0 < 1.5 * j.norm2 || p.iters <= 0) return NLOS_OK;
+  if (p.iters <= 0) return NLOS_OK;
+  const bool looped = p.eps_stop > 0.0 || L0 < 1.5 * j.norm2;
   for (auto& g : P.graphs)
     if (std::memcmp(&g.p, &p, sizeof(nlos_params)) == 0 && g.tau0 == j.tau0 && g.u_out == j.u_out &&
         g.tau_out == j.tau_out) {
@@ -1099,12 +1285,20 @@ static nlos_status job_graph(JobRun& j, cudaStream_t st, cudaGraphExec_t* exec) 
       return NLOS_OK;
     }
   if (!P.capture_stream) NLOS_CUDA(cudaStreamCreateWithFlags(&P.capture_stream, cudaStreamNonBlocking));
+  if (looped)
+    for (auto& b : P.body_stream)
+      if (!b) NLOS_CUDA(cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking));
   JobRun c = j;
   c.st = P.capture_stream;
   NLOS_CUDA(cudaStreamBeginCapture(c.st, cudaStreamCaptureModeThreadLocal));
-  nlos_status s = job_init(c);
-  while (s == NLOS_OK && !c.done) s = job_step(c);
-  if (s == NLOS_OK) s = job_finish(c);
+  nlos_status s = NLOS_OK;
+  if (looped) {
+    s = capture_looped(c, P.body_stream);
+  } else {
+    s = job_init(c);
+    while (s == NLOS_OK && !c.done) s = job_step(c);
+    if (s == NLOS_OK) s = job_finish(c);
+  }
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(c.st, &graph);
   if (s != NLOS_OK) {

@@ -75,7 +75,7 @@ struct DevScalars {
   int32_t accept;     // outcome of the last test (1 accepted)
   int32_t rej_iter;   // rejections in the current iteration
   int32_t stop;       // relative-energy stop reached
-  int32_t pad_;
+  int32_t trips;      // trips of a graph-resident iteration loop
   double primal_res;  // ||v - grad u|| of the last iteration
   double test_lhs, test_rhs;  // ||A d||^2 and L ||d||^2 of the last test
 };
@@ -186,6 +186,9 @@ struct Plan {
   };
   std::vector<GraphEntry> graphs;
   cudaStream_t capture_stream = nullptr;
+  // streams that capture the bodies of conditional nodes (iteration loop,
+  // pointer-phase switch, backtracking loop)
+  cudaStream_t body_stream[3] = {nullptr, nullptr, nullptr};
 
   // optional per-launch timing (nlos_timing_enable): event pairs recorded
   // around every kernel launch on the launch stream, harvested on read.
@@ -268,6 +271,10 @@ struct JobRun {
   // Algorithm 2 (phase 2) when the warm stage is done.
   int phase = 0;
   nlos_params main_p{};
+  // While a graph-resident loop is being captured: the stream on which the
+  // backtracking loop body is captured (the u-step then repeats on the device
+  // until the test accepts); nullptr otherwise.
+  cudaStream_t bt_stream = nullptr;
 };
 // Allocates the solver state on first use, computes (once per plan) the
 // operator norm with a host synchronisation, and enqueues the initial state.
@@ -282,15 +289,19 @@ nlos_status job_finish(JobRun& j);
 nlos_status job_collect(JobRun& j, nlos_stats* stats);
 // Enqueue the whole reconstruction of j on `launch` as one CUDA-graph launch
 // (captured on first use for these parameters and buffers, then cached in the
-// plan).  Sets *used = false, enqueuing nothing, when the run needs host
-// decisions (backtracking that can reject, relative-energy stop) or the
-// plan's kernels are being timed.
+// plan).  Runs with a fixed iteration count and no possible rejection are
+// captured unrolled; runs with a relative-energy stop or a backtracking rule
+// that can reject are captured as a device-driven loop of conditional nodes.
+// Sets *used = false, enqueuing nothing, only when the plan's kernels are
+// being timed.
 nlos_status job_enqueue_graph(JobRun& j, cudaStream_t launch, bool* used);
 // Captures and caches j's graph without launching it (*ready = false when the
-// run needs host decisions and would run without a graph).
+// run would not use a graph: kernel timing on, or no iterations).
 nlos_status job_prepare_graph(JobRun& j, cudaStream_t st, bool* ready);
 nlos_status reconstruct_prepare(Plan& P, const nlos_params& p, const float* tau0, float* u_out, float* tau_out,
                                 bool* ready, cudaStream_t st);
+// Checks the parameter rules of nlos_params (model, counts, factors, penalties).
+nlos_status validate_params(const nlos_params& p, const char* who);
 void free_graphs(Plan* P);
 
 // Launch configuration helpers

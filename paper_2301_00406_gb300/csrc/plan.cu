@@ -431,6 +431,19 @@ static nlos_status check_plan(nlos_plan plan) {
 
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// The parameter rules shared by every entry point that runs a reconstruction.
+nlos_status validate_params(const nlos_params& p, const char* who) {
+  const std::string w(who);
+  if (p.model != 1 && p.model != 2) return fail(NLOS_ERR_INVALID_ARG, w + ": model must be 1 or 2");
+  if (p.iters < 0 || !(p.eta > 1.0) || p.max_backtracks < 0 || p.max_backtracks > 1000 || p.phi < 0 ||
+      p.phi > 2 || !(p.eps_normal >= 0.0) || !(p.eps_stop >= 0.0) || p.warm_start_iters < 0)
+    return fail(NLOS_ERR_INVALID_ARG, w + ": invalid iteration parameters");
+  if ((p.model == 1 || p.warm_start_iters > 0) && !(p.mu > 0.0))
+    return fail(NLOS_ERR_INVALID_ARG, w + ": mu must be > 0");
+  if (p.model == 2 && !(p.mu1 > 0.0 && p.mu2 > 0.0 && p.mu3 > 0.0 && p.lambda >= 0.0))
+    return fail(NLOS_ERR_INVALID_ARG, w + ": mu1, mu2, mu3 must be > 0 and lambda >= 0");
+  return NLOS_OK;
+}
 }  // namespace nlos
 
 using namespace nlos;
@@ -484,6 +497,7 @@ nlos_status nlos_params_default(int32_t model, nlos_params* out) {
   out->warm_start_iters = 0;
   return NLOS_OK;
 }
+
 
 nlos_status nlos_plan_create(const nlos_geometry* geom, void* stream, nlos_plan* out) {
   API_GUARD({
@@ -585,12 +599,7 @@ nlos_status nlos_reconstruct(nlos_plan plan, const nlos_params* params, const fl
     if (!params || !tau0_dev || !u_out_dev || !aligned16(tau0_dev) || !aligned16(u_out_dev))
       return fail(NLOS_ERR_INVALID_ARG, "nlos_reconstruct: null or non-16-byte-aligned pointer");
     const nlos_params& p = *params;
-    if (p.iters < 0 || !(p.eta > 1.0) || p.max_backtracks < 0 || p.phi < 0 || p.phi > 2 || !(p.eps_normal >= 0.0) ||
-        p.warm_start_iters < 0)
-      return fail(NLOS_ERR_INVALID_ARG, "nlos_reconstruct: invalid iteration parameters");
-    if ((p.model == 1 || p.warm_start_iters > 0) && !(p.mu > 0.0)) return fail(NLOS_ERR_INVALID_ARG, "mu must be > 0");
-    if (p.model == 2 && !(p.mu1 > 0.0 && p.mu2 > 0.0 && p.mu3 > 0.0 && p.lambda >= 0.0))
-      return fail(NLOS_ERR_INVALID_ARG, "mu1, mu2, mu3 must be > 0 and lambda >= 0");
+    NLOS_TRY(validate_params(p, "nlos_reconstruct"));
     if (stats_host) std::memset(stats_host, 0, sizeof(*stats_host));
     return reconstruct(*reinterpret_cast<Plan*>(plan), p, tau0_dev, u_out_dev, tau_out_dev, stats_host,
                        reinterpret_cast<cudaStream_t>(stream));
@@ -605,9 +614,7 @@ nlos_status nlos_reconstruct_prepare(nlos_plan plan, const nlos_params* params, 
     if (!params || !tau0_dev || !u_out_dev || !aligned16(tau0_dev) || !aligned16(u_out_dev))
       return fail(NLOS_ERR_INVALID_ARG, "nlos_reconstruct_prepare: null or non-16-byte-aligned pointer");
     const nlos_params& p = *params;
-    if (p.iters < 0 || !(p.eta > 1.0) || p.max_backtracks < 0 || p.phi < 0 || p.phi > 2 || !(p.eps_normal >= 0.0) ||
-        p.warm_start_iters < 0)
-      return fail(NLOS_ERR_INVALID_ARG, "nlos_reconstruct_prepare: invalid iteration parameters");
+    NLOS_TRY(validate_params(p, "nlos_reconstruct_prepare"));
     bool ready = false;
     NLOS_TRY(reconstruct_prepare(*reinterpret_cast<Plan*>(plan), p, tau0_dev, u_out_dev, tau_out_dev, &ready,
                                  reinterpret_cast<cudaStream_t>(stream)));

@@ -484,10 +484,7 @@ nlos_status nlos_reconstruct_batch(const nlos_plan* plans, const nlos_params* pa
       P[i] = reinterpret_cast<Plan*>(plans[i]);
       if (!P[i] || !tau0[i] || !u_out[i]) return fail(NLOS_ERR_INVALID_ARG, "nlos_reconstruct_batch: null entry");
       if (P[i]->device != dev) return fail(NLOS_ERR_INVALID_ARG, "nlos_reconstruct_batch: plan on another device");
-      if (params[i].model != 1 && params[i].model != 2)
-        return fail(NLOS_ERR_INVALID_ARG, "nlos_reconstruct_batch: model must be 1 or 2");
-      if (params[i].warm_start_iters < 0)
-        return fail(NLOS_ERR_INVALID_ARG, "nlos_reconstruct_batch: warm_start_iters < 0");
+      NLOS_TRY(validate_params(params[i], "nlos_reconstruct_batch"));
       for (int k = 0; k < i; ++k)
         if (P[k] == P[i]) return fail(NLOS_ERR_INVALID_ARG, "nlos_reconstruct_batch: a plan appears twice");
     }
@@ -521,8 +518,7 @@ nlos_status nlos_submit(nlos_server server, const nlos_geometry* geom, const nlo
       return fail(NLOS_ERR_INVALID_ARG, "nlos_submit: null argument");
     int32_t n = 0;
     NLOS_TRY(nlos_geometry_tables(geom, nullptr, nullptr, nullptr, nullptr, nullptr, &n));
-    if (params->model != 1 && params->model != 2) return fail(NLOS_ERR_INVALID_ARG, "nlos_submit: model");
-    if (params->warm_start_iters < 0) return fail(NLOS_ERR_INVALID_ARG, "nlos_submit: warm_start_iters < 0");
+    NLOS_TRY(validate_params(*params, "nlos_submit"));
     Server& S = server->impl;
     auto jb = std::make_unique<Job>();
     jb->key = make_key(*geom);

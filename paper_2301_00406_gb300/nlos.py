@@ -18,6 +18,7 @@ NLOS_OK = 0
 STATUS_NAMES = {0: "NLOS_OK", -1: "NLOS_ERR_INVALID_ARG", -2: "NLOS_ERR_OOM", -3: "NLOS_ERR_CUDA",
                 -4: "NLOS_ERR_BUSY", -5: "NLOS_ERR_NOT_READY", -6: "NLOS_ERR_TIMEOUT",
                 -7: "NLOS_ERR_DIVERGED"}
+globals().update({name: code for code, name in STATUS_NAMES.items()})
 RADIOMETRY = {"compensated": 0, "raw": 1}
 # curvature weights phi(kappa) (NLOS_PHI_*): a + b kappa^2, a + b |kappa|, sqrt(a + b kappa^2)
 PHI_TSC, PHI_TAC, PHI_TRV = 0, 1, 2

@@ -4,9 +4,9 @@ stride-2 sampling, 100 iterations; lambda, a_u, b_u, a_tau, b_tau and
 mu_1..3 of the Bowling settings), tau0 the seeded pulse transients.
 
 Only oracle/ and synth/ are used.  Stored: the energy history and restart
-flags, the global 2-norms and sums of u and tau, the depth map of u, and u
-and tau on 64 fixed columns (every 64th column index plus the 32 sampled
-columns of one row).
+flags, the Lipschitz estimates, the global 2-norms of u and tau, the depth
+map of u, and u and tau on 64 fixed columns (every 64th column index plus
+the 32 sampled columns of one row).
 
     PYTHONPATH=. python tests/golden/make_c2_alg2.py     (about 20 minutes)
 """

@@ -145,5 +145,7 @@ def test_reconstruct_prepare_then_run_matches_plain_run(nlos):
     st = plan.reconstruct(job["params"], tau0.data_ptr(), u.data_ptr())
     assert torch.equal(u, u_plain) and st["energy"] == st_plain["energy"]
     p = nlos.params_default(job["params"].model)
-    p.iters, p.eps_stop = 3, 1e-9                       # needs host decisions: no graph
+    p.iters, p.eps_stop = 3, 1e-9                       # stop decided on the device: a looped graph
+    assert plan.reconstruct_prepare(p, tau0.data_ptr(), u.data_ptr()) is True
+    p.iters = 0                                         # nothing to run: no graph
     assert plan.reconstruct_prepare(p, tau0.data_ptr(), u.data_ptr()) is False
