@@ -5,7 +5,7 @@ mu_1..3 of the Bowling settings), tau0 the seeded pulse transients.
 
 Only oracle/ and synth/ are used.  Stored: the energy history and restart
 flags, the Lipschitz estimates, the global 2-norms of u and tau, the depth
-map of u, and u and tau on 64 fixed columns (every 64th column index plus
+map of u, and u and tau on 96 fixed columns (every 64th column index plus
 the 32 sampled columns of one row).
 
     PYTHONPATH=. python tests/golden/make_c2_alg2.py     (about 20 minutes)
