@@ -130,7 +130,10 @@ __device__ __forceinline__ int kfreq(int p) {
 
 // B transforms of length N (B a power of two) in shared memory; element e of
 // transform b lives at buf[addr(b, e)] (addr: any bijective layout, e.g. a
-// strided plane or a bank-swizzled one).  tw[j * tws] = exp(-2 pi i j / N)
+// strided plane or a bank-swizzled one).  The steps call addr(b, er, ec) for
+// e = er + ec where er (the same for all of a task's elements) and ec (a
+// compile-time constant after unrolling) have disjoint bits, so a layout can
+// compute the part of er once per task.  tw[j * tws] = exp(-2 pi i j / N)
 // for j < N.  All threads of the block call these; they end with
 // __syncthreads().
 //
@@ -150,7 +153,7 @@ __device__ __forceinline__ void team_fft3a(float2* buf, int B, const Addr& addr,
       const int b = it & (B - 1), n23 = it >> lb;
       float2 a[R1];
 #pragma unroll
-      for (int n = 0; n < R1; ++n) a[n] = buf[addr(b, n * M + n23)];
+      for (int n = 0; n < R1; ++n) a[n] = buf[addr(b, n23, n * M)];
       if (!INV) {
         dft_reg<R1, false>(a);
 #pragma unroll
@@ -161,7 +164,7 @@ __device__ __forceinline__ void team_fft3a(float2* buf, int B, const Addr& addr,
         dft_reg<R1, true>(a);
       }
 #pragma unroll
-      for (int n = 0; n < R1; ++n) buf[addr(b, n * M + n23)] = a[n];
+      for (int n = 0; n < R1; ++n) buf[addr(b, n23, n * M)] = a[n];
     }
     __syncthreads();
   };
@@ -172,7 +175,7 @@ __device__ __forceinline__ void team_fft3a(float2* buf, int B, const Addr& addr,
       const int e0 = k1 * M + n3;
       float2 a[R2];
 #pragma unroll
-      for (int n = 0; n < R2; ++n) a[n] = buf[addr(b, e0 + n * R3)];
+      for (int n = 0; n < R2; ++n) a[n] = buf[addr(b, e0, n * R3)];
       if (!INV) {
         dft_reg<R2, false>(a);
 #pragma unroll
@@ -183,7 +186,7 @@ __device__ __forceinline__ void team_fft3a(float2* buf, int B, const Addr& addr,
         dft_reg<R2, true>(a);
       }
 #pragma unroll
-      for (int n = 0; n < R2; ++n) buf[addr(b, e0 + n * R3)] = a[n];
+      for (int n = 0; n < R2; ++n) buf[addr(b, e0, n * R3)] = a[n];
     }
     __syncthreads();
   };
@@ -193,10 +196,10 @@ __device__ __forceinline__ void team_fft3a(float2* buf, int B, const Addr& addr,
       const int e0 = r * R3;
       float2 a[R3];
 #pragma unroll
-      for (int n = 0; n < R3; ++n) a[n] = buf[addr(b, e0 + n)];
+      for (int n = 0; n < R3; ++n) a[n] = buf[addr(b, e0, n)];
       dft_reg<R3, INV>(a);
 #pragma unroll
-      for (int n = 0; n < R3; ++n) buf[addr(b, e0 + n)] = a[n];
+      for (int n = 0; n < R3; ++n) buf[addr(b, e0, n)] = a[n];
     }
     __syncthreads();
   };
@@ -226,12 +229,12 @@ __device__ __forceinline__ void team_fft_a(float2* buf, int B, const Addr& addr,
       const int b = it & (B - 1), n2 = it >> lb;
       float2 a[R1];
 #pragma unroll
-      for (int n1 = 0; n1 < R1; ++n1) a[n1] = buf[addr(b, n1 * R2 + n2)];
+      for (int n1 = 0; n1 < R1; ++n1) a[n1] = buf[addr(b, n2, n1 * R2)];
       dft_reg<R1, false>(a);
 #pragma unroll
       for (int k1 = 1; k1 < R1; ++k1) a[k1] = cmul(a[k1], tw[((n2 * k1) & (N - 1)) * tws]);
 #pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1) buf[addr(b, k1 * R2 + n2)] = a[k1];
+      for (int k1 = 0; k1 < R1; ++k1) buf[addr(b, n2, k1 * R2)] = a[k1];
     }
     __syncthreads();
     if (R2 > 1) {
@@ -239,10 +242,10 @@ __device__ __forceinline__ void team_fft_a(float2* buf, int B, const Addr& addr,
         const int b = it & (B - 1), k1 = it >> lb;
         float2 a[R2];
 #pragma unroll
-        for (int n2 = 0; n2 < R2; ++n2) a[n2] = buf[addr(b, k1 * R2 + n2)];
+        for (int n2 = 0; n2 < R2; ++n2) a[n2] = buf[addr(b, k1 * R2, n2)];
         dft_reg<R2, false>(a);
 #pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) buf[addr(b, k1 * R2 + k2)] = a[k2];
+        for (int k2 = 0; k2 < R2; ++k2) buf[addr(b, k1 * R2, k2)] = a[k2];
       }
       __syncthreads();
     }
@@ -252,12 +255,12 @@ __device__ __forceinline__ void team_fft_a(float2* buf, int B, const Addr& addr,
         const int b = it & (B - 1), k1 = it >> lb;
         float2 a[R2];
 #pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) a[k2] = buf[addr(b, k1 * R2 + k2)];
+        for (int k2 = 0; k2 < R2; ++k2) a[k2] = buf[addr(b, k1 * R2, k2)];
         dft_reg<R2, true>(a);
 #pragma unroll
         for (int n2 = 1; n2 < R2; ++n2) a[n2] = cmulc(a[n2], tw[((n2 * k1) & (N - 1)) * tws]);
 #pragma unroll
-        for (int n2 = 0; n2 < R2; ++n2) buf[addr(b, k1 * R2 + n2)] = a[n2];
+        for (int n2 = 0; n2 < R2; ++n2) buf[addr(b, k1 * R2, n2)] = a[n2];
       }
       __syncthreads();
     }
@@ -265,10 +268,10 @@ __device__ __forceinline__ void team_fft_a(float2* buf, int B, const Addr& addr,
       const int b = it & (B - 1), n2 = it >> lb;
       float2 a[R1];
 #pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1) a[k1] = buf[addr(b, k1 * R2 + n2)];
+      for (int k1 = 0; k1 < R1; ++k1) a[k1] = buf[addr(b, n2, k1 * R2)];
       dft_reg<R1, true>(a);
 #pragma unroll
-      for (int n1 = 0; n1 < R1; ++n1) buf[addr(b, n1 * R2 + n2)] = a[n1];
+      for (int n1 = 0; n1 < R1; ++n1) buf[addr(b, n2, n1 * R2)] = a[n1];
     }
     __syncthreads();
   }
@@ -278,6 +281,7 @@ __device__ __forceinline__ void team_fft_a(float2* buf, int B, const Addr& addr,
 struct StridedAddr {
   int ts, es;
   __device__ __forceinline__ int operator()(int b, int e) const { return b * ts + e * es; }
+  __device__ __forceinline__ int operator()(int b, int er, int ec) const { return b * ts + (er + ec) * es; }
 };
 template <int N, bool INV>
 __device__ __forceinline__ void team_fft(float2* buf, int B, int ts, int es, const float2* tw, int tws, int tid,

@@ -71,7 +71,7 @@ namespace nlos {
 // ---------------------------------------------------------------------------
 namespace {
 std::mutex g_tp_mu;
-std::map<std::tuple<int, int, int>, int> g_tp_cols;  // (kind, nt, ncols) -> columns per CTA
+std::map<std::tuple<int, int, int>, int> g_tp_cols;  // (kind, nt, ncols) -> cols | hb << 8
 thread_local int g_tp_force = 0;                       // candidate under test (tuner only)
 }  // namespace
 
@@ -82,8 +82,9 @@ int tp_cols_for(int kind, int nt, int ncols) {
   return it == g_tp_cols.end() ? 0 : it->second;
 }
 
-// Times every column count for each t-pass kind the plan launches and keeps
-// the fastest.  Inputs are the plan's scratch buffers with whatever they hold
+// Times every column count (and, for the kernels with two halves, both the
+// sequential and the batched halves) for each t-pass kind the plan launches
+// and keeps the fastest.  Inputs are the plan's scratch buffers with whatever they hold
 // (the kernels' addressing depends only on the tables and the shape, so any
 // contents are safe); nothing outside the plan is written.
 nlos_status autotune_tpass(Plan& P, cudaStream_t st) {
@@ -135,17 +136,22 @@ nlos_status autotune_tpass(Plan& P, cudaStream_t st) {
       std::lock_guard<std::mutex> lock(g_tp_mu);
       if (g_tp_cols.count(std::make_tuple(c.kind, nt, c.ncols))) continue;
     }
+    const bool halves = c.kind != TPK_SFWD && c.kind != TPK_SINV;
     int best = 0;
     float best_ms = 0.f;
-    for (int cols = max_cols; cols >= 2 && status == NLOS_OK; cols >>= 1) {
+    for (int cand = 0; cand < 8 && status == NLOS_OK; ++cand) {
+      const int cols = max_cols >> (cand >> 1), hb = cand & 1;
+      if (cols < 2 || (hb && !halves)) continue;
       if (c.partials && (c.ncols + cols - 1) / cols > P.partial_blocks) continue;
-      g_tp_force = cols;
+      g_tp_force = cols | hb << 8;
       float t = 0.f;
       status = c.run();  // warm-up
+      // best of 3 timings of 4 back-to-back launches (the launch latency of a
+      // short kernel, and any per-launch overhead of a tool, is amortised)
       for (int rep = 0; rep < 3 && status == NLOS_OK; ++rep) {
         float ms = 0.f;
         if (cudaEventRecord(e0, st) != cudaSuccess) status = fail(NLOS_ERR_CUDA, "autotune: event");
-        if (status == NLOS_OK) status = c.run();
+        for (int l = 0; l < 4 && status == NLOS_OK; ++l) status = c.run();
         if (status == NLOS_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
                                   cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
           status = fail(NLOS_ERR_CUDA, "autotune: timing");
@@ -153,7 +159,7 @@ nlos_status autotune_tpass(Plan& P, cudaStream_t st) {
       }
       g_tp_force = 0;
       if (status == NLOS_OK && (best == 0 || t < best_ms)) {
-        best = cols;
+        best = cols | hb << 8;
         best_ms = t;
       }
     }

@@ -70,14 +70,16 @@ nlos_status launch_sxy(const Plan& P, float2* Sp, const DevScalars* sc, double c
 nlos_status launch_kernel_spectrum(const Plan& P, const int32_t* m0, const float2* hw, cudaStream_t st);
 
 // Launch-shape tuning of the t-passes.  Every t-pass kind picks its columns
-// per CTA (16, 8, 4 or 2) by timing at plan creation (autotune_tpass, on the
-// plan's own scratch buffers); the choice is cached for the whole process
-// per (kind, nt, launch column count), so all plans of a geometry launch the
-// same shapes and their block-partial reductions sum in the same order.
+// per CTA (16, 8, 4 or 2) and, where the kernel has two halves (even and odd
+// bins of the padded transform), whether they run as one batched FFT, by
+// timing at plan creation (autotune_tpass, on the plan's own scratch
+// buffers); the choice is cached for the whole process per (kind, nt, launch
+// column count), so all plans of a geometry launch the same shapes and their
+// block-partial reductions sum in the same order.
 enum TpKind {
   TPK_TFWD_RZ, TPK_TFWD_RTT, TPK_TINV_STORE, TPK_TINV_FIT, TPK_TADJ_STORE, TPK_TADJ_SOLVE, TPK_SFWD, TPK_SINV
 };
-// Tuned columns per CTA for a launch, or 0 (use the default rule).
+// Tuned shape of a launch, cols | hb << 8, or 0 (use the default rule).
 int tp_cols_for(int kind, int nt, int ncols);
 nlos_status autotune_tpass(Plan& P, cudaStream_t st);
 

@@ -84,6 +84,12 @@ template <int NT>
 struct WorkAddr {
   int pitch;
   __device__ __forceinline__ int operator()(int p, int e) const { return p * pitch + work_swz<NT>(e); }
+  // e = er + ec with disjoint bits: the swizzle is linear over GF(2) (an XOR
+  // of fixed masks selected by e's bits), so swz(er | ec) = swz(er) ^ swz(ec)
+  // and swz(ec) folds to a constant for a compile-time ec.
+  __device__ __forceinline__ int operator()(int p, int er, int ec) const {
+    return p * pitch + (work_swz<NT>(er) ^ work_swz<NT>(ec));
+  }
 };
 constexpr int kTpassThreads = 256;
 
@@ -96,17 +102,29 @@ struct TabLayout {
   static constexpr int SLOTS = NT + PTR4;
 };
 
+// Table staging: n 16-byte words from global to shared memory, eight loads in
+// flight per thread (a plain strided loop waits for each load in turn, which
+// dominates the short launches over the sampled columns).
+__device__ __forceinline__ void stage16(float4* dst, const float4* __restrict__ src, int n, int tid, int nthr) {
+  batched_copy<8, float4>(
+      n, tid, nthr, [&](int i) { return __ldg(src + i); }, [&](int i, float4 v) { dst[i] = v; });
+}
+// The 2 nt twiddles of the padded transform (nt 16-byte words).
+template <int NT>
+__device__ __forceinline__ void stage_twiddles(float2* tw2, const float2* __restrict__ g, int tid, int nthr) {
+  stage16(reinterpret_cast<float4*>(tw2), reinterpret_cast<const float4*>(g), NT, tid, nthr);
+}
 template <int NT>
 __device__ __forceinline__ void stage_fwd_taps(float4* tab, const float4* __restrict__ g, int tid, int nthr) {
-  for (int i = tid; i < NT; i += nthr) tab[i] = __ldg(g + i);
+  stage16(tab, g, NT, tid, nthr);
 }
 template <int NT>
 __device__ __forceinline__ void stage_csr(float4* tab, const int32_t* __restrict__ ptr, const float2* __restrict__ ent,
                                           int tid, int nthr) {
   int* p = reinterpret_cast<int*>(tab);
-  float2* e = reinterpret_cast<float2*>(tab + TabLayout<NT>::PTR4);
-  for (int i = tid; i <= NT; i += nthr) p[i] = __ldg(ptr + i);
-  for (int i = tid; i < 2 * NT; i += nthr) e[i] = __ldg(ent + i);
+  batched_copy<4, int>(
+      NT + 1, tid, nthr, [&](int i) { return __ldg(ptr + i); }, [&](int i, int v) { p[i] = v; });
+  stage16(tab + TabLayout<NT>::PTR4, reinterpret_cast<const float4*>(ent), NT, tid, nthr);
 }
 // sum over the CSR row n of w * x[index]
 template <int NT>
@@ -166,19 +184,25 @@ __device__ __forceinline__ void load_pair(const float2* __restrict__ row, int ca
 }
 
 // Post-processing of the padded forward t-FFT of packed pairs: writes bins
-// kt = 2 k' + half of both columns of every pair to S.
+// kt = 2 k' + half of both columns of every pair to S, for the halves
+// [h0, h0 + nh); the transform of pair p and half h is h * PAIRS + p when both
+// halves are in `work` (nh = 2), else p.
 template <int NT>
-__device__ __forceinline__ void tfwd_post_store(const float2* work, int half, float2* S, int pitch, int col0,
-                                                int ncols, int COLS, int tid, int nthr) {
-  const WorkAddr<NT> wa{work_pitch<NT>(COLS >> 1)};
-  const int nk = half ? NT / 2 : NT / 2 + 1;
+__device__ __forceinline__ void tfwd_post_store(const float2* work, const WorkAddr<NT>& wa, int h0, int nh,
+                                                float2* S, int pitch, int col0, int ncols, int COLS, int tid,
+                                                int nthr) {
   const int lc = __ffs(COLS) - 1;  // COLS is a power of two
-  for (int i = tid; i < nk * COLS; i += nthr) {
-    const int kp = i >> lc, c = i & (COLS - 1), p = c >> 1;
+  const int n0 = (NT / 2 + 1 - h0) * COLS;  // items of the first half
+  const int total = nh == 2 ? (NT + 1) * COLS : n0;
+  for (int i = tid; i < total; i += nthr) {
+    const int half = i < n0 ? h0 : 1;
+    const int j = i < n0 ? i : i - n0;
+    const int kp = j >> lc, c = j & (COLS - 1), p = c >> 1;
     if (col0 + c >= ncols) continue;
+    const int q = nh == 2 ? half * (COLS >> 1) + p : p;
     const int m = half ? (NT - 1 - kp) : ((NT - kp) & (NT - 1));
-    const float2 za = work[wa(p, fpos<NT>(kp))];
-    const float2 zb = work[wa(p, fpos<NT>(m))];
+    const float2 za = work[wa(q, fpos<NT>(kp))];
+    const float2 zb = work[wa(q, fpos<NT>(m))];
     float2 x;
     if ((c & 1) == 0)
       x = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
@@ -193,8 +217,8 @@ __device__ __forceinline__ void tfwd_post_store(const float2* work, int half, fl
 // using Hermitian symmetry for kt > nt, packed as Z = X_a + i X_b.
 template <int NT>
 __device__ __forceinline__ void tinv_load(const float2* __restrict__ S, int pitch, int col0, int ncols, int half,
-                                          float2* work, int PAIRS, int tid, int nthr) {
-  const WorkAddr<NT> wa{work_pitch<NT>(PAIRS)};
+                                          float2* work, const WorkAddr<NT>& wa, int q0, int PAIRS, int tid,
+                                          int nthr) {
   const int lp = __ffs(PAIRS) - 1;
   batched_copy<8, float2>(
       NT * PAIRS, tid, nthr,
@@ -212,18 +236,39 @@ __device__ __forceinline__ void tinv_load(const float2* __restrict__ S, int pitc
         }
         return make_float2(A.x - B.y, A.y + B.x);
       },
-      [&](int i, float2 z) { work[wa(i & (PAIRS - 1), fpos<NT>(i >> lp))] = z; });
+      [&](int i, float2 z) { work[wa(q0 + (i & (PAIRS - 1)), fpos<NT>(i >> lp))] = z; });
 }
 
 // Inverse padded t-FFT of the CTA's pairs: cbuf[c][n] = (1/(2nt)) * real signal
-// of column c at n in [0, nt).
+// of column c at n in [0, nt).  The even and odd bins (halves) are two
+// length-nt transforms; with hb both run in one batched FFT of 2 PAIRS
+// transforms (twice the parallelism, half the steps), else one after the
+// other.
 template <int NT>
 __device__ __forceinline__ void tinv_core(const float2* __restrict__ S, int pitch, int col0, int ncols,
-                                          float2* work, float* cbuf, const float2* tw2, int PAIRS, int tid, int nthr) {
-  const WorkAddr<NT> wa{work_pitch<NT>(PAIRS)};
+                                          float2* work, float* cbuf, const float2* tw2, int PAIRS, bool hb, int tid,
+                                          int nthr) {
   const float scale = 1.0f / (2.0f * NT);
+  if (hb) {
+    const WorkAddr<NT> wa{work_pitch<NT>(2 * PAIRS)};
+    tinv_load<NT>(S, pitch, col0, ncols, 0, work, wa, 0, PAIRS, tid, nthr);
+    tinv_load<NT>(S, pitch, col0, ncols, 1, work, wa, PAIRS, PAIRS, tid, nthr);
+    __syncthreads();
+    team_fft_a<NT, true>(work, 2 * PAIRS, wa, tw2, 2, tid, nthr);
+    for (int i = tid; i < PAIRS * NT; i += nthr) {
+      const int p = i / NT, n = i % NT;
+      const float2 z0 = work[wa(p, n)];
+      const float2 z1 = cmulc(work[wa(PAIRS + p, n)], tw2[n]);
+      float* ca = cbuf + (2 * p) * NT;
+      ca[n] = (z0.x + z1.x) * scale;
+      ca[n + NT] = (z0.y + z1.y) * scale;
+    }
+    __syncthreads();
+    return;
+  }
+  const WorkAddr<NT> wa{work_pitch<NT>(PAIRS)};
   for (int half = 0; half < 2; ++half) {
-    tinv_load<NT>(S, pitch, col0, ncols, half, work, PAIRS, tid, nthr);
+    tinv_load<NT>(S, pitch, col0, ncols, half, work, wa, 0, PAIRS, tid, nthr);
     __syncthreads();
     team_fft_a<NT, true>(work, PAIRS, wa, tw2, 2, tid, nthr);
     for (int i = tid; i < PAIRS * NT; i += nthr) {
@@ -252,17 +297,18 @@ template <int NT, int MODE>
 __global__ void __launch_bounds__(kTpassThreads)
     k_tfwd(Lin3 src, int ncols, float2* __restrict__ S, int pitch, const float4* __restrict__ ftab,
            const int32_t* __restrict__ tptr, const float2* __restrict__ tent, const float2* __restrict__ tw2g,
-           int cols) {
+           int cols, int hb) {
   const int COLS = cols, PAIRS = cols >> 1;
-  const WorkAddr<NT> wa{work_pitch<NT>(PAIRS)};
+  const int NB = hb ? 2 * PAIRS : PAIRS;  // transforms per FFT call (both halves at once with hb)
+  const WorkAddr<NT> wa{work_pitch<NT>(NB)};
   extern __shared__ float4 smem_f4[];
   float2* tw2 = reinterpret_cast<float2*>(smem_f4);
   float4* tab = reinterpret_cast<float4*>(tw2 + 2 * NT);
   float2* work = reinterpret_cast<float2*>(tab + TabLayout<NT>::SLOTS);
-  float* cbuf = reinterpret_cast<float*>(work + ((PAIRS * wa.pitch + 1) & ~1));
+  float* cbuf = reinterpret_cast<float*>(work + ((NB * wa.pitch + 1) & ~1));
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int col0 = blockIdx.x * COLS;
-  for (int i = tid; i < 2 * NT; i += nthr) tw2[i] = __ldg(tw2g + i);
+  stage_twiddles<NT>(tw2, tw2g, tid, nthr);
   if (MODE == 0)
     stage_fwd_taps<NT>(tab, ftab, tid, nthr);
   else
@@ -299,7 +345,9 @@ __global__ void __launch_bounds__(kTpassThreads)
       [&](int i, float4 v) { reinterpret_cast<float4*>(cbuf)[i] = v; });
   __syncthreads();
 
-  for (int half = 0; half < 2; ++half) {
+  // the even output bins (half 0) are the length-nt DFT of z, the odd ones
+  // (half 1) that of z w^n
+  for (int h0 = 0; h0 < 2; h0 += hb ? 2 : 1) {
     for (int i = tid; i < PAIRS * NT; i += nthr) {
       const int p = i / NT, n = i % NT;
       const float* ca = cbuf + (2 * p) * NT;
@@ -314,12 +362,16 @@ __global__ void __launch_bounds__(kTpassThreads)
         // c_n = sum over the t-bins k that interpolate v-bin n of (w wt)_k r_k
         z = csr_row2<NT>(tab, n, ca, cb);
       }
-      if (half) z = cmul(z, tw2[n]);
-      work[wa(p, n)] = z;
+      if (hb) {
+        work[wa(p, n)] = z;
+        work[wa(PAIRS + p, n)] = cmul(z, tw2[n]);
+      } else {
+        work[wa(p, n)] = h0 ? cmul(z, tw2[n]) : z;
+      }
     }
     __syncthreads();
-    team_fft_a<NT, false>(work, PAIRS, wa, tw2, 2, tid, nthr);
-    tfwd_post_store<NT>(work, half, S, pitch, col0, ncols, COLS, tid, nthr);
+    team_fft_a<NT, false>(work, NB, wa, tw2, 2, tid, nthr);
+    tfwd_post_store<NT>(work, wa, h0, hb ? 2 : 1, S, pitch, col0, ncols, COLS, tid, nthr);
     __syncthreads();
   }
 }
@@ -331,20 +383,20 @@ template <int NT, int EPI>
 __global__ void __launch_bounds__(kTpassThreads)
     k_tinv(const float2* __restrict__ S, int pitch, int ncols, float* __restrict__ out,
            const int32_t* __restrict__ outmap, FitArgs fa, const float4* __restrict__ ftab,
-           const float2* __restrict__ tw2g, int cols) {
+           const float2* __restrict__ tw2g, int cols, int hb) {
   const int COLS = cols, PAIRS = cols >> 1;
-  const WorkAddr<NT> wa{work_pitch<NT>(PAIRS)};
+  const int NB = hb ? 2 * PAIRS : PAIRS;
   extern __shared__ float4 smem_f4[];
   float2* tw2 = reinterpret_cast<float2*>(smem_f4);
   float4* tab = reinterpret_cast<float4*>(tw2 + 2 * NT);
   float2* work = reinterpret_cast<float2*>(tab + TabLayout<NT>::SLOTS);
-  float* cbuf = reinterpret_cast<float*>(work + ((PAIRS * wa.pitch + 1) & ~1));
+  float* cbuf = reinterpret_cast<float*>(work + ((NB * work_pitch<NT>(NB) + 1) & ~1));
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int col0 = blockIdx.x * COLS;
-  for (int i = tid; i < 2 * NT; i += nthr) tw2[i] = __ldg(tw2g + i);
+  stage_twiddles<NT>(tw2, tw2g, tid, nthr);
   stage_fwd_taps<NT>(tab, ftab, tid, nthr);
   __syncthreads();
-  tinv_core<NT>(S, pitch, col0, ncols, work, cbuf, tw2, PAIRS, tid, nthr);
+  tinv_core<NT>(S, pitch, col0, ncols, work, cbuf, tw2, PAIRS, hb != 0, tid, nthr);
 
   ChunkAcc<2> ca;
   float bp = 0.f;
@@ -408,20 +460,21 @@ template <int NT, int MODE>
 __global__ void __launch_bounds__(kTpassThreads)
     k_tadj(const float2* __restrict__ S, int pitch, int ncols, float* __restrict__ out, SolveRhs sr,
            float2* __restrict__ Sp, const int32_t* __restrict__ tptr, const float2* __restrict__ tent,
-           const float2* __restrict__ tw2g, int cols) {
+           const float2* __restrict__ tw2g, int cols, int hb) {
   const int COLS = cols, PAIRS = cols >> 1;
-  const WorkAddr<NT> wa{work_pitch<NT>(PAIRS)};
+  const int NB = hb ? 2 * PAIRS : PAIRS;
+  const WorkAddr<NT> wa{work_pitch<NT>(PAIRS)};  // layout of the periodic forward FFT (MODE 1)
   extern __shared__ float4 smem_f4[];
   float2* tw2 = reinterpret_cast<float2*>(smem_f4);
   float4* tab = reinterpret_cast<float4*>(tw2 + 2 * NT);
   float2* work = reinterpret_cast<float2*>(tab + TabLayout<NT>::SLOTS);
-  float* cbuf = reinterpret_cast<float*>(work + ((PAIRS * wa.pitch + 1) & ~1));
+  float* cbuf = reinterpret_cast<float*>(work + ((NB * work_pitch<NT>(NB) + 1) & ~1));
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int col0 = blockIdx.x * COLS;
-  for (int i = tid; i < 2 * NT; i += nthr) tw2[i] = __ldg(tw2g + i);
+  stage_twiddles<NT>(tw2, tw2g, tid, nthr);
   stage_csr<NT>(tab, tptr, tent, tid, nthr);
   __syncthreads();
-  tinv_core<NT>(S, pitch, col0, ncols, work, cbuf, tw2, PAIRS, tid, nthr);
+  tinv_core<NT>(S, pitch, col0, ncols, work, cbuf, tw2, PAIRS, hb != 0, tid, nthr);
 
   // g_i = sum over the v-bins j whose R_z taps touch rho-bin i of (w g)_j c_j,
   // gathered straight into the output (MODE 0) or into the solve rhs (MODE 1)
@@ -479,7 +532,7 @@ __global__ void __launch_bounds__(kTpassThreads)
   float2* work = tw2 + 2 * NT;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int col0 = blockIdx.x * COLS;
-  for (int i = tid; i < 2 * NT; i += nthr) tw2[i] = __ldg(tw2g + i);
+  stage_twiddles<NT>(tw2, tw2g, tid, nthr);
   batched_copy<8, float2>(
       PAIRS * NT, tid, nthr,
       [&](int i) {
@@ -506,7 +559,7 @@ __global__ void __launch_bounds__(kTpassThreads)
   float2* work = tw2 + 2 * NT;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int col0 = blockIdx.x * COLS;
-  for (int i = tid; i < 2 * NT; i += nthr) tw2[i] = __ldg(tw2g + i);
+  stage_twiddles<NT>(tw2, tw2g, tid, nthr);
   const int lp = __ffs(PAIRS) - 1;
   batched_copy<8, float2>(
       NT * PAIRS, tid, nthr,
@@ -559,27 +612,44 @@ static nlos_status set_smem_tp(K kernel, size_t bytes) {
 // columns, e.g. the sampled columns of A_D, so the grid still covers the
 // GPU), threads per CTA and dynamic shared memory (twiddles, the packed pair
 // transforms, `extra` real column buffers).
+// hb: both halves (even and odd bins of the padded transform) in one batched
+// FFT, for the kernels that have two halves.
 struct TpShape {
-  int cols, threads, blocks;
+  int cols, hb, threads, blocks;
   size_t smem;
 };
 
+// Dynamic shared memory of a t-pass launch: twiddles, the work region
+// (padded to an even number of float2 so the real column buffers after it
+// stay 16-byte aligned for float4 accesses), the tap table, `extra` real
+// column buffers.
 template <int NT>
-static TpShape tp_shape(int ncols, int extra, bool tab, int kind) {
+static size_t tp_smem(int cols, int hb, int extra, bool tab) {
+  const int nb = hb ? cols : cols / 2;
+  return sizeof(float2) * (2 * NT + ((nb * work_pitch<NT>(nb) + 1) & ~1)) +
+         (tab ? sizeof(float4) * TabLayout<NT>::SLOTS : 0) + sizeof(float) * extra * cols * NT;
+}
+
+// Launch shape: the tuned (columns per CTA, hb) of this kind and column count
+// (encoded cols | hb << 8), else the default rule (enough CTAs to cover the
+// GPU twice, halves one after the other).
+template <int NT>
+static TpShape tp_shape(int ncols, int extra, bool tab, int kind, bool halves) {
   TpShape sh;
   const int tuned = kind >= 0 ? tp_cols_for(kind, NT, ncols) : 0;
-  if (tuned >= 2 && tuned <= TP<NT>::COLS) {
-    sh.cols = tuned;
+  const int tc = tuned & 0xff;
+  if (tc >= 2 && tc <= TP<NT>::COLS) {
+    sh.cols = tc;
+    sh.hb = halves ? (tuned >> 8) & 1 : 0;
   } else {
     sh.cols = TP<NT>::COLS;
+    sh.hb = 0;
     while (sh.cols > 2 && div_up(ncols, sh.cols) < 2 * 152) sh.cols >>= 1;
   }
-  sh.threads = sh.cols >= 8 ? kTpassThreads : sh.cols == 4 ? 128 : 64;
+  const int work_cols = sh.hb ? 2 * sh.cols : sh.cols;  // FFT tasks scale with the transforms per CTA
+  sh.threads = work_cols >= 8 ? kTpassThreads : work_cols == 4 ? 128 : 64;
   sh.blocks = div_up(ncols, sh.cols);
-  // the work region is padded to an even number of float2 so the real column
-  // buffers after it stay 16-byte aligned (float4 accesses)
-  sh.smem = sizeof(float2) * (2 * NT + (((sh.cols / 2) * work_pitch<NT>(sh.cols / 2) + 1) & ~1)) +
-            (tab ? sizeof(float4) * TabLayout<NT>::SLOTS : 0) + sizeof(float) * extra * sh.cols * NT;
+  sh.smem = tp_smem<NT>(sh.cols, sh.hb, extra, tab);
   return sh;
 }
 
@@ -587,11 +657,11 @@ template <int NT>
 nlos_status TpassOps<NT>::tfwd_rz(const Plan& P, const float* u, int ncols, float2* S, int pitch, cudaStream_t st) {
   KTimer kt_(P, KC_TFWD, st);
   auto kern = k_tfwd<NT, 0>;
-  const TpShape sh = tp_shape<NT>(ncols, 1, true, TPK_TFWD_RZ);
+  const TpShape sh = tp_shape<NT>(ncols, 1, true, TPK_TFWD_RZ, true);
   NLOS_TRY(set_smem_tp(kern, sh.smem));
   Lin3 src{{u, nullptr, nullptr}, {1.f, 0.f, 0.f}, nullptr};
   kern<<<sh.blocks, sh.threads, sh.smem, st>>>(src, ncols, S, pitch, P.d_rz_f4, nullptr, nullptr, P.d_tw2t,
-                                               sh.cols);
+                                               sh.cols, sh.hb);
   NLOS_LAUNCH_CHECK("k_tfwd<rz>");
   return NLOS_OK;
 }
@@ -600,10 +670,10 @@ template <int NT>
 nlos_status TpassOps<NT>::tfwd_rtt(const Plan& P, const Lin3& r, int ncols, float2* S, int pitch, cudaStream_t st) {
   KTimer kt_(P, KC_TFWD, st);
   auto kern = k_tfwd<NT, 1>;
-  const TpShape sh = tp_shape<NT>(ncols, 1, true, TPK_TFWD_RTT);
+  const TpShape sh = tp_shape<NT>(ncols, 1, true, TPK_TFWD_RTT, true);
   NLOS_TRY(set_smem_tp(kern, sh.smem));
   kern<<<sh.blocks, sh.threads, sh.smem, st>>>(r, ncols, S, pitch, nullptr, P.d_rtT_ptr, P.d_rtT_ent, P.d_tw2t,
-                                               sh.cols);
+                                               sh.cols, sh.hb);
   NLOS_LAUNCH_CHECK("k_tfwd<rtt>");
   return NLOS_OK;
 }
@@ -613,10 +683,11 @@ nlos_status TpassOps<NT>::tinv_store(const Plan& P, const float2* S, int pitch, 
                                      const int32_t* outmap, cudaStream_t st) {
   KTimer kt_(P, KC_TINV, st);
   auto kern = k_tinv<NT, 0>;
-  const TpShape sh = tp_shape<NT>(ncols, 1, true, TPK_TINV_STORE);
+  const TpShape sh = tp_shape<NT>(ncols, 1, true, TPK_TINV_STORE, true);
   NLOS_TRY(set_smem_tp(kern, sh.smem));
   FitArgs fa{};
-  kern<<<sh.blocks, sh.threads, sh.smem, st>>>(S, pitch, ncols, out, outmap, fa, P.d_rt_f4, P.d_tw2t, sh.cols);
+  kern<<<sh.blocks, sh.threads, sh.smem, st>>>(S, pitch, ncols, out, outmap, fa, P.d_rt_f4, P.d_tw2t, sh.cols,
+                                               sh.hb);
   NLOS_LAUNCH_CHECK("k_tinv<store>");
   return NLOS_OK;
 }
@@ -626,11 +697,12 @@ nlos_status TpassOps<NT>::tinv_fit(const Plan& P, const float2* S, int pitch, in
                                    const FitArgs& fa, int* nblocks, cudaStream_t st) {
   KTimer kt_(P, KC_TINV, st);
   auto kern = k_tinv<NT, 1>;
-  const TpShape sh = tp_shape<NT>(ncols, 1, true, TPK_TINV_FIT);
+  const TpShape sh = tp_shape<NT>(ncols, 1, true, TPK_TINV_FIT, true);
   NLOS_TRY(set_smem_tp(kern, sh.smem));
   if (sh.blocks > P.partial_blocks) return fail(NLOS_ERR_INVALID_ARG, "partials buffer too small");
   *nblocks = sh.blocks;
-  kern<<<sh.blocks, sh.threads, sh.smem, st>>>(S, pitch, ncols, out, nullptr, fa, P.d_rt_f4, P.d_tw2t, sh.cols);
+  kern<<<sh.blocks, sh.threads, sh.smem, st>>>(S, pitch, ncols, out, nullptr, fa, P.d_rt_f4, P.d_tw2t, sh.cols,
+                                               sh.hb);
   NLOS_LAUNCH_CHECK("k_tinv<fit>");
   return NLOS_OK;
 }
@@ -640,11 +712,11 @@ nlos_status TpassOps<NT>::tadj_store(const Plan& P, const float2* S, int pitch, 
                                      cudaStream_t st) {
   KTimer kt_(P, KC_TADJ, st);
   auto kern = k_tadj<NT, 0>;
-  const TpShape sh = tp_shape<NT>(ncols, 1, true, TPK_TADJ_STORE);
+  const TpShape sh = tp_shape<NT>(ncols, 1, true, TPK_TADJ_STORE, true);
   NLOS_TRY(set_smem_tp(kern, sh.smem));
   SolveRhs sr{};
   kern<<<sh.blocks, sh.threads, sh.smem, st>>>(S, pitch, ncols, out, sr, nullptr, P.d_rzT_ptr, P.d_rzT_ent,
-                                               P.d_tw2t, sh.cols);
+                                               P.d_tw2t, sh.cols, sh.hb);
   NLOS_LAUNCH_CHECK("k_tadj<store>");
   return NLOS_OK;
 }
@@ -654,10 +726,10 @@ nlos_status TpassOps<NT>::tadj_solve(const Plan& P, const float2* S, int pitch, 
                                      float2* Sp, cudaStream_t st) {
   KTimer kt_(P, KC_TADJ, st);
   auto kern = k_tadj<NT, 1>;
-  const TpShape sh = tp_shape<NT>(ncols, 1, true, TPK_TADJ_SOLVE);
+  const TpShape sh = tp_shape<NT>(ncols, 1, true, TPK_TADJ_SOLVE, true);
   NLOS_TRY(set_smem_tp(kern, sh.smem));
   kern<<<sh.blocks, sh.threads, sh.smem, st>>>(S, pitch, ncols, nullptr, sr, Sp, P.d_rzT_ptr, P.d_rzT_ent,
-                                               P.d_tw2t, sh.cols);
+                                               P.d_tw2t, sh.cols, sh.hb);
   NLOS_LAUNCH_CHECK("k_tadj<solve>");
   return NLOS_OK;
 }
@@ -666,7 +738,7 @@ template <int NT>
 nlos_status TpassOps<NT>::sfwd(const Plan& P, const float* x, int ncols, float2* Sp, cudaStream_t st) {
   KTimer kt_(P, KC_SFWD, st);
   auto kern = k_sfwd<NT>;
-  const TpShape sh = tp_shape<NT>(ncols, 0, false, TPK_SFWD);
+  const TpShape sh = tp_shape<NT>(ncols, 0, false, TPK_SFWD, false);
   NLOS_TRY(set_smem_tp(kern, sh.smem));
   kern<<<sh.blocks, sh.threads, sh.smem, st>>>(x, ncols, Sp, P.d_tw2t, sh.cols);
   NLOS_LAUNCH_CHECK("k_sfwd");
@@ -678,7 +750,7 @@ nlos_status TpassOps<NT>::sinv(const Plan& P, const float2* Sp, int ncols, float
                                double* partials, int* nblocks, cudaStream_t st) {
   KTimer kt_(P, KC_SINV, st);
   auto kern = k_sinv<NT>;
-  const TpShape sh = tp_shape<NT>(ncols, 0, false, TPK_SINV);
+  const TpShape sh = tp_shape<NT>(ncols, 0, false, TPK_SINV, false);
   NLOS_TRY(set_smem_tp(kern, sh.smem));
   if (partials && sh.blocks > P.partial_blocks) return fail(NLOS_ERR_INVALID_ARG, "partials buffer too small");
   if (nblocks) *nblocks = sh.blocks;
@@ -689,16 +761,16 @@ nlos_status TpassOps<NT>::sinv(const Plan& P, const float2* Sp, int ncols, float
 
 template <int NT>
 nlos_status TpassOps<NT>::prepare() {
-  // largest shapes: the default rule's column count for a huge launch
-  const TpShape s1 = tp_shape<NT>(1 << 30, 1, true, -1), s2 = s1, s0 = tp_shape<NT>(1 << 30, 0, false, -1);
-  NLOS_TRY(set_smem_tp(k_tfwd<NT, 0>, s1.smem));
-  NLOS_TRY(set_smem_tp(k_tfwd<NT, 1>, s1.smem));
-  NLOS_TRY(set_smem_tp(k_tinv<NT, 0>, s1.smem));
-  NLOS_TRY(set_smem_tp(k_tinv<NT, 1>, s1.smem));
-  NLOS_TRY(set_smem_tp(k_tadj<NT, 0>, s2.smem));
-  NLOS_TRY(set_smem_tp(k_tadj<NT, 1>, s2.smem));
-  NLOS_TRY(set_smem_tp(k_sfwd<NT>, s0.smem));
-  NLOS_TRY(set_smem_tp(k_sinv<NT>, s0.smem));
+  // largest shapes: the most columns per CTA, both halves batched
+  const size_t m1 = tp_smem<NT>(TP<NT>::COLS, 1, 1, true), m0 = tp_smem<NT>(TP<NT>::COLS, 0, 0, false);
+  NLOS_TRY(set_smem_tp(k_tfwd<NT, 0>, m1));
+  NLOS_TRY(set_smem_tp(k_tfwd<NT, 1>, m1));
+  NLOS_TRY(set_smem_tp(k_tinv<NT, 0>, m1));
+  NLOS_TRY(set_smem_tp(k_tinv<NT, 1>, m1));
+  NLOS_TRY(set_smem_tp(k_tadj<NT, 0>, m1));
+  NLOS_TRY(set_smem_tp(k_tadj<NT, 1>, m1));
+  NLOS_TRY(set_smem_tp(k_sfwd<NT>, m0));
+  NLOS_TRY(set_smem_tp(k_sinv<NT>, m0));
   return NLOS_OK;
 }
 
