@@ -827,8 +827,7 @@ static nlos_status u_trial(Plan& P, SolverState* s, const UStepArgs& a, int* nbd
   SolveRhs sr{s->ub, a.reg, s->sc, 0.0};
   NLOS_TRY(launch_tadj_solve(P, P.d_S, full, full, sr, P.d_Sp, st));
   NLOS_TRY(launch_sxy(P, P.d_Sp, s->sc, 0.0, a.mu, st));
-  NLOS_TRY(launch_sinv(P, P.d_Sp, full, s->unew, s->ub, s->pa, nbd, st));
-  NLOS_TRY(launch_tfwd_rz(P, s->unew, full, P.d_S2, full, st));
+  NLOS_TRY(launch_sinv_rz(P, P.d_Sp, full, s->unew, s->ub, s->pa, nbd, P.d_S2, full, st));
   float2* Sfit = P.d_S2;
   if (a.compact) {
     NLOS_TRY(launch_conv(P, P.d_S2, false, P.d_Sc, true, false, st));

@@ -206,7 +206,7 @@ enum KernelCat {
   KC_TADJ = 3,      // k_tadj: inverse t-FFT + R_z^T (+ solve rhs, periodic t-FFT)
   KC_SXY = 4,       // k_sxy: lateral periodic solve
   KC_SFWD = 5,      // k_sfwd: periodic t-FFT of a field
-  KC_SINV = 6,      // k_sinv: periodic inverse t-FFT
+  KC_SINV = 6,      // k_sinv: periodic inverse t-FFT (k_sinv_rz: + R_z forward t-pass)
   KC_PRE = 7,       // k_pre1 / k_pre2: shrinkage + nabla^* stencils
   KC_POST = 8,      // k_post1 / k_post2: multipliers, curvature, extrapolation
   KC_SMALL = 9,     // one-thread scalar kernels, fills, gathers, reductions

@@ -61,6 +61,10 @@ nlos_status launch_sinv(const Plan& P, const float2* Sp, int ncols, float* x, co
                         int* nblocks, cudaStream_t st) {
   NLOS_DISPATCH_NT(P.nt, sinv(P, Sp, ncols, x, ref, partials, nblocks, st));
 }
+nlos_status launch_sinv_rz(const Plan& P, const float2* Sp, int ncols, float* x, const float* ref,
+                           double* partials, int* nblocks, float2* S, int pitch, cudaStream_t st) {
+  NLOS_DISPATCH_NT(P.nt, sinv_rz(P, Sp, ncols, x, ref, partials, nblocks, S, pitch, st));
+}
 
 }  // namespace nlos
 
@@ -121,6 +125,8 @@ nlos_status autotune_tpass(Plan& P, cudaStream_t st) {
       {TPK_TADJ_SOLVE, full, false, [&] { return launch_tadj_solve(P, P.d_S, full, full, sr, P.d_Sp, st); }},
       {TPK_SFWD, full, false, [&] { return launch_sfwd(P, f1, full, P.d_Sp, st); }},
       {TPK_SINV, full, true, [&] { return launch_sinv(P, P.d_Sp, full, f1, f2, P.d_partials, &nb, st); }},
+      {TPK_SINV_RZ, full, true,
+       [&] { return launch_sinv_rz(P, P.d_Sp, full, f1, f2, P.d_partials, &nb, P.d_S, full, st); }},
   };
   if (nc < full) {
     cases.push_back({TPK_TFWD_RTT, nc, false, [&, nc] { return launch_tfwd_rtt(P, r_comp, nc, P.d_Sc, nc, st); }});
@@ -136,7 +142,7 @@ nlos_status autotune_tpass(Plan& P, cudaStream_t st) {
       std::lock_guard<std::mutex> lock(g_tp_mu);
       if (g_tp_cols.count(std::make_tuple(c.kind, nt, c.ncols))) continue;
     }
-    const bool halves = c.kind != TPK_SFWD && c.kind != TPK_SINV;
+    const bool halves = c.kind != TPK_SFWD && c.kind != TPK_SINV;  // sinv_rz: its forward half
     int best = 0;
     float best_ms = 0.f;
     for (int cand = 0; cand < 8 && status == NLOS_OK; ++cand) {

@@ -53,6 +53,9 @@ nlos_status launch_tadj_solve(const Plan& P, const float2* S, int pitch, int nco
 nlos_status launch_sfwd(const Plan& P, const float* x, int ncols, float2* Sp, cudaStream_t st);
 nlos_status launch_sinv(const Plan& P, const float2* Sp, int ncols, float* x, const float* ref,
                         double* partials, int* nblocks, cudaStream_t st);
+// launch_sinv followed by launch_tfwd_rz(x -> S) in one pass (x kept on chip).
+nlos_status launch_sinv_rz(const Plan& P, const float2* Sp, int ncols, float* x, const float* ref,
+                           double* partials, int* nblocks, float2* S, int pitch, cudaStream_t st);
 // Lateral 2-D zero-padded convolution of each kt plane with H (adj: conj H).
 // in_cols/out_cols: nullptr = full plane [nx][ny]; else compact column lists
 // (the plan's sampled columns) with plane pitch ncols.
@@ -77,7 +80,8 @@ nlos_status launch_kernel_spectrum(const Plan& P, const int32_t* m0, const float
 // column count), so all plans of a geometry launch the same shapes and their
 // block-partial reductions sum in the same order.
 enum TpKind {
-  TPK_TFWD_RZ, TPK_TFWD_RTT, TPK_TINV_STORE, TPK_TINV_FIT, TPK_TADJ_STORE, TPK_TADJ_SOLVE, TPK_SFWD, TPK_SINV
+  TPK_TFWD_RZ, TPK_TFWD_RTT, TPK_TINV_STORE, TPK_TINV_FIT, TPK_TADJ_STORE, TPK_TADJ_SOLVE, TPK_SFWD, TPK_SINV,
+  TPK_SINV_RZ
 };
 // Tuned shape of a launch, cols | hb << 8, or 0 (use the default rule).
 int tp_cols_for(int kind, int nt, int ncols);

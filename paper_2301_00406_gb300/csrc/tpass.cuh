@@ -25,6 +25,8 @@ struct TpassOps {
   static nlos_status sfwd(const Plan& P, const float* x, int ncols, float2* Sp, cudaStream_t st);
   static nlos_status sinv(const Plan& P, const float2* Sp, int ncols, float* x, const float* ref, double* partials,
                           int* nblocks, cudaStream_t st);
+  static nlos_status sinv_rz(const Plan& P, const float2* Sp, int ncols, float* x, const float* ref,
+                             double* partials, int* nblocks, float2* S, int pitch, cudaStream_t st);
   // Raise every t-pass kernel's shared-memory limit to its largest launch
   // shape (so no attribute call happens later, e.g. during a stream capture).
   static nlos_status prepare();
@@ -289,6 +291,49 @@ __device__ __forceinline__ void tinv_core(const float2* __restrict__ S, int pitc
   }
 }
 
+// The resampling and padded forward t-FFT of the CTA's real columns staged in
+// cbuf (COLS columns of nt values, zero past the last column): R_z taps
+// (MODE 0) or the R_t^{-T} CSR rows (MODE 1) from tab, then both halves of
+// the padded transform, stored to S.  Starts and ends with every thread past
+// a barrier.
+template <int NT, int MODE>
+__device__ __forceinline__ void tfwd_from_cbuf(const float* cbuf, const float4* tab, float2* work, const float2* tw2,
+                                               int COLS, int hb, float2* __restrict__ S, int pitch, int col0,
+                                               int ncols, int tid, int nthr) {
+  const int PAIRS = COLS >> 1;
+  const int NB = hb ? 2 * PAIRS : PAIRS;  // transforms per FFT call (both halves at once with hb)
+  const WorkAddr<NT> wa{work_pitch<NT>(NB)};
+  // the even output bins (half 0) are the length-nt DFT of z, the odd ones
+  // (half 1) that of z w^n
+  for (int h0 = 0; h0 < 2; h0 += hb ? 2 : 1) {
+    for (int i = tid; i < PAIRS * NT; i += nthr) {
+      const int p = i / NT, n = i % NT;
+      const float* ca = cbuf + (2 * p) * NT;
+      const float* cb = ca + NT;
+      float2 z;
+      if (MODE == 0) {
+        // u~_n = (w0 g)_n u[i0_n] + (w1 g)_n u[i0_n + 1]
+        const float4 t = tab[n];
+        const int i0 = __float_as_int(t.z);
+        z = make_float2(t.x * ca[i0] + t.y * ca[i0 + 1], t.x * cb[i0] + t.y * cb[i0 + 1]);
+      } else {
+        // c_n = sum over the t-bins k that interpolate v-bin n of (w wt)_k r_k
+        z = csr_row2<NT>(tab, n, ca, cb);
+      }
+      if (hb) {
+        work[wa(p, n)] = z;
+        work[wa(PAIRS + p, n)] = cmul(z, tw2[n]);
+      } else {
+        work[wa(p, n)] = h0 ? cmul(z, tw2[n]) : z;
+      }
+    }
+    __syncthreads();
+    team_fft_a<NT, false>(work, NB, wa, tw2, 2, tid, nthr);
+    tfwd_post_store<NT>(work, wa, h0, hb ? 2 : 1, S, pitch, col0, ncols, COLS, tid, nthr);
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Forward t-pass: R_z (MODE 0) or R_t^{-T} of a residual (MODE 1), then the
 // padded real FFT.
@@ -299,13 +344,12 @@ __global__ void __launch_bounds__(kTpassThreads)
            const int32_t* __restrict__ tptr, const float2* __restrict__ tent, const float2* __restrict__ tw2g,
            int cols, int hb) {
   const int COLS = cols, PAIRS = cols >> 1;
-  const int NB = hb ? 2 * PAIRS : PAIRS;  // transforms per FFT call (both halves at once with hb)
-  const WorkAddr<NT> wa{work_pitch<NT>(NB)};
+  const int NB = hb ? 2 * PAIRS : PAIRS;
   extern __shared__ float4 smem_f4[];
   float2* tw2 = reinterpret_cast<float2*>(smem_f4);
   float4* tab = reinterpret_cast<float4*>(tw2 + 2 * NT);
   float2* work = reinterpret_cast<float2*>(tab + TabLayout<NT>::SLOTS);
-  float* cbuf = reinterpret_cast<float*>(work + ((NB * wa.pitch + 1) & ~1));
+  float* cbuf = reinterpret_cast<float*>(work + ((NB * work_pitch<NT>(NB) + 1) & ~1));
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int col0 = blockIdx.x * COLS;
   stage_twiddles<NT>(tw2, tw2g, tid, nthr);
@@ -345,35 +389,7 @@ __global__ void __launch_bounds__(kTpassThreads)
       [&](int i, float4 v) { reinterpret_cast<float4*>(cbuf)[i] = v; });
   __syncthreads();
 
-  // the even output bins (half 0) are the length-nt DFT of z, the odd ones
-  // (half 1) that of z w^n
-  for (int h0 = 0; h0 < 2; h0 += hb ? 2 : 1) {
-    for (int i = tid; i < PAIRS * NT; i += nthr) {
-      const int p = i / NT, n = i % NT;
-      const float* ca = cbuf + (2 * p) * NT;
-      const float* cb = ca + NT;
-      float2 z;
-      if (MODE == 0) {
-        // u~_n = (w0 g)_n u[i0_n] + (w1 g)_n u[i0_n + 1]
-        const float4 t = tab[n];
-        const int i0 = __float_as_int(t.z);
-        z = make_float2(t.x * ca[i0] + t.y * ca[i0 + 1], t.x * cb[i0] + t.y * cb[i0 + 1]);
-      } else {
-        // c_n = sum over the t-bins k that interpolate v-bin n of (w wt)_k r_k
-        z = csr_row2<NT>(tab, n, ca, cb);
-      }
-      if (hb) {
-        work[wa(p, n)] = z;
-        work[wa(PAIRS + p, n)] = cmul(z, tw2[n]);
-      } else {
-        work[wa(p, n)] = h0 ? cmul(z, tw2[n]) : z;
-      }
-    }
-    __syncthreads();
-    team_fft_a<NT, false>(work, NB, wa, tw2, 2, tid, nthr);
-    tfwd_post_store<NT>(work, wa, h0, hb ? 2 : 1, S, pitch, col0, ncols, COLS, tid, nthr);
-    __syncthreads();
-  }
+  tfwd_from_cbuf<NT, MODE>(cbuf, tab, work, tw2, COLS, hb, S, pitch, col0, ncols, tid, nthr);
 }
 
 // ---------------------------------------------------------------------------
@@ -603,6 +619,75 @@ __global__ void __launch_bounds__(kTpassThreads)
 }
 
 
+// Periodic inverse t-FFT fused with the forward t-pass of its result: the
+// columns x = F_t^{-1}(Sp) (u+ of the u-step, with the partial sums of
+// (x - ref)^2 as k_sinv) are written out and kept in shared memory, and R_z
+// and the padded forward t-FFT of the same columns (k_tfwd, MODE 0) follow
+// from there, so x is not read back from global memory.  The stored x and S
+// equal those of k_sinv followed by k_tfwd bit for bit.
+template <int NT>
+__global__ void __launch_bounds__(kTpassThreads)
+    k_sinv_rz(const float2* __restrict__ Sp, int ncols, float* __restrict__ x, const float* __restrict__ ref,
+              double* __restrict__ partials, float2* __restrict__ S, int pitch, const float4* __restrict__ ftab,
+              const float2* __restrict__ tw2g, int cols, int hb) {
+  const int COLS = cols, PAIRS = cols >> 1;
+  const int NB = hb ? 2 * PAIRS : PAIRS;
+  const WorkAddr<NT> wa{work_pitch<NT>(PAIRS)};  // layout of the periodic inverse FFT
+  extern __shared__ float4 smem_f4[];
+  float2* tw2 = reinterpret_cast<float2*>(smem_f4);
+  float4* tab = reinterpret_cast<float4*>(tw2 + 2 * NT);
+  float2* work = reinterpret_cast<float2*>(tab + TabLayout<NT>::SLOTS);
+  float* cbuf = reinterpret_cast<float*>(work + ((NB * work_pitch<NT>(NB) + 1) & ~1));
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int col0 = blockIdx.x * COLS;
+  stage_twiddles<NT>(tw2, tw2g, tid, nthr);
+  stage_fwd_taps<NT>(tab, ftab, tid, nthr);
+  const int lp = __ffs(PAIRS) - 1;
+  batched_copy<8, float2>(
+      NT * PAIRS, tid, nthr,
+      [&](int i) {
+        const int k = i >> lp, p = i & (PAIRS - 1);
+        int kk = k;
+        const bool mir = k > NT / 2;
+        if (mir) kk = NT - k;
+        const int ca = col0 + 2 * p;
+        float2 A, B;
+        load_pair(Sp + (size_t)kk * ncols, ca, ncols, (ncols & 1) == 0, A, B);
+        if (mir) {
+          A.y = -A.y;
+          B.y = -B.y;
+        }
+        return make_float2(A.x - B.y, A.y + B.x);
+      },
+      [&](int i, float2 z) { work[wa(i & (PAIRS - 1), fpos<NT>(i >> lp))] = z; });
+  __syncthreads();
+  team_fft_a<NT, true>(work, PAIRS, wa, tw2, 2, tid, nthr);
+  const float scale = 1.0f / NT;
+  ChunkAcc<1> ca;
+  const int total = min(COLS, ncols - col0) * NT;
+  batched_copy<8, float>(
+      total, tid, nthr, [&](int i) { return ref ? __ldg(ref + (size_t)col0 * NT + i) : 0.f; },
+      [&](int i, float rv) {
+        const int c = i / NT, n = i % NT;
+        const float2 z = work[wa(c >> 1, n)];
+        const float v = ((c & 1) ? z.y : z.x) * scale;
+        x[(size_t)col0 * NT + i] = v;
+        cbuf[i] = v;
+        if (ref) {
+          const float d = v - rv;
+          ca.add(0, d * d);
+          ca.step();
+        }
+      });
+  for (int i = total + tid; i < COLS * NT; i += nthr) cbuf[i] = 0.f;  // columns past the last
+  if (partials) {
+    ca.flush();
+    block_reduce_store<1>(ca.tot, partials);
+  }
+  __syncthreads();
+  tfwd_from_cbuf<NT, 0>(cbuf, tab, work, tw2, COLS, hb, S, pitch, col0, ncols, tid, nthr);
+}
+
 template <typename K>
 static nlos_status set_smem_tp(K kernel, size_t bytes) {
   return ensure_smem(kernel, bytes);
@@ -760,6 +845,21 @@ nlos_status TpassOps<NT>::sinv(const Plan& P, const float2* Sp, int ncols, float
 }
 
 template <int NT>
+nlos_status TpassOps<NT>::sinv_rz(const Plan& P, const float2* Sp, int ncols, float* x, const float* ref,
+                                  double* partials, int* nblocks, float2* S, int pitch, cudaStream_t st) {
+  KTimer kt_(P, KC_SINV, st);
+  auto kern = k_sinv_rz<NT>;
+  const TpShape sh = tp_shape<NT>(ncols, 1, true, TPK_SINV_RZ, true);
+  NLOS_TRY(set_smem_tp(kern, sh.smem));
+  if (partials && sh.blocks > P.partial_blocks) return fail(NLOS_ERR_INVALID_ARG, "partials buffer too small");
+  if (nblocks) *nblocks = sh.blocks;
+  kern<<<sh.blocks, sh.threads, sh.smem, st>>>(Sp, ncols, x, ref, partials, S, pitch, P.d_rz_f4, P.d_tw2t, sh.cols,
+                                               sh.hb);
+  NLOS_LAUNCH_CHECK("k_sinv_rz");
+  return NLOS_OK;
+}
+
+template <int NT>
 nlos_status TpassOps<NT>::prepare() {
   // largest shapes: the most columns per CTA, both halves batched
   const size_t m1 = tp_smem<NT>(TP<NT>::COLS, 1, 1, true), m0 = tp_smem<NT>(TP<NT>::COLS, 0, 0, false);
@@ -771,6 +871,7 @@ nlos_status TpassOps<NT>::prepare() {
   NLOS_TRY(set_smem_tp(k_tadj<NT, 1>, m1));
   NLOS_TRY(set_smem_tp(k_sfwd<NT>, m0));
   NLOS_TRY(set_smem_tp(k_sinv<NT>, m0));
+  NLOS_TRY(set_smem_tp(k_sinv_rz<NT>, m1));
   return NLOS_OK;
 }
 
