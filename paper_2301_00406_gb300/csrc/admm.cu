@@ -35,31 +35,6 @@ struct VoxIter {
   }
 };
 
-template <int NTERMS>
-__device__ __forceinline__ void block_reduce_to(double (&v)[NTERMS], double* partials) {
-  __shared__ double red[32][NTERMS];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int t = 0; t < NTERMS; ++t) {
-    double x = v[t];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    v[t] = x;
-  }
-  if (lane == 0)
-#pragma unroll
-    for (int t = 0; t < NTERMS; ++t) red[warp][t] = v[t];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
-    for (int t = 0; t < NTERMS; ++t) {
-      double s = 0.0;
-      for (int w = 0; w < nw; ++w) s += red[w][t];
-      partials[(size_t)blockIdx.x * kMaxTerms + t] = s;
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Elementwise and reduction utilities
 // ---------------------------------------------------------------------------
@@ -82,7 +57,7 @@ __global__ void __launch_bounds__(kStencilThreads)
     ca.step();
   }
   ca.flush();
-  block_reduce_to<1>(ca.tot, partials);
+  block_reduce_acc(ca, partials);
 }
 
 // Deterministic block-wide sums of per-block partials: thread i adds the
@@ -198,7 +173,7 @@ __global__ void __launch_bounds__(kStencilThreads)
     ca.step();
   }
   ca.flush();
-  block_reduce_to<2>(ca.tot, partials);
+  block_reduce_acc(ca, partials);
 }
 
 // ---------------------------------------------------------------------------
@@ -305,7 +280,7 @@ __global__ void __launch_bounds__(kStencilThreads)
     ca.step();
   }
   ca.flush();
-  block_reduce_to<7>(ca.tot, partials);
+  block_reduce_acc(ca, partials);
 }
 
 // Algorithm 2, elementwise part of the post step: Lambda_3 += mu3 (f - tau+),
@@ -331,7 +306,7 @@ __global__ void __launch_bounds__(kStencilThreads)
     ca.step();
   }
   ca.flush();
-  block_reduce_to<3>(ca.tot, partials);
+  block_reduce_acc(ca, partials);
 }
 
 // rhs of the tau-solve: x = A u+ + regt (used as the input of the periodic FFT)
@@ -507,7 +482,7 @@ __global__ void __launch_bounds__(kStencilThreads)
     ca.step();
   }
   ca.flush();
-  block_reduce_to<1>(ca.tot, partials);
+  block_reduce_acc(ca, partials);
 }
 
 // ---------------------------------------------------------------------------

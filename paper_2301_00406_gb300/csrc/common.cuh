@@ -83,38 +83,67 @@ struct DevScalars {
 // Number of FP64 partial-sum slots per block used by the reductions.
 constexpr int kMaxTerms = 8;
 
-// Per-thread accumulation of T sums: FP32 partial sums over chunks of at most
-// kChunk terms, each chunk added to an FP64 total in a fixed order.  FP64
-// arithmetic runs at a small fraction of the FP32 rate on this GPU, so an FP64
-// add per term would dominate an otherwise bandwidth-bound epilogue; a float
-// sum of 16 terms adds at most about 1e-6 relative rounding per chunk.
+// Per-thread sums of T terms in compensated FP32 (Kahan: s - c carries the
+// sum to about two roundings regardless of the term count), reduced across a
+// warp without rounding loss (TwoSum on hi/lo pairs) and converted to FP64
+// once per warp (block_reduce_acc).  FP64 instructions issue at a small
+// fraction of the FP32 rate on this GPU: an FP64 add per term, or even per
+// chunk of 16 terms, kept the FP64 pipe 40-60 % busy in the reduction
+// epilogues of otherwise FP32 kernels.  The order of every operation is fixed,
+// so the sums are reproducible bit for bit.
 template <int T>
 struct ChunkAcc {
-  static constexpr int kChunk = 16;
-  double tot[T];
-  float cur[T];
-  int n;
-  __device__ __forceinline__ ChunkAcc() : n(0) {
+  float s[T], c[T];
+  __device__ __forceinline__ ChunkAcc() {
 #pragma unroll
     for (int t = 0; t < T; ++t) {
-      tot[t] = 0.0;
-      cur[t] = 0.f;
+      s[t] = 0.f;
+      c[t] = 0.f;
     }
   }
-  __device__ __forceinline__ void add(int t, float v) { cur[t] += v; }
-  __device__ __forceinline__ void flush() {
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-      tot[t] += (double)cur[t];
-      cur[t] = 0.f;
-    }
-    n = 0;
+  __device__ __forceinline__ void add(int t, float v) {
+    const float y = v - c[t];
+    const float u = s[t] + y;
+    c[t] = (u - s[t]) - y;
+    s[t] = u;
   }
-  // call once per term group (after the add()s of one element)
-  __device__ __forceinline__ void step() {
-    if (++n == kChunk) flush();
-  }
+  // kept for the call sites' structure: nothing to do per element or at the end
+  __device__ __forceinline__ void step() {}
+  __device__ __forceinline__ void flush() {}
 };
+
+// Block-wide sums of the accumulators of every thread; thread 0 writes
+// partials[blockIdx.x * kMaxTerms + t].  Every thread of the block calls it
+// (blockDim.x a multiple of 32).
+template <int T>
+__device__ __forceinline__ void block_reduce_acc(const ChunkAcc<T>& ca, double* partials) {
+  __shared__ double red[32][T];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    float hi = ca.s[t], lo = -ca.c[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float h2 = __shfl_down_sync(0xffffffffu, hi, o);
+      const float l2 = __shfl_down_sync(0xffffffffu, lo, o);
+      const float sum = hi + h2;  // TwoSum: sum + err = hi + h2 exactly
+      const float bb = sum - hi;
+      const float err = (hi - (sum - bb)) + (h2 - bb);
+      hi = sum;
+      lo = lo + l2 + err;
+    }
+    if (lane == 0) red[warp][t] = (double)hi + (double)lo;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = blockDim.x >> 5;
+    for (int t = 0; t < T; ++t) {
+      double acc = 0.0;
+      for (int w = 0; w < nw; ++w) acc += red[w][t];
+      partials[(size_t)blockIdx.x * kMaxTerms + t] = acc;
+    }
+  }
+}
 
 // ---------------------------------------------------------------------------
 // Plan

@@ -134,8 +134,8 @@ __device__ __forceinline__ int kfreq(int p) {
 // e = er + ec where er (the same for all of a task's elements) and ec (a
 // compile-time constant after unrolling) have disjoint bits, so a layout can
 // compute the part of er once per task.  tw[j * tws] = exp(-2 pi i j / N)
-// for j < N.  All threads of the block call these; they end with
-// __syncthreads().
+// for j < N (tw: a pointer, or any table type with operator[]).  All
+// threads of the block call these; they end with __syncthreads().
 //
 // Three-step version (R3 > 1): N = R1 M, M = R2 R3.
 //   step 1 (b, n23): R1-point DFT over n1 of x[n1 M + n23], twiddle w_N^(n23 k1);
@@ -143,8 +143,8 @@ __device__ __forceinline__ int kfreq(int p) {
 //          twiddle w_M^(n3 k2) = w_N^(R1 n3 k2);
 //   step 3 (b, k1, k2): R3-point DFT over the contiguous n3.
 // The inverse runs the steps backwards with conjugate twiddles.
-template <int N, bool INV, typename Addr>
-__device__ __forceinline__ void team_fft3a(float2* buf, int B, const Addr& addr, const float2* tw, int tws, int tid,
+template <int N, bool INV, typename Addr, typename TwT>
+__device__ __forceinline__ void team_fft3a(float2* buf, int B, const Addr& addr, const TwT& tw, int tws, int tid,
                                            int nthr) {
   constexpr int R1 = FftPlan<N>::R1, R2 = FftPlan<N>::R2, R3 = FftPlan<N>::R3, M = R2 * R3;
   const int lb = __ffs(B) - 1;
@@ -215,8 +215,8 @@ __device__ __forceinline__ void team_fft3a(float2* buf, int B, const Addr& addr,
 }
 
 // Two-step version (R3 = 1; dispatches to the three-step one otherwise).
-template <int N, bool INV, typename Addr>
-__device__ __forceinline__ void team_fft_a(float2* buf, int B, const Addr& addr, const float2* tw, int tws, int tid,
+template <int N, bool INV, typename Addr, typename TwT>
+__device__ __forceinline__ void team_fft_a(float2* buf, int B, const Addr& addr, const TwT& tw, int tws, int tid,
                                            int nthr) {
   constexpr int R1 = FftPlan<N>::R1, R2 = FftPlan<N>::R2;
   if constexpr (FftPlan<N>::R3 > 1) {

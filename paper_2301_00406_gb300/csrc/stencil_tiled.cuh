@@ -196,30 +196,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     }
     cp_async_wait_all();
   }
-  ca.flush();
-  __shared__ double red[kTileThreads / 32][2];
-  double acc[2] = {ca.tot[0], ca.tot[1]};
-#pragma unroll
-  for (int t = 0; t < 2; ++t) {
-    double v = acc[t];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    acc[t] = v;
-  }
-  if (lane == 0) {
-    red[iy][0] = acc[0];
-    red[iy][1] = acc[1];
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s0 = 0.0, s1 = 0.0;
-    for (int w = 0; w < kTileThreads / 32; ++w) {
-      s0 += red[w][0];
-      s1 += red[w][1];
-    }
-    partials[(size_t)blockIdx.x * kMaxTerms + 0] = s0;
-    partials[(size_t)blockIdx.x * kMaxTerms + 1] = s1;
-  }
+  block_reduce_acc(ca, partials);
 }
 
 // Extra term of Algorithm 2's tau right-hand side: + mu3 (f + Lambda_3/mu3) with

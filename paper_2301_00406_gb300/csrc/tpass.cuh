@@ -111,10 +111,24 @@ __device__ __forceinline__ void stage16(float4* dst, const float4* __restrict__ 
   batched_copy<8, float4>(
       n, tid, nthr, [&](int i) { return __ldg(src + i); }, [&](int i, float4 v) { dst[i] = v; });
 }
-// The 2 nt twiddles of the padded transform (nt 16-byte words).
+// The 2 nt roots exp(-2 pi i j / 2nt) in shared memory, one pad slot after
+// every 16: root j at j + j / 16.  The FFT steps read roots at strided
+// indices (multiples of 2, 16, 32 ... with lanes over transforms and
+// sub-sequences); unpadded, those fall into a few float2 bank slots (up to
+// 8-way conflicts), padded they spread over all 16.
+struct Tw2 {
+  const float2* t;
+  __device__ __forceinline__ float2 operator[](int j) const { return t[j + (j >> 4)]; }
+};
 template <int NT>
-__device__ __forceinline__ void stage_twiddles(float2* tw2, const float2* __restrict__ g, int tid, int nthr) {
-  stage16(reinterpret_cast<float4*>(tw2), reinterpret_cast<const float4*>(g), NT, tid, nthr);
+__host__ __device__ constexpr int tw2_slots() {
+  return 2 * NT + (2 * NT) / 16;  // a multiple of 2 float2: the next region stays 16-byte aligned
+}
+template <int NT>
+__device__ __forceinline__ Tw2 stage_twiddles(float2* tw2, const float2* __restrict__ g, int tid, int nthr) {
+  batched_copy<8, float2>(
+      2 * NT, tid, nthr, [&](int j) { return __ldg(g + j); }, [&](int j, float2 v) { tw2[j + (j >> 4)] = v; });
+  return Tw2{tw2};
 }
 template <int NT>
 __device__ __forceinline__ void stage_fwd_taps(float4* tab, const float4* __restrict__ g, int tid, int nthr) {
@@ -144,31 +158,6 @@ __device__ __forceinline__ float2 csr_row2(const float4* tab, int n, const float
 }
 
 
-// Block-wide FP64 reduction of NTERMS values; thread 0 writes partials[blockIdx.x * kMaxTerms + t].
-template <int NTERMS>
-__device__ __forceinline__ void block_reduce_store(double (&v)[NTERMS], double* partials) {
-  __shared__ double red[32][NTERMS];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int t = 0; t < NTERMS; ++t) {
-    double x = v[t];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    v[t] = x;
-  }
-  if (lane == 0)
-#pragma unroll
-    for (int t = 0; t < NTERMS; ++t) red[warp][t] = v[t];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
-    for (int t = 0; t < NTERMS; ++t) {
-      double s = 0.0;
-      for (int w = 0; w < nw; ++w) s += red[w][t];
-      partials[(size_t)blockIdx.x * kMaxTerms + t] = s;
-    }
-  }
-}
 
 // The two columns (ca, ca + 1) of a pair from spectrum row `row`: one
 // 16-byte load when both exist and the pair is 16-byte aligned (even pitch
@@ -248,7 +237,7 @@ __device__ __forceinline__ void tinv_load(const float2* __restrict__ S, int pitc
 // other.
 template <int NT>
 __device__ __forceinline__ void tinv_core(const float2* __restrict__ S, int pitch, int col0, int ncols,
-                                          float2* work, float* cbuf, const float2* tw2, int PAIRS, bool hb, int tid,
+                                          float2* work, float* cbuf, const Tw2& tw2, int PAIRS, bool hb, int tid,
                                           int nthr) {
   const float scale = 1.0f / (2.0f * NT);
   if (hb) {
@@ -297,7 +286,7 @@ __device__ __forceinline__ void tinv_core(const float2* __restrict__ S, int pitc
 // the padded transform, stored to S.  Starts and ends with every thread past
 // a barrier.
 template <int NT, int MODE>
-__device__ __forceinline__ void tfwd_from_cbuf(const float* cbuf, const float4* tab, float2* work, const float2* tw2,
+__device__ __forceinline__ void tfwd_from_cbuf(const float* cbuf, const float4* tab, float2* work, const Tw2& tw2,
                                                int COLS, int hb, float2* __restrict__ S, int pitch, int col0,
                                                int ncols, int tid, int nthr) {
   const int PAIRS = COLS >> 1;
@@ -346,13 +335,13 @@ __global__ void __launch_bounds__(kTpassThreads)
   const int COLS = cols, PAIRS = cols >> 1;
   const int NB = hb ? 2 * PAIRS : PAIRS;
   extern __shared__ float4 smem_f4[];
-  float2* tw2 = reinterpret_cast<float2*>(smem_f4);
-  float4* tab = reinterpret_cast<float4*>(tw2 + 2 * NT);
+  float2* tw2s = reinterpret_cast<float2*>(smem_f4);
+  float4* tab = reinterpret_cast<float4*>(tw2s + tw2_slots<NT>());
   float2* work = reinterpret_cast<float2*>(tab + TabLayout<NT>::SLOTS);
   float* cbuf = reinterpret_cast<float*>(work + ((NB * work_pitch<NT>(NB) + 1) & ~1));
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int col0 = blockIdx.x * COLS;
-  stage_twiddles<NT>(tw2, tw2g, tid, nthr);
+  const Tw2 tw2 = stage_twiddles<NT>(tw2s, tw2g, tid, nthr);
   if (MODE == 0)
     stage_fwd_taps<NT>(tab, ftab, tid, nthr);
   else
@@ -403,13 +392,13 @@ __global__ void __launch_bounds__(kTpassThreads)
   const int COLS = cols, PAIRS = cols >> 1;
   const int NB = hb ? 2 * PAIRS : PAIRS;
   extern __shared__ float4 smem_f4[];
-  float2* tw2 = reinterpret_cast<float2*>(smem_f4);
-  float4* tab = reinterpret_cast<float4*>(tw2 + 2 * NT);
+  float2* tw2s = reinterpret_cast<float2*>(smem_f4);
+  float4* tab = reinterpret_cast<float4*>(tw2s + tw2_slots<NT>());
   float2* work = reinterpret_cast<float2*>(tab + TabLayout<NT>::SLOTS);
   float* cbuf = reinterpret_cast<float*>(work + ((NB * work_pitch<NT>(NB) + 1) & ~1));
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int col0 = blockIdx.x * COLS;
-  stage_twiddles<NT>(tw2, tw2g, tid, nthr);
+  const Tw2 tw2 = stage_twiddles<NT>(tw2s, tw2g, tid, nthr);
   stage_fwd_taps<NT>(tab, ftab, tid, nthr);
   __syncthreads();
   tinv_core<NT>(S, pitch, col0, ncols, work, cbuf, tw2, PAIRS, hb != 0, tid, nthr);
@@ -445,7 +434,7 @@ __global__ void __launch_bounds__(kTpassThreads)
       });
   if (EPI == 1) {
     ca.flush();
-    block_reduce_store<2>(ca.tot, fa.partials);
+    block_reduce_acc(ca, fa.partials);
   }
 }
 
@@ -481,13 +470,13 @@ __global__ void __launch_bounds__(kTpassThreads)
   const int NB = hb ? 2 * PAIRS : PAIRS;
   const WorkAddr<NT> wa{work_pitch<NT>(PAIRS)};  // layout of the periodic forward FFT (MODE 1)
   extern __shared__ float4 smem_f4[];
-  float2* tw2 = reinterpret_cast<float2*>(smem_f4);
-  float4* tab = reinterpret_cast<float4*>(tw2 + 2 * NT);
+  float2* tw2s = reinterpret_cast<float2*>(smem_f4);
+  float4* tab = reinterpret_cast<float4*>(tw2s + tw2_slots<NT>());
   float2* work = reinterpret_cast<float2*>(tab + TabLayout<NT>::SLOTS);
   float* cbuf = reinterpret_cast<float*>(work + ((NB * work_pitch<NT>(NB) + 1) & ~1));
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int col0 = blockIdx.x * COLS;
-  stage_twiddles<NT>(tw2, tw2g, tid, nthr);
+  const Tw2 tw2 = stage_twiddles<NT>(tw2s, tw2g, tid, nthr);
   stage_csr<NT>(tab, tptr, tent, tid, nthr);
   __syncthreads();
   tinv_core<NT>(S, pitch, col0, ncols, work, cbuf, tw2, PAIRS, hb != 0, tid, nthr);
@@ -544,11 +533,11 @@ __global__ void __launch_bounds__(kTpassThreads)
   const int COLS = cols, PAIRS = cols >> 1;
   const WorkAddr<NT> wa{work_pitch<NT>(PAIRS)};
   extern __shared__ float4 smem_f4[];
-  float2* tw2 = reinterpret_cast<float2*>(smem_f4);
-  float2* work = tw2 + 2 * NT;
+  float2* tw2s = reinterpret_cast<float2*>(smem_f4);
+  float2* work = tw2s + tw2_slots<NT>();
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int col0 = blockIdx.x * COLS;
-  stage_twiddles<NT>(tw2, tw2g, tid, nthr);
+  const Tw2 tw2 = stage_twiddles<NT>(tw2s, tw2g, tid, nthr);
   batched_copy<8, float2>(
       PAIRS * NT, tid, nthr,
       [&](int i) {
@@ -571,11 +560,11 @@ __global__ void __launch_bounds__(kTpassThreads)
   const int COLS = cols, PAIRS = cols >> 1;
   const WorkAddr<NT> wa{work_pitch<NT>(PAIRS)};
   extern __shared__ float4 smem_f4[];
-  float2* tw2 = reinterpret_cast<float2*>(smem_f4);
-  float2* work = tw2 + 2 * NT;
+  float2* tw2s = reinterpret_cast<float2*>(smem_f4);
+  float2* work = tw2s + tw2_slots<NT>();
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int col0 = blockIdx.x * COLS;
-  stage_twiddles<NT>(tw2, tw2g, tid, nthr);
+  const Tw2 tw2 = stage_twiddles<NT>(tw2s, tw2g, tid, nthr);
   const int lp = __ffs(PAIRS) - 1;
   batched_copy<8, float2>(
       NT * PAIRS, tid, nthr,
@@ -614,7 +603,7 @@ __global__ void __launch_bounds__(kTpassThreads)
       });
   if (partials) {
     ca.flush();
-    block_reduce_store<1>(ca.tot, partials);
+    block_reduce_acc(ca, partials);
   }
 }
 
@@ -634,13 +623,13 @@ __global__ void __launch_bounds__(kTpassThreads)
   const int NB = hb ? 2 * PAIRS : PAIRS;
   const WorkAddr<NT> wa{work_pitch<NT>(PAIRS)};  // layout of the periodic inverse FFT
   extern __shared__ float4 smem_f4[];
-  float2* tw2 = reinterpret_cast<float2*>(smem_f4);
-  float4* tab = reinterpret_cast<float4*>(tw2 + 2 * NT);
+  float2* tw2s = reinterpret_cast<float2*>(smem_f4);
+  float4* tab = reinterpret_cast<float4*>(tw2s + tw2_slots<NT>());
   float2* work = reinterpret_cast<float2*>(tab + TabLayout<NT>::SLOTS);
   float* cbuf = reinterpret_cast<float*>(work + ((NB * work_pitch<NT>(NB) + 1) & ~1));
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int col0 = blockIdx.x * COLS;
-  stage_twiddles<NT>(tw2, tw2g, tid, nthr);
+  const Tw2 tw2 = stage_twiddles<NT>(tw2s, tw2g, tid, nthr);
   stage_fwd_taps<NT>(tab, ftab, tid, nthr);
   const int lp = __ffs(PAIRS) - 1;
   batched_copy<8, float2>(
@@ -682,7 +671,7 @@ __global__ void __launch_bounds__(kTpassThreads)
   for (int i = total + tid; i < COLS * NT; i += nthr) cbuf[i] = 0.f;  // columns past the last
   if (partials) {
     ca.flush();
-    block_reduce_store<1>(ca.tot, partials);
+    block_reduce_acc(ca, partials);
   }
   __syncthreads();
   tfwd_from_cbuf<NT, 0>(cbuf, tab, work, tw2, COLS, hb, S, pitch, col0, ncols, tid, nthr);
@@ -711,7 +700,7 @@ struct TpShape {
 template <int NT>
 static size_t tp_smem(int cols, int hb, int extra, bool tab) {
   const int nb = hb ? cols : cols / 2;
-  return sizeof(float2) * (2 * NT + ((nb * work_pitch<NT>(nb) + 1) & ~1)) +
+  return sizeof(float2) * (tw2_slots<NT>() + ((nb * work_pitch<NT>(nb) + 1) & ~1)) +
          (tab ? sizeof(float4) * TabLayout<NT>::SLOTS : 0) + sizeof(float) * extra * cols * NT;
 }
 
