@@ -339,7 +339,8 @@ __global__ void __launch_bounds__(kTpassThreads)
   float4* tab = reinterpret_cast<float4*>(tw2s + tw2_slots<NT>());
   float2* work = reinterpret_cast<float2*>(tab + TabLayout<NT>::SLOTS);
   float* cbuf = reinterpret_cast<float*>(work + ((NB * work_pitch<NT>(NB) + 1) & ~1));
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int tid = threadIdx.x;
+  constexpr int nthr = kTpassThreads;  // every launch: strides fold at compile time
   const int col0 = blockIdx.x * COLS;
   const Tw2 tw2 = stage_twiddles<NT>(tw2s, tw2g, tid, nthr);
   if (MODE == 0)
@@ -396,7 +397,8 @@ __global__ void __launch_bounds__(kTpassThreads)
   float4* tab = reinterpret_cast<float4*>(tw2s + tw2_slots<NT>());
   float2* work = reinterpret_cast<float2*>(tab + TabLayout<NT>::SLOTS);
   float* cbuf = reinterpret_cast<float*>(work + ((NB * work_pitch<NT>(NB) + 1) & ~1));
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int tid = threadIdx.x;
+  constexpr int nthr = kTpassThreads;  // every launch: strides fold at compile time
   const int col0 = blockIdx.x * COLS;
   const Tw2 tw2 = stage_twiddles<NT>(tw2s, tw2g, tid, nthr);
   stage_fwd_taps<NT>(tab, ftab, tid, nthr);
@@ -474,7 +476,8 @@ __global__ void __launch_bounds__(kTpassThreads)
   float4* tab = reinterpret_cast<float4*>(tw2s + tw2_slots<NT>());
   float2* work = reinterpret_cast<float2*>(tab + TabLayout<NT>::SLOTS);
   float* cbuf = reinterpret_cast<float*>(work + ((NB * work_pitch<NT>(NB) + 1) & ~1));
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int tid = threadIdx.x;
+  constexpr int nthr = kTpassThreads;  // every launch: strides fold at compile time
   const int col0 = blockIdx.x * COLS;
   const Tw2 tw2 = stage_twiddles<NT>(tw2s, tw2g, tid, nthr);
   stage_csr<NT>(tab, tptr, tent, tid, nthr);
@@ -535,7 +538,8 @@ __global__ void __launch_bounds__(kTpassThreads)
   extern __shared__ float4 smem_f4[];
   float2* tw2s = reinterpret_cast<float2*>(smem_f4);
   float2* work = tw2s + tw2_slots<NT>();
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int tid = threadIdx.x;
+  constexpr int nthr = kTpassThreads;  // every launch: strides fold at compile time
   const int col0 = blockIdx.x * COLS;
   const Tw2 tw2 = stage_twiddles<NT>(tw2s, tw2g, tid, nthr);
   batched_copy<8, float2>(
@@ -562,7 +566,8 @@ __global__ void __launch_bounds__(kTpassThreads)
   extern __shared__ float4 smem_f4[];
   float2* tw2s = reinterpret_cast<float2*>(smem_f4);
   float2* work = tw2s + tw2_slots<NT>();
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int tid = threadIdx.x;
+  constexpr int nthr = kTpassThreads;  // every launch: strides fold at compile time
   const int col0 = blockIdx.x * COLS;
   const Tw2 tw2 = stage_twiddles<NT>(tw2s, tw2g, tid, nthr);
   const int lp = __ffs(PAIRS) - 1;
@@ -627,7 +632,8 @@ __global__ void __launch_bounds__(kTpassThreads)
   float4* tab = reinterpret_cast<float4*>(tw2s + tw2_slots<NT>());
   float2* work = reinterpret_cast<float2*>(tab + TabLayout<NT>::SLOTS);
   float* cbuf = reinterpret_cast<float*>(work + ((NB * work_pitch<NT>(NB) + 1) & ~1));
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int tid = threadIdx.x;
+  constexpr int nthr = kTpassThreads;  // every launch: strides fold at compile time
   const int col0 = blockIdx.x * COLS;
   const Tw2 tw2 = stage_twiddles<NT>(tw2s, tw2g, tid, nthr);
   stage_fwd_taps<NT>(tab, ftab, tid, nthr);
@@ -720,8 +726,7 @@ static TpShape tp_shape(int ncols, int extra, bool tab, int kind, bool halves) {
     sh.hb = 0;
     while (sh.cols > 2 && div_up(ncols, sh.cols) < 2 * 152) sh.cols >>= 1;
   }
-  const int work_cols = sh.hb ? 2 * sh.cols : sh.cols;  // FFT tasks scale with the transforms per CTA
-  sh.threads = work_cols >= 8 ? kTpassThreads : work_cols == 4 ? 128 : 64;
+  sh.threads = kTpassThreads;  // the kernels' loops assume this count
   sh.blocks = div_up(ncols, sh.cols);
   sh.smem = tp_smem<NT>(sh.cols, sh.hb, extra, tab);
   return sh;
