@@ -92,7 +92,18 @@ struct WorkAddr {
   __device__ __forceinline__ int operator()(int p, int er, int ec) const {
     return p * pitch + (work_swz<NT>(er) ^ work_swz<NT>(ec));
   }
+  // Element n of transform p in a loop whose index advances by the thread
+  // count (256): n's low eight bits stay those of the thread, whose part of
+  // the swizzle (slo = swz_lo(tid)) is computed once; only n's higher bits
+  // are swizzled per element.
+  __device__ __forceinline__ int at(int p, int n, int slo) const {
+    return p * pitch + (slo ^ work_swz<NT>(n & ~255));
+  }
 };
+template <int NT>
+__device__ __forceinline__ int swz_lo(int tid) {
+  return work_swz<NT>(tid & ((NT < 256 ? NT : 256) - 1));
+}
 constexpr int kTpassThreads = 256;
 
 // Shared-memory table region (float4 slots): forward taps use nt slots; a CSR
@@ -246,10 +257,11 @@ __device__ __forceinline__ void tinv_core(const float2* __restrict__ S, int pitc
     tinv_load<NT>(S, pitch, col0, ncols, 1, work, wa, PAIRS, PAIRS, tid, nthr);
     __syncthreads();
     team_fft_a<NT, true>(work, 2 * PAIRS, wa, tw2, 2, tid, nthr);
+    const int slo = swz_lo<NT>(tid);
     for (int i = tid; i < PAIRS * NT; i += nthr) {
       const int p = i / NT, n = i % NT;
-      const float2 z0 = work[wa(p, n)];
-      const float2 z1 = cmulc(work[wa(PAIRS + p, n)], tw2[n]);
+      const float2 z0 = work[wa.at(p, n, slo)];
+      const float2 z1 = cmulc(work[wa.at(PAIRS + p, n, slo)], tw2[n]);
       float* ca = cbuf + (2 * p) * NT;
       ca[n] = (z0.x + z1.x) * scale;
       ca[n + NT] = (z0.y + z1.y) * scale;
@@ -262,9 +274,10 @@ __device__ __forceinline__ void tinv_core(const float2* __restrict__ S, int pitc
     tinv_load<NT>(S, pitch, col0, ncols, half, work, wa, 0, PAIRS, tid, nthr);
     __syncthreads();
     team_fft_a<NT, true>(work, PAIRS, wa, tw2, 2, tid, nthr);
+    const int slo = swz_lo<NT>(tid);
     for (int i = tid; i < PAIRS * NT; i += nthr) {
       const int p = i / NT, n = i % NT;
-      float2 z = work[wa(p, n)];
+      float2 z = work[wa.at(p, n, slo)];
       if (half) z = cmulc(z, tw2[n]);
       float* ca = cbuf + (2 * p) * NT;
       float* cb = ca + NT;
@@ -294,6 +307,7 @@ __device__ __forceinline__ void tfwd_from_cbuf(const float* cbuf, const float4* 
   const WorkAddr<NT> wa{work_pitch<NT>(NB)};
   // the even output bins (half 0) are the length-nt DFT of z, the odd ones
   // (half 1) that of z w^n
+  const int slo = swz_lo<NT>(tid);
   for (int h0 = 0; h0 < 2; h0 += hb ? 2 : 1) {
     for (int i = tid; i < PAIRS * NT; i += nthr) {
       const int p = i / NT, n = i % NT;
@@ -310,10 +324,10 @@ __device__ __forceinline__ void tfwd_from_cbuf(const float* cbuf, const float4* 
         z = csr_row2<NT>(tab, n, ca, cb);
       }
       if (hb) {
-        work[wa(p, n)] = z;
-        work[wa(PAIRS + p, n)] = cmul(z, tw2[n]);
+        work[wa.at(p, n, slo)] = z;
+        work[wa.at(PAIRS + p, n, slo)] = cmul(z, tw2[n]);
       } else {
-        work[wa(p, n)] = h0 ? cmul(z, tw2[n]) : z;
+        work[wa.at(p, n, slo)] = h0 ? cmul(z, tw2[n]) : z;
       }
     }
     __syncthreads();
@@ -498,6 +512,7 @@ __global__ void __launch_bounds__(kTpassThreads)
   }
   const float L = sr.sc ? (float)sr.sc->L : (float)sr.c0_host;
   // ld: u-bar and reg of both columns of the pair; st: rhs = L u-bar - g + reg
+  const int slo = swz_lo<NT>(tid);
   batched_copy<8, float4>(
       PAIRS * NT, tid, nthr,
       [&](int i) {
@@ -522,7 +537,7 @@ __global__ void __launch_bounds__(kTpassThreads)
         const float2 gv = csr_row2<NT>(tab, n, cbuf + (2 * p) * NT, cbuf + (2 * p + 1) * NT);
         const float a = ca < ncols ? L * v.x - gv.x + v.y : 0.f;
         const float b = cb < ncols ? L * v.z - gv.y + v.w : 0.f;
-        work[wa(p, n)] = make_float2(a, b);
+        work[wa.at(p, n, slo)] = make_float2(a, b);
       });
   __syncthreads();
   team_fft_a<NT, false>(work, PAIRS, wa, tw2, 2, tid, nthr);
@@ -542,6 +557,7 @@ __global__ void __launch_bounds__(kTpassThreads)
   constexpr int nthr = kTpassThreads;  // every launch: strides fold at compile time
   const int col0 = blockIdx.x * COLS;
   const Tw2 tw2 = stage_twiddles<NT>(tw2s, tw2g, tid, nthr);
+  const int slo = swz_lo<NT>(tid);
   batched_copy<8, float2>(
       PAIRS * NT, tid, nthr,
       [&](int i) {
@@ -550,7 +566,7 @@ __global__ void __launch_bounds__(kTpassThreads)
         return make_float2(ca < ncols ? __ldg(x + (size_t)ca * NT + n) : 0.f,
                            cb < ncols ? __ldg(x + (size_t)cb * NT + n) : 0.f);
       },
-      [&](int i, float2 z) { work[wa(i / NT, i % NT)] = z; });
+      [&](int i, float2 z) { work[wa.at(i / NT, i % NT, slo)] = z; });
   __syncthreads();
   team_fft_a<NT, false>(work, PAIRS, wa, tw2, 2, tid, nthr);
   periodic_fwd_post<NT>(work, Sp, col0, ncols, ncols, COLS, tid, nthr);
@@ -591,13 +607,14 @@ __global__ void __launch_bounds__(kTpassThreads)
   __syncthreads();
   team_fft_a<NT, true>(work, PAIRS, wa, tw2, 2, tid, nthr);
   const float scale = 1.0f / NT;
+  const int slo = swz_lo<NT>(tid);
   ChunkAcc<1> ca;
   const int total = min(COLS, ncols - col0) * NT;
   batched_copy<8, float>(
       total, tid, nthr, [&](int i) { return ref ? __ldg(ref + (size_t)col0 * NT + i) : 0.f; },
       [&](int i, float rv) {
         const int c = i / NT, n = i % NT;
-        const float2 z = work[wa(c >> 1, n)];
+        const float2 z = work[wa.at(c >> 1, n, slo)];
         const float v = ((c & 1) ? z.y : z.x) * scale;
         x[(size_t)col0 * NT + i] = v;
         if (ref) {
@@ -658,13 +675,14 @@ __global__ void __launch_bounds__(kTpassThreads)
   __syncthreads();
   team_fft_a<NT, true>(work, PAIRS, wa, tw2, 2, tid, nthr);
   const float scale = 1.0f / NT;
+  const int slo = swz_lo<NT>(tid);
   ChunkAcc<1> ca;
   const int total = min(COLS, ncols - col0) * NT;
   batched_copy<8, float>(
       total, tid, nthr, [&](int i) { return ref ? __ldg(ref + (size_t)col0 * NT + i) : 0.f; },
       [&](int i, float rv) {
         const int c = i / NT, n = i % NT;
-        const float2 z = work[wa(c >> 1, n)];
+        const float2 z = work[wa.at(c >> 1, n, slo)];
         const float v = ((c & 1) ? z.y : z.x) * scale;
         x[(size_t)col0 * NT + i] = v;
         cbuf[i] = v;
