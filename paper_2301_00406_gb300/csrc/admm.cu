@@ -996,8 +996,8 @@ static nlos_status step_alg1(JobRun& j) {
   const float eps2 = (float)(p.eps_normal * p.eps_normal);
   // pipelined halo-tiled stencils when the grid tiles evenly (TT = 128 along
   // t, 8 rows in y, 4 planes in x); the plain per-voxel kernels otherwise
-  const bool tiled = P.nt % kTT == 0 && P.ny % kTY == 0 && P.nx % kPipeXB == 0;
-  const int ntiles = (P.nt / kTT) * (P.ny / kTY) * (P.nx / kPipeXB);
+  const bool tiled = P.nt % kTT == 0 && P.ny % kTY == 0;
+  const int ntiles = tiled ? stencil_steps(g) : 0;  // (tile, x plane) steps
   const int pre_grid = std::min(ntiles, 152 * 3), post_grid = std::min(ntiles, 152 * 2);
   const int post_blocks = tiled ? post_grid : kStencilBlocks;
   { KTimer kt_(P, KC_PRE, st);
@@ -1046,8 +1046,8 @@ static nlos_status step_alg2(JobRun& j) {
   const int32_t* colpos = P.full_mask ? nullptr : P.d_colpos;
   Alg2Coef c{(float)p.mu1, (float)p.mu2, (float)p.mu3, (float)p.lambda, (float)p.a_u, (float)p.b_u,
              (float)p.a_tau, (float)p.b_tau, p.phi, (float)(p.eps_normal * p.eps_normal)};
-  const bool tiled = P.nt % kTT == 0 && P.ny % kTY == 0 && P.nx % kPipeXB == 0;
-  const int ntiles = (P.nt / kTT) * (P.ny / kTY) * (P.nx / kPipeXB);
+  const bool tiled = P.nt % kTT == 0 && P.ny % kTY == 0;
+  const int ntiles = tiled ? stencil_steps(g) : 0;  // (tile, x plane) steps
   const int pre_grid = std::min(ntiles, 152 * 3), post_grid = std::min(ntiles, 152 * 2);
   { KTimer kt_(P, KC_PRE, st);
   if (tiled) {

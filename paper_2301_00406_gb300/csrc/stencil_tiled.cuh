@@ -3,8 +3,11 @@
 // twice per iteration by Algorithm 2 (u and tau).
 //
 // A block owns a TY x TT tile of the (y, t) plane (TT = 128 time bins along
-// the contiguous axis, TY = 8 rows) and marches through XB consecutive x
-// planes; a persistent grid walks the (t, y, x-chunk) tiles.  Per x plane it
+// the contiguous axis, TY = 8 rows) and marches through consecutive x planes.
+// The (tile, x plane) steps, x fastest, are split into one contiguous run per
+// block of a persistent grid, so a block pays the pipeline's prologue (the
+// first two planes in flight, the x - 1 values from global memory) only where
+// its run starts or enters the next tile, not every few planes.  Per x plane it
 // stages the fields that are read at neighbours (with their +-1 halos,
 // periodic wrap) in shared memory, evaluates the per-point quantity whose
 // backward differences are needed (the normal field n, or q = v + Lambda/mu)
@@ -32,7 +35,6 @@ constexpr int kUH = kTY + 2;                 // rows of a field staged with -1/+
 constexpr int kRW = kTT + 1, kRH = kTY + 1;  // region of per-point quantities: (TY+1) x (TT+1)
 constexpr int kP = kTT + 8;                  // staged row pitch (floats)
 constexpr int kC = 4;                        // column of t0 in a staged row (t0 - 1 at kC - 1)
-constexpr int kPipeXB = 4;                   // x planes per tile
 static_assert(kP % 4 == 0 && kC % 4 == 0, "staged rows must keep the interior 16-byte aligned");
 
 __device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
@@ -80,16 +82,27 @@ __device__ __forceinline__ void stage_interior_async(float* __restrict__ tile, c
   }
 }
 
-struct TileIdx {
-  int t0, y0, x0;
+// Number of (tile, x plane) steps of a grid.
+inline int stencil_steps(const Vox& g) { return (g.nt / kTT) * (g.ny / kTY) * g.nx; }
+
+// The next run of this block's share [cur, end) of the steps: tile (t0, y0),
+// first plane x0, cnt planes (within one tile).
+struct TileRun {
+  int t0, y0, x0, cnt;
 };
-__device__ __forceinline__ TileIdx tile_of(int tile, const Vox& g) {
-  const int ntt = g.nt / kTT, nty = g.ny / kTY;
-  TileIdx r;
+__device__ __forceinline__ TileRun run_at(int cur, int end, const Vox& g) {
+  const int ntt = g.nt / kTT;
+  const int tile = cur / g.nx, x0 = cur - tile * g.nx;
+  TileRun r;
   r.t0 = (tile % ntt) * kTT;
-  r.y0 = ((tile / ntt) % nty) * kTY;
-  r.x0 = (tile / (ntt * nty)) * kPipeXB;
+  r.y0 = (tile / ntt) * kTY;
+  r.x0 = x0;
+  r.cnt = min(end - cur, g.nx - x0);
   return r;
+}
+__device__ __forceinline__ void block_share(int nsteps, int& cur, int& end) {
+  cur = (int)((long long)nsteps * blockIdx.x / gridDim.x);
+  end = (int)((long long)nsteps * (blockIdx.x + 1) / gridDim.x);
 }
 
 // Shared layout of k_post1_pipe (floats; every region a multiple of 4):
@@ -107,7 +120,7 @@ constexpr size_t kPost1PipeSmem = sizeof(float) * (kPostU + kPostB + kPostI + 3 
 __global__ void __launch_bounds__(kTileThreads, 2)
     k_post1_pipe(const float* __restrict__ unew, const float* __restrict__ uk, const float* __restrict__ ub,
                  float* __restrict__ lam, float* __restrict__ ph, float* __restrict__ ubn,
-                 const DevScalars* __restrict__ sc, Vox g, int ntiles, float mu, float a, float b, int kind,
+                 const DevScalars* __restrict__ sc, Vox g, int nsteps, float mu, float a, float b, int kind,
                  float eps2, size_t V, double* __restrict__ partials) {
   extern __shared__ float4 smem_f4[];
   float* U = reinterpret_cast<float*>(smem_f4);
@@ -119,8 +132,11 @@ __global__ void __launch_bounds__(kTileThreads, 2)
   const float beta = (float)sc->beta;
   const float* ifields[5] = {lam, lam + V, lam + 2 * V, ph, uk};
   ChunkAcc<2> ca;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const TileIdx T = tile_of(tile, g);
+  int cur, end;
+  block_share(nsteps, cur, end);
+  while (cur < end) {
+    const TileRun T = run_at(cur, end, g);
+    cur += T.cnt;
     const int y = T.y0 + iy;
     float nx_prev[4];
     for (int j = 0; j < 4; ++j) {
@@ -135,14 +151,15 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     stage_rows_async<false, true>(B + kRH * kP, kRH, ub, g, (T.x0 + 1) & g.mx, T.y0, 0, T.t0);
     for (int f = 0; f < 5; ++f) stage_interior_async(I + f * kTY * kTT, ifields[f], g, T.x0, T.y0, T.t0);
     cp_async_commit();
-    for (int s = 0; s < kPipeXB; ++s) {
+    for (int s = 0; s < T.cnt; ++s) {
       const int x = T.x0 + s;
       // prefetch planes x + 2 and the interiors of x + 1
-      if (s + 1 < kPipeXB) {
+      if (s + 1 < T.cnt) {
         stage_rows_async<true, true>(U + ((s + 2) % 3) * kUH * kP, kUH, unew, g, (x + 2) & g.mx, T.y0, -1, T.t0);
         stage_rows_async<false, true>(B + ((s + 2) % 3) * kRH * kP, kRH, ub, g, (x + 2) & g.mx, T.y0, 0, T.t0);
         for (int f = 0; f < 5; ++f)
-          stage_interior_async(I + (((s + 1) & 1) * 5 + f) * kTY * kTT, ifields[f], g, x + 1, T.y0, T.t0);
+          stage_interior_async(I + (((s + 1) & 1) * 5 + f) * kTY * kTT, ifields[f], g, (x + 1) & g.mx, T.y0,
+                               T.t0);
       }
       cp_async_commit();
       cp_async_wait_all_but_one();
@@ -222,7 +239,7 @@ constexpr size_t kPre1PipeSmem = sizeof(float) * (kPreU + kPreL + 3 * kRH * kRW)
 template <bool FTERM>
 __global__ void __launch_bounds__(kTileThreads, 3)
     k_pre1_pipe(const float* __restrict__ ub, const float* __restrict__ lam, const float* __restrict__ ph,
-                float* __restrict__ reg, Vox g, int ntiles, float mu, size_t V, FTerm ft) {
+                float* __restrict__ reg, Vox g, int nsteps, float mu, size_t V, FTerm ft) {
   extern __shared__ float4 smem_f4[];
   float* U = reinterpret_cast<float*>(smem_f4);
   float* L = U + kPreU;
@@ -231,8 +248,11 @@ __global__ void __launch_bounds__(kTileThreads, 3)
   const float inv_mu = 1.0f / mu;
   const float* lfields[4] = {lam, lam + V, lam + 2 * V, ph};
   const float inv_d1 = 1.0f / (ft.lam_w + ft.mu3), inv_d0 = 1.0f / ft.mu3;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const TileIdx T = tile_of(tile, g);
+  int cur, end;
+  block_share(nsteps, cur, end);
+  while (cur < end) {
+    const TileRun T = run_at(cur, end, g);
+    cur += T.cnt;
     const int y = T.y0 + iy;
     float qx_prev[4];
     {
@@ -248,13 +268,13 @@ __global__ void __launch_bounds__(kTileThreads, 3)
     for (int f = 0; f < 4; ++f)
       stage_rows_async<true, false>(L + f * kRH * kP, kRH, lfields[f], g, T.x0, T.y0, -1, T.t0);
     cp_async_commit();
-    for (int s = 0; s < kPipeXB; ++s) {
+    for (int s = 0; s < T.cnt; ++s) {
       const int x = T.x0 + s;
-      if (s + 1 < kPipeXB) {
+      if (s + 1 < T.cnt) {
         stage_rows_async<true, true>(U + ((s + 2) % 3) * kUH * kP, kUH, ub, g, (x + 2) & g.mx, T.y0, -1, T.t0);
         for (int f = 0; f < 4; ++f)
-          stage_rows_async<true, false>(L + (((s + 1) & 1) * 4 + f) * kRH * kP, kRH, lfields[f], g, x + 1, T.y0,
-                                        -1, T.t0);
+          stage_rows_async<true, false>(L + (((s + 1) & 1) * 4 + f) * kRH * kP, kRH, lfields[f], g,
+                                        (x + 1) & g.mx, T.y0, -1, T.t0);
       }
       cp_async_commit();
       cp_async_wait_all_but_one();
