@@ -185,32 +185,44 @@ __device__ __forceinline__ void load_pair(const float2* __restrict__ row, int ca
   }
 }
 
+// Hermitian split of a packed pair transform at one bin (za at k, zb at the
+// mirrored bin) into the bins of its two columns ca, ca + 1 of a spectrum row:
+// one 16-byte store when both exist and the row is 16-byte aligned.
+__device__ __forceinline__ void store_pair(float2* __restrict__ row, int ca, int ncols, bool even_pitch, float2 za,
+                                           float2 zb) {
+  const float2 xa = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
+  const float2 xb = make_float2(0.5f * (za.y + zb.y), -0.5f * (za.x - zb.x));
+  if (even_pitch && ca + 1 < ncols) {
+    *reinterpret_cast<float4*>(row + ca) = make_float4(xa.x, xa.y, xb.x, xb.y);
+  } else {
+    if (ca < ncols) row[ca] = xa;
+    if (ca + 1 < ncols) row[ca + 1] = xb;
+  }
+}
+
 // Post-processing of the padded forward t-FFT of packed pairs: writes bins
 // kt = 2 k' + half of both columns of every pair to S, for the halves
 // [h0, h0 + nh); the transform of pair p and half h is h * PAIRS + p when both
-// halves are in `work` (nh = 2), else p.
+// halves are in `work` (nh = 2), else p.  One item per (bin, pair).
 template <int NT>
 __device__ __forceinline__ void tfwd_post_store(const float2* work, const WorkAddr<NT>& wa, int h0, int nh,
                                                 float2* S, int pitch, int col0, int ncols, int COLS, int tid,
                                                 int nthr) {
-  const int lc = __ffs(COLS) - 1;  // COLS is a power of two
-  const int n0 = (NT / 2 + 1 - h0) * COLS;  // items of the first half
-  const int total = nh == 2 ? (NT + 1) * COLS : n0;
+  const int PAIRS = COLS >> 1, lp = __ffs(PAIRS) - 1;  // PAIRS is a power of two
+  const int n0 = (NT / 2 + 1 - h0) * PAIRS;              // items of the first half
+  const int total = nh == 2 ? (NT + 1) * PAIRS : n0;
+  const bool even_pitch = (pitch & 1) == 0;
   for (int i = tid; i < total; i += nthr) {
     const int half = i < n0 ? h0 : 1;
     const int j = i < n0 ? i : i - n0;
-    const int kp = j >> lc, c = j & (COLS - 1), p = c >> 1;
-    if (col0 + c >= ncols) continue;
-    const int q = nh == 2 ? half * (COLS >> 1) + p : p;
+    const int kp = j >> lp, p = j & (PAIRS - 1);
+    const int ca = col0 + 2 * p;
+    if (ca >= ncols) continue;
+    const int q = nh == 2 ? half * PAIRS + p : p;
     const int m = half ? (NT - 1 - kp) : ((NT - kp) & (NT - 1));
     const float2 za = work[wa(q, fpos<NT>(kp))];
     const float2 zb = work[wa(q, fpos<NT>(m))];
-    float2 x;
-    if ((c & 1) == 0)
-      x = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
-    else
-      x = make_float2(0.5f * (za.y + zb.y), -0.5f * (za.x - zb.x));
-    S[(size_t)(2 * kp + half) * pitch + col0 + c] = x;
+    store_pair(S + (size_t)(2 * kp + half) * pitch, ca, ncols, even_pitch, za, zb);
   }
 }
 
@@ -461,19 +473,17 @@ __global__ void __launch_bounds__(kTpassThreads)
 template <int NT>
 __device__ __forceinline__ void periodic_fwd_post(const float2* work, float2* Sp, int col0, int ncols, int pitch,
                                                   int COLS, int tid, int nthr) {
-  const WorkAddr<NT> wa{work_pitch<NT>(COLS >> 1)};
-  const int lc = __ffs(COLS) - 1;  // COLS is a power of two
-  for (int i = tid; i < (NT / 2 + 1) * COLS; i += nthr) {
-    const int k = i >> lc, c = i & (COLS - 1), p = c >> 1;
-    if (col0 + c >= ncols) continue;
+  const int PAIRS = COLS >> 1;
+  const WorkAddr<NT> wa{work_pitch<NT>(PAIRS)};
+  const int lp = __ffs(PAIRS) - 1;  // PAIRS is a power of two
+  const bool even_pitch = (pitch & 1) == 0;
+  for (int i = tid; i < (NT / 2 + 1) * PAIRS; i += nthr) {
+    const int k = i >> lp, p = i & (PAIRS - 1);
+    const int ca = col0 + 2 * p;
+    if (ca >= ncols) continue;
     const float2 za = work[wa(p, fpos<NT>(k))];
     const float2 zb = work[wa(p, fpos<NT>((NT - k) & (NT - 1)))];
-    float2 x;
-    if ((c & 1) == 0)
-      x = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
-    else
-      x = make_float2(0.5f * (za.y + zb.y), -0.5f * (za.x - zb.x));
-    Sp[(size_t)k * pitch + col0 + c] = x;
+    store_pair(Sp + (size_t)k * pitch, ca, ncols, even_pitch, za, zb);
   }
 }
 
