@@ -93,7 +93,7 @@ def test_gpu_adjoint_identity(nlos, n, nt):
 
 
 @pytest.mark.parametrize("n,nt,c0,c1", [(8, 16, 1.0, 0.1), (32, 256, 93.4, 0.1), (64, 512, 3.0, 800.0),
-                                        (16, 1024, 2.0, 1.0)])
+                                        (16, 1024, 2.0, 1.0), (128, 64, 5.0, 3.0)])
 def test_solve_parity(nlos, n, nt, c0, c1):
     plan = nlos.Plan(n, n, nt, 16e-12)
     rhs = np.random.default_rng(5).standard_normal((n, n, nt))
