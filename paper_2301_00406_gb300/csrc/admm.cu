@@ -309,11 +309,6 @@ __global__ void __launch_bounds__(kStencilThreads)
   block_reduce_acc(ca, partials);
 }
 
-// rhs of the tau-solve: x = A u+ + regt (used as the input of the periodic FFT)
-__global__ void k_add(const float* __restrict__ a, const float* __restrict__ b, float* __restrict__ o, size_t n) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    o[i] = __ldg(a + i) + __ldg(b + i);
-}
 
 // ---------------------------------------------------------------------------
 // Scalar kernels (one thread)
@@ -1069,11 +1064,8 @@ static nlos_status step_alg2(JobRun& j) {
   UStepArgs ua{s->reg, p.mu1, false, s->tb, p.eta, p.max_backtracks, s->cache[j.nxt], s->cache[j.cur],
                s->cache[j.prev]};
   NLOS_TRY(u_step(P, s, ua, host_check, &j.L_host, j.bt_stream, st));
-  { KTimer kt_(P, KC_SMALL, st);
-  k_add<<<elem_grid(V), 256, 0, st>>>(s->cache[j.nxt], s->regt, s->tmp, V);
-  }
-  NLOS_LAUNCH_CHECK("k_add");
-  NLOS_TRY(launch_sfwd(P, s->tmp, full, P.d_Sp, st));
+  // rhs of the tau solve: A u+ + regt, summed as the periodic t-FFT loads it
+  NLOS_TRY(launch_sfwd(P, s->cache[j.nxt], full, P.d_Sp, st, s->regt));
   NLOS_TRY(launch_sxy(P, P.d_Sp, nullptr, 1.0 + p.mu3, p.mu2, st));
   NLOS_TRY(launch_sinv(P, P.d_Sp, full, s->tnew, nullptr, nullptr, nullptr, st));
   if (tiled) {

@@ -54,8 +54,8 @@ nlos_status launch_tadj_solve(const Plan& P, const float2* S, int pitch, int nco
                               cudaStream_t st) {
   NLOS_DISPATCH_NT(P.nt, tadj_solve(P, S, pitch, ncols, sr, Sp, st));
 }
-nlos_status launch_sfwd(const Plan& P, const float* x, int ncols, float2* Sp, cudaStream_t st) {
-  NLOS_DISPATCH_NT(P.nt, sfwd(P, x, ncols, Sp, st));
+nlos_status launch_sfwd(const Plan& P, const float* x, int ncols, float2* Sp, cudaStream_t st, const float* x2) {
+  NLOS_DISPATCH_NT(P.nt, sfwd(P, x, x2, ncols, Sp, st));
 }
 nlos_status launch_sinv(const Plan& P, const float2* Sp, int ncols, float* x, const float* ref, double* partials,
                         int* nblocks, cudaStream_t st) {

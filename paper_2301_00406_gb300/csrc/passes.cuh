@@ -48,9 +48,10 @@ nlos_status launch_tinv_fit(const Plan& P, const float2* S, int pitch, int ncols
 nlos_status launch_tadj_store(const Plan& P, const float2* S, int pitch, int ncols, float* out, cudaStream_t st);
 nlos_status launch_tadj_solve(const Plan& P, const float2* S, int pitch, int ncols, const SolveRhs& sr,
                               float2* Sp, cudaStream_t st);
-// Periodic real FFT of a field, and its inverse (optionally with partial
-// sums of (x - ref)^2 into partials[block][0]).
-nlos_status launch_sfwd(const Plan& P, const float* x, int ncols, float2* Sp, cudaStream_t st);
+// Periodic real FFT of a field (of x + x2 when x2 is given), and its inverse
+// (optionally with partial sums of (x - ref)^2 into partials[block][0]).
+nlos_status launch_sfwd(const Plan& P, const float* x, int ncols, float2* Sp, cudaStream_t st,
+                        const float* x2 = nullptr);
 nlos_status launch_sinv(const Plan& P, const float2* Sp, int ncols, float* x, const float* ref,
                         double* partials, int* nblocks, cudaStream_t st);
 // launch_sinv followed by launch_tfwd_rz(x -> S) in one pass (x kept on chip).

@@ -22,7 +22,7 @@ struct TpassOps {
   static nlos_status tadj_store(const Plan& P, const float2* S, int pitch, int ncols, float* out, cudaStream_t st);
   static nlos_status tadj_solve(const Plan& P, const float2* S, int pitch, int ncols, const SolveRhs& sr, float2* Sp,
                                 cudaStream_t st);
-  static nlos_status sfwd(const Plan& P, const float* x, int ncols, float2* Sp, cudaStream_t st);
+  static nlos_status sfwd(const Plan& P, const float* x, const float* x2, int ncols, float2* Sp, cudaStream_t st);
   static nlos_status sinv(const Plan& P, const float2* Sp, int ncols, float* x, const float* ref, double* partials,
                           int* nblocks, cudaStream_t st);
   static nlos_status sinv_rz(const Plan& P, const float2* Sp, int ncols, float* x, const float* ref,
@@ -554,10 +554,12 @@ __global__ void __launch_bounds__(kTpassThreads)
   periodic_fwd_post<NT>(work, Sp, col0, ncols, ncols, COLS, tid, nthr);
 }
 
-// Periodic real FFT of a field (rhs of a solve).
+// Periodic real FFT of a field (rhs of a solve): of x, or of x + x2 when x2
+// is given.
 template <int NT>
 __global__ void __launch_bounds__(kTpassThreads)
-    k_sfwd(const float* __restrict__ x, int ncols, float2* __restrict__ Sp, const float2* __restrict__ tw2g, int cols) {
+    k_sfwd(const float* __restrict__ x, const float* __restrict__ x2, int ncols, float2* __restrict__ Sp,
+           const float2* __restrict__ tw2g, int cols) {
   const int COLS = cols, PAIRS = cols >> 1;
   const WorkAddr<NT> wa{work_pitch<NT>(PAIRS)};
   extern __shared__ float4 smem_f4[];
@@ -573,8 +575,13 @@ __global__ void __launch_bounds__(kTpassThreads)
       [&](int i) {
         const int p = i / NT, n = i % NT;
         const int ca = col0 + 2 * p, cb = ca + 1;
-        return make_float2(ca < ncols ? __ldg(x + (size_t)ca * NT + n) : 0.f,
-                           cb < ncols ? __ldg(x + (size_t)cb * NT + n) : 0.f);
+        float2 z = make_float2(ca < ncols ? __ldg(x + (size_t)ca * NT + n) : 0.f,
+                               cb < ncols ? __ldg(x + (size_t)cb * NT + n) : 0.f);
+        if (x2) {
+          if (ca < ncols) z.x += __ldg(x2 + (size_t)ca * NT + n);
+          if (cb < ncols) z.y += __ldg(x2 + (size_t)cb * NT + n);
+        }
+        return z;
       },
       [&](int i, float2 z) { work[wa.at(i / NT, i % NT, slo)] = z; });
   __syncthreads();
@@ -842,12 +849,13 @@ nlos_status TpassOps<NT>::tadj_solve(const Plan& P, const float2* S, int pitch, 
 }
 
 template <int NT>
-nlos_status TpassOps<NT>::sfwd(const Plan& P, const float* x, int ncols, float2* Sp, cudaStream_t st) {
+nlos_status TpassOps<NT>::sfwd(const Plan& P, const float* x, const float* x2, int ncols, float2* Sp,
+                              cudaStream_t st) {
   KTimer kt_(P, KC_SFWD, st);
   auto kern = k_sfwd<NT>;
   const TpShape sh = tp_shape<NT>(ncols, 0, false, TPK_SFWD, false);
   NLOS_TRY(set_smem_tp(kern, sh.smem));
-  kern<<<sh.blocks, sh.threads, sh.smem, st>>>(x, ncols, Sp, P.d_tw2t, sh.cols);
+  kern<<<sh.blocks, sh.threads, sh.smem, st>>>(x, x2, ncols, Sp, P.d_tw2t, sh.cols);
   NLOS_LAUNCH_CHECK("k_sfwd");
   return NLOS_OK;
 }
