@@ -290,12 +290,23 @@ def run_ours(args):
     a1.record()
     torch.cuda.synchronize()
     alg2_ms = a0.elapsed_time(a1)
+    # per-kernel timing of Algorithm 2 (a second, host-stepped run)
+    plan.timing_enable(True)
+    plan.reconstruct(p2, tau0.data_ptr(), u_out.data_ptr(), tau_out.data_ptr(), stream)
+    kt2 = plan.timing_read()
+    plan.timing_enable(False)
 
     if rank != 0:
         return None
 
     # roofline of the dominant kernel
     peaks, src = measured_peaks()
+    # DRAM bytes per launch of the lateral pass from one ncu capture of this
+    # build's k_conv4 (dram__bytes_read.sum + dram__bytes_write.sum, mean of
+    # the forward launch, 135.65 + 4.75 MB, and the adjoint one, 72.60 +
+    # 25.69 MB) at 128x128x512 with 32x32 sampled columns; None for other
+    # workloads, and to be reset to None whenever k_conv4 changes
+    conv_traffic = 119.34e6 if (nx, ny, nt, int(mask.sum())) == (128, 128, 512, 1024) else None
     ncols = int(mask.sum())
     dom = max((k for k in kt if k != "small"), key=lambda k: kt[k][0])
     tot_ms, nl = kt[dom]
@@ -306,7 +317,8 @@ def run_ours(args):
         peak = alu_peak_tflops(sm_mhz)
         ach = amount / avg_s / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": round(ach, 2), "peak": round(peak, 1),
-                "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(ach / peak, 4),
+                "traffic": round(conv_traffic) if dom == "k_conv" and conv_traffic else None,
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (derived)",
                 "algorithmic_hbm_gbs": round(bytes_alg / avg_s / 1e9, 1)}
     else:
@@ -350,6 +362,7 @@ def run_ours(args):
         "iteration_roofline": iter_roof,
         "kernels": kernels,
         "secondary": {"alg2_iter_per_s": round(args.steps / (alg2_ms / 1e3), 2),
+                      "alg2_kernels_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in kt2.items() if v[1]},
                       "recon_per_s_at_50_iters": round(value / 50.0, 3),
                       "alg1_energy_last": stats["energy"]},
     }

@@ -205,13 +205,14 @@ nlos_status nlos_reconstruct_prepare(nlos_plan plan, const nlos_params* params, 
 /* Reconstruct n independent scenes at once.  plans[i] must be n distinct
  * plans (each owns its scratch; a plan appearing twice is rejected);
  * params[i], tau0[i] (device), u_out[i] (device) and tau_out[i] (device,
- * nullable array or entries) as for nlos_reconstruct.  Each scene runs on an
- * internal stream forked from `stream` and joined back to it; their
- * iterations are enqueued round-robin so the scenes' kernels overlap on the
- * GPU.  A scene's result does not depend on the other scenes of the batch.
- * Synchronises before returning; stats (nullable) receives n entries.  This
- * is the batched execution of the benchmark spec's batching workload; the paper
- * reconstructs one scene at a time. */
+ * nullable array or entries) as for nlos_reconstruct (16-byte aligned).
+ * Each scene runs on an internal stream forked from `stream` and joined back
+ * to it, as one graph launch where possible, else with its iterations
+ * enqueued round-robin, so the scenes' kernels overlap on the GPU.  A scene's
+ * result does not depend on the other scenes of the batch.  Synchronises
+ * before returning; stats (nullable) receives n entries.  The paper
+ * reconstructs one scene at a time; this is the many-scene batched
+ * execution. */
 nlos_status nlos_reconstruct_batch(const nlos_plan* plans, const nlos_params* params, const float* const* tau0,
                                    float* const* u_out, float* const* tau_out, int32_t n, nlos_stats* stats,
                                    void* stream);

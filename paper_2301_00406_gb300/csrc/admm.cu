@@ -285,27 +285,39 @@ __global__ void __launch_bounds__(kStencilThreads)
 
 // Algorithm 2, elementwise part of the post step: Lambda_3 += mu3 (f - tau+),
 // partials 0 = (A u+ - tau+)^2, 1 = M (tau+ - tau0)^2, 2 = (f - tau+)^2.
+// Four consecutive t of one column per item (16-byte loads; nt is a
+// multiple of 4 and the arrays 16-byte aligned).
 __global__ void __launch_bounds__(kStencilThreads)
     k_lam3(const float* __restrict__ tnew, const float* __restrict__ tb, const float* __restrict__ au,
            const float* __restrict__ tau0, float* __restrict__ lam3, const int32_t* __restrict__ colpos, Vox g,
            VoxIter vi, float lam_w, float mu3, size_t V, double* __restrict__ partials) {
   const float inv_d1 = 1.0f / (lam_w + mu3), inv_d0 = 1.0f / mu3;  // lambda M + mu3, M = 1 or 0
   ChunkAcc<3> ca;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V; i += (size_t)gridDim.x * blockDim.x) {
+  const size_t V4 = V / 4;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V4; i += (size_t)gridDim.x * blockDim.x) {
     int x, y, t;
-    vi.decode(i, g, x, y, t);
+    vi.decode(4 * i, g, x, y, t);
     const bool sampled = colpos ? __ldg(colpos + x * g.ny + y) >= 0 : true;
-    const float m = sampled ? 1.0f : 0.0f;
-    const float t0 = __ldg(tau0 + i), tn = __ldg(tnew + i), l3 = lam3[i];
-    const float f = (lam_w * m * t0 + mu3 * __ldg(tb + i) - l3) * (sampled ? inv_d1 : inv_d0);
-    lam3[i] = l3 + mu3 * (f - tn);
-    const float r = __ldg(au + i) - tn, sres = m * (tn - t0), fr = f - tn;
-    ca.add(0, r * r);
-    ca.add(1, sres * sres);
-    ca.add(2, fr * fr);
-    ca.step();
+    const float m = sampled ? 1.0f : 0.0f, inv_d = sampled ? inv_d1 : inv_d0;
+    const float4 t0 = __ldg(reinterpret_cast<const float4*>(tau0) + i);
+    const float4 tn = __ldg(reinterpret_cast<const float4*>(tnew) + i);
+    const float4 tbv = __ldg(reinterpret_cast<const float4*>(tb) + i);
+    const float4 auv = __ldg(reinterpret_cast<const float4*>(au) + i);
+    float4 l3 = reinterpret_cast<const float4*>(lam3)[i];
+    auto one = [&](float t0e, float tne, float tbe, float aue, float& l3e) {
+      const float f = (lam_w * m * t0e + mu3 * tbe - l3e) * inv_d;
+      l3e = l3e + mu3 * (f - tne);
+      const float r = aue - tne, sres = m * (tne - t0e), fr = f - tne;
+      ca.add(0, r * r);
+      ca.add(1, sres * sres);
+      ca.add(2, fr * fr);
+    };
+    one(t0.x, tn.x, tbv.x, auv.x, l3.x);
+    one(t0.y, tn.y, tbv.y, auv.y, l3.y);
+    one(t0.z, tn.z, tbv.z, auv.z, l3.z);
+    one(t0.w, tn.w, tbv.w, auv.w, l3.w);
+    reinterpret_cast<float4*>(lam3)[i] = l3;
   }
-  ca.flush();
   block_reduce_acc(ca, partials);
 }
 

@@ -483,6 +483,9 @@ nlos_status nlos_reconstruct_batch(const nlos_plan* plans, const nlos_params* pa
     for (int i = 0; i < n; ++i) {
       P[i] = reinterpret_cast<Plan*>(plans[i]);
       if (!P[i] || !tau0[i] || !u_out[i]) return fail(NLOS_ERR_INVALID_ARG, "nlos_reconstruct_batch: null entry");
+      if (((reinterpret_cast<uintptr_t>(tau0[i]) | reinterpret_cast<uintptr_t>(u_out[i]) |
+            reinterpret_cast<uintptr_t>(tau_out ? tau_out[i] : nullptr)) & 15) != 0)
+        return fail(NLOS_ERR_INVALID_ARG, "nlos_reconstruct_batch: device buffers must be 16-byte aligned");
       if (P[i]->device != dev) return fail(NLOS_ERR_INVALID_ARG, "nlos_reconstruct_batch: plan on another device");
       NLOS_TRY(validate_params(params[i], "nlos_reconstruct_batch"));
       for (int k = 0; k < i; ++k)
