@@ -282,6 +282,19 @@ __global__ void __launch_bounds__(kTileThreads, 3)
       const float* Ux = U + (s % 3) * kUH * kP;
       const float* Un = U + ((s + 1) % 3) * kUH * kP;
       const float* Lx = L + (s & 1) * 4 * kRH * kP;
+      // the f term's point inputs, loaded now so their latency overlaps the
+      // region pass below
+      float ft_t0[4], ft_l3[4];
+      bool ft_sampled = true;
+      if (FTERM) {
+        ft_sampled = ft.colpos ? __ldg(ft.colpos + x * g.ny + y) >= 0 : true;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const size_t gi = g.idx(x, y, T.t0 + lane + 32 * j);
+          ft_t0[j] = __ldg(ft.tau0 + gi);
+          ft_l3[j] = __ldg(ft.lam3 + gi);
+        }
+      }
       // q over the region: point (yy, tt) is voxel (y0 - 1 + yy, t0 - 1 + tt)
       for (int i = threadIdx.x; i < kRH * kRW; i += kTileThreads) {
         const int yy = i / kRW, tt = i - yy * kRW;
@@ -307,11 +320,10 @@ __global__ void __launch_bounds__(kTileThreads, 3)
         float out = -mu * div;
         if (FTERM) {
           // the denominator lambda M + mu3 takes two values: sampled or not
-          const bool sampled = ft.colpos ? __ldg(ft.colpos + x * g.ny + y) >= 0 : true;
-          const float m = sampled ? 1.0f : 0.0f;
-          const float l3 = __ldg(ft.lam3 + gi);
+          const float m = ft_sampled ? 1.0f : 0.0f;
+          const float l3 = ft_l3[j];
           const float tb = Ux[(iy + 1) * kP + it + kC];
-          const float f = (ft.lam_w * m * __ldg(ft.tau0 + gi) + ft.mu3 * tb - l3) * (sampled ? inv_d1 : inv_d0);
+          const float f = (ft.lam_w * m * ft_t0[j] + ft.mu3 * tb - l3) * (ft_sampled ? inv_d1 : inv_d0);
           out += ft.mu3 * f + l3;
         }
         reg[gi] = out;
