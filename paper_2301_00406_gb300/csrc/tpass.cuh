@@ -434,30 +434,49 @@ __global__ void __launch_bounds__(kTpassThreads)
   ChunkAcc<2> ca;
   float bp = 0.f;
   if (EPI == 1) bp = (float)fa.sc->beta_prev;
-  const int total = min(COLS, ncols - col0) * NT;
-  // ld: the data, A u^k and A u^{k-1} samples (fit epilogue only); st: resample,
-  // store and accumulate
-  batched_copy<4, float3>(
-      total, tid, nthr,
+  const int total4 = min(COLS, ncols - col0) * (NT / 4);
+  // four consecutive bins of one column per item (16-byte loads and store;
+  // nt is a multiple of 4 and every array 16-byte aligned).  ld: the data,
+  // A u^k and A u^{k-1} samples (fit epilogue only); st: resample, store and
+  // accumulate
+  struct In4 {
+    float4 d, a, b;
+  };
+  batched_copy<2, In4>(
+      total4, tid, nthr,
       [&](int i) {
-        if (EPI != 1) return make_float3(0.f, 0.f, 0.f);
-        const size_t g = (size_t)col0 * NT + i;
-        return make_float3(__ldg(fa.data + g), __ldg(fa.auk + g), __ldg(fa.aukm1 + g));
-      },
-      [&](int i, float3 in) {
-        const int c = i / NT, k = i % NT;
-        const float* cc = cbuf + c * NT;
-        const float4 t = tab[k];
-        const int k0 = __float_as_int(t.z);
-        const float tau = t.x * cc[k0] + t.y * cc[k0 + 1];
-        const int oc = outmap ? __ldg(outmap + col0 + c) : col0 + c;
-        out[(size_t)oc * NT + k] = tau;
+        In4 v;
         if (EPI == 1) {
-          const float r = tau - in.x;
-          const float d = tau - ((1.0f + bp) * in.y - bp * in.z);
-          ca.add(0, r * r);
-          ca.add(1, d * d);
-          ca.step();
+          const size_t g4 = (size_t)col0 * (NT / 4) + i;
+          v.d = __ldg(reinterpret_cast<const float4*>(fa.data) + g4);
+          v.a = __ldg(reinterpret_cast<const float4*>(fa.auk) + g4);
+          v.b = __ldg(reinterpret_cast<const float4*>(fa.aukm1) + g4);
+        }
+        return v;
+      },
+      [&](int i, const In4& in) {
+        const int c = i / (NT / 4), k = 4 * (i % (NT / 4));
+        const float* cc = cbuf + c * NT;
+        float tau[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float4 t = tab[k + e];
+          const int k0 = __float_as_int(t.z);
+          tau[e] = t.x * cc[k0] + t.y * cc[k0 + 1];
+        }
+        const int oc = outmap ? __ldg(outmap + col0 + c) : col0 + c;
+        *reinterpret_cast<float4*>(out + (size_t)oc * NT + k) = make_float4(tau[0], tau[1], tau[2], tau[3]);
+        if (EPI == 1) {
+          const float dd[4] = {in.d.x, in.d.y, in.d.z, in.d.w};
+          const float aa[4] = {in.a.x, in.a.y, in.a.z, in.a.w};
+          const float bb[4] = {in.b.x, in.b.y, in.b.z, in.b.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float r = tau[e] - dd[e];
+            const float d = tau[e] - ((1.0f + bp) * aa[e] - bp * bb[e]);
+            ca.add(0, r * r);
+            ca.add(1, d * d);
+          }
         }
       });
   if (EPI == 1) {
