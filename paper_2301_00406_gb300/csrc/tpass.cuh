@@ -127,19 +127,28 @@ __device__ __forceinline__ void stage16(float4* dst, const float4* __restrict__ 
 // indices (multiples of 2, 16, 32 ... with lanes over transforms and
 // sub-sequences); unpadded, those fall into a few float2 bank slots (up to
 // 8-way conflicts), padded they spread over all 16.
+// After the roots, fp[k] = the swizzled work position of frequency k
+// (work_swz(fpos(k))), k < nt: the spectrum loads and the Hermitian split
+// read one table entry per element instead of recomputing the digit
+// reversal and the swizzle (integer arithmetic was the busiest pipe).
 struct Tw2 {
   const float2* t;
+  const int* fp;
   __device__ __forceinline__ float2 operator[](int j) const { return t[j + (j >> 4)]; }
 };
 template <int NT>
 __host__ __device__ constexpr int tw2_slots() {
-  return 2 * NT + (2 * NT) / 16;  // a multiple of 2 float2: the next region stays 16-byte aligned
+  // roots with pads, then nt ints (nt / 2 float2); a multiple of 2 float2, so
+  // the next region stays 16-byte aligned
+  return 2 * NT + (2 * NT) / 16 + NT / 2;
 }
 template <int NT>
 __device__ __forceinline__ Tw2 stage_twiddles(float2* tw2, const float2* __restrict__ g, int tid, int nthr) {
   batched_copy<8, float2>(
       2 * NT, tid, nthr, [&](int j) { return __ldg(g + j); }, [&](int j, float2 v) { tw2[j + (j >> 4)] = v; });
-  return Tw2{tw2};
+  int* fp = reinterpret_cast<int*>(tw2 + 2 * NT + (2 * NT) / 16);
+  for (int k = tid; k < NT; k += nthr) fp[k] = work_swz<NT>(fpos<NT>(k));
+  return Tw2{tw2, fp};
 }
 template <int NT>
 __device__ __forceinline__ void stage_fwd_taps(float4* tab, const float4* __restrict__ g, int tid, int nthr) {
@@ -205,8 +214,8 @@ __device__ __forceinline__ void store_pair(float2* __restrict__ row, int ca, int
 // [h0, h0 + nh); the transform of pair p and half h is h * PAIRS + p when both
 // halves are in `work` (nh = 2), else p.  One item per (bin, pair).
 template <int NT>
-__device__ __forceinline__ void tfwd_post_store(const float2* work, const WorkAddr<NT>& wa, int h0, int nh,
-                                                float2* S, int pitch, int col0, int ncols, int COLS, int tid,
+__device__ __forceinline__ void tfwd_post_store(const float2* work, const WorkAddr<NT>& wa, const int* fp, int h0,
+                                                int nh, float2* S, int pitch, int col0, int ncols, int COLS, int tid,
                                                 int nthr) {
   const int PAIRS = COLS >> 1, lp = __ffs(PAIRS) - 1;  // PAIRS is a power of two
   const int n0 = (NT / 2 + 1 - h0) * PAIRS;              // items of the first half
@@ -220,8 +229,8 @@ __device__ __forceinline__ void tfwd_post_store(const float2* work, const WorkAd
     if (ca >= ncols) continue;
     const int q = nh == 2 ? half * PAIRS + p : p;
     const int m = half ? (NT - 1 - kp) : ((NT - kp) & (NT - 1));
-    const float2 za = work[wa(q, fpos<NT>(kp))];
-    const float2 zb = work[wa(q, fpos<NT>(m))];
+    const float2 za = work[q * wa.pitch + fp[kp]];
+    const float2 zb = work[q * wa.pitch + fp[m]];
     store_pair(S + (size_t)(2 * kp + half) * pitch, ca, ncols, even_pitch, za, zb);
   }
 }
@@ -231,8 +240,8 @@ __device__ __forceinline__ void tfwd_post_store(const float2* work, const WorkAd
 // using Hermitian symmetry for kt > nt, packed as Z = X_a + i X_b.
 template <int NT>
 __device__ __forceinline__ void tinv_load(const float2* __restrict__ S, int pitch, int col0, int ncols, int half,
-                                          float2* work, const WorkAddr<NT>& wa, int q0, int PAIRS, int tid,
-                                          int nthr) {
+                                          float2* work, const WorkAddr<NT>& wa, const int* fp, int q0, int PAIRS,
+                                          int tid, int nthr) {
   const int lp = __ffs(PAIRS) - 1;
   batched_copy<8, float2>(
       NT * PAIRS, tid, nthr,
@@ -250,7 +259,7 @@ __device__ __forceinline__ void tinv_load(const float2* __restrict__ S, int pitc
         }
         return make_float2(A.x - B.y, A.y + B.x);
       },
-      [&](int i, float2 z) { work[wa(q0 + (i & (PAIRS - 1)), fpos<NT>(i >> lp))] = z; });
+      [&](int i, float2 z) { work[(q0 + (i & (PAIRS - 1))) * wa.pitch + fp[i >> lp]] = z; });
 }
 
 // Inverse padded t-FFT of the CTA's pairs: cbuf[c][n] = (1/(2nt)) * real signal
@@ -265,8 +274,8 @@ __device__ __forceinline__ void tinv_core(const float2* __restrict__ S, int pitc
   const float scale = 1.0f / (2.0f * NT);
   if (hb) {
     const WorkAddr<NT> wa{work_pitch<NT>(2 * PAIRS)};
-    tinv_load<NT>(S, pitch, col0, ncols, 0, work, wa, 0, PAIRS, tid, nthr);
-    tinv_load<NT>(S, pitch, col0, ncols, 1, work, wa, PAIRS, PAIRS, tid, nthr);
+    tinv_load<NT>(S, pitch, col0, ncols, 0, work, wa, tw2.fp, 0, PAIRS, tid, nthr);
+    tinv_load<NT>(S, pitch, col0, ncols, 1, work, wa, tw2.fp, PAIRS, PAIRS, tid, nthr);
     __syncthreads();
     team_fft_a<NT, true>(work, 2 * PAIRS, wa, tw2, 2, tid, nthr);
     const int slo = swz_lo<NT>(tid);
@@ -283,7 +292,7 @@ __device__ __forceinline__ void tinv_core(const float2* __restrict__ S, int pitc
   }
   const WorkAddr<NT> wa{work_pitch<NT>(PAIRS)};
   for (int half = 0; half < 2; ++half) {
-    tinv_load<NT>(S, pitch, col0, ncols, half, work, wa, 0, PAIRS, tid, nthr);
+    tinv_load<NT>(S, pitch, col0, ncols, half, work, wa, tw2.fp, 0, PAIRS, tid, nthr);
     __syncthreads();
     team_fft_a<NT, true>(work, PAIRS, wa, tw2, 2, tid, nthr);
     const int slo = swz_lo<NT>(tid);
@@ -344,7 +353,7 @@ __device__ __forceinline__ void tfwd_from_cbuf(const float* cbuf, const float4* 
     }
     __syncthreads();
     team_fft_a<NT, false>(work, NB, wa, tw2, 2, tid, nthr);
-    tfwd_post_store<NT>(work, wa, h0, hb ? 2 : 1, S, pitch, col0, ncols, COLS, tid, nthr);
+    tfwd_post_store<NT>(work, wa, tw2.fp, h0, hb ? 2 : 1, S, pitch, col0, ncols, COLS, tid, nthr);
     __syncthreads();
   }
 }
@@ -490,8 +499,8 @@ __global__ void __launch_bounds__(kTpassThreads)
 // right-hand side rhs = L u-bar - g + reg and runs the periodic real FFT.
 // ---------------------------------------------------------------------------
 template <int NT>
-__device__ __forceinline__ void periodic_fwd_post(const float2* work, float2* Sp, int col0, int ncols, int pitch,
-                                                  int COLS, int tid, int nthr) {
+__device__ __forceinline__ void periodic_fwd_post(const float2* work, const int* fp, float2* Sp, int col0, int ncols,
+                                                  int pitch, int COLS, int tid, int nthr) {
   const int PAIRS = COLS >> 1;
   const WorkAddr<NT> wa{work_pitch<NT>(PAIRS)};
   const int lp = __ffs(PAIRS) - 1;  // PAIRS is a power of two
@@ -500,8 +509,8 @@ __device__ __forceinline__ void periodic_fwd_post(const float2* work, float2* Sp
     const int k = i >> lp, p = i & (PAIRS - 1);
     const int ca = col0 + 2 * p;
     if (ca >= ncols) continue;
-    const float2 za = work[wa(p, fpos<NT>(k))];
-    const float2 zb = work[wa(p, fpos<NT>((NT - k) & (NT - 1)))];
+    const float2 za = work[p * wa.pitch + fp[k]];
+    const float2 zb = work[p * wa.pitch + fp[(NT - k) & (NT - 1)]];
     store_pair(Sp + (size_t)k * pitch, ca, ncols, even_pitch, za, zb);
   }
 }
@@ -570,7 +579,7 @@ __global__ void __launch_bounds__(kTpassThreads)
       });
   __syncthreads();
   team_fft_a<NT, false>(work, PAIRS, wa, tw2, 2, tid, nthr);
-  periodic_fwd_post<NT>(work, Sp, col0, ncols, ncols, COLS, tid, nthr);
+  periodic_fwd_post<NT>(work, tw2.fp, Sp, col0, ncols, ncols, COLS, tid, nthr);
 }
 
 // Periodic real FFT of a field (rhs of a solve): of x, or of x + x2 when x2
@@ -605,7 +614,7 @@ __global__ void __launch_bounds__(kTpassThreads)
       [&](int i, float2 z) { work[wa.at(i / NT, i % NT, slo)] = z; });
   __syncthreads();
   team_fft_a<NT, false>(work, PAIRS, wa, tw2, 2, tid, nthr);
-  periodic_fwd_post<NT>(work, Sp, col0, ncols, ncols, COLS, tid, nthr);
+  periodic_fwd_post<NT>(work, tw2.fp, Sp, col0, ncols, ncols, COLS, tid, nthr);
 }
 
 // Periodic inverse real FFT to a field; optional partial sums of (x - ref)^2.
@@ -622,6 +631,7 @@ __global__ void __launch_bounds__(kTpassThreads)
   constexpr int nthr = kTpassThreads;  // every launch: strides fold at compile time
   const int col0 = blockIdx.x * COLS;
   const Tw2 tw2 = stage_twiddles<NT>(tw2s, tw2g, tid, nthr);
+  __syncthreads();  // the position table is read by the load below
   const int lp = __ffs(PAIRS) - 1;
   batched_copy<8, float2>(
       NT * PAIRS, tid, nthr,
@@ -639,7 +649,7 @@ __global__ void __launch_bounds__(kTpassThreads)
         }
         return make_float2(A.x - B.y, A.y + B.x);
       },
-      [&](int i, float2 z) { work[wa(i & (PAIRS - 1), fpos<NT>(i >> lp))] = z; });
+      [&](int i, float2 z) { work[(i & (PAIRS - 1)) * wa.pitch + tw2.fp[i >> lp]] = z; });
   __syncthreads();
   team_fft_a<NT, true>(work, PAIRS, wa, tw2, 2, tid, nthr);
   const float scale = 1.0f / NT;
@@ -690,6 +700,7 @@ __global__ void __launch_bounds__(kTpassThreads)
   const int col0 = blockIdx.x * COLS;
   const Tw2 tw2 = stage_twiddles<NT>(tw2s, tw2g, tid, nthr);
   stage_fwd_taps<NT>(tab, ftab, tid, nthr);
+  __syncthreads();  // the position table is read by the load below
   const int lp = __ffs(PAIRS) - 1;
   batched_copy<8, float2>(
       NT * PAIRS, tid, nthr,
@@ -707,7 +718,7 @@ __global__ void __launch_bounds__(kTpassThreads)
         }
         return make_float2(A.x - B.y, A.y + B.x);
       },
-      [&](int i, float2 z) { work[wa(i & (PAIRS - 1), fpos<NT>(i >> lp))] = z; });
+      [&](int i, float2 z) { work[(i & (PAIRS - 1)) * wa.pitch + tw2.fp[i >> lp]] = z; });
   __syncthreads();
   team_fft_a<NT, true>(work, PAIRS, wa, tw2, 2, tid, nthr);
   const float scale = 1.0f / NT;
