@@ -10,6 +10,7 @@
 // sequence, reduction order) does not depend on its neighbours, so its result
 // is the same alone, in a batch or in the served mix.
 #include <atomic>
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -42,8 +43,20 @@ static nlos_status reconstruct_batch(Plan** plans, const nlos_params* params, co
     cleanup();
     return cuda_fail(cudaGetLastError(), "batch: start event");
   }
+  // stream priorities by scene size: the smallest scenes (whose kernels are
+  // short and cannot fill the GPU) highest, so their blocks are dispatched as
+  // soon as the large scenes' blocks free an SM instead of waiting behind them
+  int prio_least = 0, prio_greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+  std::vector<size_t> vols(n);
+  for (int i = 0; i < n; ++i) vols[i] = (size_t)plans[i]->nx * plans[i]->ny * plans[i]->nt;
+  std::vector<size_t> sizes(vols);
+  std::sort(sizes.begin(), sizes.end());
+  sizes.erase(std::unique(sizes.begin(), sizes.end()), sizes.end());
   for (int i = 0; i < n && st == NLOS_OK; ++i) {
-    cudaError_t e = cudaStreamCreateWithFlags(&streams[i], cudaStreamNonBlocking);
+    const int rank = (int)(std::lower_bound(sizes.begin(), sizes.end(), vols[i]) - sizes.begin());
+    const int prio = std::min(prio_greatest + rank, prio_least);  // greatest is the numerically lowest
+    cudaError_t e = cudaStreamCreateWithPriority(&streams[i], cudaStreamNonBlocking, prio);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(streams[i], start_ev, 0);
     if (e != cudaSuccess) st = cuda_fail(e, "batch: stream");
     JobRun& j = jobs[i];

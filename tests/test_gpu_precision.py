@@ -3,6 +3,8 @@ generators in tests/golden/ from oracle/ and synth/ only):
 
 * precision case: Algorithm 1 on 128 x 128 x 1024 (8 ps bins, 32 x 32
   stride-4 sampling, 12 iterations);
+* the benchmark's size: Algorithm 1 on 128 x 128 x 512 (16 ps bins, 32 x 32
+  stride-4 sampling, 12 iterations), run as one graph launch like the bench;
 * dual-domain case: Algorithm 2 on 64 x 64 x 512 (16 ps bins, 32 x 32
   stride-2 sampling, 100 iterations with adaptive restart).
 
@@ -82,4 +84,35 @@ def test_c2_alg2_64x64x512_against_oracle():
     assert eu < 1e-3 and et < 1e-3 and nu < 1e-3 and ntau < 1e-3
     assert e_err < 1e-3 and l_err < 1e-3
     assert st["restarts"] == int(z["restart"].sum())
+    assert exact >= 0.99 and near >= 0.999
+
+
+GOLDEN_HEAD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "headline_alg1_128x128x512.npz")
+
+
+def test_headline_alg1_128x128x512_against_oracle():
+    from paper_2301_00406_gb300 import nlos
+    z = np.load(GOLDEN_HEAD)
+    cfg = synth.CONFIGS["headline_128x128x512"]
+    nx, ny, nt = cfg["nx"], cfg["ny"], cfg["nt"]
+    mask = synth.make_mask(cfg)
+    tau0 = synth.pulse_transients(nx, ny, nt, mask, seed=int(z["seed"]))
+    plan = nlos.Plan(nx, ny, nt, cfg["bin_width_s"], mask=mask)
+    p = nlos.params_default(1)
+    p.a, p.b, p.mu, p.iters = cfg["a"], cfg["b"], cfg["mu"], int(z["iters"])
+    t = dev(tau0)
+    u_dev = t.new_empty(t.shape)
+    assert plan.reconstruct_prepare(p, t.data_ptr(), u_dev.data_ptr()) is True   # one graph launch
+    st = plan.reconstruct(p, t.data_ptr(), u_dev.data_ptr())
+    u = host(u_dev).astype(np.float64)
+    cols_err = rel_l2(u.reshape(nx * ny, nt)[z["cols"]], z["u_cols"].astype(np.float64))
+    norm_err = abs(np.linalg.norm(u) - float(z["norm"])) / float(z["norm"])
+    e_err = abs(st["energy"] - float(z["energy"][-1])) / abs(float(z["energy"][-1]))
+    d_gpu, d_ref = admm.depth_map(u), z["depth"].astype(np.int64)
+    exact = float(np.mean(d_gpu == d_ref))
+    near = float(np.mean(np.abs(d_gpu - d_ref) <= 1))
+    print(f"headline: columns rel L2 {cols_err:.3e}, norm {norm_err:.3e}, energy {e_err:.3e}, "
+          f"depth exact {exact:.4f}, within 1 bin {near:.4f}")
+    assert st["iters_done"] == int(z["iters"]) and st["status"] == 0
+    assert cols_err < 1e-3 and norm_err < 1e-3 and e_err < 1e-3
     assert exact >= 0.99 and near >= 0.999
