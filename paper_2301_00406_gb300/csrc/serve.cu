@@ -283,7 +283,15 @@ static nlos_status acquire_ctx(Server* S, Job* jb, BaseEntry* base, JobCtx** out
   if (s == NLOS_OK && cudaMalloc(&c->d_tau0, F) != cudaSuccess) s = fail(NLOS_ERR_OOM, "server: device tau0");
   if (s == NLOS_OK && cudaMalloc(&c->d_u, F) != cudaSuccess) s = fail(NLOS_ERR_OOM, "server: device u");
   if (s == NLOS_OK && cudaMallocHost(&c->h_u, F) != cudaSuccess) s = fail(NLOS_ERR_OOM, "server: pinned staging");
-  if (s == NLOS_OK && cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess)
+  // smaller grids get higher stream priority (one level per factor 2 of
+  // voxels above 2^20): their short kernels take SMs as soon as a large job's
+  // blocks free them, which cuts the latency of small jobs in a mixed load
+  int prio_least = 0, prio_greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+  int lv = 0;
+  for (size_t v = F / sizeof(float); v > ((size_t)1 << 20); v >>= 1) ++lv;
+  const int prio = std::min(prio_greatest + lv, prio_least);
+  if (s == NLOS_OK && cudaStreamCreateWithPriority(&c->st, cudaStreamNonBlocking, prio) != cudaSuccess)
     s = fail(NLOS_ERR_CUDA, "server: stream");
   if (s == NLOS_OK && cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming) != cudaSuccess)
     s = fail(NLOS_ERR_CUDA, "server: event");
