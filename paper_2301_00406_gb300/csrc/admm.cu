@@ -50,13 +50,11 @@ __global__ void k_scale(float* __restrict__ a, const double* __restrict__ s, siz
 // partials[b][0] = sum a^2 (optionally only over columns with colpos >= 0)
 __global__ void __launch_bounds__(kStencilThreads)
     k_sumsq(const float* __restrict__ a, size_t n, double* __restrict__ partials) {
-  ChunkAcc<1> ca;
+  SumAcc<1> ca;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const float v = __ldg(a + i);
     ca.add(0, v * v);
-    ca.step();
   }
-  ca.flush();
   block_reduce_acc(ca, partials);
 }
 
@@ -153,7 +151,7 @@ __global__ void __launch_bounds__(kStencilThreads)
             Vox g, VoxIter vi, float mu, float a, float b, int kind, float eps2, size_t V, double* __restrict__ partials) {
   const float inv_mu = 1.0f / mu;
   const float beta = (float)sc->beta;
-  ChunkAcc<2> ca;
+  SumAcc<2> ca;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V; i += (size_t)gridDim.x * blockDim.x) {
     int x, y, t;
     vi.decode(i, g, x, y, t);
@@ -170,9 +168,7 @@ __global__ void __launch_bounds__(kStencilThreads)
     ubn[i] = un + beta * (un - __ldg(uk + i));
     ca.add(0, pn * sqrtf(gu.x * gu.x + gu.y * gu.y + gu.z * gu.z));
     ca.add(1, d.x * d.x + d.y * d.y + d.z * d.z);
-    ca.step();
   }
-  ca.flush();
   block_reduce_acc(ca, partials);
 }
 
@@ -240,7 +236,7 @@ __global__ void __launch_bounds__(kStencilThreads)
             VoxIter vi, Alg2Coef c, size_t V, double* __restrict__ partials) {
   const float im1 = 1.0f / c.mu1, im2 = 1.0f / c.mu2;
   const float beta = (float)sc->beta;
-  ChunkAcc<7> ca;
+  SumAcc<7> ca;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V; i += (size_t)gridDim.x * blockDim.x) {
     int x, y, t;
     vi.decode(i, g, x, y, t);
@@ -277,9 +273,7 @@ __global__ void __launch_bounds__(kStencilThreads)
     ca.add(4, dv.x * dv.x + dv.y * dv.y + dv.z * dv.z);
     ca.add(5, dw.x * dw.x + dw.y * dw.y + dw.z * dw.z);
     ca.add(6, (f - tn) * (f - tn));
-    ca.step();
   }
-  ca.flush();
   block_reduce_acc(ca, partials);
 }
 
@@ -292,7 +286,7 @@ __global__ void __launch_bounds__(kStencilThreads)
            const float* __restrict__ tau0, float* __restrict__ lam3, const int32_t* __restrict__ colpos, Vox g,
            VoxIter vi, float lam_w, float mu3, size_t V, double* __restrict__ partials) {
   const float inv_d1 = 1.0f / (lam_w + mu3), inv_d0 = 1.0f / mu3;  // lambda M + mu3, M = 1 or 0
-  ChunkAcc<3> ca;
+  SumAcc<3> ca;
   const size_t V4 = V / 4;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V4; i += (size_t)gridDim.x * blockDim.x) {
     int x, y, t;
@@ -480,15 +474,13 @@ __global__ void __launch_bounds__(kSumThreads)
 __global__ void __launch_bounds__(kStencilThreads)
     k_tv_weighted(const float* __restrict__ u, const float* __restrict__ ph, Vox g, VoxIter vi, size_t V,
                   double* __restrict__ partials) {
-  ChunkAcc<1> ca;
+  SumAcc<1> ca;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V; i += (size_t)gridDim.x * blockDim.x) {
     int x, y, t;
     vi.decode(i, g, x, y, t);
     const float3 gu = grad_at(u, g, x, y, t);
     ca.add(0, __ldg(ph + i) * sqrtf(gu.x * gu.x + gu.y * gu.y + gu.z * gu.z));
-    ca.step();
   }
-  ca.flush();
   block_reduce_acc(ca, partials);
 }
 

@@ -92,9 +92,9 @@ constexpr int kMaxTerms = 8;
 // epilogues of otherwise FP32 kernels.  The order of every operation is fixed,
 // so the sums are reproducible bit for bit.
 template <int T>
-struct ChunkAcc {
+struct SumAcc {
   float s[T], c[T];
-  __device__ __forceinline__ ChunkAcc() {
+  __device__ __forceinline__ SumAcc() {
 #pragma unroll
     for (int t = 0; t < T; ++t) {
       s[t] = 0.f;
@@ -107,16 +107,13 @@ struct ChunkAcc {
     c[t] = (u - s[t]) - y;
     s[t] = u;
   }
-  // kept for the call sites' structure: nothing to do per element or at the end
-  __device__ __forceinline__ void step() {}
-  __device__ __forceinline__ void flush() {}
 };
 
 // Block-wide sums of the accumulators of every thread; thread 0 writes
 // partials[blockIdx.x * kMaxTerms + t].  Every thread of the block calls it
 // (blockDim.x a multiple of 32).
 template <int T>
-__device__ __forceinline__ void block_reduce_acc(const ChunkAcc<T>& ca, double* partials) {
+__device__ __forceinline__ void block_reduce_acc(const SumAcc<T>& ca, double* partials) {
   __shared__ double red[32][T];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll

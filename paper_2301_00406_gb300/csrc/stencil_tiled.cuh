@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
   const float inv_mu = 1.0f / mu;
   const float beta = (float)sc->beta;
   const float* ifields[5] = {lam, lam + V, lam + 2 * V, ph, uk};
-  ChunkAcc<2> ca;
+  SumAcc<2> ca;
   int cur, end;
   block_share(nsteps, cur, end);
   while (cur < end) {
@@ -207,7 +207,6 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         ubn[gi] = uc + beta * (uc - Ix[4 * kTY * kTT + ii]);
         ca.add(0, pn * sqrtf(gu.x * gu.x + gu.y * gu.y + gu.z * gu.z));
         ca.add(1, d.x * d.x + d.y * d.y + d.z * d.z);
-        ca.step();
       }
       __syncthreads();
     }

@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(kTpassThreads)
   __syncthreads();
   tinv_core<NT>(S, pitch, col0, ncols, work, cbuf, tw2, PAIRS, hb != 0, tid, nthr);
 
-  ChunkAcc<2> ca;
+  SumAcc<2> ca;
   float bp = 0.f;
   if (EPI == 1) bp = (float)fa.sc->beta_prev;
   const int total4 = min(COLS, ncols - col0) * (NT / 4);
@@ -489,7 +489,6 @@ __global__ void __launch_bounds__(kTpassThreads)
         }
       });
   if (EPI == 1) {
-    ca.flush();
     block_reduce_acc(ca, fa.partials);
   }
 }
@@ -654,7 +653,7 @@ __global__ void __launch_bounds__(kTpassThreads)
   team_fft_a<NT, true>(work, PAIRS, wa, tw2, 2, tid, nthr);
   const float scale = 1.0f / NT;
   const int slo = swz_lo<NT>(tid);
-  ChunkAcc<1> ca;
+  SumAcc<1> ca;
   const int total = min(COLS, ncols - col0) * NT;
   batched_copy<8, float>(
       total, tid, nthr, [&](int i) { return ref ? __ldg(ref + (size_t)col0 * NT + i) : 0.f; },
@@ -666,11 +665,9 @@ __global__ void __launch_bounds__(kTpassThreads)
         if (ref) {
           const float d = v - rv;
           ca.add(0, d * d);
-          ca.step();
         }
       });
   if (partials) {
-    ca.flush();
     block_reduce_acc(ca, partials);
   }
 }
@@ -723,7 +720,7 @@ __global__ void __launch_bounds__(kTpassThreads)
   team_fft_a<NT, true>(work, PAIRS, wa, tw2, 2, tid, nthr);
   const float scale = 1.0f / NT;
   const int slo = swz_lo<NT>(tid);
-  ChunkAcc<1> ca;
+  SumAcc<1> ca;
   const int total = min(COLS, ncols - col0) * NT;
   batched_copy<8, float>(
       total, tid, nthr, [&](int i) { return ref ? __ldg(ref + (size_t)col0 * NT + i) : 0.f; },
@@ -736,12 +733,10 @@ __global__ void __launch_bounds__(kTpassThreads)
         if (ref) {
           const float d = v - rv;
           ca.add(0, d * d);
-          ca.step();
         }
       });
   for (int i = total + tid; i < COLS * NT; i += nthr) cbuf[i] = 0.f;  // columns past the last
   if (partials) {
-    ca.flush();
     block_reduce_acc(ca, partials);
   }
   __syncthreads();
