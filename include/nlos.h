@@ -134,6 +134,23 @@ nlos_status nlos_plan_create(const nlos_geometry* geom, void* stream, nlos_plan*
  * NULL is accepted. */
 nlos_status nlos_plan_destroy(nlos_plan plan);
 
+/* Select how the plan computes the lateral convolution of every kt plane
+ * with the cone-kernel spectrum (the H of Eq. 3 and its conjugate in A^T):
+ *   0  hand-written FFT kernels in FP32 (default);
+ *   1  dense DFT-matrix products on the tensor cores (cuBLAS strided-batched
+ *      BF16 GEMMs with FP32 accumulation on real planar operands; every
+ *      operand split into hi + lo BF16 terms and the products hi hi + hi lo
+ *      + lo hi summed: the split-BF16 variant of the precision comparison);
+ *   2  the same GEMMs with the hi terms only (one BF16 pass).
+ * Modes 1 and 2 allocate a workspace of about 144 nx^2 (nt + 1) bytes on
+ * first use (freed by mode 0 or nlos_plan_destroy) and run
+ * reconstructions stepped from the host, without a CUDA graph; they need
+ * nx = ny.  Results are those of mode 0 within the GEMM's rounding.  Not
+ * thread-safe with other calls on the same plan.  Errors: invalid mode or
+ * nx != ny (NLOS_ERR_INVALID_ARG), device memory (NLOS_ERR_OOM), cuBLAS
+ * (NLOS_ERR_CUDA). */
+nlos_status nlos_plan_set_lateral(nlos_plan plan, int32_t mode, void* stream);
+
 /* ||A_D||_2^2 (masked != 0) or ||A||_2^2 by power iteration on A_D^T A_D from
  * the all-ones vector (up to 200 steps, relative change < 1e-12), as used for
  * L0 = 2 ||A_D||^2 (below Eq. 10).  Computed once per plan and cached;

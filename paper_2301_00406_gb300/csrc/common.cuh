@@ -147,6 +147,8 @@ __device__ __forceinline__ void block_reduce_acc(const SumAcc<T>& ca, double* pa
 // ---------------------------------------------------------------------------
 struct SolverState;  // defined in admm.cu
 
+struct LateralGemm;  // optional GEMM lateral stage (conv_gemm.cu)
+
 struct Plan {
   int nx, ny, nt;
   double bin_width_s, wall_width_m, range_m;
@@ -215,6 +217,10 @@ struct Plan {
   // streams that capture the bodies of conditional nodes (iteration loop,
   // pointer-phase switch, backtracking loop)
   cudaStream_t body_stream[3] = {nullptr, nullptr, nullptr};
+
+  // lateral stage on the tensor cores as DFT-matrix GEMMs (nlos_plan_set_lateral);
+  // nullptr: the FFT kernels
+  LateralGemm* lateral = nullptr;
 
   // optional per-launch timing (nlos_timing_enable): event pairs recorded
   // around every kernel launch on the launch stream, harvested on read.

@@ -62,6 +62,14 @@ nlos_status launch_sinv_rz(const Plan& P, const float2* Sp, int ncols, float* x,
 // (the plan's sampled columns) with plane pitch ncols.
 nlos_status launch_conv(const Plan& P, const float2* Sin, bool in_compact, float2* Sout, bool out_compact,
                         bool adj, cudaStream_t st);
+// The same as DFT-matrix GEMMs on the tensor cores (plans with P.lateral set).
+nlos_status launch_conv_gemm(const Plan& P, const float2* Sin, bool in_compact, float2* Sout, bool out_compact,
+                             bool adj, cudaStream_t st);
+// Select the lateral stage: 0 FFT kernels, 1 GEMMs with BF16x9-emulated FP32,
+// 2 GEMMs with single-pass BF16 inputs (FP32 accumulate).  Allocates its
+// workspace on the first non-zero mode.
+nlos_status set_lateral_mode(Plan& P, int mode, cudaStream_t st);
+void free_lateral_gemm(Plan* P);
 // Four-CTA-cluster lateral convolution for nx in {32, 64, 128} (conv4.cu);
 // launch_conv dispatches to it.
 nlos_status launch_conv4(const Plan& P, const float2* Sin, bool in_compact, float2* Sout, bool out_compact,

@@ -196,6 +196,7 @@ static void destroy_plan(Plan* P) {
   if (!P) return;
   cudaDeviceSynchronize();
   free_workspace(P);
+  free_lateral_gemm(P);
   if (P->owns_tables) {
     void* ptrs[] = {P->d_rz_i0, P->d_rz_w, P->d_rzt_start, P->d_rt_k0, P->d_rt_w, P->d_rtt_start, P->d_cols,
                     P->d_colpos, P->d_tw2t, P->d_twt, P->d_twx, P->d_twy, P->d_lamx, P->d_lamy, P->d_lamt,
@@ -234,6 +235,8 @@ Plan* plan_clone_workspace(const Plan& base, nlos_status* status) {
   P->ev_used = 0;
   P->graphs.clear();
   P->capture_stream = nullptr;
+  for (auto& b : P->body_stream) b = nullptr;  // the base's streams stay the base's
+  P->lateral = nullptr;                         // a clone uses the FFT lateral stage
   nlos_status s = alloc_workspace(P);
   if (s != NLOS_OK) {
     destroy_plan(P);
@@ -506,6 +509,15 @@ nlos_status nlos_plan_create(const nlos_geometry* geom, void* stream, nlos_plan*
     if (s != NLOS_OK) return s;
     *out = reinterpret_cast<nlos_plan>(P);
     return NLOS_OK;
+  })
+}
+
+nlos_status nlos_plan_set_lateral(nlos_plan plan, int32_t mode, void* stream) {
+  API_GUARD({
+    NLOS_TRY(check_plan(plan));
+    Plan& P = *reinterpret_cast<Plan*>(plan);
+    free_graphs(&P);  // cached graphs hold the previous lateral stage
+    return set_lateral_mode(P, mode, reinterpret_cast<cudaStream_t>(stream));
   })
 }
 

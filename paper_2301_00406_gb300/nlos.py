@@ -21,6 +21,7 @@ STATUS_NAMES = {0: "NLOS_OK", -1: "NLOS_ERR_INVALID_ARG", -2: "NLOS_ERR_OOM", -3
 globals().update({name: code for code, name in STATUS_NAMES.items()})
 RADIOMETRY = {"compensated": 0, "raw": 1}
 # curvature weights phi(kappa) (NLOS_PHI_*): a + b kappa^2, a + b |kappa|, sqrt(a + b kappa^2)
+LATERAL_FFT, LATERAL_GEMM_BF16X3, LATERAL_GEMM_BF16 = 0, 1, 2
 PHI_TSC, PHI_TAC, PHI_TRV = 0, 1, 2
 PHI = {"tsc": 0, "tac": 1, "trv": 2}
 
@@ -95,6 +96,7 @@ _SIGS = {
     "nlos_server_info": (ctypes.c_int32, [_P, _P]),
     "nlos_server_destroy": (ctypes.c_int32, [_P, ctypes.c_int32, ctypes.c_double]),
     "nlos_timing_enable": (ctypes.c_int32, [_P, ctypes.c_int32]),
+    "nlos_plan_set_lateral": (ctypes.c_int32, [_P, ctypes.c_int32, _P]),
     "nlos_timing_read": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32]),
 }
 
@@ -191,6 +193,10 @@ class Plan:
         out = ctypes.c_double()
         check(load().nlos_plan_norm2(self.handle, int(masked), stream, ctypes.byref(out)))
         return out.value
+
+    def set_lateral(self, mode, stream=0):
+        """Lateral stage: 0 FFT kernels, 1 split-BF16 DFT GEMMs, 2 single-BF16 DFT GEMMs."""
+        check(load().nlos_plan_set_lateral(self.handle, int(mode), stream))
 
     def timing_enable(self, enable=True):
         check(load().nlos_timing_enable(self.handle, int(enable)))
