@@ -261,6 +261,22 @@ nlos_status nlos_poll(nlos_server server, uint64_t job_id, nlos_stats* out);
 nlos_status nlos_wait(nlos_server server, uint64_t job_id, double timeout_s, nlos_stats* out);
 nlos_status nlos_job_times(nlos_server server, uint64_t job_id, double* queued_s, double* total_s);
 nlos_status nlos_server_info(nlos_server server, int64_t* counters8);
+/* Warm-up before traffic.  The first job of a geometry makes the worker
+ * build that geometry's plan (tables, kernel spectrum, tuned launch shapes,
+ * ||A_D||^2 by power iteration), and the first job of each (geometry, model)
+ * in a new job context also allocates the context and captures its graph;
+ * while the worker does that no other job is admitted or retired.
+ * nlos_server_prepare does this work ahead of time: it builds the plan of
+ * `geom` and keeps `contexts` idle job contexts of the kind `params` needs,
+ * each with the graph of a run of `params` captured, so later jobs with the
+ * same geometry and parameters start at once.  Existing idle contexts of that
+ * kind count towards `contexts`; new ones are created only while they fit the
+ * HBM budget (nothing is evicted for them), and *ready (nullable) receives
+ * how many are ready.  Blocks until the worker has done it or timeout_s has
+ * passed (NLOS_ERR_TIMEOUT; the warm-up still completes).  Thread-safe;
+ * NLOS_ERR_BUSY after nlos_server_destroy has begun. */
+nlos_status nlos_server_prepare(nlos_server server, const nlos_geometry* geom, const nlos_params* params,
+                                int32_t contexts, double timeout_s, int32_t* ready);
 nlos_status nlos_server_destroy(nlos_server server, int32_t cancel_pending, double timeout_s);
 
 /* The periodic FFT solve of nlos_solve for callers that cannot allocate

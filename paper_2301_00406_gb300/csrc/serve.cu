@@ -169,6 +169,17 @@ struct BaseEntry {
   size_t bytes = 0;
 };
 
+// A warm-up request (nlos_server_prepare): the geometry's base plan and
+// `want` idle job contexts whose graphs for `params` are already captured.
+struct Prep {
+  GeomKey key;
+  nlos_params params{};
+  int want = 0;
+  int ready = 0;
+  nlos_status status = NLOS_OK;
+  bool done = false;
+};
+
 struct ServerInfo {
   int64_t queued = 0, active = 0, completed = 0, failed = 0, peak_active = 0;
   size_t bytes_in_use = 0, bytes_peak = 0;
@@ -182,6 +193,7 @@ struct Server {
   std::condition_variable cv;       // wakes the worker (new jobs, shutdown)
   std::condition_variable done_cv;  // wakes waiters (job finished)
   std::deque<Job*> incoming;
+  std::deque<std::shared_ptr<Prep>> preps;  // warm-up requests, handled before admission
   std::map<uint64_t, std::unique_ptr<Job>> jobs;
   uint64_t next_id = 1;
   bool stopping = false;
@@ -265,17 +277,10 @@ static void release_idle(Server* S, size_t need) {
   }
 }
 
-static nlos_status acquire_ctx(Server* S, Job* jb, BaseEntry* base, JobCtx** out) {
-  const auto k = std::make_pair(jb->key, ctx_kind(jb->params));
-  auto it = S->idle.find(k);
-  if (it != S->idle.end()) {
-    *out = it->second;
-    S->idle.erase(it);
-    return NLOS_OK;
-  }
+static nlos_status create_ctx(Server* S, const GeomKey& key, int kind, BaseEntry* base, JobCtx** out) {
   JobCtx* c = new JobCtx();
-  c->key = jb->key;
-  c->model = ctx_kind(jb->params);
+  c->key = key;
+  c->model = kind;
   c->bytes = ctx_bytes(*base->plan, c->model);
   const size_t F = (size_t)base->plan->nx * base->plan->ny * base->plan->nt * sizeof(float);
   nlos_status s = NLOS_OK;
@@ -303,6 +308,65 @@ static nlos_status acquire_ctx(Server* S, Job* jb, BaseEntry* base, JobCtx** out
   S->used += c->bytes;
   *out = c;
   return NLOS_OK;
+}
+
+static nlos_status acquire_ctx(Server* S, Job* jb, BaseEntry* base, JobCtx** out) {
+  const auto k = std::make_pair(jb->key, ctx_kind(jb->params));
+  auto it = S->idle.find(k);
+  if (it != S->idle.end()) {
+    *out = it->second;
+    S->idle.erase(it);
+    return NLOS_OK;
+  }
+  return create_ctx(S, k.first, k.second, base, out);
+}
+
+// Captures (or finds cached) the graph of a run of `p` in context c, with the
+// context's own buffers, exactly as start_job will enqueue it.
+static nlos_status warm_ctx(JobCtx* c, const nlos_params& p) {
+  JobRun r;
+  r.P = c->ws;
+  r.p = p;
+  r.tau0 = c->d_tau0;
+  r.u_out = c->d_u;
+  r.tau_out = nullptr;
+  r.st = c->st;
+  bool ready = false;
+  NLOS_TRY(job_prepare_graph(r, c->st, &ready));
+  return cudaStreamSynchronize(c->st) == cudaSuccess ? NLOS_OK : fail(NLOS_ERR_CUDA, "server: warm-up");
+}
+
+// Serves one warm-up request: the base plan, then up to `want` idle contexts
+// of the request's kind (existing idle ones first), each with its graph
+// captured.  Contexts that would exceed the HBM budget are not created and
+// nothing else is evicted for them.
+static void run_prep(Server* S, Prep& pr) {
+  const int kind = ctx_kind(pr.params);
+  BaseEntry* base = nullptr;
+  nlos_status s = get_base(S, pr.key, kind, &base);
+  int ready = 0;
+  if (s == NLOS_OK) {
+    auto range = S->idle.equal_range(std::make_pair(pr.key, kind));
+    for (auto it = range.first; it != range.second && ready < pr.want && s == NLOS_OK; ++it) {
+      s = warm_ctx(it->second, pr.params);
+      if (s == NLOS_OK) ++ready;
+    }
+  }
+  while (s == NLOS_OK && ready < pr.want && S->used + ctx_bytes(*base->plan, kind) <= S->budget) {
+    JobCtx* c = nullptr;
+    s = create_ctx(S, pr.key, kind, base, &c);
+    if (s != NLOS_OK) break;
+    S->idle.emplace(std::make_pair(pr.key, kind), c);
+    s = warm_ctx(c, pr.params);
+    if (s == NLOS_OK) ++ready;
+  }
+  std::lock_guard<std::mutex> lock(S->mu);
+  pr.ready = ready;
+  pr.status = s;
+  pr.done = true;
+  S->info.bytes_in_use = S->used;
+  S->info.bytes_peak = std::max(S->info.bytes_peak, S->used);
+  S->done_cv.notify_all();
 }
 
 static void finish_job(Server* S, Job* jb, JobState state, nlos_status status) {
@@ -358,7 +422,7 @@ static void worker_main(Server* S) {
   for (;;) {
     {
       std::unique_lock<std::mutex> lock(S->mu);
-      if (S->active.empty() && S->pending.empty() && S->incoming.empty() && !S->stopping)
+      if (S->active.empty() && S->pending.empty() && S->incoming.empty() && S->preps.empty() && !S->stopping)
         S->cv.wait_for(lock, std::chrono::milliseconds(50));
       while (!S->incoming.empty()) {
         S->pending.push_back(S->incoming.front());
@@ -374,10 +438,21 @@ static void worker_main(Server* S) {
         S->pending.clear();
         S->done_cv.notify_all();
       }
-      if (S->stopping && S->pending.empty() && S->active.empty()) break;
+      if (S->stopping && S->pending.empty() && S->active.empty() && S->preps.empty()) break;
       S->info.queued = (int64_t)S->pending.size();
     }
     bool progressed = false;
+    for (;;) {
+      std::shared_ptr<Prep> pr;
+      {
+        std::lock_guard<std::mutex> lock(S->mu);
+        if (S->preps.empty()) break;
+        pr = S->preps.front();
+        S->preps.pop_front();
+      }
+      run_prep(S, *pr);
+      progressed = true;
+    }
     // admission: in arrival order, while a slot and the HBM budget allow
     while (!S->pending.empty() && (int)S->active.size() < S->max_slots) {
       Job* jb = S->pending.front();
@@ -562,6 +637,36 @@ nlos_status nlos_submit(nlos_server server, const nlos_geometry* geom, const nlo
     return NLOS_OK;
   } catch (...) {
     return fail(NLOS_ERR_OOM, "nlos_submit: host allocation failed");
+  }
+}
+
+nlos_status nlos_server_prepare(nlos_server server, const nlos_geometry* geom, const nlos_params* params,
+                                int32_t contexts, double timeout_s, int32_t* ready) {
+  try {
+    if (ready) *ready = 0;
+    if (!server || !geom || !params || contexts < 0)
+      return fail(NLOS_ERR_INVALID_ARG, "nlos_server_prepare: null argument or contexts < 0");
+    int32_t n = 0;
+    NLOS_TRY(nlos_geometry_tables(geom, nullptr, nullptr, nullptr, nullptr, nullptr, &n));
+    NLOS_TRY(validate_params(*params, "nlos_server_prepare"));
+    Server& S = server->impl;
+    auto pr = std::make_shared<Prep>();
+    pr->key = make_key(*geom);
+    pr->params = *params;
+    pr->want = contexts;
+    std::unique_lock<std::mutex> lock(S.mu);
+    if (S.stopping) return fail(NLOS_ERR_BUSY, "nlos_server_prepare: server is shutting down");
+    S.preps.push_back(pr);
+    S.cv.notify_one();
+    const auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(
+                                             std::chrono::duration<double>(timeout_s > 0 ? timeout_s : 0.0));
+    while (!pr->done)
+      if (S.done_cv.wait_until(lock, deadline) == std::cv_status::timeout && !pr->done)
+        return fail(NLOS_ERR_TIMEOUT, "nlos_server_prepare: timed out (the warm-up still completes)");
+    if (ready) *ready = pr->ready;
+    return pr->status == NLOS_OK ? NLOS_OK : fail(pr->status, "nlos_server_prepare: warm-up failed");
+  } catch (...) {
+    return fail(NLOS_ERR_OOM, "nlos_server_prepare: host allocation failed");
   }
 }
 

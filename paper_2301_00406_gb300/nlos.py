@@ -94,6 +94,8 @@ _SIGS = {
     "nlos_job_times": (ctypes.c_int32, [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_double)]),
     "nlos_server_info": (ctypes.c_int32, [_P, _P]),
+    "nlos_server_prepare": (ctypes.c_int32, [_P, ctypes.POINTER(Geometry), ctypes.POINTER(Params), ctypes.c_int32,
+                                             ctypes.c_double, ctypes.POINTER(ctypes.c_int32)]),
     "nlos_server_destroy": (ctypes.c_int32, [_P, ctypes.c_int32, ctypes.c_double]),
     "nlos_timing_enable": (ctypes.c_int32, [_P, ctypes.c_int32]),
     "nlos_plan_set_lateral": (ctypes.c_int32, [_P, ctypes.c_int32, _P]),
@@ -271,6 +273,16 @@ class Server:
                                  u_out.ctypes.data, ctypes.byref(jid)))
         self._keep[jid.value] = u_out   # the caller's buffer must outlive the job
         return jid.value
+
+    def prepare(self, nx, ny, nt, bin_width_s, params, contexts=1, timeout_s=600.0, wall_width_m=1.0,
+                radiometry="compensated", mask=None):
+        """nlos_server_prepare: build the geometry's plan and `contexts` idle job contexts with the
+        graph of `params` captured; returns how many contexts are ready."""
+        g, keep = _geometry(nx, ny, nt, bin_width_s, wall_width_m, radiometry, mask)
+        ready = ctypes.c_int32()
+        check(load().nlos_server_prepare(self.handle, ctypes.byref(g), ctypes.byref(params), int(contexts),
+                                         float(timeout_s), ctypes.byref(ready)))
+        return ready.value
 
     def poll(self, job_id):
         st = Stats()

@@ -110,6 +110,34 @@ def test_admission_respects_budget(nlos):
         assert np.array_equal(o, ref)
 
 
+def test_server_prepare_warms_contexts(nlos):
+    """nlos_server_prepare builds the plan and idle contexts with captured graphs
+    ahead of the jobs; jobs then reuse them (no new device memory) and give the
+    same result as the plan alone; contexts beyond the budget are not made."""
+    j = make_job(nlos, 1)                       # 32x32x128, model 2
+    srv = nlos.Server(hbm_budget_bytes=8 << 30, max_slots=4)
+    assert srv.prepare(j["n"], j["n"], j["nt"], j["bw"], j["params"], contexts=2, mask=j["mask"]) == 2
+    warm = srv.info()
+    assert warm["running"] == 0 and warm["completed"] == 0 and warm["bytes_in_use"] > 0
+    # asking again creates nothing new
+    assert srv.prepare(j["n"], j["n"], j["nt"], j["bw"], j["params"], contexts=2, mask=j["mask"]) == 2
+    assert srv.info()["bytes_in_use"] == warm["bytes_in_use"]
+    outs = [np.full(j["tau0"].shape, np.nan, np.float32) for _ in range(2)]
+    ids = [srv.submit(j["n"], j["n"], j["nt"], j["bw"], j["params"], j["tau0"], o, mask=j["mask"]) for o in outs]
+    for jid in ids:
+        assert srv.wait(jid, timeout_s=120.0)["status"] == 0
+    info = srv.info()
+    assert info["completed"] == 2 and info["bytes_peak"] == warm["bytes_in_use"]
+    srv.close()
+    ref = alone(nlos, j).astype(np.float32)
+    for o in outs:
+        assert np.array_equal(o, ref)
+    # a budget that holds the plan but no context: nothing is made, no error
+    tiny = nlos.Server(hbm_budget_bytes=1 << 20, max_slots=2)
+    assert tiny.prepare(j["n"], j["n"], j["nt"], j["bw"], j["params"], contexts=3, mask=j["mask"]) == 0
+    tiny.close()
+
+
 def test_job_larger_than_budget_fails(nlos):
     j = make_job(nlos, 0)
     srv = nlos.Server(hbm_budget_bytes=1 << 20, max_slots=2)
