@@ -42,8 +42,25 @@ nlos_status cuda_fail(cudaError_t e, const char* what);
 // ---------------------------------------------------------------------------
 // Complex helpers (float2 = re, im)
 // ---------------------------------------------------------------------------
-__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// On the device the complex add and subtract are single paired-FP32
+// instructions (sm_100 and later): both components in one issue slot, each
+// rounded to nearest exactly as a scalar add would be.  a - b is computed as
+// the fused b * (-1) + a, whose one rounding of the exact a - b is the
+// subtraction's result.
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+#ifdef __CUDA_ARCH__
+  return __fadd2_rn(a, b);
+#else
+  return make_float2(a.x + b.x, a.y + b.y);
+#endif
+}
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) {
+#ifdef __CUDA_ARCH__
+  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+#else
+  return make_float2(a.x - b.x, a.y - b.y);
+#endif
+}
 __host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }

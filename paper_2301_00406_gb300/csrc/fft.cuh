@@ -87,8 +87,8 @@ __device__ __forceinline__ void dft_reg(float2 (&a)[R]) {
       for (int j = 0; j < span; ++j) {
         const float2 x0 = a[blk + j];
         const float2 x1 = a[blk + j + span];
-        a[blk + j] = make_float2(x0.x + x1.x, x0.y + x1.y);
-        a[blk + j + span] = twmul64<INV>(make_float2(x0.x - x1.x, x0.y - x1.y), j * (64 / (2 * span)));
+        a[blk + j] = cadd(x0, x1);
+        a[blk + j + span] = twmul64<INV>(csub(x0, x1), j * (64 / (2 * span)));
       }
     }
   }
