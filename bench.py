@@ -305,10 +305,11 @@ def run_ours(args):
     peaks, src = measured_peaks()
     # DRAM bytes per launch of the lateral pass from one ncu capture of this
     # build's k_conv4 (dram__bytes_read.sum + dram__bytes_write.sum, mean of
-    # the forward launch, 135.65 + 4.75 MB, and the adjoint one, 72.60 +
-    # 25.69 MB) at 128x128x512 with 32x32 sampled columns; None for other
-    # workloads, and to be reset to None whenever k_conv4 changes
-    conv_traffic = 119.34e6 if (nx, ny, nt, int(mask.sum())) == (128, 128, 512, 1024) else None
+    # two forward launches, 135.62 + 1.63 and 135.63 + 1.34 MB, and two
+    # adjoint ones, 72.61 + 25.24 and 72.60 + 22.35 MB) at 128x128x512 with
+    # 32x32 sampled columns; None for other workloads, and to be reset to
+    # None whenever k_conv4 changes
+    conv_traffic = 116.76e6 if (nx, ny, nt, int(mask.sum())) == (128, 128, 512, 1024) else None
     ncols = int(mask.sum())
     dom = max((k for k in kt if k != "small"), key=lambda k: kt[k][0])
     tot_ms, nl = kt[dom]
