@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrivals per second")
     ap.add_argument("--budget-gb", type=float, default=0.0, help="serve: HBM budget (0 = 80 percent of free)")
-    ap.add_argument("--slots", type=int, default=8, help="serve: jobs running at once")
+    ap.add_argument("--slots", type=int, default=4, help="serve: jobs running at once")
     ap.add_argument("--prewarm", type=int, default=2,
                     help="serve: job contexts per (grid, sampling, model) prepared before the arrivals start")
     return ap.parse_args()
