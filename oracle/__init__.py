@@ -18,10 +18,12 @@ lct     the discrete light-cone-transform operator A = R_t^{-1} H R_z (Eq. 3),
         ||A_D||_2^2.
 admm    finite differences, curvature, shrinkage (Eq. 7), the FFT solve
         (Eq. 11), Algorithm 1 and Algorithm 2.
+nonconfocal  the midpoint conversion of non-confocal transients into
+        confocal ones (Sec. 4, evaluation on non-confocal data).
 
 Parity status of every function is stated in its docstring; all functions
 are pinned by ``tests/test_oracle_*.py`` except where the docstring says
 "parity unpinned".
 """
 
-from . import lct, admm  # noqa: F401
+from . import lct, admm, nonconfocal  # noqa: F401
