@@ -302,6 +302,34 @@ nlos_status nlos_server_destroy(nlos_server server, int32_t cancel_pending, doub
 nlos_status nlos_solve_static(int32_t nx, int32_t ny, int32_t nt, const float* rhs_dev, float* x_dev, double c0,
                               double c1, void* stream);
 
+/* Midpoint conversion of non-confocal transients into confocal ones
+ * (Sec. 4, evaluation on non-confocal data: the confocal solvers run on a
+ * non-confocal measurement after the midpoint approximation, which the
+ * paper cites from f-k migration without stating it).
+ *
+ * Input: tau_nc_dev, device, float32 [nx][ny][nt], the transients of a
+ * non-confocal scan with the laser fixed at the wall point
+ * (laser_x_m, laser_y_m) and the detector at the scan grid centres
+ * x_i = (i + 1/2 - nx/2) wall_width_m / nx (y likewise), bins of
+ * bin_width_s.  Output: tau_c_dev, device, float32 [nx][ny][nt], the
+ * confocal transients at the midpoints m_ij = (laser + s_ij) / 2, i.e. a
+ * confocal scan of wall width wall_width_m / 2 centred at laser / 2, to be
+ * reconstructed with a plan of that wall width.  Confocal bin k (centre
+ * t_k = (k + 1/2) dt) reads the non-confocal record at the time
+ * sqrt(t_k^2 + |s_ij - laser|^2 / c^2), exact for scatterers on the wall
+ * normal through the midpoint, by two-tap linear interpolation between bin
+ * centres (zero past the last bin); the amplitude is not changed.  The tap
+ * positions are computed in FP64 without fused operations, the
+ * interpolation in FP32.
+ *
+ * nx, ny, nt powers of two >= 2; bin_width_s > 0, wall_width_m > 0, finite
+ * laser coordinates; the buffers 4-byte aligned and not overlapping
+ * (NLOS_ERR_INVALID_ARG otherwise).  The caller owns both buffers.  Queued
+ * on `stream`, no host synchronisation, no allocation. */
+nlos_status nlos_midpoint_confocal(int32_t nx, int32_t ny, int32_t nt, double bin_width_s, double wall_width_m,
+                                   double laser_x_m, double laser_y_m, const float* tau_nc_dev, float* tau_c_dev,
+                                   void* stream);
+
 /* Per-launch timing of a plan's kernels, for profiling.  When enabled, every
  * kernel the plan launches is bracketed by a pair of CUDA events recorded on
  * its launch stream.  nlos_timing_read synchronises the device, returns per

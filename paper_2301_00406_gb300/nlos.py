@@ -97,6 +97,8 @@ _SIGS = {
     "nlos_server_prepare": (ctypes.c_int32, [_P, ctypes.POINTER(Geometry), ctypes.POINTER(Params), ctypes.c_int32,
                                              ctypes.c_double, ctypes.POINTER(ctypes.c_int32)]),
     "nlos_server_destroy": (ctypes.c_int32, [_P, ctypes.c_int32, ctypes.c_double]),
+    "nlos_midpoint_confocal": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                                ctypes.c_double, ctypes.c_double, ctypes.c_double, _P, _P, _P]),
     "nlos_timing_enable": (ctypes.c_int32, [_P, ctypes.c_int32]),
     "nlos_plan_set_lateral": (ctypes.c_int32, [_P, ctypes.c_int32, _P]),
     "nlos_timing_read": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32]),
@@ -331,6 +333,23 @@ class Server:
 def _stream():
     import torch
     return torch.cuda.current_stream().cuda_stream
+
+
+def midpoint_confocal(nx, ny, nt, bin_width_s, wall_width_m, laser_xy, tau_nc_ptr, tau_c_ptr, stream=0):
+    """nlos_midpoint_confocal: confocal transients at the midpoints of the detector grid and the laser point
+    from non-confocal ones (device pointers, [nx][ny][nt] float32); the result is a confocal scan of wall
+    width wall_width_m / 2 centred at laser_xy / 2."""
+    check(load().nlos_midpoint_confocal(int(nx), int(ny), int(nt), float(bin_width_s), float(wall_width_m),
+                                        float(laser_xy[0]), float(laser_xy[1]), tau_nc_ptr, tau_c_ptr, stream))
+
+
+def midpoint_confocal_t(tau_nc, bin_width_s, wall_width_m, laser_xy):
+    """Torch convenience: tau_nc a [nx][ny][nt] float32 CUDA tensor; returns the converted tensor."""
+    import torch
+    out = torch.empty_like(tau_nc)
+    nx, ny, nt = tau_nc.shape
+    midpoint_confocal(nx, ny, nt, bin_width_s, wall_width_m, laser_xy, tau_nc.data_ptr(), out.data_ptr(), _stream())
+    return out
 
 
 def forward_t(plan, u, apply_mask=False):
