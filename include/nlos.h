@@ -319,10 +319,10 @@ nlos_status nlos_solve_static(int32_t nx, int32_t ny, int32_t nt, const float* r
  * sqrt(t_k^2 + |s_ij - laser|^2 / c^2), exact for scatterers on the wall
  * normal through the midpoint, by two-tap linear interpolation between bin
  * centres (zero past the last bin); the amplitude is not changed.  The tap
- * positions are computed in FP64 without fused operations, the
- * interpolation in FP32.
+ * positions are accurate to about 1e-11 bins (FP32 with a compensated square
+ * root), the interpolation is FP32.
  *
- * nx, ny, nt powers of two >= 2; bin_width_s > 0, wall_width_m > 0, finite
+ * nx, ny, nt powers of two >= 2, nt <= 2048; bin_width_s > 0, wall_width_m > 0, finite
  * laser coordinates; the buffers 4-byte aligned and not overlapping
  * (NLOS_ERR_INVALID_ARG otherwise).  The caller owns both buffers.  Queued
  * on `stream`, no host synchronisation, no allocation. */
