@@ -381,8 +381,8 @@ def cpu_baseline(cfg, tau0_h, mask, max_steps=1, budget_s=100.0, warmup=0):
     from oracle import admm, lct
     g = lct.Geometry(cfg["nx"], cfg["ny"], cfg["nt"], cfg["bin_width_s"])
     op = lct.Operator(g, mask)
-    for _ in range(warmup):
-        admm.alg1(tau0_h, mask, g, cfg["a"], cfg["b"], cfg["mu"], 1, L0=1.0, op=op)
+    for _ in range(warmup):  # bounded warm-up steps: one adjoint operator application each
+        op.adjoint_d(tau0_h)
     times = []
     t_start = time.perf_counter()
     while len(times) < max_steps:
@@ -394,7 +394,8 @@ def cpu_baseline(cfg, tau0_h, mask, max_steps=1, budget_s=100.0, warmup=0):
     per = statistics.median(times)
     return {"value": round(1.0 / per, 5), "unit": "iter/s", "cores": 1, "kind": "oracle",
             "sample": f"{len(times)} Algorithm-1 iteration(s) of the FP64 NumPy oracle at 128x128x512 "
-                      f"(median {per:.1f} s each; numpy.fft single-threaded), host cores available: {os.cpu_count()}"}
+                      f"(median {per:.1f} s each; numpy.fft single-threaded) after {warmup} warm-up step(s) of one "
+                      f"adjoint operator application each, host cores available: {os.cpu_count()}"}
 
 
 def run_reference(args):
@@ -406,12 +407,11 @@ def run_reference(args):
     g = lct.Geometry(cfg["nx"], cfg["ny"], cfg["nt"], cfg["bin_width_s"])
     sig = lct.Operator(g, mask).forward_d(vol)
     tau0_h = synth.poisson_measurement(sig, mask, cfg["peak"], cfg["background"], seed=100)
-    cb = cpu_baseline(cfg, tau0_h, mask, max_steps=max(1, args.steps), budget_s=150.0,
-                      warmup=min(args.warmup, 1))
+    cb = cpu_baseline(cfg, tau0_h, mask, max_steps=max(1, args.steps), budget_s=150.0, warmup=args.warmup)
     steps = int(cb["sample"].split()[0])
     value = cb["value"]
     return {"metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": steps,
-            "warmup": min(args.warmup, 1), "ms_per_step": round(1e3 / value, 1), "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": round(1e3 / value, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": round(value / PAPER_ITER_PER_S, 4), "dtype": "f64",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": "alg1_128x128x512_16ps_32x32_sampled", "nx": cfg["nx"], "ny": cfg["ny"],
