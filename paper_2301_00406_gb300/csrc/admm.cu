@@ -277,45 +277,6 @@ __global__ void __launch_bounds__(kStencilThreads)
   block_reduce_acc(ca, partials);
 }
 
-// Algorithm 2, elementwise part of the post step: Lambda_3 += mu3 (f - tau+),
-// partials 0 = (A u+ - tau+)^2, 1 = M (tau+ - tau0)^2, 2 = (f - tau+)^2.
-// Four consecutive t of one column per item (16-byte loads; nt is a
-// multiple of 4 and the arrays 16-byte aligned).
-__global__ void __launch_bounds__(kStencilThreads)
-    k_lam3(const float* __restrict__ tnew, const float* __restrict__ tb, const float* __restrict__ au,
-           const float* __restrict__ tau0, float* __restrict__ lam3, const int32_t* __restrict__ colpos, Vox g,
-           VoxIter vi, float lam_w, float mu3, size_t V, double* __restrict__ partials) {
-  const float inv_d1 = 1.0f / (lam_w + mu3), inv_d0 = 1.0f / mu3;  // lambda M + mu3, M = 1 or 0
-  SumAcc<3> ca;
-  const size_t V4 = V / 4;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V4; i += (size_t)gridDim.x * blockDim.x) {
-    int x, y, t;
-    vi.decode(4 * i, g, x, y, t);
-    const bool sampled = colpos ? __ldg(colpos + x * g.ny + y) >= 0 : true;
-    const float m = sampled ? 1.0f : 0.0f, inv_d = sampled ? inv_d1 : inv_d0;
-    const float4 t0 = __ldg(reinterpret_cast<const float4*>(tau0) + i);
-    const float4 tn = __ldg(reinterpret_cast<const float4*>(tnew) + i);
-    const float4 tbv = __ldg(reinterpret_cast<const float4*>(tb) + i);
-    const float4 auv = __ldg(reinterpret_cast<const float4*>(au) + i);
-    float4 l3 = reinterpret_cast<const float4*>(lam3)[i];
-    auto one = [&](float t0e, float tne, float tbe, float aue, float& l3e) {
-      const float f = (lam_w * m * t0e + mu3 * tbe - l3e) * inv_d;
-      l3e = l3e + mu3 * (f - tne);
-      const float r = aue - tne, sres = m * (tne - t0e), fr = f - tne;
-      ca.add(0, r * r);
-      ca.add(1, sres * sres);
-      ca.add(2, fr * fr);
-    };
-    one(t0.x, tn.x, tbv.x, auv.x, l3.x);
-    one(t0.y, tn.y, tbv.y, auv.y, l3.y);
-    one(t0.z, tn.z, tbv.z, auv.z, l3.z);
-    one(t0.w, tn.w, tbv.w, auv.w, l3.w);
-    reinterpret_cast<float4*>(lam3)[i] = l3;
-  }
-  block_reduce_acc(ca, partials);
-}
-
-
 // ---------------------------------------------------------------------------
 // Scalar kernels (one thread)
 // ---------------------------------------------------------------------------
@@ -421,12 +382,13 @@ __global__ void __launch_bounds__(kSumThreads)
 
 // End of an Algorithm-2 iteration from the partials of the split post step
 // (u: phi|grad u|, |v - grad u|^2; tau: phi|grad tau|, |w - grad tau|^2;
-// elementwise: (A u - tau)^2, M (tau - tau0)^2, (f - tau)^2).
+// elementwise, terms t3 .. t3 + 2 of p3: (A u - tau)^2, M (tau - tau0)^2,
+// (f - tau)^2).
 __global__ void __launch_bounds__(kSumThreads)
     k_finalize2(DevScalars* sc, const double* __restrict__ pu, int nbu, const double* __restrict__ pt, int nbt,
-                const double* __restrict__ p3, int nb3, double lam_w, int restart, double eps_stop) {
+                const double* __restrict__ p3, int nb3, int t3, double lam_w, int restart, double eps_stop) {
   const int t01[2] = {0, 1};
-  const int t012[3] = {0, 1, 2};
+  const int t012[3] = {t3, t3 + 1, t3 + 2};
   double u[2], t[2], e3[3];
   sum_partials_block<2>(pu, nbu, t01, u);
   sum_partials_block<2>(pt, nbt, t01, t);
@@ -722,7 +684,8 @@ static void swap_ptr(T*& a, T*& b) {
 nlos_status prepare_stencils() {
   NLOS_TRY(ensure_smem(k_pre1_pipe<false>, kPre1PipeSmem));
   NLOS_TRY(ensure_smem(k_pre1_pipe<true>, kPre1PipeSmem));
-  NLOS_TRY(ensure_smem(k_post1_pipe, kPost1PipeSmem));
+  NLOS_TRY(ensure_smem(k_post1_pipe<false>, kPost1PipeSmem));
+  NLOS_TRY(ensure_smem(k_post1_pipe<true>, kPost1PipeSmem));
   return NLOS_OK;
 }
 
@@ -1016,9 +979,9 @@ static nlos_status step_alg1(JobRun& j) {
   NLOS_TRY(u_step(P, s, ua, host_check, &j.L_host, j.bt_stream, st));
   { KTimer kt_(P, KC_POST, st);
   if (tiled)
-    k_post1_pipe<<<post_grid, kTileThreads, kPost1PipeSmem, st>>>(s->unew, s->uk, s->ub, s->lam, s->ph, s->ubn,
-                                                                  s->sc, g, ntiles, (float)p.mu, (float)p.a,
-                                                                  (float)p.b, p.phi, eps2, V, s->pc);
+    k_post1_pipe<false><<<post_grid, kTileThreads, kPost1PipeSmem, st>>>(
+        s->unew, s->uk, s->ub, s->lam, s->ph, s->ubn, s->sc, g, ntiles, (float)p.mu, (float)p.a, (float)p.b, p.phi,
+        eps2, V, s->pc, L3Term{});
   else
     k_post1<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->unew, s->uk, s->ub, s->lam, s->ph, s->ubn, s->sc, g, vi,
                                                         (float)p.mu, (float)p.a, (float)p.b, p.phi, eps2, V, s->pc);
@@ -1073,21 +1036,21 @@ static nlos_status step_alg2(JobRun& j) {
   NLOS_TRY(launch_sxy(P, P.d_Sp, nullptr, 1.0 + p.mu3, p.mu2, st));
   NLOS_TRY(launch_sinv(P, P.d_Sp, full, s->tnew, nullptr, nullptr, nullptr, st));
   if (tiled) {
-    // u and tau halves of the post step, then the elementwise Lambda_3 part;
-    // the u-step partial buffers (pa, pb) are free again at this point
+    // u and tau halves of the post step; the tau half also does the
+    // elementwise Lambda_3 part.  The u-step partial buffer pa is free again
+    // at this point.
     { KTimer kt_(P, KC_POST, st);
-    k_lam3<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->tnew, s->tb, s->cache[j.nxt], j.tau0, s->lam3, colpos, g,
-                                                       vi, (float)p.lambda, (float)p.mu3, V, s->pb);
-    k_post1_pipe<<<post_grid, kTileThreads, kPost1PipeSmem, st>>>(s->unew, s->uk, s->ub, s->lam, s->ph, s->ubn,
-                                                                  s->sc, g, ntiles, (float)p.mu1, (float)p.a_u,
-                                                                  (float)p.b_u, p.phi, c.eps2, V, s->pc);
-    k_post1_pipe<<<post_grid, kTileThreads, kPost1PipeSmem, st>>>(s->tnew, s->tk, s->tb, s->lam2, s->pht, s->tbn,
-                                                                  s->sc, g, ntiles, (float)p.mu2, (float)p.a_tau,
-                                                                  (float)p.b_tau, p.phi, c.eps2, V, s->pa);
+    k_post1_pipe<false><<<post_grid, kTileThreads, kPost1PipeSmem, st>>>(
+        s->unew, s->uk, s->ub, s->lam, s->ph, s->ubn, s->sc, g, ntiles, (float)p.mu1, (float)p.a_u, (float)p.b_u,
+        p.phi, c.eps2, V, s->pc, L3Term{});
+    const L3Term l3{j.tau0, s->cache[j.nxt], s->lam3, colpos, (float)p.lambda, (float)p.mu3};
+    k_post1_pipe<true><<<post_grid, kTileThreads, kPost1PipeSmem, st>>>(
+        s->tnew, s->tk, s->tb, s->lam2, s->pht, s->tbn, s->sc, g, ntiles, (float)p.mu2, (float)p.a_tau,
+        (float)p.b_tau, p.phi, c.eps2, V, s->pa, l3);
     }
     NLOS_LAUNCH_CHECK("k_post2");
     { KTimer kt_(P, KC_SMALL, st);
-    k_finalize2<<<1, kSumThreads, 0, st>>>(s->sc, s->pc, post_grid, s->pa, post_grid, s->pb, kStencilBlocks,
+    k_finalize2<<<1, kSumThreads, 0, st>>>(s->sc, s->pc, post_grid, s->pa, post_grid, s->pa, post_grid, 2,
                                            p.lambda, j.restart, p.eps_stop);
     }
     NLOS_LAUNCH_CHECK("k_finalize2");

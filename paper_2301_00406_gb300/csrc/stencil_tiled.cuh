@@ -114,14 +114,29 @@ constexpr int kPostU = 3 * kUH * kP, kPostB = 3 * kRH * kP, kPostI = 2 * 5 * kTY
 static_assert(kPostU % 4 == 0 && kPostB % 4 == 0, "staging regions must keep 16-byte alignment");
 constexpr size_t kPost1PipeSmem = sizeof(float) * (kPostU + kPostB + kPostI + 3 * kRH * kRW);
 
+// The elementwise Lambda_3 part of Algorithm 2's multiplier update, done by
+// the tau half of the post step (u+ there is tau+, ubar is tau-bar):
+// f = (lambda M tau0 + mu3 tau-bar - Lambda_3) / (lambda M + mu3),
+// Lambda_3 += mu3 (f - tau+).
+struct L3Term {
+  const float* tau0;
+  const float* au;  // A u+
+  float* lam3;
+  const int32_t* colpos;  // nullptr: every column sampled
+  float lam_w, mu3;
+};
+
 // lam += mu (v - grad u+), phi = phi(kappa(u+)), ubar_next = u+ + beta (u+ - u^k)
 // (Algorithm 1); partials 0 = sum phi |grad u+|, 1 = sum |v - grad u+|^2,
-// v = shrink(grad ubar - lam/mu, phi/mu).
+// v = shrink(grad ubar - lam/mu, phi/mu).  With L3 also the Lambda_3 update
+// above and partials 2 = sum (A u+ - tau+)^2, 3 = sum M (tau+ - tau0)^2,
+// 4 = sum (f - tau+)^2.
+template <bool L3>
 __global__ void __launch_bounds__(kTileThreads, 2)
     k_post1_pipe(const float* __restrict__ unew, const float* __restrict__ uk, const float* __restrict__ ub,
                  float* __restrict__ lam, float* __restrict__ ph, float* __restrict__ ubn,
                  const DevScalars* __restrict__ sc, Vox g, int nsteps, float mu, float a, float b, int kind,
-                 float eps2, size_t V, double* __restrict__ partials) {
+                 float eps2, size_t V, double* __restrict__ partials, L3Term l3) {
   extern __shared__ float4 smem_f4[];
   float* U = reinterpret_cast<float*>(smem_f4);
   float* B = U + kPostU;
@@ -131,7 +146,9 @@ __global__ void __launch_bounds__(kTileThreads, 2)
   const float inv_mu = 1.0f / mu;
   const float beta = (float)sc->beta;
   const float* ifields[5] = {lam, lam + V, lam + 2 * V, ph, uk};
-  SumAcc<2> ca;
+  // 1 / (lambda M + mu3) for M = 1 and M = 0
+  const float l3_d1 = L3 ? 1.0f / (l3.lam_w + l3.mu3) : 0.0f, l3_d0 = L3 ? 1.0f / l3.mu3 : 0.0f;
+  SumAcc<L3 ? 5 : 2> ca;
   int cur, end;
   block_share(nsteps, cur, end);
   while (cur < end) {
@@ -169,6 +186,20 @@ __global__ void __launch_bounds__(kTileThreads, 2)
       const float* Bx = B + (s % 3) * kRH * kP;
       const float* Bn = B + ((s + 1) % 3) * kRH * kP;
       const float* Ix = I + (s & 1) * 5 * kTY * kTT;
+      // the Lambda_3 inputs of this row, loaded now so their latency overlaps
+      // the region pass below
+      float l3_t0[4], l3_au[4], l3_l[4];
+      bool l3_sampled = true;
+      if (L3) {
+        l3_sampled = l3.colpos ? __ldg(l3.colpos + x * g.ny + y) >= 0 : true;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const size_t gi = g.idx(x, y, T.t0 + lane + 32 * j);
+          l3_t0[j] = __ldg(l3.tau0 + gi);
+          l3_au[j] = __ldg(l3.au + gi);
+          l3_l[j] = l3.lam3[gi];
+        }
+      }
       // normals over the region: point (yy, tt) is voxel (y0 - 1 + yy, t0 - 1 + tt)
       for (int i = threadIdx.x; i < kRH * kRW; i += kTileThreads) {
         const int yy = i / kRW, tt = i - yy * kRW;
@@ -207,6 +238,15 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         ubn[gi] = uc + beta * (uc - Ix[4 * kTY * kTT + ii]);
         ca.add(0, pn * sqrtf(gu.x * gu.x + gu.y * gu.y + gu.z * gu.z));
         ca.add(1, d.x * d.x + d.y * d.y + d.z * d.z);
+        if (L3) {
+          const float m = l3_sampled ? 1.0f : 0.0f;
+          const float f = (l3.lam_w * m * l3_t0[j] + l3.mu3 * bc - l3_l[j]) * (l3_sampled ? l3_d1 : l3_d0);
+          l3.lam3[gi] = l3_l[j] + l3.mu3 * (f - uc);
+          const float r = l3_au[j] - uc, sres = m * (uc - l3_t0[j]), fr = f - uc;
+          ca.add(2, r * r);
+          ca.add(3, sres * sres);
+          ca.add(4, fr * fr);
+        }
       }
       __syncthreads();
     }
