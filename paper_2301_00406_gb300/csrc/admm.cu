@@ -703,6 +703,9 @@ struct UStepArgs {
   float* au_out;       // cache slot receiving A u+
   const float* auk;
   const float* aukm1;
+  // model 2: the tau-solve regulariser term; the fit pass then also writes
+  // the periodic t-spectrum of A u+ + tau_reg to d_Sp (the tau-solve rhs)
+  const float* tau_reg = nullptr;
 };
 
 // Helpers for conditional nodes added during a stream capture.
@@ -772,7 +775,7 @@ static nlos_status u_trial(Plan& P, SolverState* s, const UStepArgs& a, int* nbd
   } else {
     NLOS_TRY(launch_conv(P, P.d_S2, false, P.d_S2, false, false, st));
   }
-  FitArgs fa{a.data, a.auk, a.aukm1, s->sc, s->pb};
+  FitArgs fa{a.data, a.auk, a.aukm1, s->sc, s->pb, a.tau_reg, a.tau_reg ? P.d_Sp : nullptr};
   NLOS_TRY(launch_tinv_fit(P, Sfit, ncols, ncols, a.au_out, fa, nbf, st));
   return NLOS_OK;
 }
@@ -1028,11 +1031,11 @@ static nlos_status step_alg2(JobRun& j) {
   NLOS_TRY(launch_tfwd_rtt(P, r, full, P.d_S, full, st));
   NLOS_TRY(launch_conv(P, P.d_S, false, P.d_S, false, true, st));
   const bool host_check = j.L_host < 1.5 * j.norm2;
+  // the fit pass of the u-step also leaves the t-spectrum of the tau-solve
+  // rhs, A u+ + regt, in d_Sp
   UStepArgs ua{s->reg, p.mu1, false, s->tb, p.eta, p.max_backtracks, s->cache[j.nxt], s->cache[j.cur],
-               s->cache[j.prev]};
+               s->cache[j.prev], s->regt};
   NLOS_TRY(u_step(P, s, ua, host_check, &j.L_host, j.bt_stream, st));
-  // rhs of the tau solve: A u+ + regt, summed as the periodic t-FFT loads it
-  NLOS_TRY(launch_sfwd(P, s->cache[j.nxt], full, P.d_Sp, st, s->regt));
   NLOS_TRY(launch_sxy(P, P.d_Sp, nullptr, 1.0 + p.mu3, p.mu2, st));
   NLOS_TRY(launch_sinv(P, P.d_Sp, full, s->tnew, nullptr, nullptr, nullptr, st));
   if (tiled) {

@@ -22,6 +22,10 @@ struct FitArgs {
   const float* aukm1;  // [cols][nt] A u^{k-1} (cache)
   const DevScalars* sc;
   double* partials;    // [gridDim][kMaxTerms]: 0 = sum (A u - data)^2, 1 = sum (A u - A u-bar)^2
+  // optional (full columns only): Sp receives the periodic t-spectrum of
+  // A u + x2, the right-hand side of Algorithm 2's tau solve
+  const float* x2 = nullptr;
+  float2* Sp = nullptr;
 };
 
 // Solve-mode arguments of the adjoint end pass: rhs = c0 * ubar - grad f + reg.

@@ -417,8 +417,30 @@ __global__ void __launch_bounds__(kTpassThreads)
   tfwd_from_cbuf<NT, MODE>(cbuf, tab, work, tw2, COLS, hb, S, pitch, col0, ncols, tid, nthr);
 }
 
+// Hermitian split of the periodic forward FFT of the CTA's packed pairs:
+// bins k <= nt / 2 of both columns of every pair, stored to Sp [k][column].
+template <int NT>
+__device__ __forceinline__ void periodic_fwd_post(const float2* work, const int* fp, float2* Sp, int col0, int ncols,
+                                                  int pitch, int COLS, int tid, int nthr) {
+  const int PAIRS = COLS >> 1;
+  const WorkAddr<NT> wa{work_pitch<NT>(PAIRS)};
+  const int lp = __ffs(PAIRS) - 1;  // PAIRS is a power of two
+  const bool even_pitch = (pitch & 1) == 0;
+  for (int i = tid; i < (NT / 2 + 1) * PAIRS; i += nthr) {
+    const int k = i >> lp, p = i & (PAIRS - 1);
+    const int ca = col0 + 2 * p;
+    if (ca >= ncols) continue;
+    const float2 za = work[p * wa.pitch + fp[k]];
+    const float2 zb = work[p * wa.pitch + fp[(NT - k) & (NT - 1)]];
+    store_pair(Sp + (size_t)k * pitch, ca, ncols, even_pitch, za, zb);
+  }
+}
+
 // ---------------------------------------------------------------------------
-// Forward t-inverse: C2R, crop, R_t^{-1}; store or fit epilogue.
+// Forward t-inverse: C2R, crop, R_t^{-1}; store (EPI 0) or fit epilogue
+// (EPI 1).  EPI 2 is the fit epilogue that also forms A u + fa.x2 in the
+// packed-pair layout and runs its periodic forward FFT into fa.Sp (the
+// tau-solve rhs of Algorithm 2).
 // ---------------------------------------------------------------------------
 template <int NT, int EPI>
 __global__ void __launch_bounds__(kTpassThreads)
@@ -442,24 +464,27 @@ __global__ void __launch_bounds__(kTpassThreads)
 
   SumAcc<2> ca;
   float bp = 0.f;
-  if (EPI == 1) bp = (float)fa.sc->beta_prev;
+  if (EPI >= 1) bp = (float)fa.sc->beta_prev;
   const int total4 = min(COLS, ncols - col0) * (NT / 4);
   // four consecutive bins of one column per item (16-byte loads and store;
   // nt is a multiple of 4 and every array 16-byte aligned).  ld: the data,
   // A u^k and A u^{k-1} samples (fit epilogue only); st: resample, store and
   // accumulate
   struct In4 {
-    float4 d, a, b;
+    float4 d, a, b, x2;
   };
+  constexpr bool fuse = EPI == 2;  // tau-solve rhs spectrum as well
+  const WorkAddr<NT> wp{work_pitch<NT>(PAIRS)};    // layout of that periodic FFT
   batched_copy<2, In4>(
       total4, tid, nthr,
       [&](int i) {
         In4 v;
-        if (EPI == 1) {
+        if (EPI >= 1) {
           const size_t g4 = (size_t)col0 * (NT / 4) + i;
           v.d = __ldg(reinterpret_cast<const float4*>(fa.data) + g4);
           v.a = __ldg(reinterpret_cast<const float4*>(fa.auk) + g4);
           v.b = __ldg(reinterpret_cast<const float4*>(fa.aukm1) + g4);
+          if (fuse) v.x2 = __ldg(reinterpret_cast<const float4*>(fa.x2) + g4);
         }
         return v;
       },
@@ -475,7 +500,7 @@ __global__ void __launch_bounds__(kTpassThreads)
         }
         const int oc = outmap ? __ldg(outmap + col0 + c) : col0 + c;
         *reinterpret_cast<float4*>(out + (size_t)oc * NT + k) = make_float4(tau[0], tau[1], tau[2], tau[3]);
-        if (EPI == 1) {
+        if (EPI >= 1) {
           const float dd[4] = {in.d.x, in.d.y, in.d.z, in.d.w};
           const float aa[4] = {in.a.x, in.a.y, in.a.z, in.a.w};
           const float bb[4] = {in.b.x, in.b.y, in.b.z, in.b.w};
@@ -486,10 +511,28 @@ __global__ void __launch_bounds__(kTpassThreads)
             ca.add(0, r * r);
             ca.add(1, d * d);
           }
+          if (fuse) {
+            // A u + x2 of column c into its packed pair (column 2p real, 2p + 1 imaginary)
+            const float xx[4] = {in.x2.x, in.x2.y, in.x2.z, in.x2.w};
+            float* wf = reinterpret_cast<float*>(work);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) wf[2 * wp(c >> 1, k + e) + (c & 1)] = tau[e] + xx[e];
+          }
         }
       });
-  if (EPI == 1) {
+  if (EPI >= 1) {
     block_reduce_acc(ca, fa.partials);
+  }
+  if (fuse) {
+    // a missing partner column (ragged last CTA) transforms as zero
+    const int valid = min(COLS, ncols - col0);
+    if (valid & 1) {
+      float* wf = reinterpret_cast<float*>(work);
+      for (int n = tid; n < NT; n += nthr) wf[2 * wp(valid >> 1, n) + 1] = 0.0f;
+    }
+    __syncthreads();
+    team_fft_a<NT, false>(work, PAIRS, wp, tw2, 2, tid, nthr);
+    periodic_fwd_post<NT>(work, tw2.fp, fa.Sp, col0, ncols, ncols, COLS, tid, nthr);
   }
 }
 
@@ -497,23 +540,6 @@ __global__ void __launch_bounds__(kTpassThreads)
 // Adjoint end: C2R, crop, R_z^T.  MODE 0 stores g; MODE 1 forms the solve
 // right-hand side rhs = L u-bar - g + reg and runs the periodic real FFT.
 // ---------------------------------------------------------------------------
-template <int NT>
-__device__ __forceinline__ void periodic_fwd_post(const float2* work, const int* fp, float2* Sp, int col0, int ncols,
-                                                  int pitch, int COLS, int tid, int nthr) {
-  const int PAIRS = COLS >> 1;
-  const WorkAddr<NT> wa{work_pitch<NT>(PAIRS)};
-  const int lp = __ffs(PAIRS) - 1;  // PAIRS is a power of two
-  const bool even_pitch = (pitch & 1) == 0;
-  for (int i = tid; i < (NT / 2 + 1) * PAIRS; i += nthr) {
-    const int k = i >> lp, p = i & (PAIRS - 1);
-    const int ca = col0 + 2 * p;
-    if (ca >= ncols) continue;
-    const float2 za = work[p * wa.pitch + fp[k]];
-    const float2 zb = work[p * wa.pitch + fp[(NT - k) & (NT - 1)]];
-    store_pair(Sp + (size_t)k * pitch, ca, ncols, even_pitch, za, zb);
-  }
-}
-
 template <int NT, int MODE>
 __global__ void __launch_bounds__(kTpassThreads)
     k_tadj(const float2* __restrict__ S, int pitch, int ncols, float* __restrict__ out, SolveRhs sr,
@@ -835,7 +861,7 @@ template <int NT>
 nlos_status TpassOps<NT>::tinv_fit(const Plan& P, const float2* S, int pitch, int ncols, float* out,
                                    const FitArgs& fa, int* nblocks, cudaStream_t st) {
   KTimer kt_(P, KC_TINV, st);
-  auto kern = k_tinv<NT, 1>;
+  auto kern = fa.Sp ? k_tinv<NT, 2> : k_tinv<NT, 1>;
   const TpShape sh = tp_shape<NT>(ncols, 1, true, TPK_TINV_FIT, true);
   NLOS_TRY(set_smem_tp(kern, sh.smem));
   if (sh.blocks > P.partial_blocks) return fail(NLOS_ERR_INVALID_ARG, "partials buffer too small");
@@ -922,6 +948,7 @@ nlos_status TpassOps<NT>::prepare() {
   NLOS_TRY(set_smem_tp(k_tfwd<NT, 1>, m1));
   NLOS_TRY(set_smem_tp(k_tinv<NT, 0>, m1));
   NLOS_TRY(set_smem_tp(k_tinv<NT, 1>, m1));
+  NLOS_TRY(set_smem_tp(k_tinv<NT, 2>, m1));
   NLOS_TRY(set_smem_tp(k_tadj<NT, 0>, m1));
   NLOS_TRY(set_smem_tp(k_tadj<NT, 1>, m1));
   NLOS_TRY(set_smem_tp(k_sfwd<NT>, m0));
