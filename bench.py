@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-system", action="store_true",
+                    help="skip the short batched and served runs of the default line's `system` key")
     ap.add_argument("--ops", action="store_true",
                     help="only apply the forward and adjoint operators --steps times (for profiler captures)")
     ap.add_argument("--workload", default="headline", choices=["headline", "batch16", "serve"],
@@ -369,9 +371,36 @@ def run_ours(args):
                       "recon_per_s_at_50_iters": round(value / 50.0, 3),
                       "alg1_energy_last": stats["energy"]},
     }
+    if world == 1 and not args.no_system:
+        out["system"] = system_summary(args)
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(cfg, tau0_h, mask, max_steps=1)
     return out
+
+
+def system_summary(args):
+    """The batched and served forms beside the one-scene numbers: the 16-scene
+    batch against its sequential run, and 10 s of Poisson arrivals at 20 jobs/s
+    through the server (4 jobs at once, contexts prepared before the arrivals).
+    A failure here is reported in the line, not raised."""
+    res = {}
+    try:
+        b = run_batch16(args)
+        res["batch16"] = {k: b[k] for k in ("value", "unit", "batched_s", "sequential_s", "speedup_vs_sequential",
+                                            "results_identical_to_sequential")}
+    except Exception as e:  # noqa: BLE001
+        res["batch16"] = {"error": f"{type(e).__name__}: {e}"}
+    try:
+        sa = argparse.Namespace(**vars(args))
+        sa.duration, sa.rate, sa.slots, sa.prewarm, sa.budget_gb = 10.0, 20.0, 4, 2, 0.0
+        v = run_serve(sa)
+        res["serve"] = {k: v[k] for k in ("p50_s", "p99_s", "max_s", "mean_queue_s", "jobs", "throughput_jobs_per_s",
+                                          "prewarm")}
+        res["serve"]["config"] = "10 s of Poisson arrivals at 20/s, 64^2 or 128^2 x 512 grids, 3 samplings, " \
+                                 "Algorithm 1 or 2, 50 iterations, 4 jobs at once"
+    except Exception as e:  # noqa: BLE001
+        res["serve"] = {"error": f"{type(e).__name__}: {e}"}
+    return res
 
 
 # ---------------------------------------------------------------------------
