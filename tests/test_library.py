@@ -96,3 +96,32 @@ def test_params_default_match_paper(nlos):
         gp["alg2_lambda_8x8"], gp["alg2_a_u_8x8"], gp["alg2_b_u_8x8"], gp["alg2_a_tau_8x8"], gp["alg2_b_tau_8x8"])
     with pytest.raises(nlos.NlosError):
         nlos.params_default(3)
+
+
+def test_midpoint_conversion_validates_before_any_device_work(nlos):
+    # every rejection happens on the host, before a launch: no GPU is needed
+    buf_a, buf_b = 1 << 20, 1 << 30          # fake, 16-byte aligned, disjoint device addresses
+    bad = [
+        dict(nx=8, ny=8, nt=60),              # nt not a power of two
+        dict(nx=6, ny=8, nt=64),              # nx not a power of two
+        dict(nx=8, ny=8, nt=4096),            # nt above 2048
+        dict(bin_width_s=0.0), dict(bin_width_s=float("inf")), dict(wall_width_m=-1.0),
+        dict(laser=(float("nan"), 0.0)),
+        dict(src=0), dict(dst=buf_a + 4),     # null input; output overlapping the input
+        dict(dst=buf_b + 2),                  # misaligned output
+    ]
+    for b in bad:
+        a = dict(nx=8, ny=8, nt=64, bin_width_s=32e-12, wall_width_m=1.0, laser=(0.0, 0.0), src=buf_a, dst=buf_b)
+        a.update(b)
+        with pytest.raises(nlos.NlosError) as e:
+            nlos.midpoint_confocal(a["nx"], a["ny"], a["nt"], a["bin_width_s"], a["wall_width_m"], a["laser"],
+                                   a["src"], a["dst"])
+        assert e.value.status == -1, b
+
+
+def test_server_prepare_validates_arguments(nlos):
+    # argument checks of nlos_server_prepare need no device either
+    lib = nlos.load()
+    p = nlos.params_default(1)
+    g, _keep = nlos._geometry(8, 8, 64, 32e-12, 1.0, "compensated", None)
+    assert lib.nlos_server_prepare(None, ctypes.byref(g), ctypes.byref(p), 1, 1.0, None) == -1
