@@ -21,10 +21,14 @@
  *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
  *    stream.  Work is queued on that stream without host synchronisation
  *    unless the function says otherwise.
- *  - Sizes: nx, ny are powers of two in [8, 128]; nt is a power of two in
- *    [16, 1024].  Other sizes return NLOS_ERR_INVALID_ARG.
+ *  - Sizes of plans (and of everything that takes a geometry): nx, ny are
+ *    powers of two in [8, 128]; nt is a power of two in [16, 1024].  Other
+ *    sizes return NLOS_ERR_INVALID_ARG.  nlos_solve_static and
+ *    nlos_midpoint_confocal state their own limits.
  *  - A plan is not thread-safe: serialise calls that use the same plan.
- *    Server entry points (nlos_submit, nlos_poll) are thread-safe.
+ *    The server entry points other than create and destroy (nlos_submit,
+ *    nlos_poll, nlos_wait, nlos_job_times, nlos_server_info,
+ *    nlos_server_prepare) are thread-safe.
  */
 #ifndef NLOS_H
 #define NLOS_H
