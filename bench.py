@@ -46,6 +46,8 @@ def parse():
                     help="skip the short batched and served runs of the default line's `system` key")
     ap.add_argument("--ops", action="store_true",
                     help="only apply the forward and adjoint operators --steps times (for profiler captures)")
+    ap.add_argument("--lateral", type=int, default=0,
+                    help="ops: lateral stage of the plan (0 FFT kernels, 1 split-BF16 GEMMs, 2 BF16 GEMMs)")
     ap.add_argument("--workload", default="headline", choices=["headline", "batch16", "serve"],
                     help="headline: one 128x128x512 scene; batch16: 16 mixed scenes batched vs one by one; "
                          "serve: Poisson-arrival stream through the server")
@@ -450,17 +452,37 @@ def run_reference(args):
 
 
 def run_ops(args):
-    """Forward and adjoint operator applications only (few launches)."""
+    """Forward and adjoint operator applications only (few launches), then the
+    time of the unmasked forward operator A and of its lateral stage (CUDA
+    events: 3 warm-up calls, 10 timed; then 10 calls with per-kernel timing),
+    with the plan's lateral stage set by --lateral."""
     import torch
     from paper_2301_00406_gb300 import nlos
     cfg, vol, mask = make_inputs(seed=0)
     plan = nlos.Plan(cfg["nx"], cfg["ny"], cfg["nt"], cfg["bin_width_s"], mask=mask)
+    if args.lateral:
+        plan.set_lateral(args.lateral)
     u = torch.tensor(vol, dtype=torch.float32, device="cuda")
     for _ in range(args.steps):
         tau = nlos.forward_t(plan, u, apply_mask=True)
         u = nlos.adjoint_t(plan, tau, apply_mask=True)
     torch.cuda.synchronize()
-    return {"ops": args.steps, "checksum": float(u.double().sum().item())}
+    x = torch.tensor(vol, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        nlos.forward_t(plan, x)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        nlos.forward_t(plan, x)
+    e1.record()
+    torch.cuda.synchronize()
+    plan.timing_enable(True)
+    for _ in range(10):
+        nlos.forward_t(plan, x)
+    kt = plan.timing_read()
+    plan.timing_enable(False)
+    return {"ops": args.steps, "checksum": float(u.double().sum().item()), "lateral_mode": args.lateral,
+            "forward_ms": round(e0.elapsed_time(e1) / 10, 4), "lateral_stage_ms": round(kt["k_conv"][0] / 10, 4)}
 
 
 # ---------------------------------------------------------------------------
