@@ -761,13 +761,20 @@ static nlos_status capture_body(cudaStream_t bs, cudaGraph_t body, Fn&& fn) {
 
 // One trial of the linearised u-step: solve for u+ at the current L, A u+
 // (sampled columns for model 1) and the partial sums of the test.
-static nlos_status u_trial(Plan& P, SolverState* s, const UStepArgs& a, int* nbd, int* nbf, cudaStream_t st) {
+// One trial of the u-step.  test: the backtracking rule can reject, so the
+// trial also forms the partial sums of ||d||^2 and ||A d||^2 it needs; when
+// it cannot (L >= 1.5 ||A_D||^2, the descent lemma), those terms are skipped
+// (one field pass fewer) and k_test sums no blocks for them.
+static nlos_status u_trial(Plan& P, SolverState* s, const UStepArgs& a, bool test, int* nbd, int* nbf,
+                           cudaStream_t st) {
   const int full = P.nx * P.ny;
   const int ncols = a.compact ? P.ncols : full;
   SolveRhs sr{s->ub, a.reg, s->sc, 0.0};
   NLOS_TRY(launch_tadj_solve(P, P.d_S, full, full, sr, P.d_Sp, st));
   NLOS_TRY(launch_sxy(P, P.d_Sp, s->sc, 0.0, a.mu, st));
-  NLOS_TRY(launch_sinv_rz(P, P.d_Sp, full, s->unew, s->ub, s->pa, nbd, P.d_S2, full, st));
+  NLOS_TRY(launch_sinv_rz(P, P.d_Sp, full, s->unew, test ? s->ub : nullptr, test ? s->pa : nullptr, nbd, P.d_S2,
+                          full, st));
+  if (!test) *nbd = 0;
   float2* Sfit = P.d_S2;
   if (a.compact) {
     NLOS_TRY(launch_conv(P, P.d_S2, false, P.d_Sc, true, false, st));
@@ -775,7 +782,7 @@ static nlos_status u_trial(Plan& P, SolverState* s, const UStepArgs& a, int* nbd
   } else {
     NLOS_TRY(launch_conv(P, P.d_S2, false, P.d_S2, false, false, st));
   }
-  FitArgs fa{a.data, a.auk, a.aukm1, s->sc, s->pb, a.tau_reg, a.tau_reg ? P.d_Sp : nullptr};
+  FitArgs fa{a.data, a.auk, a.aukm1, s->sc, s->pb, a.tau_reg, a.tau_reg ? P.d_Sp : nullptr, test};
   NLOS_TRY(launch_tinv_fit(P, Sfit, ncols, ncols, a.au_out, fa, nbf, st));
   return NLOS_OK;
 }
@@ -791,14 +798,14 @@ static nlos_status u_step(Plan& P, SolverState* s, const UStepArgs& a, bool host
     cudaGraphConditionalHandle redo = 0;
     NLOS_TRY(cond_handle(st, 0, 0, &redo));
     int nbd = 0, nbf = 0;
-    NLOS_TRY(u_trial(P, s, a, &nbd, &nbf, st));
+    NLOS_TRY(u_trial(P, s, a, true, &nbd, &nbf, st));
     k_test<<<1, kSumThreads, 0, st>>>(s->sc, s->pa, nbd, s->pb, nbf, a.eta, a.max_bt, 0, redo, 1);
     NLOS_LAUNCH_CHECK("k_test");
     cudaGraph_t body = nullptr;
     NLOS_TRY(add_cond_node(st, redo, cudaGraphCondTypeWhile, 1, &body));
     return capture_body(bt_stream, body, [&](cudaStream_t bs) -> nlos_status {
       int nbd2 = 0, nbf2 = 0;
-      NLOS_TRY(u_trial(P, s, a, &nbd2, &nbf2, bs));
+      NLOS_TRY(u_trial(P, s, a, true, &nbd2, &nbf2, bs));
       k_test<<<1, kSumThreads, 0, bs>>>(s->sc, s->pa, nbd2, s->pb, nbf2, a.eta, a.max_bt, 0, redo, 1);
       NLOS_LAUNCH_CHECK("k_test");
       return NLOS_OK;
@@ -806,7 +813,7 @@ static nlos_status u_step(Plan& P, SolverState* s, const UStepArgs& a, bool host
   }
   for (;;) {
     int nbd = 0, nbf = 0;
-    NLOS_TRY(u_trial(P, s, a, &nbd, &nbf, st));
+    NLOS_TRY(u_trial(P, s, a, host_check, &nbd, &nbf, st));
     { KTimer kt_(P, KC_SMALL, st);
     k_test<<<1, kSumThreads, 0, st>>>(s->sc, s->pa, nbd, s->pb, nbf, a.eta, a.max_bt, host_check ? 0 : 1, 0, 0);
     }

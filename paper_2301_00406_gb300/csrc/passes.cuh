@@ -26,6 +26,9 @@ struct FitArgs {
   // A u + x2, the right-hand side of Algorithm 2's tau solve
   const float* x2 = nullptr;
   float2* Sp = nullptr;
+  // false when the backtracking test cannot reject (its A d term is then
+  // neither loaded nor summed; partial 1 stays 0)
+  bool need_d = true;
 };
 
 // Solve-mode arguments of the adjoint end pass: rhs = c0 * ubar - grad f + reg.

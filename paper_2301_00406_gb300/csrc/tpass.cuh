@@ -482,8 +482,10 @@ __global__ void __launch_bounds__(kTpassThreads)
         if (EPI >= 1) {
           const size_t g4 = (size_t)col0 * (NT / 4) + i;
           v.d = __ldg(reinterpret_cast<const float4*>(fa.data) + g4);
-          v.a = __ldg(reinterpret_cast<const float4*>(fa.auk) + g4);
-          v.b = __ldg(reinterpret_cast<const float4*>(fa.aukm1) + g4);
+          if (fa.need_d) {
+            v.a = __ldg(reinterpret_cast<const float4*>(fa.auk) + g4);
+            v.b = __ldg(reinterpret_cast<const float4*>(fa.aukm1) + g4);
+          }
           if (fuse) v.x2 = __ldg(reinterpret_cast<const float4*>(fa.x2) + g4);
         }
         return v;
@@ -507,9 +509,11 @@ __global__ void __launch_bounds__(kTpassThreads)
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             const float r = tau[e] - dd[e];
-            const float d = tau[e] - ((1.0f + bp) * aa[e] - bp * bb[e]);
             ca.add(0, r * r);
-            ca.add(1, d * d);
+            if (fa.need_d) {
+              const float d = tau[e] - ((1.0f + bp) * aa[e] - bp * bb[e]);
+              ca.add(1, d * d);
+            }
           }
           if (fuse) {
             // A u + x2 of column c into its packed pair (column 2p real, 2p + 1 imaginary)
