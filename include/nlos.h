@@ -21,8 +21,10 @@
  *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
  *    stream.  Work is queued on that stream without host synchronisation
  *    unless the function says otherwise.
- *  - Sizes of plans (and of everything that takes a geometry): nx, ny are
- *    powers of two in [8, 128]; nt is a power of two in [16, 1024].  Other
+ *  - Sizes of plans (and of everything that takes a geometry): nx = ny, a
+ *    power of two in [8, 128] (the lateral convolution uses the symmetry of
+ *    the cone kernel's spectrum under exchange of x and y); nt is a power of
+ *    two in [16, 1024].  Other
  *    sizes return NLOS_ERR_INVALID_ARG.  nlos_solve_static and
  *    nlos_midpoint_confocal state their own limits.
  *  - A plan is not thread-safe: serialise calls that use the same plan.
@@ -141,17 +143,21 @@ nlos_status nlos_plan_destroy(nlos_plan plan);
 /* Select how the plan computes the lateral convolution of every kt plane
  * with the cone-kernel spectrum (the H of Eq. 3 and its conjugate in A^T):
  *   0  hand-written FFT kernels in FP32 (default);
- *   1  dense DFT-matrix products on the tensor cores (cuBLAS strided-batched
- *      BF16 GEMMs with FP32 accumulation on real planar operands; every
- *      operand split into hi + lo BF16 terms and the products hi hi + hi lo
- *      + lo hi summed: the split-BF16 variant of the precision comparison);
- *   2  the same GEMMs with the hi terms only (one BF16 pass).
- * Modes 1 and 2 allocate a workspace of about 144 nx^2 (nt + 1) bytes on
- * first use (freed by mode 0 or nlos_plan_destroy) and run
- * reconstructions stepped from the host, without a CUDA graph; they need
- * nx = ny.  Results are those of mode 0 within the GEMM's rounding.  Not
+ *   1  DFT-matrix products on the tensor cores (tcgen05.mma issued from a
+ *      hand-written kernel, accumulators in tensor memory): every operand
+ *      split into hi + lo BF16 terms and the products hi hi + hi lo + lo hi
+ *      accumulated in FP32 (the split-BF16 variant of the precision
+ *      comparison);
+ *   2  the same with the hi terms only (one BF16 product, FP32 accumulate).
+ * Modes 1 and 2 need nx = ny = 128.  The first non-zero mode builds the
+ * block DFT constant and a copy of the kernel spectrum rearranged for the
+ * kernel's reads (16 (nt + 1) 129 64 bytes of device memory, freed by mode 0
+ * or nlos_plan_destroy) and synchronises `stream`.  Results are those of
+ * mode 0 within the split's rounding.  Every MMA completion wait of the
+ * kernel gives up after one second; the next call of this function then
+ * returns NLOS_ERR_TIMEOUT (the output of that launch is undefined).  Not
  * thread-safe with other calls on the same plan.  Errors: invalid mode or
- * nx != ny (NLOS_ERR_INVALID_ARG), device memory (NLOS_ERR_OOM), cuBLAS
+ * size (NLOS_ERR_INVALID_ARG), device memory (NLOS_ERR_OOM), CUDA
  * (NLOS_ERR_CUDA). */
 nlos_status nlos_plan_set_lateral(nlos_plan plan, int32_t mode, void* stream);
 

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnlos.so")
-SOURCES = ["lct.cu", "xy.cu", "conv4.cu", "conv_gemm.cu", "tpass_small.cu", "tpass_256.cu", "tpass_512.cu",
+SOURCES = ["lct.cu", "xy.cu", "conv4.cu", "conv_tc.cu", "tpass_small.cu", "tpass_256.cu", "tpass_512.cu",
            "tpass_1024.cu", "admm.cu", "plan.cu", "static_solve.cu", "serve.cu", "midpoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -58,7 +58,7 @@ def build_library(force=False, verbose=False):
             sys.stderr.write(log)
     objs = [o for o, _ in results]
     tmp = LIB + ".tmp"
-    cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC", "-lcublas"]
+    cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

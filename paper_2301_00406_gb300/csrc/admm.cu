@@ -1208,7 +1208,7 @@ static nlos_status job_graph(JobRun& j, cudaStream_t st, cudaGraphExec_t* exec) 
   *exec = nullptr;
   Plan& P = *j.P;
   const nlos_params& p = j.p;
-  if (P.timing || P.lateral) return NLOS_OK;  // timed kernels, or cuBLAS lateral stage: stepped
+  if (P.timing) return NLOS_OK;  // timed kernels: stepped
   // everything that may synchronise or allocate happens before the capture
   NLOS_TRY(get_solver(P, p.model, &j.s));
   NLOS_TRY(plan_norm2(P, p.model == 1, st, &j.norm2));

@@ -164,7 +164,7 @@ __device__ __forceinline__ void block_reduce_acc(const SumAcc<T>& ca, double* pa
 // ---------------------------------------------------------------------------
 struct SolverState;  // defined in admm.cu
 
-struct LateralGemm;  // optional GEMM lateral stage (conv_gemm.cu)
+struct LateralTC;  // optional tensor-core lateral stage (conv_tc.cu)
 
 struct Plan {
   int nx, ny, nt;
@@ -235,9 +235,9 @@ struct Plan {
   // pointer-phase switch, backtracking loop)
   cudaStream_t body_stream[3] = {nullptr, nullptr, nullptr};
 
-  // lateral stage on the tensor cores as DFT-matrix GEMMs (nlos_plan_set_lateral);
-  // nullptr: the FFT kernels
-  LateralGemm* lateral = nullptr;
+  // lateral stage as DFT-matrix products on the tensor cores
+  // (nlos_plan_set_lateral); nullptr: the FFT kernels
+  LateralTC* lateral = nullptr;
 
   // optional per-launch timing (nlos_timing_enable): event pairs recorded
   // around every kernel launch on the launch stream, harvested on read.

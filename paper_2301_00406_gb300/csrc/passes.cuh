@@ -69,14 +69,18 @@ nlos_status launch_sinv_rz(const Plan& P, const float2* Sp, int ncols, float* x,
 // (the plan's sampled columns) with plane pitch ncols.
 nlos_status launch_conv(const Plan& P, const float2* Sin, bool in_compact, float2* Sout, bool out_compact,
                         bool adj, cudaStream_t st);
-// The same as DFT-matrix GEMMs on the tensor cores (plans with P.lateral set).
-nlos_status launch_conv_gemm(const Plan& P, const float2* Sin, bool in_compact, float2* Sout, bool out_compact,
-                             bool adj, cudaStream_t st);
-// Select the lateral stage: 0 FFT kernels, 1 GEMMs with BF16x9-emulated FP32,
-// 2 GEMMs with single-pass BF16 inputs (FP32 accumulate).  Allocates its
-// workspace on the first non-zero mode.
+// The same on the tensor cores (plans with P.lateral set; conv_tc.cu).
+nlos_status launch_conv_tc(const Plan& P, const float2* Sin, bool in_compact, float2* Sout, bool out_compact,
+                           bool adj, cudaStream_t st);
+// Select the lateral stage: 0 FFT kernels, 1 tcgen05 MMAs on split-BF16
+// operands (three products), 2 the same with the hi terms only.  Builds the
+// block DFT constant and the rearranged kernel spectrum on the first non-zero
+// mode (synchronises st).
 nlos_status set_lateral_mode(Plan& P, int mode, cudaStream_t st);
-void free_lateral_gemm(Plan* P);
+void free_lateral_tc(Plan* P);
+// NLOS_ERR_TIMEOUT (and the flag cleared) if a wait of the tensor-core
+// lateral kernel gave up since the last check; synchronous.
+nlos_status lateral_status(const Plan& P);
 // Four-CTA-cluster lateral convolution for nx in {32, 64, 128} (conv4.cu);
 // launch_conv dispatches to it.
 nlos_status launch_conv4(const Plan& P, const float2* Sin, bool in_compact, float2* Sout, bool out_compact,

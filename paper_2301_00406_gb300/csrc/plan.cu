@@ -196,7 +196,7 @@ static void destroy_plan(Plan* P) {
   if (!P) return;
   cudaDeviceSynchronize();
   free_workspace(P);
-  free_lateral_gemm(P);
+  free_lateral_tc(P);
   if (P->owns_tables) {
     void* ptrs[] = {P->d_rz_i0, P->d_rz_w, P->d_rzt_start, P->d_rt_k0, P->d_rt_w, P->d_rtt_start, P->d_cols,
                     P->d_colpos, P->d_tw2t, P->d_twt, P->d_twx, P->d_twy, P->d_lamx, P->d_lamy, P->d_lamt,

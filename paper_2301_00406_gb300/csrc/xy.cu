@@ -372,7 +372,7 @@ nlos_status prepare_xy(int n) {
 nlos_status launch_conv(const Plan& P, const float2* Sin, bool in_compact, float2* Sout, bool out_compact, bool adj,
                         cudaStream_t st) {
   KTimer kt_(P, KC_CONV, st);
-  if (P.lateral) return launch_conv_gemm(P, Sin, in_compact, Sout, out_compact, adj, st);
+  if (P.lateral) return launch_conv_tc(P, Sin, in_compact, Sout, out_compact, adj, st);
   if (P.nx >= 32) return launch_conv4(P, Sin, in_compact, Sout, out_compact, adj, st);
   return dispatch_n(P.nx, [&](auto nc) -> nlos_status {
     constexpr int N = decltype(nc)::value;

@@ -199,7 +199,7 @@ class Plan:
         return out.value
 
     def set_lateral(self, mode, stream=0):
-        """Lateral stage: 0 FFT kernels, 1 split-BF16 DFT GEMMs, 2 single-BF16 DFT GEMMs."""
+        """Lateral stage: 0 FFT kernels, 1 split-BF16 tensor-core DFT products, 2 single-BF16 ones."""
         check(load().nlos_plan_set_lateral(self.handle, int(mode), stream))
 
     def timing_enable(self, enable=True):

@@ -1,14 +1,18 @@
-"""The optional GEMM lateral stage (nlos_plan_set_lateral): the H convolution
-of every kt plane as DFT-matrix products on the tensor cores, split-BF16
+"""The tensor-core lateral stage (nlos_plan_set_lateral): the H convolution
+of every kt plane as DFT-matrix products with tcgen05.mma, split-BF16
 (mode 1) or single-pass BF16 (mode 2), against the FP64 oracle.
 
-* Operator parity: A, A_D, A^T, A_D^T on random inputs; mode 1 within the
+* Operator parity: A, A_D, A^T, A_D^T on random inputs at 128 x 128 lateral
+  size (the size the stage supports), nt = 64 and 512; mode 1 within the
   1e-5 bar of the FP32 kernels, mode 2 within 1e-2 (one BF16 rounding per
   operand and four chained products).
+* Repeat launches give identical bits (fixed accumulation order), and no
+  MMA completion wait gave up.
+* Sizes other than 128 are refused.
 * The precision case (128 x 128 x 1024, 12 Algorithm-1 iterations) against
   the stored FP64 oracle run, with the relative L2 and the depth-map
-  agreement of each mode printed: the split-BF16 variant of the comparison
-  between the FP32 lateral stage and a BF16 GEMM one."""
+  agreement of each mode printed: the comparison between the FP32 lateral
+  stage and the split-BF16 tensor-core one."""
 import os
 
 import numpy as np
@@ -31,27 +35,43 @@ def nlos():
 
 
 @pytest.mark.parametrize("mode", [1, 2])
-@pytest.mark.parametrize("n,nt", [(32, 64), (128, 64)])
-def test_gemm_lateral_operator_parity(nlos, mode, n, nt):
+@pytest.mark.parametrize("nt,stride", [(64, 4), (512, 4), (64, 3)])
+def test_tc_lateral_operator_parity(nlos, mode, nt, stride):
+    n = 128
     bw = 32e-12 * 256 / nt
     g = lct.Geometry(n, n, nt, bw)
-    mask = synth.stride_mask(n, n, 4)
+    mask = synth.stride_mask(n, n, stride)
     plan = nlos.Plan(n, n, nt, bw, mask=mask)
     plan.set_lateral(mode)
     op = lct.Operator(g, mask)
-    rng = np.random.default_rng(n + nt + mode)
+    rng = np.random.default_rng(n + nt + mode + stride)
     u, r = rng.random(g.shape), rng.standard_normal(g.shape)
-    errs = [rel_l2(host(nlos.forward_t(plan, dev(u), apply_mask=False)), op.forward(u)),
-            rel_l2(host(nlos.forward_t(plan, dev(u), apply_mask=True)), op.forward_d(u)),
-            rel_l2(host(nlos.adjoint_t(plan, dev(r), apply_mask=False)), op.adjoint(r)),
-            rel_l2(host(nlos.adjoint_t(plan, dev(r), apply_mask=True)), op.adjoint_d(r))]
-    print(f"mode {mode} n {n}: A {errs[0]:.2e}, A_D {errs[1]:.2e}, A^T {errs[2]:.2e}, A_D^T {errs[3]:.2e}")
+    outs = [host(nlos.forward_t(plan, dev(u), apply_mask=False)), host(nlos.forward_t(plan, dev(u), apply_mask=True)),
+            host(nlos.adjoint_t(plan, dev(r), apply_mask=False)), host(nlos.adjoint_t(plan, dev(r), apply_mask=True))]
+    errs = [rel_l2(outs[0], op.forward(u)), rel_l2(outs[1], op.forward_d(u)),
+            rel_l2(outs[2], op.adjoint(r)), rel_l2(outs[3], op.adjoint_d(r))]
+    print(f"mode {mode} nt {nt} stride {stride}: A {errs[0]:.2e}, A_D {errs[1]:.2e}, A^T {errs[2]:.2e}, "
+          f"A_D^T {errs[3]:.2e}")
     assert max(errs) < TOL[mode], errs
+    # unsampled columns of A_D u are exactly zero
+    m = np.asarray(mask, dtype=bool)
+    assert np.all(outs[1][~m] == 0)
+    # identical bits on a second launch
+    again = host(nlos.adjoint_t(plan, dev(r), apply_mask=True))
+    assert np.array_equal(again, outs[3])
+    plan.set_lateral(mode)                                # raises if a wait gave up
     plan.set_lateral(0)                                   # back to the FFT kernels
     assert rel_l2(host(nlos.forward_t(plan, dev(u), apply_mask=False)), op.forward(u)) < 1e-5
 
 
-def test_gemm_lateral_precision_case(nlos):
+def test_tc_lateral_refuses_other_sizes(nlos):
+    plan = nlos.Plan(64, 64, 64, 64e-12)
+    with pytest.raises(nlos.NlosError):
+        plan.set_lateral(1)
+    plan.set_lateral(0)
+
+
+def test_tc_lateral_precision_case(nlos):
     z = np.load(GOLDEN)
     cfg = synth.CONFIGS["c4_alg1_128x128x1024"]
     nx, ny, nt = cfg["nx"], cfg["ny"], cfg["nt"]
