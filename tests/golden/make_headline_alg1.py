@@ -1,6 +1,6 @@
 """Writes tests/golden/headline_alg1_128x128x512.npz: the FP64 oracle's
 Algorithm-1 reconstruction at the benchmark's size (128 x 128 x 512, 16 ps
-bins, 32 x 32 stride-4 sampling; a, b, mu of the Bowling settings), 12
+bins, 32 x 32 stride-4 sampling; a, b, mu of the Bowling settings), 50
 iterations, tau0 the seeded pulse transients.
 
 Only oracle/ and synth/ are used.  Stored: the energy history, the Lipschitz
@@ -9,7 +9,7 @@ fixed columns (every 256th column index plus the 32 sampled columns of one
 row), so a GPU run at the benchmark's launch configuration can be compared
 without the 34 MB volume.
 
-    PYTHONPATH=. python tests/golden/make_headline_alg1.py     (about 15 minutes)
+    PYTHONPATH=. python tests/golden/make_headline_alg1.py     (about 25 minutes)
 """
 import os
 import sys
@@ -24,7 +24,7 @@ import synth  # noqa: E402
 from oracle import admm, lct  # noqa: E402
 
 NAME = "headline_alg1_128x128x512"
-ITERS = 12
+ITERS = 50
 SEED = 2
 
 

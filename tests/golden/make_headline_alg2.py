@@ -1,7 +1,7 @@
 """Writes tests/golden/headline_alg2_128x128x512.npz: the FP64 oracle's
 Algorithm-2 reconstruction at the benchmark's size (128 x 128 x 512, 16 ps
 bins, 32 x 32 stride-4 sampling; lambda, a_u, b_u, a_tau, b_tau and mu_1..3
-of the Bowling settings), 6 iterations, tau0 the seeded pulse transients.
+of the Bowling settings), 50 iterations, tau0 the seeded pulse transients.
 The GPU test runs it as one graph launch, as the benchmark's Algorithm-2
 line does.
 
@@ -10,7 +10,7 @@ flags, the Lipschitz estimates, the global 2-norms of u and tau, the depth
 map of u, and u and tau on 96 fixed columns (every 256th column index plus
 the 32 sampled columns of one row).
 
-    PYTHONPATH=. python tests/golden/make_headline_alg2.py     (about 15 minutes)
+    PYTHONPATH=. python tests/golden/make_headline_alg2.py     (about 60 minutes)
 """
 import os
 import sys
@@ -25,7 +25,7 @@ import synth  # noqa: E402
 from oracle import admm, lct  # noqa: E402
 
 NAME = "headline_alg2_128x128x512"
-ITERS = 6
+ITERS = 50
 SEED = 2
 
 
