@@ -229,6 +229,20 @@ nlos_status nlos_reconstruct(nlos_plan plan, const nlos_params* params, const fl
 nlos_status nlos_reconstruct_prepare(nlos_plan plan, const nlos_params* params, const float* tau0_dev,
                                      float* u_out_dev, float* tau_out_dev, int32_t* graphed, void* stream);
 
+/* nlos_reconstruct from host memory: tau0_host (nx*ny*nt float32) is
+ * copied to a device buffer owned by the plan (three field-sized buffers,
+ * allocated on the first call and reused), the reconstruction runs as
+ * nlos_reconstruct does (one cached graph launch where possible), and u
+ * (and, for model 2 when tau_out_host is not NULL, tau) is copied back to
+ * u_out_host / tau_out_host.  Synchronises `stream` before returning.  Host
+ * buffers may be pageable or page-locked (page-locked memory copies
+ * asynchronously and faster); the caller owns them.  The end-to-end form of
+ * the paper's reconstruction (Algorithms 1-2) for a caller whose data lives
+ * on the host.  Errors as nlos_reconstruct, and NLOS_ERR_OOM if the device
+ * buffers cannot be allocated. */
+nlos_status nlos_reconstruct_host(nlos_plan plan, const nlos_params* params, const float* tau0_host,
+                                  float* u_out_host, float* tau_out_host, nlos_stats* stats_host, void* stream);
+
 /* Reconstruct n independent scenes at once.  plans[i] must be n distinct
  * plans (each owns its scratch; a plan appearing twice is rejected);
  * params[i], tau0[i] (device), u_out[i] (device) and tau_out[i] (device,
@@ -290,11 +304,10 @@ nlos_status nlos_server_prepare(nlos_server server, const nlos_geometry* geom, c
 nlos_status nlos_server_destroy(nlos_server server, int32_t cancel_pending, double timeout_s);
 
 /* The periodic FFT solve of nlos_solve for callers that cannot allocate
- * device memory when they solve: code running while its stream is being
- * captured into a CUDA graph (allocations are refused during a capture),
- * code whose device memory is owned by another allocator or capped by a
- * fixed budget, and real-time loops that must stay off the driver's
- * allocation path, which can synchronise the device.  The paper has no
+ * device memory when they solve: code whose device memory is owned by
+ * another allocator (a framework's caching pool) or capped by a fixed
+ * budget, and real-time loops that must stay off the driver's allocation
+ * path, which can synchronise the whole device.  The paper has no
  * counterpart: this is a deployment variant of the solve above.
  *
  * No plan: pass the grid (nx == ny, powers of two, 8 <= nx <= 64,
@@ -303,12 +316,14 @@ nlos_status nlos_server_destroy(nlos_server server, int32_t cancel_pending, doub
  * static device array of 64 * 64 * 257 complex values (8 MiB) that every
  * GPU loading the library holds until the process exits; larger grids
  * return NLOS_ERR_INVALID_ARG (use nlos_solve).  The first call on a device
- * (with that device current) looks up the array's device address and fills
- * small twiddle tables; make that first call before any stream capture.
+ * (with that device current) is the set-up: it looks up the array's device
+ * address, fills small twiddle tables, sets the kernels' shared-memory
+ * limits and synchronises the device; later calls only launch kernels.
  * All calls share the scratch: calls whose kernels overlap on the GPU
  * (other streams or other host threads) race and must be serialised by the
  * caller.  It keeps the last call's contents, but no call reads a value an
- * earlier call left behind.  Queued on `stream`, no host synchronisation. */
+ * earlier call left behind.  Queued on `stream`, no host synchronisation
+ * after the set-up. */
 nlos_status nlos_solve_static(int32_t nx, int32_t ny, int32_t nt, const float* rhs_dev, float* x_dev, double c0,
                               double c1, void* stream);
 

@@ -18,7 +18,6 @@
 namespace nlos {
 
 constexpr int kStencilThreads = 256;
-constexpr int kStencilBlocks = 152 * 8;  // grid-stride; also the partial-sum count
 
 __host__ __device__ inline int ilog2i(int n) {
   int r = 0;
@@ -522,7 +521,7 @@ static nlos_status get_solver(Plan& P, int model, SolverState** out) {
   return NLOS_OK;
 }
 
-static int elem_grid(size_t n) { return (int)std::min<size_t>((n + 255) / 256, (size_t)152 * 16); }
+static int elem_grid(size_t n) { return (int)std::min<size_t>((n + 255) / 256, (size_t)device_sm_count() * 16); }
 
 // Operator applications shared by the C API and the solvers.
 nlos_status apply_forward(const Plan& P, const float* u, float* out, bool compact, cudaStream_t st) {
@@ -575,7 +574,7 @@ nlos_status apply_curvature_weight(const Plan& P, const float* u, float* ph, dou
   VoxIter vi{ilog2i(P.nt), ilog2i(P.ny)};
   const size_t V = (size_t)P.nx * P.ny * P.nt;
   { KTimer kt_(P, KC_SMALL, st);
-  k_curv_weight<<<kStencilBlocks, kStencilThreads, 0, st>>>(u, ph, g, vi, (float)a, (float)b, kind,
+  k_curv_weight<<<stencil_blocks(P), kStencilThreads, 0, st>>>(u, ph, g, vi, (float)a, (float)b, kind,
                                                             (float)(eps * eps), V);
   }
   NLOS_LAUNCH_CHECK("k_curv_weight");
@@ -585,12 +584,12 @@ nlos_status apply_curvature_weight(const Plan& P, const float* u, float* ph, dou
 // Sum of squares of n floats, read back to the host (synchronises st).
 static nlos_status host_sumsq(const Plan& P, const float* a, size_t n, double* out, cudaStream_t st) {
   { KTimer kt_(P, KC_SMALL, st);
-  k_sumsq<<<kStencilBlocks, kStencilThreads, 0, st>>>(a, n, P.d_partials);
+  k_sumsq<<<stencil_blocks(P), kStencilThreads, 0, st>>>(a, n, P.d_partials);
   }
   NLOS_LAUNCH_CHECK("k_sumsq");
   double* d_out = reinterpret_cast<double*>(P.d_scal);
   { KTimer kt_(P, KC_SMALL, st);
-  k_sum_to<<<1, kSumThreads, 0, st>>>(P.d_partials, kStencilBlocks, 0, d_out);
+  k_sum_to<<<1, kSumThreads, 0, st>>>(P.d_partials, stencil_blocks(P), 0, d_out);
   }
   NLOS_LAUNCH_CHECK("k_sum_to");
   NLOS_CUDA(cudaMemcpyAsync(out, d_out, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -848,23 +847,23 @@ static nlos_status init_scalars(Plan& P, SolverState* s, double L0, const float*
                                 cudaStream_t st, const float* au0 = nullptr, const float* u0 = nullptr,
                                 const float* ph0 = nullptr) {
   { KTimer kt_(P, KC_SMALL, st);
-  k_sumsq<<<kStencilBlocks, kStencilThreads, 0, st>>>(sumsq_src, n, s->pc);
+  k_sumsq<<<stencil_blocks(P), kStencilThreads, 0, st>>>(sumsq_src, n, s->pc);
   }
   NLOS_LAUNCH_CHECK("k_sumsq");
   if (au0) {
     const Vox g = make_vox(P.nx, P.ny, P.nt);
     const VoxIter vi{ilog2i(P.nt), ilog2i(P.ny)};
     { KTimer kt_(P, KC_SMALL, st);
-    k_sumsq<<<kStencilBlocks, kStencilThreads, 0, st>>>(au0, s->V, s->pa);
+    k_sumsq<<<stencil_blocks(P), kStencilThreads, 0, st>>>(au0, s->V, s->pa);
     }
     NLOS_LAUNCH_CHECK("k_sumsq");
     { KTimer kt_(P, KC_SMALL, st);
-    k_tv_weighted<<<kStencilBlocks, kStencilThreads, 0, st>>>(u0, ph0, g, vi, s->V, s->pb);
+    k_tv_weighted<<<stencil_blocks(P), kStencilThreads, 0, st>>>(u0, ph0, g, vi, s->V, s->pb);
     }
     NLOS_LAUNCH_CHECK("k_tv_weighted");
   }
   { KTimer kt_(P, KC_SMALL, st);
-  k_init_scalars<<<1, kSumThreads, 0, st>>>(s->sc, L0, kStencilBlocks, s->pc, scale, au0 ? s->pa : nullptr, 0.5,
+  k_init_scalars<<<1, kSumThreads, 0, st>>>(s->sc, L0, stencil_blocks(P), s->pc, scale, au0 ? s->pa : nullptr, 0.5,
                                             au0 ? s->pb : nullptr, 1.0);
   }
   NLOS_LAUNCH_CHECK("k_init_scalars");
@@ -970,14 +969,14 @@ static nlos_status step_alg1(JobRun& j) {
   // t, 8 rows in y, 4 planes in x); the plain per-voxel kernels otherwise
   const bool tiled = P.nt % kTT == 0 && P.ny % kTY == 0;
   const int ntiles = tiled ? stencil_steps(g) : 0;  // (tile, x plane) steps
-  const int pre_grid = std::min(ntiles, 152 * 3), post_grid = std::min(ntiles, 152 * 2);
-  const int post_blocks = tiled ? post_grid : kStencilBlocks;
+  const int pre_grid = std::min(ntiles, P.sms * 3), post_grid = std::min(ntiles, P.sms * 2);
+  const int post_blocks = tiled ? post_grid : stencil_blocks(P);
   { KTimer kt_(P, KC_PRE, st);
   if (tiled)
     k_pre1_pipe<false><<<pre_grid, kTileThreads, kPre1PipeSmem, st>>>(s->ub, s->lam, s->ph, s->reg, g, ntiles,
                                                                       (float)p.mu, V, FTerm{});
   else
-    k_pre1<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->ub, s->lam, s->ph, s->reg, g, vi, (float)p.mu, V);
+    k_pre1<<<stencil_blocks(P), kStencilThreads, 0, st>>>(s->ub, s->lam, s->ph, s->reg, g, vi, (float)p.mu, V);
   }
   NLOS_LAUNCH_CHECK("k_pre1");
   Lin3 r{{s->cache[j.cur], s->cache[j.prev], s->tau0c}, {0.f, 0.f, 0.f}, s->sc};
@@ -993,7 +992,7 @@ static nlos_status step_alg1(JobRun& j) {
         s->unew, s->uk, s->ub, s->lam, s->ph, s->ubn, s->sc, g, ntiles, (float)p.mu, (float)p.a, (float)p.b, p.phi,
         eps2, V, s->pc, L3Term{});
   else
-    k_post1<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->unew, s->uk, s->ub, s->lam, s->ph, s->ubn, s->sc, g, vi,
+    k_post1<<<stencil_blocks(P), kStencilThreads, 0, st>>>(s->unew, s->uk, s->ub, s->lam, s->ph, s->ubn, s->sc, g, vi,
                                                         (float)p.mu, (float)p.a, (float)p.b, p.phi, eps2, V, s->pc);
   }
   NLOS_LAUNCH_CHECK("k_post1");
@@ -1020,7 +1019,7 @@ static nlos_status step_alg2(JobRun& j) {
              (float)p.a_tau, (float)p.b_tau, p.phi, (float)(p.eps_normal * p.eps_normal)};
   const bool tiled = P.nt % kTT == 0 && P.ny % kTY == 0;
   const int ntiles = tiled ? stencil_steps(g) : 0;  // (tile, x plane) steps
-  const int pre_grid = std::min(ntiles, 152 * 3), post_grid = std::min(ntiles, 152 * 2);
+  const int pre_grid = std::min(ntiles, P.sms * 3), post_grid = std::min(ntiles, P.sms * 2);
   { KTimer kt_(P, KC_PRE, st);
   if (tiled) {
     k_pre1_pipe<false><<<pre_grid, kTileThreads, kPre1PipeSmem, st>>>(s->ub, s->lam, s->ph, s->reg, g, ntiles,
@@ -1029,7 +1028,7 @@ static nlos_status step_alg2(JobRun& j) {
     k_pre1_pipe<true><<<pre_grid, kTileThreads, kPre1PipeSmem, st>>>(s->tb, s->lam2, s->pht, s->regt, g, ntiles,
                                                                      (float)p.mu2, V, ft);
   } else {
-    k_pre2<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->ub, s->tb, s->lam, s->lam2, s->lam3, s->ph, s->pht,
+    k_pre2<<<stencil_blocks(P), kStencilThreads, 0, st>>>(s->ub, s->tb, s->lam, s->lam2, s->lam3, s->ph, s->pht,
                                                        j.tau0, colpos, s->reg, s->regt, g, vi, c, V);
   }
   }
@@ -1066,13 +1065,13 @@ static nlos_status step_alg2(JobRun& j) {
     NLOS_LAUNCH_CHECK("k_finalize2");
   } else {
     { KTimer kt_(P, KC_POST, st);
-    k_post2<<<kStencilBlocks, kStencilThreads, 0, st>>>(s->unew, s->uk, s->ub, s->tnew, s->tk, s->tb, s->lam,
+    k_post2<<<stencil_blocks(P), kStencilThreads, 0, st>>>(s->unew, s->uk, s->ub, s->tnew, s->tk, s->tb, s->lam,
                                                         s->lam2, s->lam3, s->ph, s->pht, s->ubn, s->tbn,
                                                         s->cache[j.nxt], j.tau0, colpos, s->sc, g, vi, c, V, s->pc);
     }
     NLOS_LAUNCH_CHECK("k_post2");
     { KTimer kt_(P, KC_SMALL, st);
-    k_finalize<<<1, kSumThreads, 0, st>>>(s->sc, s->pc, kStencilBlocks, 2, p.lambda, j.restart, p.eps_stop);
+    k_finalize<<<1, kSumThreads, 0, st>>>(s->sc, s->pc, stencil_blocks(P), 2, p.lambda, j.restart, p.eps_stop);
     }
     NLOS_LAUNCH_CHECK("k_finalize");
   }
@@ -1310,6 +1309,44 @@ nlos_status reconstruct(Plan& P, const nlos_params& p, const float* tau0, float*
     while (!j.done) NLOS_TRY(job_step(j));
     NLOS_TRY(job_finish(j));
   }
+  NLOS_CUDA(cudaStreamSynchronize(st));
+  return job_collect(j, stats);
+}
+
+}  // namespace nlos
+
+namespace nlos {
+
+nlos_status reconstruct_host(Plan& P, const nlos_params& p, const float* tau0_host, float* u_out_host,
+                             float* tau_out_host, nlos_stats* stats, cudaStream_t st) {
+  if (p.model != 1 && p.model != 2) return fail(NLOS_ERR_INVALID_ARG, "params->model must be 1 or 2");
+  const size_t F = (size_t)P.nx * P.ny * P.nt * sizeof(float);
+  for (int i = 0; i < 3; ++i)
+    if (!P.d_io[i]) {
+      if (cudaMalloc(&P.d_io[i], F) != cudaSuccess) {
+        cudaGetLastError();
+        P.d_io[i] = nullptr;
+        return fail(NLOS_ERR_OOM, "nlos_reconstruct_host: device buffers");
+      }
+    }
+  JobRun j;
+  j.P = &P;
+  j.p = p;
+  j.tau0 = P.d_io[0];
+  j.u_out = P.d_io[1];
+  j.tau_out = P.d_io[2];
+  j.st = st;
+  NLOS_CUDA(cudaMemcpyAsync(P.d_io[0], tau0_host, F, cudaMemcpyHostToDevice, st));
+  bool graphed = false;
+  NLOS_TRY(job_enqueue_graph(j, st, &graphed));
+  if (!graphed) {
+    NLOS_TRY(job_init(j));
+    while (!j.done) NLOS_TRY(job_step(j));
+    NLOS_TRY(job_finish(j));
+  }
+  NLOS_CUDA(cudaMemcpyAsync(u_out_host, P.d_io[1], F, cudaMemcpyDeviceToHost, st));
+  if (tau_out_host && p.model == 2)
+    NLOS_CUDA(cudaMemcpyAsync(tau_out_host, P.d_io[2], F, cudaMemcpyDeviceToHost, st));
   NLOS_CUDA(cudaStreamSynchronize(st));
   return job_collect(j, stats);
 }

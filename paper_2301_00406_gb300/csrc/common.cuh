@@ -173,6 +173,8 @@ struct Plan {
   int ncols;          // number of sampled columns
   bool full_mask;     // every column sampled
   int device;
+  int sms;            // streaming multiprocessors of the device (queried at plan creation); sets the
+                      // grid of the grid-stride reductions, hence their summation order
 
   // host tables (FP64-derived, stored as the device uses them)
   std::vector<int32_t> h_rz_i0, h_rt_k0, h_cols;
@@ -213,6 +215,7 @@ struct Plan {
   float2* d_Sp = nullptr;        // [(nt/2+1)][nx][ny] periodic spectrum (solve)
   float* d_tmpc = nullptr;       // [ncols][nt] compact transient scratch
   double* d_partials = nullptr;  // reduction partials
+  float* d_io[3] = {nullptr, nullptr, nullptr};  // tau0, u, tau of nlos_reconstruct_host (allocated on use)
   int partial_blocks = 0;
   DevScalars* d_scal = nullptr;  // scratch scalars (norm, diagnostics)
 
@@ -284,6 +287,10 @@ nlos_status apply_curvature_weight(const Plan& P, const float* u, float* ph, dou
 nlos_status plan_norm2(Plan& P, bool masked, cudaStream_t st, double* out);
 nlos_status reconstruct(Plan& P, const nlos_params& p, const float* tau0, float* u_out, float* tau_out,
                         nlos_stats* stats, cudaStream_t st);
+// The same from host memory through the plan's own device buffers (copies in
+// and out on st, then synchronises).
+nlos_status reconstruct_host(Plan& P, const nlos_params& p, const float* tau0_host, float* u_out_host,
+                             float* tau_out_host, nlos_stats* stats, cudaStream_t st);
 void free_solver(SolverState* s);
 
 // Per-job workspace: a copy of `base` that shares its read-only device tables
@@ -355,6 +362,11 @@ void free_graphs(Plan* P);
 
 // Launch configuration helpers
 inline int div_up(int a, int b) { return (a + b - 1) / b; }
+// Streaming multiprocessors of the current device (queried once per device).
+int device_sm_count();
+// Grid of the grid-stride stencil and reduction kernels: eight blocks per SM,
+// at most the 4096 partial-sum slots a solver state holds.
+inline int stencil_blocks(const Plan& P) { return P.sms * 8 < 4096 ? P.sms * 8 : 4096; }
 
 // Raise a kernel's dynamic shared-memory limit once per (device, kernel):
 // the attribute call is not repeated on every launch (nor during a stream

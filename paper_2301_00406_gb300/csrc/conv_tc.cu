@@ -627,7 +627,7 @@ nlos_status set_lateral_mode(Plan& P, int mode, cudaStream_t st) {
       cudaMemsetAsync(L->d_status, 0, sizeof(int), st) != cudaSuccess)
     return cleanup(cuda_fail(cudaGetLastError(), "tensor-core lateral stage: constants"));
   k_tc_bimage<<<64, 256, 0, st>>>(d_Bf, reinterpret_cast<uint16_t*>(L->d_B));
-  k_tc_hperm<<<152 * 8, 256, 0, st>>>(P.d_H, L->d_Hp, planes);
+  k_tc_hperm<<<device_sm_count() * 8, 256, 0, st>>>(P.d_H, L->d_Hp, planes);
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
     return cleanup(cuda_fail(cudaGetLastError(), "tensor-core lateral stage: set-up kernels"));
   cudaFree(d_Bf);

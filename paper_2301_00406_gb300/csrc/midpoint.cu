@@ -101,7 +101,7 @@ extern "C" nlos_status nlos_midpoint_confocal(int32_t nx, int32_t ny, int32_t nt
       return fail(NLOS_ERR_INVALID_ARG, "nlos_midpoint_confocal: input and output overlap");
     const int ncols = nx * ny;
     const int per_block = kMidThreads / 32;
-    const int blocks = (int)std::min<long long>((ncols + per_block - 1) / per_block, 152LL * 16);
+    const int blocks = (int)std::min<long long>((ncols + per_block - 1) / per_block, (long long)device_sm_count() * 16);
     k_midpoint<<<blocks, kMidThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
         tau_nc_dev, tau_c_dev, nx, ny, nt, 1.0 / (bin_width_s * bin_width_s), wall_width_m / nx, wall_width_m / ny,
         laser_x_m, laser_y_m, 1.0 / (kLightSpeedMps * kLightSpeedMps));

@@ -1,5 +1,6 @@
 // Plan construction (geometry tables of Eq. 3 in FP64 on the host, the
 // cone-kernel spectrum on the device) and the extern "C" entry points.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -8,6 +9,24 @@
 #include "passes.cuh"
 
 namespace nlos {
+
+int device_sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    dev = 0;
+  }
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v <= 0) {
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+      cudaGetLastError();
+      v = 1;
+    }
+    cache[dev].store(v, std::memory_order_relaxed);
+  }
+  return v;
+}
 
 static thread_local std::string g_last_error;
 
@@ -185,7 +204,8 @@ static void free_workspace(Plan* P) {
     free_solver(P->solver[m]);
     P->solver[m] = nullptr;
   }
-  void* ws[] = {P->d_S, P->d_S2, P->d_Sc, P->d_Sp, P->d_tmpc, P->d_partials, P->d_scal};
+  void* ws[] = {P->d_S, P->d_S2, P->d_Sc, P->d_Sp, P->d_tmpc, P->d_partials, P->d_scal, P->d_io[0], P->d_io[1],
+                P->d_io[2]};
   for (void* p : ws)
     if (p) cudaFree(p);
   for (cudaEvent_t e : P->ev) cudaEventDestroy(e);
@@ -229,6 +249,7 @@ Plan* plan_clone_workspace(const Plan& base, nlos_status* status) {
   P->d_tmpc = nullptr;
   P->d_partials = nullptr;
   P->d_scal = nullptr;
+  for (auto& b : P->d_io) b = nullptr;
   P->timing = false;
   P->ev.clear();
   P->ev_cat.clear();
@@ -317,6 +338,7 @@ static nlos_status create_plan(const nlos_geometry* g, cudaStream_t st, Plan** o
     }
   }
   cudaGetDevice(&P->device);
+  P->sms = device_sm_count();
   const int nx = P->nx, ny = P->ny, nt = P->nt, full = nx * ny;
   const auto rzs = starts_of(P->h_rz_i0, nt);
   const auto rts = starts_of(P->h_rt_k0, nt);
@@ -615,6 +637,20 @@ nlos_status nlos_reconstruct(nlos_plan plan, const nlos_params* params, const fl
     if (stats_host) std::memset(stats_host, 0, sizeof(*stats_host));
     return reconstruct(*reinterpret_cast<Plan*>(plan), p, tau0_dev, u_out_dev, tau_out_dev, stats_host,
                        reinterpret_cast<cudaStream_t>(stream));
+  })
+}
+
+nlos_status nlos_reconstruct_host(nlos_plan plan, const nlos_params* params, const float* tau0_host,
+                                  float* u_out_host, float* tau_out_host, nlos_stats* stats_host, void* stream) {
+  API_GUARD({
+    NLOS_TRY(check_plan(plan));
+    if (!params || !tau0_host || !u_out_host)
+      return fail(NLOS_ERR_INVALID_ARG, "nlos_reconstruct_host: null pointer");
+    const nlos_params& p = *params;
+    NLOS_TRY(validate_params(p, "nlos_reconstruct_host"));
+    if (stats_host) std::memset(stats_host, 0, sizeof(*stats_host));
+    return reconstruct_host(*reinterpret_cast<Plan*>(plan), p, tau0_host, u_out_host, tau_out_host, stats_host,
+                            reinterpret_cast<cudaStream_t>(stream));
   })
 }
 

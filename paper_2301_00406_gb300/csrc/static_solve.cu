@@ -1,12 +1,12 @@
 // nlos_solve_static: the periodic FFT solve of nlos_solve without any device
 // allocation and without a plan.
 //
-// Who needs it: callers that cannot call cudaMalloc at the moment they solve,
-// e.g. code running while its stream is being captured into a CUDA graph (an
-// allocation inside a capture is refused), code whose device memory is all
-// handed to another allocator or capped by a fixed budget, and real-time
-// loops that must not take the driver's allocation path, which can
-// synchronise the device.  They pass only their input and output buffers.
+// Who needs it: callers that cannot call cudaMalloc at the moment they solve.
+// Code whose device memory is owned by another allocator (a framework's
+// caching pool) or capped by a fixed budget has no room to take from the
+// driver, and real-time loops must stay off the driver's allocation path,
+// which can synchronise the whole device.  They pass only their input and
+// output buffers.
 //
 // Scratch: the periodic spectrum lives in g_static_spectrum, a file-scope
 // __device__ array of kStaticSpectrumMax complex values (8 MiB, enough for
@@ -20,9 +20,12 @@
 //
 // Set-up: the first call on a device, with that device current, looks up
 // the device addresses of the arrays (cudaGetSymbolAddress; host code may not
-// use the array names as device pointers) and fills the tables with
-// cudaMemcpyToSymbol.  That first call should come before any stream capture.
-// Later calls on that device only launch the three kernels.
+// use the array names as device pointers), fills the tables with
+// cudaMemcpyToSymbol, sets the shared-memory limits of every kernel a later
+// call can launch, and synchronises the device, so the tables are in place
+// before any stream (also one that does not wait for the legacy default
+// stream) runs a solve.  Later calls on that device only launch three
+// kernels.
 #include <cmath>
 #include <mutex>
 
@@ -103,6 +106,12 @@ nlos_status setup_device(int dev, StaticDevice* d) {
   NLOS_CUDA(cudaMemcpyToSymbol(g_static_tw_x, twx.data(), sizeof(float2) * kTwXLen));
   NLOS_CUDA(cudaMemcpyToSymbol(g_static_lam_t, lt.data(), sizeof(float) * kLamTLen));
   NLOS_CUDA(cudaMemcpyToSymbol(g_static_lam_x, lx.data(), sizeof(float) * kLamXLen));
+  for (int nt = 16; nt <= kStaticMaxNt; nt *= 2) NLOS_TRY(prepare_tpass(nt));
+  for (int n = 8; n <= kStaticMaxN; n *= 2) NLOS_TRY(prepare_xy(n));
+  // the copies above are ordered on the legacy stream only, and a copy from
+  // pageable memory may return before it lands: finish them before any call
+  // launches on another stream
+  NLOS_CUDA(cudaDeviceSynchronize());
   d->ready = true;
   (void)dev;
   return NLOS_OK;

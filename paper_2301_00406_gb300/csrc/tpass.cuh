@@ -814,7 +814,7 @@ static TpShape tp_shape(int ncols, int extra, bool tab, int kind, bool halves) {
   } else {
     sh.cols = TP<NT>::COLS;
     sh.hb = 0;
-    while (sh.cols > 2 && div_up(ncols, sh.cols) < 2 * 152) sh.cols >>= 1;
+    while (sh.cols > 2 && div_up(ncols, sh.cols) < 2 * device_sm_count()) sh.cols >>= 1;
   }
   sh.threads = kTpassThreads;  // the kernels' loops assume this count
   sh.blocks = div_up(ncols, sh.cols);

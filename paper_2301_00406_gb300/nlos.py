@@ -80,6 +80,7 @@ _SIGS = {
                                                ctypes.c_int32, ctypes.c_double, _P]),
     "nlos_reconstruct": (ctypes.c_int32, [_P, ctypes.POINTER(Params), _P, _P, _P,
                                           ctypes.POINTER(Stats), _P]),
+    "nlos_reconstruct_host": (ctypes.c_int32, [_P, ctypes.POINTER(Params), _P, _P, _P, ctypes.POINTER(Stats), _P]),
     "nlos_reconstruct_prepare": (ctypes.c_int32, [_P, ctypes.POINTER(Params), _P, _P, _P,
                                                   ctypes.POINTER(ctypes.c_int32), _P]),
     "nlos_solve_static": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P,
@@ -231,6 +232,13 @@ class Plan:
         check(load().nlos_reconstruct_prepare(self.handle, ctypes.byref(params), tau0_ptr, u_ptr,
                                               tau_out_ptr or None, ctypes.byref(g), stream))
         return bool(g.value)
+
+    def reconstruct_host(self, params, tau0_ptr, u_ptr, tau_out_ptr=0, stream=0):
+        """nlos_reconstruct_host on host pointers (e.g. numpy arrays' or pinned tensors' data pointers)."""
+        st = Stats()
+        check(load().nlos_reconstruct_host(self.handle, ctypes.byref(params), tau0_ptr, u_ptr, tau_out_ptr or None,
+                                           ctypes.byref(st), stream))
+        return st.as_dict()
 
     def reconstruct(self, params, tau0_ptr, u_ptr, tau_out_ptr=0, stream=0):
         st = Stats()

@@ -167,3 +167,36 @@ def test_alg2_phi_variant_parity(nlos):
     u_ref, tau_ref, h = admm.alg2(tau0, mask, g, cfg["a_u"], cfg["b_u"], cfg["a_tau"], cfg["b_tau"], cfg["lam"],
                                   cfg["mu1"], cfg["mu2"], cfg["mu3"], iters, L0=2 * n2, op=op, phi_kind="tac")
     assert rel_l2(host(u_gpu), u_ref) < 1e-3 and rel_l2(host(tau_gpu), tau_ref) < 1e-3
+
+
+@pytest.mark.parametrize("model", [1, 2])
+def test_reconstruct_from_host_memory_equals_device_call(nlos, model):
+    """nlos_reconstruct_host (tau0 from host memory, u and tau back to host
+    memory, pageable and pinned buffers) gives the bits of nlos_reconstruct
+    on device buffers, and the same statistics."""
+    import torch
+    n, nt = 32, 128
+    cfg, g, mask, vol, tau0 = scene(model, n, nt, seed=4)
+    plan = nlos.Plan(n, n, nt, cfg["bin_width_s"], mask=mask)
+    p = alg1_params(nlos, cfg, 9, 0.0) if model == 1 else alg2_params(nlos, cfg, 9, 0.0)
+    t = dev(tau0)
+    u_dev, tau_dev = torch.empty_like(t), torch.empty_like(t)
+    st_dev = plan.reconstruct(p, t.data_ptr(), u_dev.data_ptr(), tau_dev.data_ptr() if model == 2 else 0)
+    t_host = np.ascontiguousarray(tau0, dtype=np.float32)
+    for pinned in (False, True):
+        if pinned:
+            tin = torch.tensor(t_host).pin_memory()
+            uo, to = torch.empty_like(tin).pin_memory(), torch.empty_like(tin).pin_memory()
+            ptrs = (tin.data_ptr(), uo.data_ptr(), to.data_ptr())
+            get = (lambda: (uo.numpy(), to.numpy()))
+        else:
+            uo_np, to_np = np.full_like(t_host, np.nan), np.full_like(t_host, np.nan)
+            ptrs = (t_host.ctypes.data, uo_np.ctypes.data, to_np.ctypes.data)
+            get = (lambda: (uo_np, to_np))
+        st_host = plan.reconstruct_host(p, ptrs[0], ptrs[1], ptrs[2] if model == 2 else 0)
+        u_h, tau_h = get()
+        assert np.array_equal(u_h, host(u_dev).astype(np.float32))
+        if model == 2:
+            assert np.array_equal(tau_h, host(tau_dev).astype(np.float32))
+        assert st_host["iters_done"] == st_dev["iters_done"] and st_host["energy"] == st_dev["energy"]
+    plan.close()
