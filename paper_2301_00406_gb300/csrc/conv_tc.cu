@@ -48,6 +48,7 @@
 #include <cooperative_groups.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -60,25 +61,29 @@ namespace nlos {
 struct LateralTC {
   int mode = 0;                // 1 split BF16 (three products), 2 BF16 hi only
   uint4* d_B = nullptr;        // shared-memory image of the block constant: hi tile, lo tile
-  float2* d_Hp = nullptr;      // H rearranged [kt][fold ky][p][m], kx = 4 m + p
+  float2* d_Hp = nullptr;      // H rearranged [kt][q][fold kx][row]
   int* d_status = nullptr;     // nonzero after a bounded wait gave up
 };
 
 namespace {
 
 constexpr int kTcN = 128;
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 512;
 constexpr int kTcGroups = 14;
 constexpr uint32_t kTile = 128 * 128 * 2;               // one 16-bit 128 x 128 operand tile
 constexpr uint32_t kOffB = 0;                           // constant: hi, lo
 constexpr uint32_t kOffA0 = 2 * kTile;                  // A buffer 0: hi, lo
 constexpr uint32_t kOffA1 = 4 * kTile;                  // A buffer 1: hi, lo
-constexpr uint32_t kOffTw = 6 * kTile;                  // 256 twiddles w^e
+constexpr int kExPitch = 130;                           // float2 per row of the staging buffers
+constexpr uint32_t kStage = 64 * kExPitch * 8;          // 64 rows of a CTA's partial results
+constexpr uint32_t kOffEx = kOffA0;                     // final stage: rows of the partner CTA
+constexpr uint32_t kOffOwn = kOffEx + kStage;           //              this CTA's own rows
+constexpr uint32_t kOffTw = kOffOwn + kStage;           // 256 twiddles w^e
 constexpr uint32_t kOffBar = kOffTw + 256 * 8;          // one mbarrier per MMA group
 constexpr uint32_t kOffMisc = kOffBar + 16 * 8;         // tensor-memory base, failure flag
 constexpr uint32_t kTcSmem = kOffMisc + 16;
-constexpr int kExPitch = 130;                           // float2 per row of the exchange buffer
-static_assert(kOffA0 + 64 * kExPitch * 8 <= kOffTw, "exchange buffer overlaps the twiddles");
+static_assert(kOffTw >= kOffA1 + 2 * kTile, "staging buffers must cover only the operand buffers");
+static_assert(kTcSmem <= 227 * 1024, "shared memory per CTA");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -117,18 +122,19 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Wait for phase 0 of an mbarrier, giving up after one second: the failure
-// is recorded (shared flag and the plan's status word) and every later wait
-// of the CTA returns at once, so the kernel still runs to its end.
-__device__ __forceinline__ void tc_wait(uint32_t bar, volatile int* fail, int* status) {
+// Wait for the phase of an mbarrier with the given parity, giving up after
+// one second: the failure is recorded (shared flag and the plan's status
+// word) and every later wait of the CTA returns at once, so the kernel still
+// runs to its end.
+__device__ __forceinline__ void tc_wait(uint32_t bar, uint32_t parity, volatile int* fail, int* status) {
   if (!*fail) {
     const uint64_t t0 = global_ns();
     for (;;) {
       uint32_t done;
       asm volatile(
-          "{\n.reg .pred P;\nmbarrier.try_wait.parity.shared::cta.b64 P, [%1], 0;\nselp.b32 %0, 1, 0, P;\n}\n"
+          "{\n.reg .pred P;\nmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\nselp.b32 %0, 1, 0, P;\n}\n"
           : "=r"(done)
-          : "r"(bar)
+          : "r"(bar), "r"(parity)
           : "memory");
       if (done) break;
       if (global_ns() - t0 > 1000000000ull) {
@@ -196,15 +202,17 @@ template <int TERMS>
 __device__ __forceinline__ void tc_issue(uint32_t sbase, uint32_t abuf, bool a_mn, uint32_t d, uint32_t bar) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t idesc = tc_idesc(a_mn);
-  const uint32_t a_lbo = a_mn ? 2048 : 128, a_sbo = a_mn ? 128 : 2048, a_step = a_mn ? 4096 : 256;
+  const uint32_t a_step = a_mn ? 4096 : 256;
+  // the start address is the descriptor's low field (16-byte units, below
+  // 256 KB here), so later K steps and the lo tiles are added to it
+  const uint64_t a0 = umma_desc(sbase + abuf, a_mn ? 2048 : 128, a_mn ? 128 : 2048);
+  const uint64_t b0 = umma_desc(sbase + kOffB, 128, 2048);
 #pragma unroll
   for (int t = 0; t < TERMS; ++t) {
-    const uint32_t a = sbase + abuf + (t == 2 ? kTile : 0);
-    const uint32_t b = sbase + kOffB + (t == 1 ? kTile : 0);
+    const uint64_t at = a0 + ((t == 2 ? kTile : 0) >> 4), bt = b0 + ((t == 1 ? kTile : 0) >> 4);
 #pragma unroll
     for (int ks = 0; ks < 8; ++ks)
-      tc_mma(d, umma_desc(a + ks * a_step, a_lbo, a_sbo), umma_desc(b + ks * 256, 128, 2048), idesc,
-             (t | ks) != 0 ? 1u : 0u);
+      tc_mma(d, at + ((ks * a_step) >> 4), bt + ((ks * 256) >> 4), idesc, (t | ks) != 0 ? 1u : 0u);
   }
   tc_commit(bar);
 }
@@ -239,69 +247,91 @@ __device__ __forceinline__ void load8(const float2* __restrict__ src, const int3
   }
 }
 
-// Operands of the y transforms of x parities p0 and p0 + 1 (buffers 0 and
-// 1): row 64 s + x0, K = n (real part) and 64 + n (imaginary part) holds
-//   w^(q' n + p x0) [(X[x0][n] + (-i)^q' X[x0][n+64]) + (-i)^p (X[x0+64][n] + (-i)^q' X[x0+64][n+64])].
-template <int TERMS>
-__device__ __forceinline__ void tc_build_y(uint8_t* smem, const float2* __restrict__ src,
-                                           const int32_t* __restrict__ pos, const float2* tw, int q, int p0,
-                                           int tid) {
-#pragma unroll 1
-  for (int it = 0; it < 2; ++it) {
-    const int item = tid + kTcThreads * it;
-    const int x0 = item & 63, n0 = (item >> 6) * 8;
-    float2 e0[8], o0[8], e1[8], o1[8];
-    load8(src, pos, x0, n0, e0);
-    load8(src, pos, x0, 64 + n0, o0);
-    load8(src, pos, x0 + 64, n0, e1);
-    load8(src, pos, x0 + 64, 64 + n0, o1);
+// The four values a thread folds for each of its eight rows: X[x][n],
+// X[x][n + 64], X[x + 64][n], X[x + 64][n + 64] for x = xb + r.  Loaded once
+// per plane and kept in registers for both operand passes.
+struct YIn {
+  float2 e0[8], o0[8], e1[8], o1[8];
+};
+
+// Thread (n, eight consecutive x0): the lanes of a warp read 32 consecutive
+// values of a row.
+__device__ __forceinline__ void tc_load_y(YIn& in, const float2* __restrict__ src, const int32_t* __restrict__ pos,
+                                          int q, int tid) {
+  const int n = tid & 63, xb = (tid >> 6) * 8;
+  auto ld = [&](int x, int y) -> float2 {
+    if (pos == nullptr) return __ldg(src + x * kTcN + y);
+    const int j = __ldg(pos + x * kTcN + y);
+    return j >= 0 ? __ldg(src + j) : make_float2(0.f, 0.f);
+  };
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      o0[i] = rot_mi(o0[i], q);
-      o1[i] = rot_mi(o1[i], q);
-    }
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      const int qq = q + 2 * s;
-      float2 a[8], b[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        a[i] = s ? csub(e0[i], o0[i]) : cadd(e0[i], o0[i]);
-        b[i] = s ? csub(e1[i], o1[i]) : cadd(e1[i], o1[i]);
-      }
-#pragma unroll
-      for (int pp = 0; pp < 2; ++pp) {
-        const int p = p0 + pp;
-        float re[8], im[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const float2 v = cmul(cadd(a[i], rot_mi(b[i], p)), tw[(qq * (n0 + i) + p * x0) & 255]);
-          re[i] = v.x;
-          im[i] = v.y;
-        }
-        uint8_t* buf = smem + (pp ? kOffA1 : kOffA0);
-        const int r = 64 * s + x0;
-        store8<TERMS>(buf, kmaj(r, n0), re);
-        store8<TERMS>(buf, kmaj(r, 64 + n0), im);
-      }
-    }
+  for (int r = 0; r < 8; ++r) {
+    in.e0[r] = ld(xb + r, n);
+    in.o0[r] = ld(xb + r, 64 + n);
+    in.e1[r] = ld(xb + r + 64, n);
+    in.o1[r] = ld(xb + r + 64, 64 + n);
   }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    in.o0[r] = rot_mi(in.o0[r], q);
+    in.o1[r] = rot_mi(in.o1[r], q);
+  }
+}
+
+// Operand of the y transform of x parity p (one buffer), MN-major: row 64 s + x0, K = n (real part) and 64 + n (imaginary part)
+// holds
+//   w^(q' n + p x0) [(X[x0][n] + (-i)^q' X[x0][n+64]) + (-i)^p (X[x0+64][n] + (-i)^q' X[x0+64][n+64])];
+// each thread writes 16-byte runs of eight rows.
+template <int TERMS>
+__device__ __forceinline__ void tc_build_y(uint8_t* buf, const YIn& in, const float2* tw, int q, int p, int tid) {
+  const int n = tid & 63, xb = (tid >> 6) * 8;
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const int qq = q + 2 * s;
+    float re[8], im[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const float2 a = s ? csub(in.e0[r], in.o0[r]) : cadd(in.e0[r], in.o0[r]);
+      const float2 b = s ? csub(in.e1[r], in.o1[r]) : cadd(in.e1[r], in.o1[r]);
+      const float2 v = cmul(cadd(a, rot_mi(b, p)), tw[(qq * n + p * (xb + r)) & 255]);
+      re[r] = v.x;
+      im[r] = v.y;
+    }
+    const int r0 = 64 * s + xb;
+    store8<TERMS>(buf, mnmaj(r0, n), re);
+    store8<TERMS>(buf, mnmaj(r0, 64 + n), im);
+  }
+}
+
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 }  // namespace
 
+// Persistent: each cluster of two CTAs runs the planes kt = cluster, cluster
+// + clusters, ...; the constant, the twiddles, the barriers and the tensor
+// memory are set up once.  Each of the 16 warps reads the tensor-memory
+// lanes of quarter (warp mod 4) and a quarter of every region's columns.
 template <int TERMS>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
     k_conv_tc(const float2* __restrict__ Sin, int in_pitch, const int32_t* __restrict__ in_pos,
               float2* __restrict__ Sout, int out_pitch, const int32_t* __restrict__ out_pos,
-              const float2* __restrict__ Hp, const uint4* __restrict__ Bimg, const float2* __restrict__ twg,
-              int adj, int* __restrict__ status) {
+              const float2* __restrict__ Hq, const uint4* __restrict__ Bimg, const float2* __restrict__ twg,
+              int planes, int adj, int* __restrict__ status) {
   extern __shared__ __align__(1024) uint8_t smem[];
   cg::cluster_group cluster = cg::this_cluster();
   const int q = (int)cluster.block_rank();
-  const int kt = blockIdx.x >> 1;
+  const int cid = blockIdx.x >> 1, nclusters = gridDim.x >> 1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int qw = warp & 3, hw = warp >> 2;
+  const int qw = warp & 3, cq = warp >> 2;
   const int L = 32 * qw + lane;  // tensor-memory lane (matrix row) this thread reads
   float2* tw = reinterpret_cast<float2*>(smem + kOffTw);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kOffMisc);
@@ -309,7 +339,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
   const uint32_t sbase = smem_u32(smem);
   const uint32_t bar0 = sbase + kOffBar;
 
-  // constant, twiddles, barriers, tensor memory
+  // constant, twiddles, barriers, tensor memory (once)
   {
     const int nb = TERMS > 1 ? 2 * kTile / 16 : kTile / 16;
     uint4* bs = reinterpret_cast<uint4*>(smem + kOffB);
@@ -330,205 +360,208 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tbase = *tslot;
   const uint32_t tl = tbase + ((uint32_t)(32 * qw) << 16);  // this warp's lane quarter
-  const float2* src = Sin + (size_t)kt * in_pitch;
+  const float scale = 1.0f / (4.0f * kTcN * kTcN);
+  const bool own = (L >> 6) == q;
 
-  // 1. y transforms (groups 0-3), operands built from the input plane in two passes
-  tc_build_y<TERMS>(smem, src, in_pos, tw, q, 0, tid);
-  tc_sync_for_mma();
-  if (tid == 0) {
-    tc_issue<TERMS>(sbase, kOffA0, false, tbase + 0, bar0 + 0);
-    tc_issue<TERMS>(sbase, kOffA1, false, tbase + 128, bar0 + 8);
-  }
-  tc_wait(bar0 + 8, fail, status);
-  tc_build_y<TERMS>(smem, src, in_pos, tw, q, 2, tid);
-  tc_sync_for_mma();
-  if (tid == 0) {
-    tc_issue<TERMS>(sbase, kOffA0, false, tbase + 256, bar0 + 16);
-    tc_issue<TERMS>(sbase, kOffA1, false, tbase + 384, bar0 + 24);
-  }
-
-  // 2. x transforms (groups 4-7): region p (rows (s, x0), columns j) -> MN-major
-  // operand rows (s, j), K = x0
 #pragma unroll 1
-  for (int p = 0; p < 4; ++p) {
-    tc_wait(bar0 + 8 * (2 + p), fail, status);
-    const int s = L >> 6, x0 = L & 63;
-    float re[32], im[32];
-    tld16(tl + 128 * p + 32 * hw, re);
-    tld16(tl + 128 * p + 32 * hw + 16, re + 16);
-    tld16(tl + 128 * p + 64 + 32 * hw, im);
-    tld16(tl + 128 * p + 64 + 32 * hw + 16, im + 16);
-    tld_wait();
-    uint8_t* buf = smem + ((p & 1) ? kOffA1 : kOffA0);
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      const int r0 = 64 * s + 32 * hw + 8 * g;
-      store8<TERMS>(buf, mnmaj(r0, x0), re + 8 * g);
-      store8<TERMS>(buf, mnmaj(r0, 64 + x0), im + 8 * g);
-    }
-    tc_sync_for_mma();
-    if (tid == 0) tc_issue<TERMS>(sbase, (p & 1) ? kOffA1 : kOffA0, true, tbase + 128 * p, bar0 + 8 * (4 + p));
-  }
+  for (int kt = cid, it = 0; kt < planes; kt += nclusters, ++it) {
+    const uint32_t ph = (uint32_t)it & 1u;  // barrier phase of this plane
+    const float2* src = Sin + (size_t)kt * in_pitch;
 
-  // 3. multiply by H (conj H for the adjoint), inverse x transforms (groups
-  // 8-11): rows (s, j) stay; the operand is written conjugated
+    // 1. y transforms (groups 0-3), operands built from the input plane (read
+    // once per plane into registers), one buffer at a time: parity p into
+    // buffer p mod 2 once the group that last read it (p - 2) is done
+    YIn yin;
+    tc_load_y(yin, src, in_pos, q, tid);
+    if (it > 0) cluster_wait();  // the partner has read the previous plane's staging rows (buffers 0, 1)
 #pragma unroll 1
-  for (int p = 0; p < 4; ++p) {
-    const int s = L >> 6, j = L & 63;
-    const int ky = 4 * j + q + 2 * s, fy = ky <= kTcN ? ky : 2 * kTcN - ky;
-    const float4* hrow = reinterpret_cast<const float4*>(Hp + (((size_t)kt * (kTcN + 1) + fy) * 4 + p) * 64 + 32 * hw);
-    float4 h[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) h[i] = __ldg(hrow + i);
-    tc_wait(bar0 + 8 * (6 + p), fail, status);
-    float re[32], im[32];
-    tld16(tl + 128 * p + 32 * hw, re);
-    tld16(tl + 128 * p + 32 * hw + 16, re + 16);
-    tld16(tl + 128 * p + 64 + 32 * hw, im);
-    tld16(tl + 128 * p + 64 + 32 * hw + 16, im + 16);
-    tld_wait();
-    const float sg = adj ? -1.f : 1.f;
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
-      const float hr = (i & 1) ? h[i >> 1].z : h[i >> 1].x;
-      const float hi = sg * ((i & 1) ? h[i >> 1].w : h[i >> 1].y);
-      const float zr = re[i], zi = im[i];
-      re[i] = zr * hr - zi * hi;
-      im[i] = -(zr * hi + zi * hr);
+    for (int p = 0; p < 4; ++p) {
+      if (p >= 2) tc_wait(bar0 + 8 * (p - 2), ph, fail, status);
+      tc_build_y<TERMS>(smem + ((p & 1) ? kOffA1 : kOffA0), yin, tw, q, p, tid);
+      tc_sync_for_mma();
+      if (tid == 0) tc_issue<TERMS>(sbase, (p & 1) ? kOffA1 : kOffA0, true, tbase + 128 * p, bar0 + 8 * p);
     }
-    uint8_t* buf = smem + ((p & 1) ? kOffA1 : kOffA0);
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      const int k0 = 32 * hw + 8 * g;
-      store8<TERMS>(buf, kmaj(L, k0), re + 8 * g);
-      store8<TERMS>(buf, kmaj(L, 64 + k0), im + 8 * g);
-    }
-    tc_sync_for_mma();
-    if (tid == 0) tc_issue<TERMS>(sbase, (p & 1) ? kOffA1 : kOffA0, false, tbase + 128 * p, bar0 + 8 * (8 + p));
-  }
 
-  // 4. recombine the four x parities, out[x0 + 64 t] = sum_p i^(p t) w^(-p x0) I_p[x0]
-  // with I_p = conj(region p), into the inverse y operands (buffer s, MN-major
-  // rows x, K = j, conjugated)
-  tc_wait(bar0 + 8 * 11, fail, status);
-  {
-    const int s = L >> 6, j = L & 63;
-    uint8_t* buf = smem + (s ? kOffA1 : kOffA0);
+    // 2. x transforms (groups 4-7): region p (rows (s, x0), columns j) ->
+    // MN-major operand rows (s, j), K = x0
 #pragma unroll 1
-    for (int c = 0; c < 4; ++c) {
-      const int xb = 32 * hw + 8 * c;
-      float ur[4][8], ui[4][8];
-#pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        tld8(tl + 128 * p + xb, ur[p]);
-        tld8(tl + 128 * p + 64 + xb, ui[p]);
-      }
+    for (int p = 0; p < 4; ++p) {
+      tc_wait(bar0 + 8 * (2 + p), ph, fail, status);
+      const int s = L >> 6, x0 = L & 63;
+      float re[16], im[16];
+      tld16(tl + 128 * p + 16 * cq, re);
+      tld16(tl + 128 * p + 64 + 16 * cq, im);
       tld_wait();
-      float v0r[8], v0i[8], v1r[8], v1i[8];
+      uint8_t* buf = smem + ((p & 1) ? kOffA1 : kOffA0);
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        float2 u[4];
+      for (int g = 0; g < 2; ++g) {
+        const int r0 = 64 * s + 16 * cq + 8 * g;
+        store8<TERMS>(buf, mnmaj(r0, x0), re + 8 * g);
+        store8<TERMS>(buf, mnmaj(r0, 64 + x0), im + 8 * g);
+      }
+      tc_sync_for_mma();
+      if (tid == 0) tc_issue<TERMS>(sbase, (p & 1) ? kOffA1 : kOffA0, true, tbase + 128 * p, bar0 + 8 * (4 + p));
+    }
+
+    // 3. multiply by H (conj H for the adjoint), inverse x transforms (groups
+    // 8-11): rows (s, j) stay; the operand is written conjugated
+#pragma unroll 1
+    for (int p = 0; p < 4; ++p) {
+      // H(kx = 4 m + p, ky of row L) at Hq[kt][q][fold kx][L]: a warp reads 32 consecutive values
+      const float2* hcol = Hq + ((size_t)kt * 2 + q) * (kTcN + 1) * 128 + L;
+      float2 h[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int kx = 4 * (16 * cq + i) + p, fx = kx <= kTcN ? kx : 2 * kTcN - kx;
+        h[i] = __ldg(hcol + fx * 128);
+      }
+      tc_wait(bar0 + 8 * (6 + p), ph, fail, status);
+      float re[16], im[16];
+      tld16(tl + 128 * p + 16 * cq, re);
+      tld16(tl + 128 * p + 64 + 16 * cq, im);
+      tld_wait();
+      const float sg = adj ? -1.f : 1.f;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const float hr = h[i].x, hi = sg * h[i].y;
+        const float zr = re[i], zi = im[i];
+        re[i] = zr * hr - zi * hi;
+        im[i] = -(zr * hi + zi * hr);
+      }
+      uint8_t* buf = smem + ((p & 1) ? kOffA1 : kOffA0);
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+        const int k0 = 16 * cq + 8 * g;
+        store8<TERMS>(buf, kmaj(L, k0), re + 8 * g);
+        store8<TERMS>(buf, kmaj(L, 64 + k0), im + 8 * g);
+      }
+      tc_sync_for_mma();
+      if (tid == 0) tc_issue<TERMS>(sbase, (p & 1) ? kOffA1 : kOffA0, false, tbase + 128 * p, bar0 + 8 * (8 + p));
+    }
+
+    // 4. recombine the four x parities, out[x0 + 64 t] = sum_p i^(p t) w^(-p x0) I_p[x0]
+    // with I_p = conj(region p), into the inverse y operands (buffer s, MN-major
+    // rows x, K = j, conjugated)
+    tc_wait(bar0 + 8 * 11, ph, fail, status);
+    {
+      const int s = L >> 6, j = L & 63;
+      uint8_t* buf = smem + (s ? kOffA1 : kOffA0);
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int xb = 16 * cq + 8 * c;
+        float ur[4][8], ui[4][8];
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
-          u[p] = make_float2(ur[p][i], -ui[p][i]);
-          if (p) u[p] = cmulc(u[p], tw[(p * (xb + i)) & 255]);
+          tld8(tl + 128 * p + xb, ur[p]);
+          tld8(tl + 128 * p + 64 + xb, ui[p]);
         }
-        const float2 e02 = cadd(u[0], u[2]), d02 = csub(u[0], u[2]);
-        const float2 e13 = cadd(u[1], u[3]), d13 = csub(u[1], u[3]);
-        v0r[i] = e02.x + e13.x;
-        v0i[i] = -(e02.y + e13.y);
-        v1r[i] = d02.x - d13.y;
-        v1i[i] = -(d02.y + d13.x);
-      }
-      store8<TERMS>(buf, mnmaj(xb, j), v0r);
-      store8<TERMS>(buf, mnmaj(xb, 64 + j), v0i);
-      store8<TERMS>(buf, mnmaj(64 + xb, j), v1r);
-      store8<TERMS>(buf, mnmaj(64 + xb, 64 + j), v1i);
-    }
-  }
-  tc_sync_for_mma();
-  if (tid == 0) {
-    tc_issue<TERMS>(sbase, kOffA0, true, tbase + 0, bar0 + 8 * 12);
-    tc_issue<TERMS>(sbase, kOffA1, true, tbase + 128, bar0 + 8 * 13);
-  }
-
-  // 5. recombine the two ky sub-parities: this CTA's part
-  //   P[x][y0 + 64 t] = sum_s i^(q' t) w^(-q' y0) conj(region s)[x][y0],
-  // and sum the two CTAs' parts; CTA q writes rows [64 q, 64 q + 64)
-  tc_wait(bar0 + 8 * 13, fail, status);
-  const float scale = 1.0f / (4.0f * kTcN * kTcN);
-  float2* ex = reinterpret_cast<float2*>(smem + kOffA0);  // rows of the partner CTA
-  const bool own = (L >> 6) == q;
-  auto part = [&](int c, float2 (&o0)[8], float2 (&o1)[8]) {
-    const int yb = 32 * hw + 8 * c;
-    float r0[8], i0[8], r1[8], i1[8];
-    tld8(tl + yb, r0);
-    tld8(tl + 64 + yb, i0);
-    tld8(tl + 128 + yb, r1);
-    tld8(tl + 192 + yb, i1);
-    tld_wait();
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int y0 = yb + i;
-      const float2 u0 = cmulc(make_float2(r0[i], -i0[i]), tw[(q * y0) & 255]);
-      const float2 u1 = cmulc(make_float2(r1[i], -i1[i]), tw[((q + 2) * y0) & 255]);
-      o0[i] = cscale(cadd(u0, u1), scale);
-      o1[i] = cscale(rot_i(csub(u0, u1), q), scale);
-    }
-  };
-  if (!own) {
-    float2* row = ex + (L & 63) * kExPitch;
-#pragma unroll 1
-    for (int c = 0; c < 4; ++c) {
-      float2 o0[8], o1[8];
-      part(c, o0, o1);
-      const int yb = 32 * hw + 8 * c;
-#pragma unroll
-      for (int i = 0; i < 8; i += 2) {
-        *reinterpret_cast<float4*>(row + yb + i) = make_float4(o0[i].x, o0[i].y, o0[i + 1].x, o0[i + 1].y);
-        *reinterpret_cast<float4*>(row + 64 + yb + i) = make_float4(o1[i].x, o1[i].y, o1[i + 1].x, o1[i + 1].y);
-      }
-    }
-  }
-  cluster.sync();
-  if (own) {
-    const float2* prow = cluster.map_shared_rank(ex, 1 - q) + (L & 63) * kExPitch;
-    float2* dst = Sout + (size_t)kt * out_pitch;
-    const int x = L;
-#pragma unroll 1
-    for (int c = 0; c < 4; ++c) {
-      float2 o0[8], o1[8];
-      part(c, o0, o1);
-      const int yb = 32 * hw + 8 * c;
-#pragma unroll
-      for (int i = 0; i < 8; i += 2) {
-        const float4 a = *reinterpret_cast<const float4*>(prow + yb + i);
-        const float4 b = *reinterpret_cast<const float4*>(prow + 64 + yb + i);
-        o0[i] = cadd(o0[i], make_float2(a.x, a.y));
-        o0[i + 1] = cadd(o0[i + 1], make_float2(a.z, a.w));
-        o1[i] = cadd(o1[i], make_float2(b.x, b.y));
-        o1[i + 1] = cadd(o1[i + 1], make_float2(b.z, b.w));
-      }
-      if (out_pos == nullptr) {
-        float4* d0 = reinterpret_cast<float4*>(dst + x * kTcN + yb);
-        float4* d1 = reinterpret_cast<float4*>(dst + x * kTcN + 64 + yb);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          d0[i] = make_float4(o0[2 * i].x, o0[2 * i].y, o0[2 * i + 1].x, o0[2 * i + 1].y);
-          d1[i] = make_float4(o1[2 * i].x, o1[2 * i].y, o1[2 * i + 1].x, o1[2 * i + 1].y);
-        }
-      } else {
+        tld_wait();
+        float v0r[8], v0i[8], v1r[8], v1i[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          const int j0 = __ldg(out_pos + x * kTcN + yb + i), j1 = __ldg(out_pos + x * kTcN + 64 + yb + i);
-          if (j0 >= 0) dst[j0] = o0[i];
-          if (j1 >= 0) dst[j1] = o1[i];
+          float2 u[4];
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            u[p] = make_float2(ur[p][i], -ui[p][i]);
+            if (p) u[p] = cmulc(u[p], tw[(p * (xb + i)) & 255]);
+          }
+          const float2 e02 = cadd(u[0], u[2]), d02 = csub(u[0], u[2]);
+          const float2 e13 = cadd(u[1], u[3]), d13 = csub(u[1], u[3]);
+          v0r[i] = e02.x + e13.x;
+          v0i[i] = -(e02.y + e13.y);
+          v1r[i] = d02.x - d13.y;
+          v1i[i] = -(d02.y + d13.x);
+        }
+        store8<TERMS>(buf, mnmaj(xb, j), v0r);
+        store8<TERMS>(buf, mnmaj(xb, 64 + j), v0i);
+        store8<TERMS>(buf, mnmaj(64 + xb, j), v1r);
+        store8<TERMS>(buf, mnmaj(64 + xb, 64 + j), v1i);
+      }
+    }
+    tc_sync_for_mma();
+    if (tid == 0) {
+      tc_issue<TERMS>(sbase, kOffA0, true, tbase + 0, bar0 + 8 * 12);
+      tc_issue<TERMS>(sbase, kOffA1, true, tbase + 128, bar0 + 8 * 13);
+    }
+
+    // 5. recombine the two ky sub-parities: this CTA's part
+    //   P[x][y0 + 64 t] = sum_s i^(q' t) w^(-q' y0) conj(region s)[x][y0],
+    // and sum the two CTAs' parts; CTA q writes rows [64 q, 64 q + 64)
+    tc_wait(bar0 + 8 * 13, ph, fail, status);
+    if (tid == 0 && kt + nclusters < planes) {  // the next plane's input and spectrum into L2
+      if (in_pos == nullptr) prefetch_l2(Sin + (size_t)(kt + nclusters) * in_pitch, kTcN * kTcN * 8);
+      prefetch_l2(Hq + ((size_t)(kt + nclusters) * 2 + q) * (kTcN + 1) * 128, (kTcN + 1) * 128 * 8);
+    }
+    auto part = [&](int c, float2 (&o0)[8], float2 (&o1)[8]) {
+      const int yb = 16 * cq + 8 * c;
+      float r0[8], i0[8], r1[8], i1[8];
+      tld8(tl + yb, r0);
+      tld8(tl + 64 + yb, i0);
+      tld8(tl + 128 + yb, r1);
+      tld8(tl + 192 + yb, i1);
+      tld_wait();
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int y0 = yb + i;
+        const float2 u0 = cmulc(make_float2(r0[i], -i0[i]), tw[(q * y0) & 255]);
+        const float2 u1 = cmulc(make_float2(r1[i], -i1[i]), tw[((q + 2) * y0) & 255]);
+        o0[i] = cscale(cadd(u0, u1), scale);
+        o1[i] = cscale(rot_i(csub(u0, u1), q), scale);
+      }
+    };
+    {
+      // every row's partial into shared memory: own rows to the own buffer,
+      // the partner's rows to the exchange buffer it reads
+      float2* row = reinterpret_cast<float2*>(smem + (own ? kOffOwn : kOffEx)) + (L & 63) * kExPitch;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        float2 o0[8], o1[8];
+        part(c, o0, o1);
+        const int yb = 16 * cq + 8 * c;
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) {
+          *reinterpret_cast<float4*>(row + yb + i) = make_float4(o0[i].x, o0[i].y, o0[i + 1].x, o0[i + 1].y);
+          *reinterpret_cast<float4*>(row + 64 + yb + i) = make_float4(o1[i].x, o1[i].y, o1[i + 1].x, o1[i + 1].y);
         }
       }
     }
+    cluster.sync();
+    {
+      // rows [64 q, 64 q + 64): own part + the partner's, a warp per 32
+      // consecutive y of a row
+      const float2* mine = reinterpret_cast<const float2*>(smem + kOffOwn);
+      const float2* theirs = cluster.map_shared_rank(reinterpret_cast<const float2*>(smem + kOffEx), 1 - q);
+      float2* dst = Sout + (size_t)kt * out_pitch;
+      const int y = tid & 127, r0 = tid >> 7;
+      constexpr int R = 64 / (kTcThreads / 128);
+      float2 a[R], b[R];
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        const int r = r0 + i * (kTcThreads / 128);
+        a[i] = mine[r * kExPitch + y];
+        b[i] = theirs[r * kExPitch + y];
+      }
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        const float2 v = cadd(a[i], b[i]);
+        const int x = 64 * q + r0 + i * (kTcThreads / 128);
+        if (out_pos == nullptr) {
+          dst[x * kTcN + y] = v;
+        } else {
+          const int j = __ldg(out_pos + x * kTcN + y);
+          if (j >= 0) dst[j] = v;
+        }
+      }
+    }
+    // done reading the partner's staging rows; the matching wait comes before
+    // the next plane writes buffers 0 and 1 (or before the exit), so the
+    // next plane's input loads overlap the partner's last reads
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    cluster_arrive();
   }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  cluster.sync();  // the partner has read this CTA's exchange rows; no tensor-memory access in flight
+  if (cid < planes) cluster_wait();
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase));
 }
 
@@ -546,18 +579,20 @@ __global__ void k_tc_bimage(const float* __restrict__ Bf, uint16_t* __restrict__
   img[kTile / 2 + off] = *reinterpret_cast<const uint16_t*>(&lo);
 }
 
-// H rearranged for the kernel's reads: Hp[kt][fy][p][m] = H(kx = 4 m + p, ky)
-// with fy = fold(ky); the plan stores H[kt][fold kx][fold ky], fold(k) =
-// min(k, 2N - k).
-__global__ void k_tc_hperm(const float2* __restrict__ H, float2* __restrict__ Hp, int planes) {
-  const size_t total = (size_t)planes * (kTcN + 1) * 4 * 64;
+// H rearranged for the kernel's reads: Hq[kt][q][fx][L] = H(kx, ky) for
+// every kx with fold(kx) = fx and the ky of row L = 64 s + j of CTA q,
+// ky = 4 j + q + 2 s; the plan stores H[kt][fold kx][fold ky], fold(k) =
+// min(k, 2N - k).  A warp's 32 rows are then 32 consecutive values.
+__global__ void k_tc_hperm(const float2* __restrict__ H, float2* __restrict__ Hq, int planes) {
+  const size_t total = (size_t)planes * 2 * (kTcN + 1) * 128;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const int m = (int)(i & 63), p = (int)((i >> 6) & 3);
-    const size_t r = i >> 8;
-    const int fy = (int)(r % (kTcN + 1));
-    const size_t kt = r / (kTcN + 1);
-    const int kx = 4 * m + p, fx = kx <= kTcN ? kx : 2 * kTcN - kx;
-    Hp[i] = H[(kt * (kTcN + 1) + fx) * (kTcN + 1) + fy];
+    const int L = (int)(i & 127);
+    const size_t r = i >> 7;
+    const int fx = (int)(r % (kTcN + 1));
+    const int q = (int)((r / (kTcN + 1)) & 1);
+    const size_t kt = r / (2 * (kTcN + 1));
+    const int ky = 4 * (L & 63) + q + 2 * (L >> 6), fy = ky <= kTcN ? ky : 2 * kTcN - ky;
+    Hq[i] = H[(kt * (kTcN + 1) + fx) * (kTcN + 1) + fy];
   }
 }
 
@@ -598,7 +633,7 @@ nlos_status set_lateral_mode(Plan& P, int mode, cudaStream_t st) {
   LateralTC* L = new LateralTC();
   P.lateral = L;
   const int planes = P.nt + 1;
-  const size_t hp = (size_t)planes * (kTcN + 1) * 4 * 64;
+  const size_t hp = (size_t)planes * 2 * (kTcN + 1) * 128;
   float* d_Bf = nullptr;
   auto cleanup = [&](nlos_status s) {
     cudaFree(d_Bf);
@@ -644,9 +679,11 @@ nlos_status launch_conv_tc(const Plan& P, const float2* Sin, bool in_compact, fl
     return fail(NLOS_ERR_INVALID_ARG, "tensor-core lateral stage: spectra must be 16-byte aligned");
   auto kern = L->mode == 2 ? k_conv_tc<1> : k_conv_tc<3>;
   NLOS_TRY(ensure_smem(kern, kTcSmem));
-  kern<<<2 * (P.nt + 1), kTcThreads, kTcSmem, st>>>(
+  const int planes = P.nt + 1;
+  const int clusters = std::min(planes, std::max(1, device_sm_count() / 2));
+  kern<<<2 * clusters, kTcThreads, kTcSmem, st>>>(
       Sin, in_compact ? P.ncols : full, in_compact ? P.d_colpos : nullptr, Sout, out_compact ? P.ncols : full,
-      out_compact ? P.d_colpos : nullptr, L->d_Hp, L->d_B, P.d_twx, adj ? 1 : 0, L->d_status);
+      out_compact ? P.d_colpos : nullptr, L->d_Hp, L->d_B, P.d_twx, planes, adj ? 1 : 0, L->d_status);
   NLOS_LAUNCH_CHECK("k_conv_tc");
   return NLOS_OK;
 }
