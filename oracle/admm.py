@@ -188,7 +188,7 @@ def linearised_step(fwd, adj, data, u_bar, rhs_reg, L, c1, eta, max_backtracks):
 
 def alg1(tau0, mask, geom, a, b, mu, iters, L0=None, eta=2.0, eps_normal=1e-6,
          phi_kind="tsc", eps_stop=0.0, max_backtracks=30, norm2=None, op=None,
-         restart=False):
+         restart=False, u_init=None):
     """Algorithm 1: ADMM for min_u 1/2 ||A u - tau0||^2_{Omega minus X} + R(kappa(u)).
 
     Per iteration, in order: v (Eq. 7 at u-bar), the linearised u-step with
@@ -196,7 +196,8 @@ def alg1(tau0, mask, geom, a, b, mu, iters, L0=None, eta=2.0, eps_normal=1e-6,
     (FISTA extrapolation of Algorithm 1), phi(kappa(u^{k+1})) and the
     relative energy change e^{k+1}.  With ``restart`` the FISTA sequence is
     reset (t <- 1, so the next extrapolation weight is 0) whenever the energy
-    increases.  Returns (u, history).
+    increases.  ``u_init`` replaces the zero start u^0 = u-bar^0 = 0 (phi and
+    the initial energy are then those of u_init).  Returns (u, history).
     """
     if op is None:
         op = Operator(geom, mask)
@@ -209,8 +210,8 @@ def alg1(tau0, mask, geom, a, b, mu, iters, L0=None, eta=2.0, eps_normal=1e-6,
         L0 = 2.0 * norm2
     L = float(L0)
 
-    u = np.zeros(shape)
-    u_bar = np.zeros(shape)
+    u = np.zeros(shape) if u_init is None else np.array(u_init, dtype=np.float64)
+    u_bar = u.copy()
     lam = np.zeros((3,) + shape)
     ph = phi(curvature(u, eps_normal), a, b, phi_kind)
     t = 1.0
@@ -250,6 +251,22 @@ def alg1(tau0, mask, geom, a, b, mu, iters, L0=None, eta=2.0, eps_normal=1e-6,
         if eps_stop > 0.0 and e <= eps_stop:
             break
     return u, hist
+
+
+def backprojection_init(op, tau0):
+    """Back-projection start u^0 = s A_D^T tau0 (the direct back-projection
+    reconstruction the paper contrasts with the iterative methods, Sec. 1;
+    used here, like the Algorithm-1 start of Algorithm 2 in the remark after
+    Algorithm 2, to initialise the ADMM).  The paper fixes no scale; reading:
+    s minimises the data term 1/2 ||A_D (s g) - tau0||^2 over s, with
+    g = A_D^T tau0, which is s = <A_D g, tau0> / ||A_D g||^2 = ||g||^2 / ||A_D g||^2
+    (the exact line-search step of steepest descent from u = 0); s = 0 when
+    A_D g = 0.  Returns (u0, s)."""
+    g = op.adjoint_d(tau0)
+    ag = op.forward_d(g)
+    den = float(np.sum(ag * ag))
+    sc = float(np.sum(g * g)) / den if den > 0.0 else 0.0
+    return sc * g, sc
 
 
 # ---------------------------------------------------------------------------

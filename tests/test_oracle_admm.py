@@ -305,3 +305,67 @@ def test_configs_use_paper_parameters():
         gp["alg2_lambda_8x8"], gp["alg2_a_tau_8x8"], gp["alg2_b_tau_8x8"],
         gp["alg2_a_u_8x8"], gp["alg2_b_u_8x8"])
     assert c1["bin_width_s"] == gp["bowling_bin_width_s"] and c1["nt"] == gp["bowling_bins"]
+
+
+def test_backprojection_init_against_explicit_matrix_least_squares():
+    """u0 = s A_D^T tau0 with s the least-squares scale, recomputed from the
+    explicit matrix of A_D and numpy's least-squares solver on a tiny grid."""
+    g = lct.Geometry(8, 8, 16, 128e-12)
+    mask = synth.stride_mask(8, 8, 2)
+    op = lct.Operator(g, mask)
+    tau0 = np.random.default_rng(5).random(g.shape) * op.M
+    u0, sc = admm.backprojection_init(op, tau0)
+    A = lct.explicit_matrix(op)                      # A_D: rows of unsampled columns are zero
+    b = tau0.ravel()
+    gv = A.T @ b
+    s_ls = np.linalg.lstsq((A @ gv)[:, None], b, rcond=None)[0][0]
+    assert abs(sc - s_ls) <= 1e-10 * abs(s_ls)
+    assert np.allclose(u0.ravel(), s_ls * gv, rtol=1e-10, atol=1e-14 * np.abs(gv).max())
+
+
+def test_backprojection_scale_minimises_the_data_term():
+    cfg, g, mask, vol, tau0 = _small_scene(1, 16, 64)
+    op = lct.Operator(g, mask)
+    u0, sc = admm.backprojection_init(op, tau0)
+    d = op.M * tau0
+
+    def f(s):
+        r = op.forward_d(u0 * (s / sc)) - d
+        return 0.5 * float(np.sum(r * r))
+    assert sc > 0
+    for s in (0.5 * sc, 0.9 * sc, 0.99 * sc, 1.01 * sc, 1.1 * sc, 2.0 * sc, 0.0):
+        assert f(sc) <= f(s)
+
+
+def test_backprojection_of_point_scatterer_peaks_at_it():
+    n, nt = 16, 64
+    g = lct.Geometry(n, n, nt, 32e-12 * 256 / nt)
+    mask = synth.stride_mask(n, n, 2)
+    op = lct.Operator(g, mask)
+    vol = np.zeros(g.shape)
+    vol[8, 8, 30] = 1.0                              # a sampled column (stride 2, offset 1 would be odd)
+    vol[9, 9, 30] = 1.0
+    u0, _ = admm.backprojection_init(op, op.forward_d(vol))
+    x, y, t = np.unravel_index(np.argmax(u0), u0.shape)
+    assert abs(t - 30) <= 1 and abs(x - 8.5) <= 1.5 and abs(y - 8.5) <= 1.5
+
+
+def test_backprojection_zero_data_and_default_start():
+    cfg, g, mask, _, tau0 = _small_scene(1, 8, 32)
+    op = lct.Operator(g, mask)
+    u0, sc = admm.backprojection_init(op, np.zeros(g.shape))
+    assert sc == 0.0 and np.all(u0 == 0.0)
+    # an explicit zero start is the default start, bit for bit
+    ua, ha = admm.alg1(tau0, mask, g, cfg["a"], cfg["b"], cfg["mu"], 4, op=op)
+    ub, hb = admm.alg1(tau0, mask, g, cfg["a"], cfg["b"], cfg["mu"], 4, op=op, u_init=np.zeros(g.shape))
+    assert np.array_equal(ua, ub) and ha["E"] == hb["E"]
+
+
+def test_alg1_from_backprojection_decreases_energy():
+    cfg, g, mask, vol, tau0 = _small_scene(1)
+    op = lct.Operator(g, mask)
+    u0, _ = admm.backprojection_init(op, tau0)
+    u, h = admm.alg1(tau0, mask, g, cfg["a"], cfg["b"], cfg["mu"], 30, op=op, u_init=u0)
+    E = np.array(h["E"])
+    assert E[-1] < E[0] and np.mean(np.diff(E) < 0) >= 0.8
+    assert sum(h["backtracks"]) == 0
