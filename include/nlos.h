@@ -56,6 +56,10 @@ typedef int32_t nlos_status;
 #define NLOS_RADIOMETRY_COMPENSATED 0 /* transient pre-multiplied by t^4: weight rho   */
 #define NLOS_RADIOMETRY_RAW 1         /* 1/d^4 fall-off of Eq. 2: weight rho^-3       */
 
+/* Start of the ADMM iterations (nlos_params.init). */
+#define NLOS_INIT_ZERO 0         /* u0 = 0 (Algorithms 1-2 as printed)                        */
+#define NLOS_INIT_BACKPROJECT 1  /* u0 = s A_D^T tau0, s = ||A_D^T tau0||^2 / ||A_D A_D^T tau0||^2 */
+
 /* phi(kappa) of Sec. 3 (below Eq. 4). */
 #define NLOS_PHI_TSC 0 /* a + b kappa^2 (the paper's choice) */
 #define NLOS_PHI_TAC 1 /* a + b |kappa|                      */
@@ -99,6 +103,13 @@ typedef struct {
                             (a, b, mu, default L0, no restart) and start Algorithm 2 from
                             their u (the remark after Algorithm 2; tau starts at 0);
                             0 = start from u = 0.  Ignored for model 1; < 0 is an error. */
+  int32_t init;          /* NLOS_INIT_*: start of the first phase (the warm stage when
+                            warm_start_iters > 0).  NLOS_INIT_BACKPROJECT starts from the
+                            back-projection of the data (the direct method of Sec. 1) scaled
+                            by the s that minimises 1/2 ||A_D (s g) - tau0||^2, g = A_D^T tau0
+                            (s = 0 for zero data); phi and the initial energy are those of
+                            u0; tau starts at 0 (model 2).  Computed on the device (no host
+                            synchronisation). */
 } nlos_params;
 
 /* Per-reconstruction statistics (host struct, filled after the run). */
@@ -125,7 +136,8 @@ int32_t nlos_version(void);
  * settings of Sec. 5.2.1 (a = 9e-5, b = 2e-5, mu = 0.1; lambda = 235,
  * a_tau = 4e-4, b_tau = 3e-2, a_u = 2e-4, b_u = 4.5e-4), mu1..3 = 1, 800, 2 and
  * T_max = 200 / 300 (Sec. 5.1), eps_stop = 0, L0 = 0 (= 2||A_D||^2), eta = 2,
- * max_backtracks = 30, eps_normal = 1e-6, restart = -1, warm_start_iters = 0.
+ * max_backtracks = 30, eps_normal = 1e-6, restart = -1, warm_start_iters = 0,
+ * init = NLOS_INIT_ZERO.
  * Host only. */
 nlos_status nlos_params_default(int32_t model, nlos_params* out);
 

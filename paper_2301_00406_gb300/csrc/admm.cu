@@ -94,6 +94,37 @@ __global__ void __launch_bounds__(kSumThreads) k_sum_to(const double* __restrict
   if (threadIdx.x == 0) *out = r[0];
 }
 
+// s = sum(pnum) / sum(pden) over nb block partials (0 when the denominator is
+// 0), the back-projection scale, into *out.
+__global__ void __launch_bounds__(kSumThreads) k_ratio(const double* __restrict__ pnum,
+                                                       const double* __restrict__ pden, int nb,
+                                                       double* __restrict__ out) {
+  const int t0[1] = {0};
+  double n[1], d[1];
+  sum_partials_block<1>(pnum, nb, t0, n);
+  sum_partials_block<1>(pden, nb, t0, d);
+  if (threadIdx.x == 0) *out = d[0] > 0.0 ? n[0] / d[0] : 0.0;
+}
+
+// out = a x + b y
+__global__ void k_axpby(const float* __restrict__ x, float a, const float* __restrict__ y, float b,
+                        float* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = a * x[i] + b * y[i];
+}
+
+// x *= s, y *= s for the device scalar s (FP64, applied in FP32).
+__global__ void k_scale2(float* __restrict__ x, size_t nx, float* __restrict__ y, size_t ny,
+                         const double* __restrict__ s) {
+  const float f = (float)*s;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nx + ny; i += (size_t)gridDim.x * blockDim.x) {
+    if (i < nx)
+      x[i] *= f;
+    else
+      y[i - nx] *= f;
+  }
+}
+
 // Copy the sampled columns of a full [nx*ny][nt] array into compact form.
 __global__ void k_gather_cols(const float* __restrict__ full, const int32_t* __restrict__ cols, int ncols, int nt,
                               float* __restrict__ out) {
@@ -846,17 +877,20 @@ static float phi_zero(double a, double b, int kind) {
 static nlos_status init_scalars(Plan& P, SolverState* s, double L0, const float* sumsq_src, size_t n, double scale,
                                 cudaStream_t st, const float* au0 = nullptr, const float* u0 = nullptr,
                                 const float* ph0 = nullptr) {
+  // (au0 == nullptr with u0 given: the sum phi |grad u0| term alone)
   { KTimer kt_(P, KC_SMALL, st);
   k_sumsq<<<stencil_blocks(P), kStencilThreads, 0, st>>>(sumsq_src, n, s->pc);
   }
   NLOS_LAUNCH_CHECK("k_sumsq");
   if (au0) {
-    const Vox g = make_vox(P.nx, P.ny, P.nt);
-    const VoxIter vi{ilog2i(P.nt), ilog2i(P.ny)};
     { KTimer kt_(P, KC_SMALL, st);
     k_sumsq<<<stencil_blocks(P), kStencilThreads, 0, st>>>(au0, s->V, s->pa);
     }
     NLOS_LAUNCH_CHECK("k_sumsq");
+  }
+  if (u0) {
+    const Vox g = make_vox(P.nx, P.ny, P.nt);
+    const VoxIter vi{ilog2i(P.nt), ilog2i(P.ny)};
     { KTimer kt_(P, KC_SMALL, st);
     k_tv_weighted<<<stencil_blocks(P), kStencilThreads, 0, st>>>(u0, ph0, g, vi, s->V, s->pb);
     }
@@ -864,7 +898,7 @@ static nlos_status init_scalars(Plan& P, SolverState* s, double L0, const float*
   }
   { KTimer kt_(P, KC_SMALL, st);
   k_init_scalars<<<1, kSumThreads, 0, st>>>(s->sc, L0, stencil_blocks(P), s->pc, scale, au0 ? s->pa : nullptr, 0.5,
-                                            au0 ? s->pb : nullptr, 1.0);
+                                            u0 ? s->pb : nullptr, 1.0);
   }
   NLOS_LAUNCH_CHECK("k_init_scalars");
   return NLOS_OK;
@@ -877,6 +911,28 @@ static nlos_status init_scalars(Plan& P, SolverState* s, double L0, const float*
 // server interleave the steps of many jobs on their own streams.
 // ---------------------------------------------------------------------------
 // Initial state of the run j.p (u0 = u_init for model 2 when given, else 0).
+// u0 = s A_D^T tau0 into u (full field) and s A_D u0 / s into au (compact
+// sampled columns) with s = ||g||^2 / ||A_D g||^2, g = A_D^T tau0, computed on
+// the device from the compact data tau0c; partials pa / pb of the solver state
+// and the plan's scalar scratch are used.
+static nlos_status backproject(JobRun& j, const float* tau0c, float* u, float* au) {
+  Plan& P = *j.P;
+  SolverState* s = j.s;
+  cudaStream_t st = j.st;
+  const size_t V = s->V, C = (size_t)P.ncols * P.nt;
+  NLOS_TRY(apply_adjoint(P, tau0c, u, true, st));
+  NLOS_TRY(apply_forward(P, u, au, true, st));
+  double* d_s = reinterpret_cast<double*>(P.d_scal);
+  { KTimer kt_(P, KC_SMALL, st);
+  k_sumsq<<<stencil_blocks(P), kStencilThreads, 0, st>>>(u, V, s->pa);
+  k_sumsq<<<stencil_blocks(P), kStencilThreads, 0, st>>>(au, C, s->pb);
+  k_ratio<<<1, kSumThreads, 0, st>>>(s->pa, s->pb, stencil_blocks(P), d_s);
+  k_scale2<<<elem_grid(V + C), 256, 0, st>>>(u, V, au, C, d_s);
+  }
+  NLOS_LAUNCH_CHECK("back-projection start");
+  return NLOS_OK;
+}
+
 static nlos_status init_run(JobRun& j, const float* u_init) {
   Plan& P = *j.P;
   const nlos_params& p = j.p;
@@ -895,17 +951,40 @@ static nlos_status init_run(JobRun& j, const float* u_init) {
   j.done = p.iters == 0;
   if (p.model == 1) {
     const size_t C = (size_t)P.ncols * P.nt;
-    NLOS_TRY(zero(s->uk, V, st));
-    NLOS_TRY(zero(s->ub, V, st));
     NLOS_TRY(zero(s->lam, 3 * V, st));
-    for (int i = 0; i < 3; ++i) NLOS_TRY(zero(s->cache[i], C, st));
-    NLOS_TRY(fill(s->ph, phi_zero(p.a, p.b, p.phi), V, st));
     NLOS_TRY(gather_columns(P, j.tau0, s->tau0c, st));
-    NLOS_TRY(init_scalars(P, s, j.L0, s->tau0c, C, 0.5, st));
+    if (p.init == NLOS_INIT_BACKPROJECT) {
+      // u0 = u-bar0 = s A_D^T tau0 with its cached A_D u0 (u^{-1} = u0),
+      // phi = phi(kappa(u0)), E_prev = 1/2 ||A_D u0 - tau0||^2 + sum phi |grad u0|
+      NLOS_TRY(backproject(j, s->tau0c, s->uk, s->cache[j.cur]));
+      NLOS_CUDA(cudaMemcpyAsync(s->ub, s->uk, V * sizeof(float), cudaMemcpyDeviceToDevice, st));
+      NLOS_CUDA(cudaMemcpyAsync(s->cache[j.prev], s->cache[j.cur], C * sizeof(float), cudaMemcpyDeviceToDevice,
+                                st));
+      NLOS_TRY(zero(s->cache[j.nxt], C, st));
+      NLOS_TRY(apply_curvature_weight(P, s->uk, s->ph, p.a, p.b, p.phi, p.eps_normal, st));
+      { KTimer kt_(P, KC_SMALL, st);
+      k_axpby<<<elem_grid(C), 256, 0, st>>>(s->cache[j.cur], 1.f, s->tau0c, -1.f, P.d_tmpc, C);
+      }
+      NLOS_LAUNCH_CHECK("k_axpby");
+      NLOS_TRY(init_scalars(P, s, j.L0, P.d_tmpc, C, 0.5, st, nullptr, s->uk, s->ph));
+    } else {
+      NLOS_TRY(zero(s->uk, V, st));
+      NLOS_TRY(zero(s->ub, V, st));
+      for (int i = 0; i < 3; ++i) NLOS_TRY(zero(s->cache[i], C, st));
+      NLOS_TRY(fill(s->ph, phi_zero(p.a, p.b, p.phi), V, st));
+      NLOS_TRY(init_scalars(P, s, j.L0, s->tau0c, C, 0.5, st));
+    }
   } else {
     for (float* f : {s->tk, s->tb, s->lam3}) NLOS_TRY(zero(f, V, st));
     NLOS_TRY(zero(s->lam, 3 * V, st));
     NLOS_TRY(zero(s->lam2, 3 * V, st));
+    if (!u_init && p.init == NLOS_INIT_BACKPROJECT) {
+      // the back-projection start, from the compact data (into tmp and the
+      // plan's compact scratch), then the warm-start path below
+      NLOS_TRY(gather_columns(P, j.tau0, P.d_tmpc, st));
+      NLOS_TRY(backproject(j, P.d_tmpc, s->tmp, s->cache[j.nxt]));
+      u_init = s->tmp;
+    }
     if (u_init) {
       // warm start: u0 = u-bar0 = u_init, cached A u0 (u-bar0 = u0, so A u^{-1} = A u0),
       // phi_u = phi(kappa(u0))

@@ -461,7 +461,8 @@ nlos_status validate_params(const nlos_params& p, const char* who) {
   const std::string w(who);
   if (p.model != 1 && p.model != 2) return fail(NLOS_ERR_INVALID_ARG, w + ": model must be 1 or 2");
   if (p.iters < 0 || !(p.eta > 1.0) || p.max_backtracks < 0 || p.max_backtracks > 1000 || p.phi < 0 ||
-      p.phi > 2 || !(p.eps_normal >= 0.0) || !(p.eps_stop >= 0.0) || p.warm_start_iters < 0)
+      p.phi > 2 || !(p.eps_normal >= 0.0) || !(p.eps_stop >= 0.0) || p.warm_start_iters < 0 ||
+      (p.init != NLOS_INIT_ZERO && p.init != NLOS_INIT_BACKPROJECT))
     return fail(NLOS_ERR_INVALID_ARG, w + ": invalid iteration parameters");
   if ((p.model == 1 || p.warm_start_iters > 0) && !(p.mu > 0.0))
     return fail(NLOS_ERR_INVALID_ARG, w + ": mu must be > 0");
@@ -520,6 +521,7 @@ nlos_status nlos_params_default(int32_t model, nlos_params* out) {
   out->eps_normal = 1e-6;
   out->restart = -1;
   out->warm_start_iters = 0;
+  out->init = NLOS_INIT_ZERO;
   return NLOS_OK;
 }
 

@@ -23,6 +23,7 @@ RADIOMETRY = {"compensated": 0, "raw": 1}
 # curvature weights phi(kappa) (NLOS_PHI_*): a + b kappa^2, a + b |kappa|, sqrt(a + b kappa^2)
 LATERAL_FFT, LATERAL_GEMM_BF16X3, LATERAL_GEMM_BF16 = 0, 1, 2
 PHI_TSC, PHI_TAC, PHI_TRV = 0, 1, 2
+INIT_ZERO, INIT_BACKPROJECT = 0, 1
 PHI = {"tsc": 0, "tac": 1, "trv": 2}
 
 
@@ -41,7 +42,7 @@ class Params(ctypes.Structure):
                 ("iters", ctypes.c_int32), ("eps_stop", ctypes.c_double), ("L0", ctypes.c_double),
                 ("eta", ctypes.c_double), ("max_backtracks", ctypes.c_int32),
                 ("eps_normal", ctypes.c_double), ("restart", ctypes.c_int32),
-                ("warm_start_iters", ctypes.c_int32)]
+                ("warm_start_iters", ctypes.c_int32), ("init", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

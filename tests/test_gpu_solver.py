@@ -200,3 +200,49 @@ def test_reconstruct_from_host_memory_equals_device_call(nlos, model):
             assert np.array_equal(tau_h, host(tau_dev).astype(np.float32))
         assert st_host["iters_done"] == st_dev["iters_done"] and st_host["energy"] == st_dev["energy"]
     plan.close()
+
+
+@pytest.mark.parametrize("n,nt,mask_kind", [(16, 64, "stride"), (32, 256, "stride"), (32, 128, "random")])
+def test_backprojection_start_against_oracle(nlos, n, nt, mask_kind):
+    """NLOS_INIT_BACKPROJECT with no iterations returns u0 = s A_D^T tau0
+    (the device-computed scale s = ||g||^2 / ||A_D g||^2), within the
+    operator tolerance of the FP64 oracle."""
+    cfg, g, mask, vol, tau0 = scene(1, n, nt, seed=3, mask_kind=mask_kind)
+    op = lct.Operator(g, mask)
+    plan = nlos.Plan(n, n, nt, cfg["bin_width_s"], mask=mask)
+    p = alg1_params(nlos, cfg, 0, 1.0)
+    p.init = nlos.INIT_BACKPROJECT
+    u_gpu, st = nlos.reconstruct_t(plan, p, dev(tau0))
+    u_ref, s_ref = admm.backprojection_init(op, tau0)
+    assert s_ref > 0
+    err = rel_l2(host(u_gpu), u_ref)
+    assert err < 1e-5, err
+
+
+@pytest.mark.parametrize("model,iters", [(1, 20), (2, 12)])
+def test_reconstruction_from_backprojection_start(nlos, model, iters):
+    """Algorithms 1 and 2 started from the back-projection against the
+    oracle's runs from its own back-projection start."""
+    n, nt = 16, 128
+    cfg, g, mask, vol, tau0 = scene(model, n, nt, seed=6)
+    op = lct.Operator(g, mask)
+    n2, _ = lct.power_norm2(op, masked=model == 1)
+    plan = nlos.Plan(n, n, nt, cfg["bin_width_s"], mask=mask)
+    u0, _ = admm.backprojection_init(op, tau0)
+    if model == 1:
+        p = alg1_params(nlos, cfg, iters, 2 * n2)
+        p.init = nlos.INIT_BACKPROJECT
+        u_gpu, st = nlos.reconstruct_t(plan, p, dev(tau0))
+        u_ref, h = admm.alg1(tau0, mask, g, cfg["a"], cfg["b"], cfg["mu"], iters, L0=2 * n2, op=op, u_init=u0)
+    else:
+        p = alg2_params(nlos, cfg, iters, 2 * n2)
+        p.init = nlos.INIT_BACKPROJECT
+        u_gpu, tau_gpu, st = nlos.reconstruct_t(plan, p, dev(tau0), want_tau=True)
+        u_ref, tau_ref, h = admm.alg2(tau0, mask, g, cfg["a_u"], cfg["b_u"], cfg["a_tau"], cfg["b_tau"], cfg["lam"],
+                                      cfg["mu1"], cfg["mu2"], cfg["mu3"], iters, L0=2 * n2, op=op, u_init=u0)
+        assert rel_l2(host(tau_gpu), tau_ref) < 1e-3
+        assert st["restarts"] == sum(h["restart"])
+    assert st["status"] == 0 and st["iters_done"] == iters
+    assert rel_l2(host(u_gpu), u_ref) < 1e-3
+    assert abs(st["energy"] - h["E"][-1]) <= 1e-3 * abs(h["E"][-1])
+    assert abs(st["rel_change"] - h["e"][-1]) <= 1e-2 * h["e"][-1] + 1e-9
