@@ -532,24 +532,27 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
       const float2* mine = reinterpret_cast<const float2*>(smem + kOffOwn);
       const float2* theirs = cluster.map_shared_rank(reinterpret_cast<const float2*>(smem + kOffEx), 1 - q);
       float2* dst = Sout + (size_t)kt * out_pitch;
-      const int y = tid & 127, r0 = tid >> 7;
-      constexpr int R = 64 / (kTcThreads / 128);
-      float2 a[R], b[R];
+      // two consecutive y per thread (16-byte accesses), 8 rows per pass
+      const int y = 2 * (tid & 63), r0 = tid >> 6;
+      constexpr int RS = kTcThreads / 64, R = 64 / RS;
+      float4 a[R], b[R];
 #pragma unroll
       for (int i = 0; i < R; ++i) {
-        const int r = r0 + i * (kTcThreads / 128);
-        a[i] = mine[r * kExPitch + y];
-        b[i] = theirs[r * kExPitch + y];
+        const int r = r0 + i * RS;
+        a[i] = *reinterpret_cast<const float4*>(mine + r * kExPitch + y);
+        b[i] = *reinterpret_cast<const float4*>(theirs + r * kExPitch + y);
       }
 #pragma unroll
       for (int i = 0; i < R; ++i) {
-        const float2 v = cadd(a[i], b[i]);
-        const int x = 64 * q + r0 + i * (kTcThreads / 128);
+        const float2 v0 = cadd(make_float2(a[i].x, a[i].y), make_float2(b[i].x, b[i].y));
+        const float2 v1 = cadd(make_float2(a[i].z, a[i].w), make_float2(b[i].z, b[i].w));
+        const int x = 64 * q + r0 + i * RS;
         if (out_pos == nullptr) {
-          dst[x * kTcN + y] = v;
+          *reinterpret_cast<float4*>(dst + x * kTcN + y) = make_float4(v0.x, v0.y, v1.x, v1.y);
         } else {
-          const int j = __ldg(out_pos + x * kTcN + y);
-          if (j >= 0) dst[j] = v;
+          const int2 j = __ldg(reinterpret_cast<const int2*>(out_pos + x * kTcN + y));
+          if (j.x >= 0) dst[j.x] = v0;
+          if (j.y >= 0) dst[j.y] = v1;
         }
       }
     }
