@@ -342,3 +342,89 @@ def direct_summation(u, geom: Geometry):
         rho = (np.arange(nt) + 0.5) / nt
         tau *= rho ** 4
     return tau
+
+
+# ---------------------------------------------------------------------------
+# Directional (normal-weighted) confocal model (Sec. 2)
+# ---------------------------------------------------------------------------
+
+def directional_terms(geom: Geometry, normals):
+    """The six (input field factor, output weight) pairs of the directional
+    confocal operator, coordinates in units of the range R.
+
+    The paper's non-confocal direction-albedo model (Sec. 2) weights u(x) by
+    the two cosines ((x'_i - x) . n / d_i) ((x'_d - x) . n / d_d) on top of the
+    albedo model's fall-off; with illumination and detection at the same wall
+    point x' (the confocal case) the weight is ((x' - x) . n(x))^2 / d^2.
+    Reading: this is the directional model "before the albedo reduction"
+    (the printed confocal formula writes the two normal factors without the
+    direction, n . n, which is 1 for unit normals).  With n = (a, b, c) and
+    g = X a + Y b + Z c (X, Y the voxel's lateral coordinates, Z its depth),
+    (x' - x) . n = X' a + Y' b - g, and its square expands into
+        X'^2 a^2 + Y'^2 b^2 + g^2 + 2 X'Y' a b - 2 X' a g - 2 Y' b g,
+    a sum of products of a field on the voxel grid and a weight on the scan
+    point, so tau = sum_t w_t(x', t) A(f_t u) with the albedo operator A of
+    Eq. 3 and w_t including 1 / d^2 = 1 / rho_t^2 (distance of the time bin's
+    cone, rho_t = (k + 1/2) / nt).  Returns [(f_t, w_t)], f_t of the volume's
+    shape, w_t of shape (nx, ny, nt)."""
+    nx, ny, nt = geom.shape
+    W, R = geom.wall_width_m, geom.range_m
+    X = (np.arange(nx) + 0.5 - nx / 2) * W / nx / R
+    Y = (np.arange(ny) + 0.5 - ny / 2) * W / ny / R
+    Z = (np.arange(nt) + 0.5) / nt
+    a, b, c = (np.asarray(n, dtype=np.float64) for n in normals)
+    g = X[:, None, None] * a + Y[None, :, None] * b + Z[None, None, :] * c
+    inv_d2 = 1.0 / (Z * Z)                       # time bin k: d / R = (k + 1/2) / nt
+    Xp = np.broadcast_to(X[:, None, None], geom.shape)
+    Yp = np.broadcast_to(Y[None, :, None], geom.shape)
+    w = lambda s: s * inv_d2[None, None, :]      # noqa: E731
+    return [(a * a, w(Xp * Xp)), (b * b, w(Yp * Yp)), (g * g, w(np.ones(geom.shape))),
+            (a * b, w(2.0 * Xp * Yp)), (a * g, w(-2.0 * Xp)), (b * g, w(-2.0 * Yp))]
+
+
+def directional_forward(op: Operator, u, normals, masked=True):
+    """tau = D sum_t w_t A(f_t u): the directional confocal model (see
+    directional_terms) on the plan's discretisation of A (Eq. 3)."""
+    tau = np.zeros(op.geom.shape)
+    for f, w in directional_terms(op.geom, normals):
+        tau += w * op.forward(f * u)
+    return op.M * tau if masked else tau
+
+
+def directional_adjoint(op: Operator, tau, normals, masked=True):
+    """Transpose of directional_forward: sum_t f_t A^T(w_t D^T tau)."""
+    r = op.M * tau if masked else tau
+    u = np.zeros(op.geom.shape)
+    for f, w in directional_terms(op.geom, normals):
+        u += f * op.adjoint(w * r)
+    return u
+
+
+def directional_direct_summation(u, normals, geom: Geometry):
+    """The directional confocal model summed voxel by voxel: as
+    direct_summation, with each voxel's contribution weighted by
+    ((x' - x) . n(x) / d)^2."""
+    nx, ny, nt = geom.shape
+    W, R, dt = geom.wall_width_m, geom.range_m, geom.bin_width_s
+    xs = (np.arange(nx) + 0.5 - nx / 2) * W / nx
+    ys = (np.arange(ny) + 0.5 - ny / 2) * W / ny
+    zs = (np.arange(nt) + 0.5) / nt * R
+    a, b, c = (np.asarray(n, dtype=np.float64) for n in normals)
+    tau = np.zeros((nx, ny, nt))
+    for (p, q, s) in np.argwhere(u != 0):
+        dxw = xs[:, None] - xs[p]
+        dyw = ys[None, :] - ys[q]
+        d = np.sqrt(dxw ** 2 + dyw ** 2 + zs[s] ** 2)
+        cosv = (dxw * a[p, q, s] + dyw * b[p, q, s] - zs[s] * c[p, q, s]) / d
+        pos = 2.0 * d / (C_LIGHT * dt) - 0.5
+        k0 = np.floor(pos).astype(np.int64)
+        fr = pos - k0
+        amp = u[p, q, s] * cosv * cosv / d ** 4
+        for kk, wgt in ((k0, 1.0 - fr), (k0 + 1, fr)):
+            ok = (kk >= 0) & (kk < nt)
+            ii, jj = np.nonzero(ok)
+            np.add.at(tau, (ii, jj, kk[ok]), (amp * wgt)[ok])
+    if geom.radiometry == "compensated":
+        rho = (np.arange(nt) + 0.5) / nt
+        tau *= rho ** 4
+    return tau
