@@ -201,6 +201,25 @@ nlos_status nlos_forward(nlos_plan plan, const float* u_dev, float* tau_dev, int
 nlos_status nlos_adjoint(nlos_plan plan, const float* tau_dev, float* u_dev, int32_t apply_mask,
                          void* stream);
 
+/* The directional (normal-weighted) confocal model of Sec. 2 for a given
+ * normal field: tau(x', t) = sum over voxels x of u(x) ((x' - x) . n(x) / d)^2
+ * / d^4 delta(2 d - t c), the confocal case (illumination and detection at
+ * the same wall point x') of the paper's non-confocal direction-albedo
+ * model, on the plan's discretisation of A (Eq. 3): the squared cosine is
+ * expanded into six products of a voxel field and a scan-point weight, so
+ * the operator is six applications of A.  normals_dev: device, float32
+ * [3][nx][ny][nt] (the components n_x, n_y, n_z of each voxel's normal, the
+ * wall at z = 0 and the scene at z > 0; any length: the weight scales with
+ * |n|^2).  apply_mask as nlos_forward.  nlos_adjoint_directional is its
+ * transpose in u for the same normals.  Two field-sized device buffers are
+ * allocated in the plan on the first call.  The output must not overlap an
+ * input (NLOS_ERR_INVALID_ARG); NLOS_ERR_OOM if the buffers cannot be
+ * allocated.  Queued on `stream`, no host synchronisation. */
+nlos_status nlos_forward_directional(nlos_plan plan, const float* u_dev, const float* normals_dev, float* tau_dev,
+                                     int32_t apply_mask, void* stream);
+nlos_status nlos_adjoint_directional(nlos_plan plan, const float* tau_dev, const float* normals_dev, float* u_dev,
+                                     int32_t apply_mask, void* stream);
+
 /* x = F^{-1}[F(rhs) / (c0 + c1 lambda(k))] on the periodic nx x ny x nt grid,
  * lambda(k) = sum_d 4 sin^2(pi k_d / N_d): the solve of (c0 I + c1 nabla^*
  * nabla) x = rhs of Eq. 11 (forward differences, unit spacing).  c0 > 0,

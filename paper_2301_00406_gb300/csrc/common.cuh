@@ -216,6 +216,7 @@ struct Plan {
   float* d_tmpc = nullptr;       // [ncols][nt] compact transient scratch
   double* d_partials = nullptr;  // reduction partials
   float* d_io[3] = {nullptr, nullptr, nullptr};  // tau0, u, tau of nlos_reconstruct_host (allocated on use)
+  float* d_dir[2] = {nullptr, nullptr};  // scratch fields of the directional model (allocated on use)
   int partial_blocks = 0;
   DevScalars* d_scal = nullptr;  // scratch scalars (norm, diagnostics)
 
@@ -276,6 +277,13 @@ struct KTimer {
   KTimer(const Plan& p, int cat, cudaStream_t s);
   ~KTimer();
 };
+
+// The directional (normal-weighted) model of Sec. 2 for the normal field
+// normals = [3][nx][ny][nt] (directional.cu): six applications of A.
+nlos_status apply_forward_directional(Plan& P, const float* u, const float* normals, float* tau, bool masked,
+                                      cudaStream_t st);
+nlos_status apply_adjoint_directional(Plan& P, const float* tau, const float* normals, float* u, bool masked,
+                                      cudaStream_t st);
 
 // Operator applications (admm.cu)
 nlos_status apply_forward(const Plan& P, const float* u, float* out, bool compact, cudaStream_t st);

@@ -205,7 +205,7 @@ static void free_workspace(Plan* P) {
     P->solver[m] = nullptr;
   }
   void* ws[] = {P->d_S, P->d_S2, P->d_Sc, P->d_Sp, P->d_tmpc, P->d_partials, P->d_scal, P->d_io[0], P->d_io[1],
-                P->d_io[2]};
+                P->d_io[2], P->d_dir[0], P->d_dir[1]};
   for (void* p : ws)
     if (p) cudaFree(p);
   for (cudaEvent_t e : P->ev) cudaEventDestroy(e);
@@ -250,6 +250,7 @@ Plan* plan_clone_workspace(const Plan& base, nlos_status* status) {
   P->d_partials = nullptr;
   P->d_scal = nullptr;
   for (auto& b : P->d_io) b = nullptr;
+  for (auto& b : P->d_dir) b = nullptr;
   P->timing = false;
   P->ev.clear();
   P->ev_cat.clear();
@@ -603,6 +604,37 @@ nlos_status nlos_adjoint(nlos_plan plan, const float* tau_dev, float* u_dev, int
     if (!apply_mask || P.full_mask) return apply_adjoint(P, tau_dev, u_dev, false, st);
     NLOS_TRY(gather_columns(P, tau_dev, P.d_tmpc, st));
     return apply_adjoint(P, P.d_tmpc, u_dev, true, st);
+  })
+}
+
+static nlos_status check_directional(nlos_plan plan, const void* in, const void* normals, const void* out,
+                                     const char* who) {
+  NLOS_TRY(check_plan(plan));
+  const Plan& P = *reinterpret_cast<const Plan*>(plan);
+  if (!in || !normals || !out) return fail(NLOS_ERR_INVALID_ARG, std::string(who) + ": null pointer");
+  const size_t F = (size_t)P.nx * P.ny * P.nt * sizeof(float);
+  const uintptr_t a = reinterpret_cast<uintptr_t>(in), n = reinterpret_cast<uintptr_t>(normals),
+                  o = reinterpret_cast<uintptr_t>(out);
+  if ((o < a + F && a < o + F) || (o < n + 3 * F && n < o + F))
+    return fail(NLOS_ERR_INVALID_ARG, std::string(who) + ": the output overlaps an input");
+  return NLOS_OK;
+}
+
+nlos_status nlos_forward_directional(nlos_plan plan, const float* u_dev, const float* normals_dev, float* tau_dev,
+                                     int32_t apply_mask, void* stream) {
+  API_GUARD({
+    NLOS_TRY(check_directional(plan, u_dev, normals_dev, tau_dev, "nlos_forward_directional"));
+    return apply_forward_directional(*reinterpret_cast<Plan*>(plan), u_dev, normals_dev, tau_dev, apply_mask != 0,
+                                     reinterpret_cast<cudaStream_t>(stream));
+  })
+}
+
+nlos_status nlos_adjoint_directional(nlos_plan plan, const float* tau_dev, const float* normals_dev, float* u_dev,
+                                     int32_t apply_mask, void* stream) {
+  API_GUARD({
+    NLOS_TRY(check_directional(plan, tau_dev, normals_dev, u_dev, "nlos_adjoint_directional"));
+    return apply_adjoint_directional(*reinterpret_cast<Plan*>(plan), tau_dev, normals_dev, u_dev, apply_mask != 0,
+                                     reinterpret_cast<cudaStream_t>(stream));
   })
 }
 

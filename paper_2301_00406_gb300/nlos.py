@@ -81,6 +81,8 @@ _SIGS = {
                                                ctypes.c_int32, ctypes.c_double, _P]),
     "nlos_reconstruct": (ctypes.c_int32, [_P, ctypes.POINTER(Params), _P, _P, _P,
                                           ctypes.POINTER(Stats), _P]),
+    "nlos_forward_directional": (ctypes.c_int32, [_P, _P, _P, _P, ctypes.c_int32, _P]),
+    "nlos_adjoint_directional": (ctypes.c_int32, [_P, _P, _P, _P, ctypes.c_int32, _P]),
     "nlos_reconstruct_host": (ctypes.c_int32, [_P, ctypes.POINTER(Params), _P, _P, _P, ctypes.POINTER(Stats), _P]),
     "nlos_reconstruct_prepare": (ctypes.c_int32, [_P, ctypes.POINTER(Params), _P, _P, _P,
                                                   ctypes.POINTER(ctypes.c_int32), _P]),
@@ -372,6 +374,24 @@ def adjoint_t(plan, tau, apply_mask=False):
     import torch
     u = torch.empty_like(tau)
     plan.adjoint(tau.data_ptr(), u.data_ptr(), apply_mask, _stream())
+    return u
+
+
+def forward_directional_t(plan, u, normals, apply_mask=False):
+    """nlos_forward_directional on tensors; normals: [3, nx, ny, nt] float32 on the device."""
+    import torch
+    tau = torch.empty_like(u)
+    check(load().nlos_forward_directional(plan.handle, u.data_ptr(), normals.data_ptr(), tau.data_ptr(),
+                                          int(bool(apply_mask)), _stream()))
+    return tau
+
+
+def adjoint_directional_t(plan, tau, normals, apply_mask=False):
+    """nlos_adjoint_directional on tensors."""
+    import torch
+    u = torch.empty_like(tau)
+    check(load().nlos_adjoint_directional(plan.handle, tau.data_ptr(), normals.data_ptr(), u.data_ptr(),
+                                          int(bool(apply_mask)), _stream()))
     return u
 
 
