@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnlos.so")
 SOURCES = ["lct.cu", "xy.cu", "conv4.cu", "conv_tc.cu", "tpass_small.cu", "tpass_256.cu", "tpass_512.cu",
-           "tpass_1024.cu", "admm.cu", "plan.cu", "static_solve.cu", "serve.cu", "midpoint.cu",
+           "tpass_1024.cu", "tpass_warp.cu", "admm.cu", "plan.cu", "static_solve.cu", "serve.cu", "midpoint.cu",
            "directional.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -803,7 +803,7 @@ static nlos_status u_trial(Plan& P, SolverState* s, const UStepArgs& a, bool tes
   NLOS_TRY(launch_tadj_solve(P, P.d_S, full, full, sr, P.d_Sp, st));
   NLOS_TRY(launch_sxy(P, P.d_Sp, s->sc, 0.0, a.mu, st));
   NLOS_TRY(launch_sinv_rz(P, P.d_Sp, full, s->unew, test ? s->ub : nullptr, test ? s->pa : nullptr, nbd, P.d_S2,
-                          full, st));
+                          full, st, s->sc));
   if (!test) *nbd = 0;
   float2* Sfit = P.d_S2;
   if (a.compact) {
@@ -1202,7 +1202,8 @@ nlos_status job_finish(JobRun& j) {
 nlos_status job_collect(JobRun& j, nlos_stats* stats) {
   fill_stats(*j.s->h_sc, stats);
   if (j.s->h_sc->status != NLOS_OK)
-    return fail(j.s->h_sc->status, "reconstruction stopped: non-finite energy or backtracking gave up");
+    return fail(j.s->h_sc->status,
+                "reconstruction stopped: non-finite energy, backtracking gave up, or a t-pass tile wait timed out");
   return NLOS_OK;
 }
 

@@ -31,7 +31,10 @@ extern template struct TpassOps<1024>;
   }                                                                  \
   return fail(NLOS_ERR_INVALID_ARG, "unsupported nt")
 
-nlos_status prepare_tpass(int nt) { NLOS_DISPATCH_NT(nt, prepare()); }
+nlos_status prepare_tpass(int nt) {
+  NLOS_TRY(prepare_tpass_warp(nt));
+  NLOS_DISPATCH_NT(nt, prepare());
+}
 
 nlos_status launch_tfwd_rz(const Plan& P, const float* u, int ncols, float2* S, int pitch, cudaStream_t st) {
   NLOS_DISPATCH_NT(P.nt, tfwd_rz(P, u, ncols, S, pitch, st));
@@ -52,6 +55,7 @@ nlos_status launch_tadj_store(const Plan& P, const float2* S, int pitch, int nco
 }
 nlos_status launch_tadj_solve(const Plan& P, const float2* S, int pitch, int ncols, const SolveRhs& sr, float2* Sp,
                               cudaStream_t st) {
+  if (tpass_warp_applies(P, ncols, pitch)) return launch_tadj_solve_warp(P, S, pitch, sr, Sp, st);
   NLOS_DISPATCH_NT(P.nt, tadj_solve(P, S, pitch, ncols, sr, Sp, st));
 }
 nlos_status launch_sfwd(const Plan& P, const float* x, int ncols, float2* Sp, cudaStream_t st, const float* x2) {
@@ -62,7 +66,9 @@ nlos_status launch_sinv(const Plan& P, const float2* Sp, int ncols, float* x, co
   NLOS_DISPATCH_NT(P.nt, sinv(P, Sp, ncols, x, ref, partials, nblocks, st));
 }
 nlos_status launch_sinv_rz(const Plan& P, const float2* Sp, int ncols, float* x, const float* ref,
-                           double* partials, int* nblocks, float2* S, int pitch, cudaStream_t st) {
+                           double* partials, int* nblocks, float2* S, int pitch, cudaStream_t st, DevScalars* sc) {
+  if (tpass_warp_applies(P, ncols, pitch))
+    return launch_sinv_rz_warp(P, Sp, pitch, x, ref, partials, nblocks, S, sc, st);
   NLOS_DISPATCH_NT(P.nt, sinv_rz(P, Sp, ncols, x, ref, partials, nblocks, S, pitch, st));
 }
 
@@ -142,6 +148,8 @@ nlos_status autotune_tpass(Plan& P, cudaStream_t st) {
       std::lock_guard<std::mutex> lock(g_tp_mu);
       if (g_tp_cols.count(std::make_tuple(c.kind, nt, c.ncols))) continue;
     }
+    // the warp-per-pair kernels have a fixed shape: nothing to tune
+    if ((c.kind == TPK_TADJ_SOLVE || c.kind == TPK_SINV_RZ) && tpass_warp_applies(P, c.ncols, c.ncols)) continue;
     const bool halves = c.kind != TPK_SFWD && c.kind != TPK_SINV;  // sinv_rz: its forward half
     int best = 0;
     float best_ms = 0.f;

@@ -62,8 +62,21 @@ nlos_status launch_sfwd(const Plan& P, const float* x, int ncols, float2* Sp, cu
 nlos_status launch_sinv(const Plan& P, const float2* Sp, int ncols, float* x, const float* ref,
                         double* partials, int* nblocks, cudaStream_t st);
 // launch_sinv followed by launch_tfwd_rz(x -> S) in one pass (x kept on chip).
+// sc (nullable): the solver's scalars, whose status a timed-out wait of the
+// full-grid kernel sets to NLOS_ERR_TIMEOUT.
 nlos_status launch_sinv_rz(const Plan& P, const float2* Sp, int ncols, float* x, const float* ref,
-                           double* partials, int* nblocks, float2* S, int pitch, cudaStream_t st);
+                           double* partials, int* nblocks, float2* S, int pitch, cudaStream_t st,
+                           DevScalars* sc = nullptr);
+// Full-grid tadj (solve mode) and sinv_rz passes with one warp per column
+// pair and TMA tile transfers (tpass_warp.cu), for nt in {128, 256, 512};
+// launch_tadj_solve and launch_sinv_rz dispatch to them when
+// tpass_warp_applies.
+bool tpass_warp_applies(const Plan& P, int ncols, int pitch);
+nlos_status prepare_tpass_warp(int nt);
+nlos_status launch_tadj_solve_warp(const Plan& P, const float2* S, int pitch, const SolveRhs& sr, float2* Sp,
+                                   cudaStream_t st);
+nlos_status launch_sinv_rz_warp(const Plan& P, const float2* Sp, int pitch, float* x, const float* ref,
+                                double* partials, int* nblocks, float2* S, DevScalars* sc, cudaStream_t st);
 // Lateral 2-D zero-padded convolution of each kt plane with H (adj: conj H).
 // in_cols/out_cols: nullptr = full plane [nx][ny]; else compact column lists
 // (the plan's sampled columns) with plane pitch ncols.

@@ -1,0 +1,581 @@
+// Full-grid t-passes of the u-step with one warp per column pair: the adjoint
+// end of A^T fused with the solve right-hand side (the tadj pass: inverse
+// padded t-FFT, R_z^T, rhs = L u-bar - A^T r + reg, periodic t-FFT) and the
+// solve's inverse fused with the forward start of A (the sinv_rz pass:
+// periodic inverse t-FFT to u+, R_z, padded t-FFT), for nt = 128, 256, 512.
+//
+// Layout.  A CTA owns 16 consecutive columns (8 pairs, 8 warps).  The
+// spectra are stored [bin][column] (float2), so the CTA's part of one bin is
+// one 128-byte row segment; the CTA's whole spectrum tile (nt + 1 or nt/2 + 1
+// rows) arrives in shared memory by TMA tile loads with the 128-byte swizzle
+// (16-byte chunk c of row r at chunk c ^ (r mod 8)) and the output tile
+// leaves by TMA tile stores from the same region.  The last row of each
+// spectrum (bin nt or nt/2) moves by plain loads and stores, so the boxes
+// stay a power of two high.  The real columns (u-bar, reg, u+) are stored
+// [column][bin]; a warp reads and writes its two columns as 128-byte runs.
+//
+// Transforms.  Warp w transforms the packed pair z = x_{2w} + i x_{2w+1}.
+// A length-N transform (N = 32 V) is held in registers, V values per lane,
+// and factored as N = V x 32: a V-point register DFT over the stride-32
+// elements of each lane, the twiddles w_N^(l k1), an exchange through the
+// warp's shared scratch that gives each group of G = 32 / V lanes one of the
+// V length-32 sequences, a V-point register DFT over the stride-G elements,
+// the twiddles w_32^(g a), and a G-point DFT across the G lanes by shuffles
+// (radix-2, decimation in frequency).  Input in natural order (lane l,
+// register m: element l + 32 m) gives frequency k1 + V a + V^2 rev_G(g) in
+// lane k1 G + g, register a (rev_G: bit reversal of log2 G bits); the
+// inverse runs the same steps backwards with conjugate twiddles, from that
+// order back to natural order (unnormalised).  The padded real transform of
+// length 2N splits into the even and odd bins, two length-N transforms of
+// z and z w_2N^n; the two real columns of a pair separate by Hermitian
+// symmetry.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "fft.cuh"
+#include "passes.cuh"
+#include "tma.cuh"
+
+namespace nlos {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWarpThreads = 256;  // 8 warps: 8 column pairs, 16 columns per CTA
+constexpr int kWarpCols = 16;
+
+template <int V>
+struct WP {
+  static constexpr int N = 32 * V;                        // time bins
+  static constexpr int G = 32 / V;                        // lanes per length-32 sequence
+  static constexpr int XP = 32 + G;                       // scratch row pitch of the exchange (float2)
+  static constexpr int SCR = V * XP > N + 2 ? V * XP : N + 2;  // scratch per warp (float2)
+  static constexpr int BOX = N < 256 ? N : 256;           // rows per TMA box, padded spectrum
+  static constexpr int BOXP = N / 2 < 256 ? N / 2 : 256;  // rows per TMA box, periodic spectrum
+  static constexpr int TILE = ((N + 1) * 128 + 1023) / 1024 * 1024;
+  static constexpr int OFF_TW1 = TILE;                    // [k1][l] w_N^(l k1)
+  static constexpr int OFF_TWC = OFF_TW1 + 8 * N;         // [n] w_2N^n, n < N
+  static constexpr int OFF_SCR = OFF_TWC + 8 * N;
+  static constexpr int OFF_BAR = OFF_SCR + 8 * 8 * SCR;
+  static constexpr int SMEM = OFF_BAR + 64 + 1024;        // + slack to align the base to 1024
+  // R_z^T rows of the tadj pass, staged into the tile region behind the
+  // output rows [0, N/2) once the input tile has been read
+  static constexpr int OFF_RPTR = (N / 2) * 128;
+  static constexpr int OFF_RENT = OFF_RPTR + ((N + 1) * 4 + 15) / 16 * 16;
+  static_assert(OFF_RENT + 2 * N * 8 <= TILE, "R_z^T rows must fit behind the output rows");
+};
+
+// Byte offset of 16-byte chunk c of row r in a swizzled tile.
+__device__ __forceinline__ int tile_off(int r, int c) { return r * 128 + ((c ^ (r & 7)) << 4); }
+
+__device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
+  return make_float2(__shfl_xor_sync(kFull, v.x, m), __shfl_xor_sync(kFull, v.y, m));
+}
+
+// Streaming load: read once, not kept in L1 (the tables read through L1 stay there).
+__device__ __forceinline__ float ld_stream(const float* p) {
+  float v;
+  asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+// Asynchronous global -> shared copies (no registers); completed by cp_async_wait.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+}
+// Pulls a contiguous range (16-byte aligned, a multiple of 16 bytes) into L2.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+template <int G>
+__device__ __forceinline__ int rev_bits(int g) {
+  int r = 0;
+#pragma unroll
+  for (int b = 1; b < G; b <<= 1) r = (r << 1) | ((g & b) ? 1 : 0);
+  return r;
+}
+
+// G-point DFT across the lanes g of each sequence (every register a), radix
+// 2.  Forward: decimation in frequency, natural lane order in, bit-reversed
+// out; each stage of half-size h takes (u, v) = (lane g, lane g + h) to
+// (u + v, (u - v) w_2h^(g mod h)).  Inverse: the stages backwards with
+// conjugate twiddles (unnormalised).  The twiddle w_2h^j is w_2N^(j N / h).
+template <int V, bool INV>
+__device__ __forceinline__ void lane_dft(float2 (&b)[V], int g, const float2* twc) {
+  constexpr int G = 32 / V, N = 32 * V;
+  if constexpr (G > 1) {
+    if constexpr (!INV) {
+#pragma unroll
+      for (int h = G / 2; h >= 1; h >>= 1) {
+        const bool up = (g & h) != 0;
+        const float s = up ? -1.0f : 1.0f;
+        const float2 w = h > 1 && up ? twc[(g & (h - 1)) * (N / h)] : make_float2(1.0f, 0.0f);
+#pragma unroll
+        for (int a = 0; a < V; ++a) {
+          const float2 p = shfl_xor2(b[a], h);
+          // lower lane: u + v; upper lane: u - v (u the lower lane's value)
+          const float2 r = __ffma2_rn(b[a], make_float2(s, s), p);
+          b[a] = h > 1 ? cmul(r, w) : r;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int h = 1; h < G; h <<= 1) {
+        const bool up = (g & h) != 0;
+        const float s = up ? -1.0f : 1.0f;
+        const float2 w = h > 1 && up ? twc[(g & (h - 1)) * (N / h)] : make_float2(1.0f, 0.0f);
+#pragma unroll
+        for (int a = 0; a < V; ++a) {
+          const float2 t = h > 1 ? cmulc(b[a], w) : b[a];
+          const float2 p = shfl_xor2(t, h);
+          b[a] = __ffma2_rn(t, make_float2(s, s), p);
+        }
+      }
+    }
+  }
+}
+
+// Forward length-N transform of the warp's sequence: natural order in, the
+// order of the file header out.  scr: the warp's scratch.
+template <int V>
+__device__ __forceinline__ void wfft_fwd(float2 (&a)[V], float2* scr, const float2* tw1, const float2* twc,
+                                         int lane) {
+  constexpr int G = WP<V>::G, XP = WP<V>::XP;
+  dft_reg<V, false>(a);
+#pragma unroll
+  for (int k1 = 1; k1 < V; ++k1) a[k1] = cmul(a[k1], tw1[k1 * 32 + lane]);
+#pragma unroll
+  for (int k1 = 0; k1 < V; ++k1) scr[k1 * XP + lane] = a[k1];
+  __syncwarp();
+  const int k1 = lane / G, g = lane % G;
+#pragma unroll
+  for (int j = 0; j < V; ++j) a[j] = scr[k1 * XP + g + G * j];
+  __syncwarp();
+  dft_reg<V, false>(a);
+  if constexpr (G > 1) {
+#pragma unroll
+    for (int q = 1; q < V; ++q) a[q] = cmul(a[q], tw1[q * 32 + V * g]);
+  }
+  lane_dft<V, false>(a, g, twc);
+}
+
+// Inverse of wfft_fwd (times N): the header's order in, natural order out.
+template <int V>
+__device__ __forceinline__ void wfft_inv(float2 (&a)[V], float2* scr, const float2* tw1, const float2* twc,
+                                         int lane) {
+  constexpr int G = WP<V>::G, XP = WP<V>::XP;
+  const int k1 = lane / G, g = lane % G;
+  lane_dft<V, true>(a, g, twc);
+  if constexpr (G > 1) {
+#pragma unroll
+    for (int q = 1; q < V; ++q) a[q] = cmulc(a[q], tw1[q * 32 + V * g]);
+  }
+  dft_reg<V, true>(a);
+#pragma unroll
+  for (int j = 0; j < V; ++j) scr[k1 * XP + g + G * j] = a[j];
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < V; ++q) a[q] = scr[q * XP + lane];
+  __syncwarp();
+#pragma unroll
+  for (int q = 1; q < V; ++q) a[q] = cmulc(a[q], tw1[q * 32 + lane]);
+  dft_reg<V, true>(a);
+}
+
+// Bin kt in [0, 2N) of the padded spectrum of the pair in chunk c of the
+// tile (rows 0..N), packed z = X_a + i X_b; bins above N by Hermitian
+// symmetry of the real columns.
+template <int N>
+__device__ __forceinline__ float2 padded_bin(const unsigned char* tile, int kt, int c) {
+  const bool mir = kt > N;
+  const int r = mir ? 2 * N - kt : kt;
+  const float4 v = *reinterpret_cast<const float4*>(tile + tile_off(r, c));
+  const float ay = mir ? -v.y : v.y, by = mir ? -v.w : v.w;
+  return make_float2(v.x - by, ay + v.z);
+}
+// Bin k in [0, N) of the periodic spectrum (rows 0..N/2), packed likewise.
+template <int N>
+__device__ __forceinline__ float2 periodic_bin(const unsigned char* tile, int k, int c) {
+  const bool mir = k > N / 2;
+  const int r = mir ? N - k : k;
+  const float4 v = *reinterpret_cast<const float4*>(tile + tile_off(r, c));
+  const float ay = mir ? -v.y : v.y, by = mir ? -v.w : v.w;
+  return make_float2(v.x - by, ay + v.z);
+}
+// The bins of both real columns from the packed transform at k (za) and at
+// the mirrored bin (zb): X_a = (za + conj zb) / 2, X_b = (za - conj zb) / 2i.
+__device__ __forceinline__ float4 hermitian_split(float2 za, float2 zb) {
+  return make_float4(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y), 0.5f * (za.y + zb.y), -0.5f * (za.x - zb.x));
+}
+
+// Stage the twiddle tables of one CTA from the 2N roots w_2N^j (j < 2N).
+template <int V>
+__device__ __forceinline__ void stage_wtw(float2* tw1, float2* twc, const float2* __restrict__ tw2g, int tid) {
+  constexpr int N = WP<V>::N;
+  for (int i = tid; i < N; i += kWarpThreads) {
+    tw1[i] = __ldg(tw2g + ((2 * (i & 31) * (i >> 5)) & (2 * N - 1)));
+    twc[i] = __ldg(tw2g + i);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// tadj pass: S (padded spectrum of A^T's lateral output, full grid) ->
+// rhs = c0 u-bar - R_z^T F^{-1} S + reg -> Sp (periodic spectrum of rhs).
+// ---------------------------------------------------------------------------
+template <int V>
+__global__ void __launch_bounds__(kWarpThreads, 2)
+    k_tadj_w(const __grid_constant__ CUtensorMap tm_s, const float2* __restrict__ S,
+             const __grid_constant__ CUtensorMap tm_sp, float2* __restrict__ Sp, int pitch, SolveRhs sr,
+             const int32_t* __restrict__ rptr, const float2* __restrict__ rent, const float2* __restrict__ tw2g,
+             int32_t* status) {
+  using W = WP<V>;
+  constexpr int N = W::N, G = W::G;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ int fail;
+  unsigned char* sm = align1024(smem_raw);
+  float2* tw1 = reinterpret_cast<float2*>(sm + W::OFF_TW1);
+  float2* twc = reinterpret_cast<float2*>(sm + W::OFF_TWC);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  float2* scr = reinterpret_cast<float2*>(sm + W::OFF_SCR) + warp * W::SCR;
+  const int col0 = blockIdx.x * kWarpCols;
+  const uint32_t tile = smem_u32(sm), bar = smem_u32(sm + W::OFF_BAR);
+  if (tid == 0) {
+    fail = 0;
+    mbar_init(bar, 1);
+    mbar_expect_tx(bar, N * 128);
+#pragma unroll 1
+    for (int r0 = 0; r0 < N; r0 += W::BOX) tma_load_2d(tile + r0 * 128, &tm_s, 2 * col0, r0, bar);
+    // the CTA's u-bar and reg columns are read after the inverse transforms
+    prefetch_l2(sr.ubar + (size_t)col0 * N, kWarpCols * N * 4);
+    prefetch_l2(sr.reg + (size_t)col0 * N, kWarpCols * N * 4);
+  }
+  if (tid < 8) {  // row N (the Nyquist bin)
+    const float4 v = __ldg(reinterpret_cast<const float4*>(S + (size_t)N * pitch + col0) + tid);
+    *reinterpret_cast<float4*>(sm + tile_off(N, tid)) = v;
+  }
+  stage_wtw<V>(tw1, twc, tw2g, tid);
+  const int ca = col0 + 2 * warp, cb = ca + 1;
+  const float* ubar_a = sr.ubar + (size_t)ca * N;
+  const float* ubar_b = sr.ubar + (size_t)cb * N;
+  const float* reg_a = sr.reg + (size_t)ca * N;
+  const float* reg_b = sr.reg + (size_t)cb * N;
+  __syncthreads();
+  mbar_wait_bounded(bar, 0, &fail, status);
+
+  // inverse padded transform: even bins (e) and odd bins (o), each a
+  // length-N inverse DFT of the packed pair
+  const int k1 = lane / G, gr = rev_bits<G>(lane % G);
+  float2 e[V], o[V];
+#pragma unroll
+  for (int a = 0; a < V; ++a) {
+    const int k = k1 + V * a + V * V * gr;
+    e[a] = padded_bin<N>(sm, 2 * k, warp);
+    o[a] = padded_bin<N>(sm, 2 * k + 1, warp);
+  }
+  __syncthreads();  // every pair is read: the tile region now takes the output rows and the R_z^T rows
+  int* s_rptr = reinterpret_cast<int*>(sm + W::OFF_RPTR);
+  float2* s_rent = reinterpret_cast<float2*>(sm + W::OFF_RENT);
+  for (int i = tid; i <= N; i += kWarpThreads) cp_async4(s_rptr + i, rptr + i);
+  for (int i = tid; i < N; i += kWarpThreads) cp_async16(s_rent + 2 * i, rent + 2 * i);
+  wfft_inv<V>(e, scr, tw1, twc, lane);
+  wfft_inv<V>(o, scr, tw1, twc, lane);
+  // c[n] = (even[n] + conj(w_2N^n) odd[n]) / 2N, n = lane + 32 m (the first N
+  // samples of the length-2N real inverse of both columns)
+  const float scale = 1.0f / (2.0f * N);
+#pragma unroll
+  for (int m = 0; m < V; ++m) {
+    const int n = lane + 32 * m;
+    scr[n] = cscale(cadd(e[m], cmulc(o[m], twc[n])), scale);
+  }
+  cp_async_wait();
+  __syncthreads();  // the R_z^T rows are staged; every warp's c is in its scratch
+
+  // g = R_z^T c (CSR rows, the order of the rows' entries), rhs = c0 u-bar - g + reg
+  const float c0 = sr.sc ? (float)sr.sc->L : (float)sr.c0_host;
+  float2 r[V];
+#pragma unroll
+  for (int m = 0; m < V; ++m) {
+    const int i = lane + 32 * m;
+    r[m] = make_float2(c0 * ld_stream(ubar_a + i) + ld_stream(reg_a + i),
+                       c0 * ld_stream(ubar_b + i) + ld_stream(reg_b + i));
+  }
+#pragma unroll
+  for (int m = 0; m < V; ++m) {
+    const int i = lane + 32 * m;
+    const int q0 = s_rptr[i], q1 = s_rptr[i + 1];
+    float ga = 0.f, gb = 0.f;
+    for (int q = q0; q < q1; ++q) {
+      const float2 w = s_rent[q];
+      const float2 c = scr[__float_as_int(w.y)];
+      ga += w.x * c.x;
+      gb += w.x * c.y;
+    }
+    r[m].x -= ga;
+    r[m].y -= gb;
+  }
+  __syncwarp();
+
+  // periodic forward transform of the rhs pair, bins k <= N/2 of both columns
+  wfft_fwd<V>(r, scr, tw1, twc, lane);
+#pragma unroll
+  for (int a = 0; a < V; ++a) scr[k1 + V * a + V * V * gr] = r[a];
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j <= N / 64; ++j) {
+    const int k = lane + 32 * j;
+    if (k <= N / 2) {
+      const float4 x = hermitian_split(scr[k], scr[(N - k) & (N - 1)]);
+      if (k < N / 2)
+        *reinterpret_cast<float4*>(sm + tile_off(k, warp)) = x;
+      else
+        *reinterpret_cast<float4*>(Sp + (size_t)k * pitch + ca) = x;
+    }
+  }
+  fence_async_smem();
+  __syncthreads();
+  if (tid == 0) {
+#pragma unroll 1
+    for (int r0 = 0; r0 < N / 2; r0 += W::BOXP) tma_store_2d(&tm_sp, 2 * col0, r0, tile + r0 * 128);
+    bulk_commit();
+    bulk_wait_all();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// sinv_rz pass: Sp (periodic spectrum of the solution, full grid) -> u+ =
+// F^{-1} Sp (stored; partial sums of (u+ - ref)^2) -> R_z u+ -> S (padded
+// spectrum, the forward start of A u+).
+// ---------------------------------------------------------------------------
+template <int V>
+__global__ void __launch_bounds__(kWarpThreads, 2)
+    k_sinv_rz_w(const __grid_constant__ CUtensorMap tm_sp, const float2* __restrict__ Sp,
+                const __grid_constant__ CUtensorMap tm_s, float2* __restrict__ S, int pitch, float* __restrict__ x,
+                const float* __restrict__ ref, double* __restrict__ partials, const float4* __restrict__ ftab,
+                const float2* __restrict__ tw2g, int32_t* status) {
+  using W = WP<V>;
+  constexpr int N = W::N, G = W::G;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ int fail;
+  unsigned char* sm = align1024(smem_raw);
+  float2* tw1 = reinterpret_cast<float2*>(sm + W::OFF_TW1);
+  float2* twc = reinterpret_cast<float2*>(sm + W::OFF_TWC);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  float2* scr = reinterpret_cast<float2*>(sm + W::OFF_SCR) + warp * W::SCR;
+  const int col0 = blockIdx.x * kWarpCols;
+  const uint32_t tile = smem_u32(sm), bar = smem_u32(sm + W::OFF_BAR);
+  if (tid == 0) {
+    fail = 0;
+    mbar_init(bar, 1);
+    mbar_expect_tx(bar, (N / 2) * 128);
+#pragma unroll 1
+    for (int r0 = 0; r0 < N / 2; r0 += W::BOXP) tma_load_2d(tile + r0 * 128, &tm_sp, 2 * col0, r0, bar);
+    if (ref) prefetch_l2(ref + (size_t)col0 * N, kWarpCols * N * 4);
+  }
+  if (tid < 8) {  // row N/2 (the Nyquist bin)
+    const float4 v = __ldg(reinterpret_cast<const float4*>(Sp + (size_t)(N / 2) * pitch + col0) + tid);
+    *reinterpret_cast<float4*>(sm + tile_off(N / 2, tid)) = v;
+  }
+  stage_wtw<V>(tw1, twc, tw2g, tid);
+  const int ca = col0 + 2 * warp, cb = ca + 1;
+  __syncthreads();
+  mbar_wait_bounded(bar, 0, &fail, status);
+
+  const int k1 = lane / G, gr = rev_bits<G>(lane % G);
+  float2 z[V];
+#pragma unroll
+  for (int a = 0; a < V; ++a) z[a] = periodic_bin<N>(sm, k1 + V * a + V * V * gr, warp);
+  __syncthreads();  // every pair is read: the tile region now takes the output rows
+  wfft_inv<V>(z, scr, tw1, twc, lane);
+
+  // u+ of both columns, n = lane + 32 m: stored, summed against ref, and kept
+  // in the scratch for the R_z taps
+  const float scale = 1.0f / N;
+  SumAcc<1> acc;
+#pragma unroll
+  for (int m = 0; m < V; ++m) {
+    const int n = lane + 32 * m;
+    const float2 v = cscale(z[m], scale);
+    x[(size_t)ca * N + n] = v.x;
+    x[(size_t)cb * N + n] = v.y;
+    if (ref) {
+      const float da = v.x - ld_stream(ref + (size_t)ca * N + n), db = v.y - ld_stream(ref + (size_t)cb * N + n);
+      acc.add(0, da * da);
+      acc.add(0, db * db);
+    }
+    scr[n] = v;
+  }
+  if (lane == 0) scr[N] = make_float2(0.f, 0.f);  // read with weight 0 by a last tap at i0 = N - 1
+  __syncwarp();
+  // u~_n = (w0 g)_n u[i0_n] + (w1 g)_n u[i0_n + 1]; the odd bins transform u~ w_2N^n
+  float2 zo[V];
+#pragma unroll
+  for (int m = 0; m < V; ++m) {
+    const int n = lane + 32 * m;
+    const float4 t = __ldg(ftab + n);
+    const int i0 = __float_as_int(t.z);
+    const float2 u0 = scr[i0], u1 = scr[i0 + 1];
+    z[m] = make_float2(t.x * u0.x + t.y * u1.x, t.x * u0.y + t.y * u1.y);
+    zo[m] = cmul(z[m], twc[n]);
+  }
+  __syncwarp();
+
+  // even bins kt = 2 k, k <= N/2, then odd bins kt = 2 k + 1, k < N/2
+  wfft_fwd<V>(z, scr, tw1, twc, lane);
+#pragma unroll
+  for (int a = 0; a < V; ++a) scr[k1 + V * a + V * V * gr] = z[a];
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j <= N / 64; ++j) {
+    const int k = lane + 32 * j;
+    if (k <= N / 2) {
+      const float4 v = hermitian_split(scr[k], scr[(N - k) & (N - 1)]);
+      if (k < N / 2)
+        *reinterpret_cast<float4*>(sm + tile_off(2 * k, warp)) = v;
+      else
+        *reinterpret_cast<float4*>(S + (size_t)N * pitch + ca) = v;
+    }
+  }
+  __syncwarp();
+  wfft_fwd<V>(zo, scr, tw1, twc, lane);
+#pragma unroll
+  for (int a = 0; a < V; ++a) scr[k1 + V * a + V * V * gr] = zo[a];
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < N / 64; ++j) {
+    const int k = lane + 32 * j;
+    const float4 v = hermitian_split(scr[k], scr[N - 1 - k]);
+    *reinterpret_cast<float4*>(sm + tile_off(2 * k + 1, warp)) = v;
+  }
+  fence_async_smem();
+  __syncthreads();
+  if (tid == 0) {
+#pragma unroll 1
+    for (int r0 = 0; r0 < N; r0 += W::BOX) tma_store_2d(&tm_s, 2 * col0, r0, tile + r0 * 128);
+    bulk_commit();
+  }
+  if (partials) block_reduce_acc(acc, partials);
+  if (tid == 0) bulk_wait_all();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+template <int V>
+nlos_status tadj_solve_w(const Plan& P, const float2* S, int pitch, const SolveRhs& sr, float2* Sp,
+                         cudaStream_t st) {
+  using W = WP<V>;
+  CUtensorMap ms, mp;
+  NLOS_TRY(make_tmap_2d(&ms, S, 2ull * pitch, W::N + 1, 8ull * pitch, 32, W::BOX));
+  NLOS_TRY(make_tmap_2d(&mp, Sp, 2ull * pitch, W::N / 2 + 1, 8ull * pitch, 32, W::BOXP));
+  int32_t* status = sr.sc ? const_cast<int32_t*>(&sr.sc->status) : nullptr;
+  KTimer kt_(P, KC_TADJ, st);
+  k_tadj_w<V><<<pitch / kWarpCols, kWarpThreads, W::SMEM, st>>>(ms, S, mp, Sp, pitch, sr, P.d_rzT_ptr, P.d_rzT_ent,
+                                                                 P.d_tw2t, status);
+  NLOS_LAUNCH_CHECK("k_tadj_w");
+  return NLOS_OK;
+}
+
+template <int V>
+nlos_status sinv_rz_w(const Plan& P, const float2* Sp, int pitch, float* x, const float* ref, double* partials,
+                      int* nblocks, float2* S, DevScalars* sc, cudaStream_t st) {
+  using W = WP<V>;
+  const int blocks = pitch / kWarpCols;
+  if (partials && blocks > P.partial_blocks) return fail(NLOS_ERR_INVALID_ARG, "partials buffer too small");
+  if (nblocks) *nblocks = blocks;
+  CUtensorMap mp, ms;
+  NLOS_TRY(make_tmap_2d(&mp, Sp, 2ull * pitch, W::N / 2 + 1, 8ull * pitch, 32, W::BOXP));
+  NLOS_TRY(make_tmap_2d(&ms, S, 2ull * pitch, W::N + 1, 8ull * pitch, 32, W::BOX));
+  KTimer kt_(P, KC_SINV, st);
+  k_sinv_rz_w<V><<<blocks, kWarpThreads, W::SMEM, st>>>(mp, Sp, ms, S, pitch, x, ref, partials, P.d_rz_f4, P.d_tw2t,
+                                                         sc ? &sc->status : nullptr);
+  NLOS_LAUNCH_CHECK("k_sinv_rz_w");
+  return NLOS_OK;
+}
+
+template <int V>
+nlos_status prepare_w() {
+  NLOS_TRY(ensure_smem(k_tadj_w<V>, WP<V>::SMEM));
+  NLOS_TRY(ensure_smem(k_sinv_rz_w<V>, WP<V>::SMEM));
+  return NLOS_OK;
+}
+
+}  // namespace
+
+nlos_status make_tmap_2d(CUtensorMap* map, const void* base, uint64_t row_floats, uint64_t rows,
+                         uint64_t pitch_bytes, uint32_t box_x, uint32_t box_y) {
+  const PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled();
+  if (!fn) return fail(NLOS_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  const cuuint64_t dims[2] = {row_floats, rows};
+  const cuuint64_t strides[1] = {pitch_bytes};
+  const cuuint32_t box[2] = {box_x, box_y};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(NLOS_ERR_CUDA, "cuTensorMapEncodeTiled failed (CUresult " + std::to_string((int)r) + ")");
+  return NLOS_OK;
+}
+
+bool tpass_warp_applies(const Plan& P, int ncols, int pitch) {
+  return (P.nt == 128 || P.nt == 256 || P.nt == 512) && ncols == P.nx * P.ny && pitch == ncols &&
+         ncols % kWarpCols == 0;
+}
+
+nlos_status prepare_tpass_warp(int nt) {
+  switch (nt) {
+    case 128: return prepare_w<4>();
+    case 256: return prepare_w<8>();
+    case 512: return prepare_w<16>();
+  }
+  return NLOS_OK;
+}
+
+nlos_status launch_tadj_solve_warp(const Plan& P, const float2* S, int pitch, const SolveRhs& sr, float2* Sp,
+                                   cudaStream_t st) {
+  switch (P.nt) {
+    case 128: return tadj_solve_w<4>(P, S, pitch, sr, Sp, st);
+    case 256: return tadj_solve_w<8>(P, S, pitch, sr, Sp, st);
+    case 512: return tadj_solve_w<16>(P, S, pitch, sr, Sp, st);
+  }
+  return fail(NLOS_ERR_INVALID_ARG, "warp t-pass: unsupported nt");
+}
+
+nlos_status launch_sinv_rz_warp(const Plan& P, const float2* Sp, int pitch, float* x, const float* ref,
+                                double* partials, int* nblocks, float2* S, DevScalars* sc, cudaStream_t st) {
+  switch (P.nt) {
+    case 128: return sinv_rz_w<4>(P, Sp, pitch, x, ref, partials, nblocks, S, sc, st);
+    case 256: return sinv_rz_w<8>(P, Sp, pitch, x, ref, partials, nblocks, S, sc, st);
+    case 512: return sinv_rz_w<16>(P, Sp, pitch, x, ref, partials, nblocks, S, sc, st);
+  }
+  return fail(NLOS_ERR_INVALID_ARG, "warp t-pass: unsupported nt");
+}
+
+}  // namespace nlos
