@@ -77,12 +77,27 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// 3-D tile load: box at (x, y, z).
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
 // 2-D tile store from shared memory at src to the box at (x, y); part of the
 // thread's current bulk group.
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, uint32_t src) {
   asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
                    reinterpret_cast<uint64_t>(map)),
                "r"(x), "r"(y), "r"(src)
+               : "memory");
+}
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, int x, int y, int z, uint32_t src) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(z), "r"(src)
                : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
@@ -99,5 +114,11 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 // skipped.
 nlos_status make_tmap_2d(CUtensorMap* map, const void* base, uint64_t row_floats, uint64_t rows,
                          uint64_t pitch_bytes, uint32_t box_x, uint32_t box_y);
+// Host: the rows [0, 2 pairs) of the same layout as a 3-D map over (float in
+// row, row parity, row pair): element (x, p, r) is float x of row 2 r + p.  A
+// box {box_x, 1, box_r} then holds box_r rows of one parity, consecutive in
+// shared memory.
+nlos_status make_tmap_rowpairs(CUtensorMap* map, const void* base, uint64_t row_floats, uint64_t pairs,
+                               uint64_t pitch_bytes, uint32_t box_x, uint32_t box_r);
 
 }  // namespace nlos

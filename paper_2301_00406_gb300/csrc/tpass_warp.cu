@@ -51,8 +51,8 @@ struct WP {
   static constexpr int N = 32 * V;                        // time bins
   static constexpr int G = 32 / V;                        // lanes per length-32 sequence
   static constexpr int XP = 32 + G;                       // scratch row pitch of the exchange (float2)
-  static constexpr int SCR = V * XP > N + 2 ? V * XP : N + 2;  // scratch per warp (float2)
-  static constexpr int BOX = N < 256 ? N : 256;           // rows per TMA box, padded spectrum
+  static constexpr int SCR = V * XP > N + 16 ? V * XP : N + 16;  // scratch per warp (float2)
+  static constexpr int BOX2 = N / 2 < 256 ? N / 2 : 256;  // rows of one parity per TMA box, padded spectrum
   static constexpr int BOXP = N / 2 < 256 ? N / 2 : 256;  // rows per TMA box, periodic spectrum
   static constexpr int TILE = ((N + 1) * 128 + 1023) / 1024 * 1024;
   static constexpr int OFF_TW1 = TILE;                    // [k1][l] w_N^(l k1)
@@ -69,6 +69,21 @@ struct WP {
 
 // Byte offset of 16-byte chunk c of row r in a swizzled tile.
 __device__ __forceinline__ int tile_off(int r, int c) { return r * 128 + ((c ^ (r & 7)) << 4); }
+// Tile row of padded-spectrum bin kt: the even bins in rows [0, N/2), the odd
+// bins in rows [N/2, N) (each half loaded or stored as one run of rows, so
+// the bins 2k of consecutive k sit in consecutive rows), bin N in row N.
+template <int N>
+__device__ __forceinline__ int prow(int kt) {
+  return kt == N ? N : (kt & 1) * (N / 2) + (kt >> 1);
+}
+// Scratch position of frequency k when a transform's output (the header's
+// order) is written out in natural order: padded so that the 16 lanes of a
+// half-warp, which hold frequencies k1 + V^2 rev(g), fall in distinct banks.
+template <int V>
+__device__ __forceinline__ int natp(int k) {
+  constexpr int G = 32 / V;
+  return k + ((k / (V * V)) % G) * (16 / G);
+}
 
 __device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
   return make_float2(__shfl_xor_sync(kFull, v.x, m), __shfl_xor_sync(kFull, v.y, m));
@@ -191,12 +206,12 @@ __device__ __forceinline__ void wfft_inv(float2 (&a)[V], float2* scr, const floa
 }
 
 // Bin kt in [0, 2N) of the padded spectrum of the pair in chunk c of the
-// tile (rows 0..N), packed z = X_a + i X_b; bins above N by Hermitian
+// tile (rows prow(0..N)), packed z = X_a + i X_b; bins above N by Hermitian
 // symmetry of the real columns.
 template <int N>
 __device__ __forceinline__ float2 padded_bin(const unsigned char* tile, int kt, int c) {
   const bool mir = kt > N;
-  const int r = mir ? 2 * N - kt : kt;
+  const int r = prow<N>(mir ? 2 * N - kt : kt);
   const float4 v = *reinterpret_cast<const float4*>(tile + tile_off(r, c));
   const float ay = mir ? -v.y : v.y, by = mir ? -v.w : v.w;
   return make_float2(v.x - by, ay + v.z);
@@ -252,7 +267,9 @@ __global__ void __launch_bounds__(kWarpThreads, 2)
     mbar_init(bar, 1);
     mbar_expect_tx(bar, N * 128);
 #pragma unroll 1
-    for (int r0 = 0; r0 < N; r0 += W::BOX) tma_load_2d(tile + r0 * 128, &tm_s, 2 * col0, r0, bar);
+    for (int par = 0; par < 2; ++par)
+      for (int r0 = 0; r0 < N / 2; r0 += W::BOX2)
+        tma_load_3d(tile + (par * (N / 2) + r0) * 128, &tm_s, 2 * col0, par, r0, bar);
     // the CTA's u-bar and reg columns are read after the inverse transforms
     prefetch_l2(sr.ubar + (size_t)col0 * N, kWarpCols * N * 4);
     prefetch_l2(sr.reg + (size_t)col0 * N, kWarpCols * N * 4);
@@ -326,13 +343,13 @@ __global__ void __launch_bounds__(kWarpThreads, 2)
   // periodic forward transform of the rhs pair, bins k <= N/2 of both columns
   wfft_fwd<V>(r, scr, tw1, twc, lane);
 #pragma unroll
-  for (int a = 0; a < V; ++a) scr[k1 + V * a + V * V * gr] = r[a];
+  for (int a = 0; a < V; ++a) scr[natp<V>(k1 + V * a + V * V * gr)] = r[a];
   __syncwarp();
 #pragma unroll
   for (int j = 0; j <= N / 64; ++j) {
     const int k = lane + 32 * j;
     if (k <= N / 2) {
-      const float4 x = hermitian_split(scr[k], scr[(N - k) & (N - 1)]);
+      const float4 x = hermitian_split(scr[natp<V>(k)], scr[natp<V>((N - k) & (N - 1))]);
       if (k < N / 2)
         *reinterpret_cast<float4*>(sm + tile_off(k, warp)) = x;
       else
@@ -430,15 +447,15 @@ __global__ void __launch_bounds__(kWarpThreads, 2)
   // even bins kt = 2 k, k <= N/2, then odd bins kt = 2 k + 1, k < N/2
   wfft_fwd<V>(z, scr, tw1, twc, lane);
 #pragma unroll
-  for (int a = 0; a < V; ++a) scr[k1 + V * a + V * V * gr] = z[a];
+  for (int a = 0; a < V; ++a) scr[natp<V>(k1 + V * a + V * V * gr)] = z[a];
   __syncwarp();
 #pragma unroll
   for (int j = 0; j <= N / 64; ++j) {
     const int k = lane + 32 * j;
     if (k <= N / 2) {
-      const float4 v = hermitian_split(scr[k], scr[(N - k) & (N - 1)]);
+      const float4 v = hermitian_split(scr[natp<V>(k)], scr[natp<V>((N - k) & (N - 1))]);
       if (k < N / 2)
-        *reinterpret_cast<float4*>(sm + tile_off(2 * k, warp)) = v;
+        *reinterpret_cast<float4*>(sm + tile_off(k, warp)) = v;  // bin 2k
       else
         *reinterpret_cast<float4*>(S + (size_t)N * pitch + ca) = v;
     }
@@ -446,19 +463,21 @@ __global__ void __launch_bounds__(kWarpThreads, 2)
   __syncwarp();
   wfft_fwd<V>(zo, scr, tw1, twc, lane);
 #pragma unroll
-  for (int a = 0; a < V; ++a) scr[k1 + V * a + V * V * gr] = zo[a];
+  for (int a = 0; a < V; ++a) scr[natp<V>(k1 + V * a + V * V * gr)] = zo[a];
   __syncwarp();
 #pragma unroll
   for (int j = 0; j < N / 64; ++j) {
     const int k = lane + 32 * j;
-    const float4 v = hermitian_split(scr[k], scr[N - 1 - k]);
-    *reinterpret_cast<float4*>(sm + tile_off(2 * k + 1, warp)) = v;
+    const float4 v = hermitian_split(scr[natp<V>(k)], scr[natp<V>(N - 1 - k)]);
+    *reinterpret_cast<float4*>(sm + tile_off(N / 2 + k, warp)) = v;  // bin 2k + 1
   }
   fence_async_smem();
   __syncthreads();
   if (tid == 0) {
 #pragma unroll 1
-    for (int r0 = 0; r0 < N; r0 += W::BOX) tma_store_2d(&tm_s, 2 * col0, r0, tile + r0 * 128);
+    for (int par = 0; par < 2; ++par)
+      for (int r0 = 0; r0 < N / 2; r0 += W::BOX2)
+        tma_store_3d(&tm_s, 2 * col0, par, r0, tile + (par * (N / 2) + r0) * 128);
     bulk_commit();
   }
   if (partials) block_reduce_acc(acc, partials);
@@ -493,7 +512,7 @@ nlos_status tadj_solve_w(const Plan& P, const float2* S, int pitch, const SolveR
                          cudaStream_t st) {
   using W = WP<V>;
   CUtensorMap ms, mp;
-  NLOS_TRY(make_tmap_2d(&ms, S, 2ull * pitch, W::N + 1, 8ull * pitch, 32, W::BOX));
+  NLOS_TRY(make_tmap_rowpairs(&ms, S, 2ull * pitch, W::N / 2, 8ull * pitch, 32, W::BOX2));
   NLOS_TRY(make_tmap_2d(&mp, Sp, 2ull * pitch, W::N / 2 + 1, 8ull * pitch, 32, W::BOXP));
   int32_t* status = sr.sc ? const_cast<int32_t*>(&sr.sc->status) : nullptr;
   KTimer kt_(P, KC_TADJ, st);
@@ -512,7 +531,7 @@ nlos_status sinv_rz_w(const Plan& P, const float2* Sp, int pitch, float* x, cons
   if (nblocks) *nblocks = blocks;
   CUtensorMap mp, ms;
   NLOS_TRY(make_tmap_2d(&mp, Sp, 2ull * pitch, W::N / 2 + 1, 8ull * pitch, 32, W::BOXP));
-  NLOS_TRY(make_tmap_2d(&ms, S, 2ull * pitch, W::N + 1, 8ull * pitch, 32, W::BOX));
+  NLOS_TRY(make_tmap_rowpairs(&ms, S, 2ull * pitch, W::N / 2, 8ull * pitch, 32, W::BOX2));
   KTimer kt_(P, KC_SINV, st);
   k_sinv_rz_w<V><<<blocks, kWarpThreads, W::SMEM, st>>>(mp, Sp, ms, S, pitch, x, ref, partials, P.d_rz_f4, P.d_tw2t,
                                                          sc ? &sc->status : nullptr);
@@ -541,6 +560,22 @@ nlos_status make_tmap_2d(CUtensorMap* map, const void* base, uint64_t row_floats
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(NLOS_ERR_CUDA, "cuTensorMapEncodeTiled failed (CUresult " + std::to_string((int)r) + ")");
+  return NLOS_OK;
+}
+
+nlos_status make_tmap_rowpairs(CUtensorMap* map, const void* base, uint64_t row_floats, uint64_t pairs,
+                               uint64_t pitch_bytes, uint32_t box_x, uint32_t box_r) {
+  const PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled();
+  if (!fn) return fail(NLOS_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  const cuuint64_t dims[3] = {row_floats, 2, pairs};
+  const cuuint64_t strides[2] = {pitch_bytes, 2 * pitch_bytes};
+  const cuuint32_t box[3] = {box_x, 1, box_r};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return fail(NLOS_ERR_CUDA, "cuTensorMapEncodeTiled (row pairs) failed (CUresult " + std::to_string((int)r) + ")");
   return NLOS_OK;
 }
 
