@@ -57,7 +57,8 @@ struct C4 {
   static constexpr int SPX = N == 128 ? 72 : N == 64 ? 40 : 18;  // x scratch pitch per (column, parity)
   static constexpr int WSCR = CW * 4 * SPX;  // x scratch per warp (float2)
   static constexpr int WARPS = 8, THREADS = 256;
-  static constexpr int REGION = ROWS * SP > WARPS * WSCR ? ROWS * SP : WARPS * WSCR;
+  static constexpr int ZB = N == 128 ? 4 * 72 : 0;  // folded-bin buffer per warp (lattice modes)
+  static constexpr int REGION = ROWS * SP > WARPS * (WSCR + ZB) ? ROWS * SP : WARPS * (WSCR + ZB);
   static constexpr size_t smem = sizeof(float2) * (N * M + REGION + 2 * N) + sizeof(int) * 2 * N;
 };
 
@@ -276,10 +277,24 @@ __device__ __forceinline__ void c4_yinv(float2* __restrict__ plane, const float2
 }
 
 // Phase 3: x convolution of the CTA's M columns (ky = 4 c + q).
-template <int N>
+//
+// XM 0: any input and output rows.  XM 1 (N = 128): the output is needed at
+// the sampled rows x = 4 m + r0 only (a lattice of stride 4), so after the
+// forward steps and H the lane's eight bins kx = 4 k1B + pB + 32 k2 fold to
+// two, Z[k''] = w^(-k'' r0) sum_j Y[k'' + 64 j] i^(j r0) for k'' = 4 k1B +
+// pB + 32 e (w = exp(-2 pi i / 2N)), and the 64-point inverse of Z at m < 32
+// is the output at x = 4 m + r0; a warp folds four columns, then runs their
+// inverses together, eight lanes per column.  XM 2 (N = 128): the input
+// holds the lattice rows only, so the padded x spectrum is w^(kx r0)
+// S[kx mod 64] with S the 64-point transform of the column's 32 lattice
+// samples (computed four columns at a time, eight lanes per column); the
+// lane's eight bins follow from two values of S by quarter turns, and H and
+// the inverse steps are those of XM 0.
+template <int N, int XM>
 __device__ __forceinline__ void c4_xconv(float2* __restrict__ plane, float2* __restrict__ scr,
-                                         const float2* __restrict__ tw, const float2* __restrict__ Hk, int q, int adj,
-                                         int warp, int lane) {
+                                         float2* __restrict__ zbuf, const float2* __restrict__ tw,
+                                         const float2* __restrict__ Hk, int q, int adj, int r0, int warp, int lane) {
+  static_assert(XM == 0 || N == 128, "lattice modes are written for N = 128 (CW = 1, R2 = 8)");
   using C = C4<N>;
   constexpr int M = C::M, R2 = C::R2, CW = C::CW, SPX = C::SPX;
   const int cs = lane / (4 * R2), p = (lane / R2) % 4, n2 = lane % R2;
@@ -324,79 +339,225 @@ __device__ __forceinline__ void c4_xconv(float2* __restrict__ plane, float2* __r
       }
     }
   };
-  for (int cb = warp * CW; cb < M; cb += C::WARPS * CW) {
-    const int c = cb + cs;
-    float2 hv[CW][R2];
-    fetch_h(cb, hv);
-    // A: fold, first step, twiddles -> scratch
-    {
-      float2 a[8];
-#pragma unroll
-      for (int n1 = 0; n1 < 8; ++n1) {
-        const int r0 = n2 + R2 * n1;
-        const float2 u = plane[r0 * M + (c ^ sn2 ^ swz<N>(R2 * n1))];
-        const float2 v = plane[(r0 + M) * M + (c ^ sn2 ^ swz<N>(R2 * n1) ^ swz<N>(M))];
-        a[n1] = cmul(cadd(u, rot_mi(v, p)), w32[n1]);
+
+  if constexpr (XM == 0) {
+    for (int cb = warp * CW; cb < M; cb += C::WARPS * CW) {
+      const int c = cb + cs;
+      float2 hv[CW][R2];
+      fetch_h(cb, hv);
+      // A: fold, first step, twiddles -> scratch
+      {
+        float2 a[8];
+  #pragma unroll
+        for (int n1 = 0; n1 < 8; ++n1) {
+          const int r0 = n2 + R2 * n1;
+          const float2 u = plane[r0 * M + (c ^ sn2 ^ swz<N>(R2 * n1))];
+          const float2 v = plane[(r0 + M) * M + (c ^ sn2 ^ swz<N>(R2 * n1) ^ swz<N>(M))];
+          a[n1] = cmul(cadd(u, rot_mi(v, p)), w32[n1]);
+        }
+        dft_reg<8, false>(a);
+  #pragma unroll
+        for (int k1 = 0; k1 < 8; ++k1) myscr[ipos(n2, k1)] = cmul(a[k1], twa[k1]);
       }
-      dft_reg<8, false>(a);
-#pragma unroll
-      for (int k1 = 0; k1 < 8; ++k1) myscr[ipos(n2, k1)] = cmul(a[k1], twa[k1]);
-    }
-    __syncwarp();
-    // B: second step, multiply by H, inverse second step, inverse twiddles
-#pragma unroll
-    for (int j = 0; j < CW; ++j) {
-      float2* s = scr + (j * 4 + pB) * SPX;
-      float2 b[R2];
-#pragma unroll
-      for (int m = 0; m < R2; ++m) b[m] = s[ipos(m, k1B)];
-      dft_reg<R2, false>(b);
-#pragma unroll
-      for (int k2 = 0; k2 < R2; ++k2) b[k2] = cmul(b[k2], hv[j][k2]);
-      dft_reg<R2, true>(b);
-#pragma unroll
-      for (int m = 0; m < R2; ++m) s[ipos(m, k1B)] = m == 0 ? b[0] : cmul(b[m], twb[m]);
-    }
-    __syncwarp();
-    // A': inverse first step, untwist, recombine the four parities
-    {
-      float2 e[8];
-#pragma unroll
-      for (int k1 = 0; k1 < 8; ++k1) e[k1] = myscr[ipos(n2, k1)];
-      dft_reg<8, true>(e);
-      // v_p[n] = w^(-p n) I_p[n]; the w^(-p n2) part is already applied in B
-      float2 keep[8];
-#pragma unroll
-      for (int n1 = 0; n1 < 8; ++n1) {
-        const float2 v = cmulc(e[n1], w32[n1]);
-        const float2 v1 = rot_i(v, p);        // contribution to out[n + M]
-        const float2 send = (p & 1) ? v : v1;  // the half this lane gives away
-        const float2 mine = (p & 1) ? v1 : v;
-        const float2 got = make_float2(__shfl_xor_sync(0xffffffffu, send.x, R2),
-                                       __shfl_xor_sync(0xffffffffu, send.y, R2));
-        keep[n1] = cadd(mine, got);
+      __syncwarp();
+      // B: second step, multiply by H, inverse second step, inverse twiddles
+  #pragma unroll
+      for (int j = 0; j < CW; ++j) {
+        float2* s = scr + (j * 4 + pB) * SPX;
+        float2 b[R2];
+  #pragma unroll
+        for (int m = 0; m < R2; ++m) b[m] = s[ipos(m, k1B)];
+        dft_reg<R2, false>(b);
+  #pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) b[k2] = cmul(b[k2], hv[j][k2]);
+        dft_reg<R2, true>(b);
+  #pragma unroll
+        for (int m = 0; m < R2; ++m) s[ipos(m, k1B)] = m == 0 ? b[0] : cmul(b[m], twb[m]);
       }
-      const int h = p & 1, hi = p >> 1;
-      const int s_out = sn2 ^ swz<N>(R2 * 4 * hi + M * h);  // row bits fixed per lane
+      __syncwarp();
+      // A': inverse first step, untwist, recombine the four parities
+      {
+        float2 e[8];
+  #pragma unroll
+        for (int k1 = 0; k1 < 8; ++k1) e[k1] = myscr[ipos(n2, k1)];
+        dft_reg<8, true>(e);
+        // v_p[n] = w^(-p n) I_p[n]; the w^(-p n2) part is already applied in B
+        float2 keep[8];
+  #pragma unroll
+        for (int n1 = 0; n1 < 8; ++n1) {
+          const float2 v = cmulc(e[n1], w32[n1]);
+          const float2 v1 = rot_i(v, p);        // contribution to out[n + M]
+          const float2 send = (p & 1) ? v : v1;  // the half this lane gives away
+          const float2 mine = (p & 1) ? v1 : v;
+          const float2 got = make_float2(__shfl_xor_sync(0xffffffffu, send.x, R2),
+                                         __shfl_xor_sync(0xffffffffu, send.y, R2));
+          keep[n1] = cadd(mine, got);
+        }
+        const int h = p & 1, hi = p >> 1;
+        const int s_out = sn2 ^ swz<N>(R2 * 4 * hi + M * h);  // row bits fixed per lane
+  #pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          const float2 send = hi ? keep[jj] : keep[4 + jj];
+          const float2 mine = hi ? keep[4 + jj] : keep[jj];
+          const float2 got = make_float2(__shfl_xor_sync(0xffffffffu, send.x, 2 * R2),
+                                         __shfl_xor_sync(0xffffffffu, send.y, 2 * R2));
+          const int x = n2 + R2 * (4 * hi + jj) + M * h;
+          plane[x * M + (c ^ s_out ^ swz<N>(R2 * jj))] = cadd(mine, got);
+        }
+      }
+      __syncwarp();
+    }
+
+  } else {
+    // zbuf: four columns of 64 bins (pitch 72) per warp; entry (r, c) of the
+    // 8 x 8 exchange of column jj at jj * 72 + 8 r + (c ^ r)
+    constexpr int ZP = 72;
+    const int jz = lane >> 3, tz = lane & 7;
+    float2* zc = zbuf + jz * ZP;
+    const int kk0 = 4 * k1B + pB;  // the lane's two folded bins kk0, kk0 + 32
+#pragma unroll 1
+    for (int g = 0; g < M / (4 * C::WARPS); ++g) {
+      if constexpr (XM == 2) {
+        // S = 64-point transform of the lattice samples s[m] = col[4 m + r0], m < 32
+        const int c = warp + C::WARPS * (4 * g + jz);
+        float2 a[8];
 #pragma unroll
+        for (int m1 = 0; m1 < 8; ++m1) {
+          if (m1 < 4) {
+            const int x = 4 * (8 * m1 + tz) + r0;
+            a[m1] = plane[x * M + (c ^ swz<N>(x))];
+          } else {
+            a[m1] = make_float2(0.f, 0.f);
+          }
+        }
+        dft_reg<8, false>(a);
+#pragma unroll
+        for (int k1 = 1; k1 < 8; ++k1) a[k1] = cmul(a[k1], tw[(4 * k1 * tz) & (2 * N - 1)]);
+#pragma unroll
+        for (int k1 = 0; k1 < 8; ++k1) zc[8 * k1 + (tz ^ k1)] = a[k1];
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < 8; ++t) a[t] = zc[8 * tz + (t ^ tz)];
+        __syncwarp();
+        dft_reg<8, false>(a);
+#pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) zc[tz + 8 * k2] = a[k2];  // S[tz + 8 k2], natural order
+        __syncwarp();
+      }
+#pragma unroll 1
       for (int jj = 0; jj < 4; ++jj) {
-        const float2 send = hi ? keep[jj] : keep[4 + jj];
-        const float2 mine = hi ? keep[4 + jj] : keep[jj];
-        const float2 got = make_float2(__shfl_xor_sync(0xffffffffu, send.x, 2 * R2),
-                                       __shfl_xor_sync(0xffffffffu, send.y, 2 * R2));
-        const int x = n2 + R2 * (4 * hi + jj) + M * h;
-        plane[x * M + (c ^ s_out ^ swz<N>(R2 * jj))] = cadd(mine, got);
+        const int c = warp + C::WARPS * (4 * g + jj);
+        float2 hv[CW][R2];
+        fetch_h(c, hv);
+        float2* s = scr + pB * SPX;
+        float2 b[R2];
+        if constexpr (XM == 1) {
+          // A: fold, first step, twiddles -> scratch (as XM 0)
+          float2 a[8];
+#pragma unroll
+          for (int n1 = 0; n1 < 8; ++n1) {
+            const int rr = n2 + R2 * n1;
+            const float2 u = plane[rr * M + (c ^ sn2 ^ swz<N>(R2 * n1))];
+            const float2 v = plane[(rr + M) * M + (c ^ sn2 ^ swz<N>(R2 * n1) ^ swz<N>(M))];
+            a[n1] = cmul(cadd(u, rot_mi(v, p)), w32[n1]);
+          }
+          dft_reg<8, false>(a);
+#pragma unroll
+          for (int k1 = 0; k1 < 8; ++k1) myscr[ipos(n2, k1)] = cmul(a[k1], twa[k1]);
+          __syncwarp();
+#pragma unroll
+          for (int m = 0; m < R2; ++m) b[m] = s[ipos(m, k1B)];
+          dft_reg<R2, false>(b);
+#pragma unroll
+          for (int k2 = 0; k2 < R2; ++k2) b[k2] = cmul(b[k2], hv[0][k2]);
+          // fold the four j of each e, then the twist w^(-k'' r0)
+          float2 z0 = b[0], z1 = b[1];
+#pragma unroll
+          for (int j = 1; j < 4; ++j) {
+            z0 = cadd(z0, rot_i(b[2 * j], (j * r0) & 3));
+            z1 = cadd(z1, rot_i(b[2 * j + 1], (j * r0) & 3));
+          }
+          float2* zj = zbuf + jj * ZP;
+          zj[kk0] = cmulc(z0, tw[(kk0 * r0) & (2 * N - 1)]);
+          zj[kk0 + 32] = cmulc(z1, tw[((kk0 + 32) * r0) & (2 * N - 1)]);
+          __syncwarp();
+        } else {
+          // the lane's bins from S: b[e + 2 j] = w^(kk r0) S[kk] (-i)^(j r0), kk = kk0 + 32 e
+          const float2* zj = zbuf + jj * ZP;
+          const float2 s0 = cmul(zj[kk0], tw[(kk0 * r0) & (2 * N - 1)]);
+          const float2 s1 = cmul(zj[kk0 + 32], tw[((kk0 + 32) * r0) & (2 * N - 1)]);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            b[2 * j] = cmul(rot_mi(s0, (j * r0) & 3), hv[0][2 * j]);
+            b[2 * j + 1] = cmul(rot_mi(s1, (j * r0) & 3), hv[0][2 * j + 1]);
+          }
+          // inverse second step and inverse twiddles -> scratch, then A' as XM 0
+          dft_reg<R2, true>(b);
+#pragma unroll
+          for (int m = 0; m < R2; ++m) s[ipos(m, k1B)] = m == 0 ? b[0] : cmul(b[m], twb[m]);
+          __syncwarp();
+          float2 e[8];
+#pragma unroll
+          for (int k1 = 0; k1 < 8; ++k1) e[k1] = myscr[ipos(n2, k1)];
+          dft_reg<8, true>(e);
+          float2 keep[8];
+#pragma unroll
+          for (int n1 = 0; n1 < 8; ++n1) {
+            const float2 v = cmulc(e[n1], w32[n1]);
+            const float2 v1 = rot_i(v, p);
+            const float2 send = (p & 1) ? v : v1;
+            const float2 mine = (p & 1) ? v1 : v;
+            const float2 got = make_float2(__shfl_xor_sync(0xffffffffu, send.x, R2),
+                                           __shfl_xor_sync(0xffffffffu, send.y, R2));
+            keep[n1] = cadd(mine, got);
+          }
+          const int h = p & 1, hi = p >> 1;
+          const int s_out = sn2 ^ swz<N>(R2 * 4 * hi + M * h);
+#pragma unroll
+          for (int j4 = 0; j4 < 4; ++j4) {
+            const float2 send = hi ? keep[j4] : keep[4 + j4];
+            const float2 mine = hi ? keep[4 + j4] : keep[j4];
+            const float2 got = make_float2(__shfl_xor_sync(0xffffffffu, send.x, 2 * R2),
+                                           __shfl_xor_sync(0xffffffffu, send.y, 2 * R2));
+            const int x = n2 + R2 * (4 * hi + j4) + M * h;
+            plane[x * M + (c ^ s_out ^ swz<N>(R2 * j4))] = cadd(mine, got);
+          }
+          __syncwarp();
+        }
+      }
+      if constexpr (XM == 1) {
+        // 64-point inverses of the four folded columns: lane (jz, tz) holds
+        // Z[tz + 8 u]; out[mu1 + 8 mu2] for mu2 < 4 is the value at x = 4 (mu1 + 8 mu2) + r0
+        float2 a[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] = zc[tz + 8 * u];
+        __syncwarp();
+        dft_reg<8, true>(a);
+#pragma unroll
+        for (int mu1 = 1; mu1 < 8; ++mu1) a[mu1] = cmulc(a[mu1], tw[(4 * tz * mu1) & (2 * N - 1)]);
+#pragma unroll
+        for (int mu1 = 0; mu1 < 8; ++mu1) zc[8 * mu1 + (tz ^ mu1)] = a[mu1];
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < 8; ++t) a[t] = zc[8 * tz + (t ^ tz)];
+        __syncwarp();
+        dft_reg<8, true>(a);
+        const int c = warp + C::WARPS * (4 * g + jz);
+#pragma unroll
+        for (int mu2 = 0; mu2 < 4; ++mu2) {
+          const int x = 4 * (tz + 8 * mu2) + r0;
+          plane[x * M + (c ^ swz<N>(x))] = a[mu2];
+        }
       }
     }
-    __syncwarp();
   }
 }
 
-template <int N>
+template <int N, int XM>
 __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(256, 2)
     k_conv4(const float2* __restrict__ Sin, int in_pitch, const int32_t* __restrict__ in_cols, int in_n,
             float2* __restrict__ Sout, int out_pitch, const int32_t* __restrict__ out_cols, int out_n,
-            const float2* __restrict__ H, int adj, const float2* __restrict__ twg) {
+            const float2* __restrict__ H, int adj, const float2* __restrict__ twg, int r0) {
   using C = C4<N>;
   constexpr int M = C::M, ROWS = C::ROWS, SP = C::SP;
   extern __shared__ float4 smem_f4[];
@@ -459,7 +620,8 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(256, 2)
 
   // 3. x convolution
   const float2* Hk = H + (size_t)kt * (N + 1) * (N + 1);
-  c4_xconv<N>(plane, region + warp * C::WSCR, tw, Hk, q, adj, warp, lane);
+  c4_xconv<N, XM>(plane, region + warp * C::WSCR, region + C::WARPS * C::WSCR + warp * C::ZB, tw, Hk, q, adj, r0,
+                  warp, lane);
   __syncthreads();
 
   // 4. inverse y transform
@@ -536,9 +698,12 @@ size_t conv4_smem_bytes(int n) {
 
 nlos_status prepare_conv4(int n) {
   switch (n) {
-    case 32: return ensure_smem(k_conv4<32>, C4<32>::smem);
-    case 64: return ensure_smem(k_conv4<64>, C4<64>::smem);
-    case 128: return ensure_smem(k_conv4<128>, C4<128>::smem);
+    case 32: return ensure_smem(k_conv4<32, 0>, C4<32>::smem);
+    case 64: return ensure_smem(k_conv4<64, 0>, C4<64>::smem);
+    case 128:
+      NLOS_TRY(ensure_smem(k_conv4<128, 1>, C4<128>::smem));
+      NLOS_TRY(ensure_smem(k_conv4<128, 2>, C4<128>::smem));
+      return ensure_smem(k_conv4<128, 0>, C4<128>::smem);
   }
   return NLOS_OK;
 }
@@ -553,14 +718,18 @@ nlos_status launch_conv4(const Plan& P, const float2* Sin, bool in_compact, floa
     NLOS_TRY(ensure_smem(kern, smem));
     kern<<<4 * (P.nt + 1), 256, smem, st>>>(Sin, in_pitch, in_compact ? P.d_cols : nullptr, P.ncols, Sout,
                                             out_pitch, out_compact ? P.d_cols : nullptr, P.ncols, P.d_H,
-                                            adj ? 1 : 0, P.d_twx);
+                                            adj ? 1 : 0, P.d_twx, P.lattice_rx);
     NLOS_LAUNCH_CHECK("k_conv4");
     return NLOS_OK;
   };
   switch (P.nx) {
-    case 32: return go(k_conv4<32>, C4<32>::smem);
-    case 64: return go(k_conv4<64>, C4<64>::smem);
-    case 128: return go(k_conv4<128>, C4<128>::smem);
+    case 32: return go(k_conv4<32, 0>, C4<32>::smem);
+    case 64: return go(k_conv4<64, 0>, C4<64>::smem);
+    case 128:
+      // sampled rows on one residue class mod 4: fold the x work to the lattice
+      if (P.lattice_rx >= 0 && out_compact && !in_compact) return go(k_conv4<128, 1>, C4<128>::smem);
+      if (P.lattice_rx >= 0 && in_compact && !out_compact) return go(k_conv4<128, 2>, C4<128>::smem);
+      return go(k_conv4<128, 0>, C4<128>::smem);
   }
   return fail(NLOS_ERR_INVALID_ARG, "conv4: unsupported nx");
 }

@@ -322,6 +322,13 @@ static nlos_status host_plan(const nlos_geometry* g, Plan* P, std::vector<int32_
     }
   P->ncols = (int)P->h_cols.size();
   P->full_mask = P->ncols == full;
+  P->lattice_rx = -1;
+  if (!P->full_mask) {
+    const int r = P->h_cols[0] / P->ny % 4;
+    bool one_class = true;
+    for (int c : P->h_cols) one_class = one_class && (c / P->ny) % 4 == r;
+    if (one_class) P->lattice_rx = r;
+  }
   if (P->ncols == 0) return fail(NLOS_ERR_INVALID_ARG, "mask samples no scan point");
   build_tables(*P);
   return NLOS_OK;

@@ -30,6 +30,10 @@ CASES = [
     (64, 512, "compensated", "stride2"),
     (64, 256, "compensated", "random"),    # four-CTA lateral pass, scattered sampled rows
     (128, 64, "compensated", "ragged"),    # four-CTA lateral pass at N = 128, ragged sample list
+    # sampled rows on one residue class mod 4 (x passes folded to the lattice)
+    (128, 64, "compensated", "lattice4_0"),
+    (128, 32, "raw", "lattice4_3"),
+    (128, 64, "compensated", "rows1mod4"),  # rows x = 1 mod 4, scattered y, some rows empty
 ]
 
 
@@ -40,6 +44,17 @@ def make_mask(n, kind, seed=3):
         return synth.stride_mask(n, n, 2)
     if kind == "random":
         return synth.random_mask(n, n, 0.25, seed)
+    if kind.startswith("lattice4_"):
+        r = int(kind[-1])
+        m = np.zeros((n, n), np.uint8)
+        m[r::4, (r + 1) % 4::4] = 1
+        return m
+    if kind == "rows1mod4":
+        m = np.zeros((n, n), np.uint8)
+        rng = np.random.default_rng(seed)
+        for x in range(1, n - 8, 4):
+            m[x, rng.permutation(n)[:rng.integers(1, 9)]] = 1
+        return m
     if kind == "ragged":
         m = np.zeros(n * n, np.uint8)
         m[np.random.default_rng(seed).permutation(n * n)[:37]] = 1
