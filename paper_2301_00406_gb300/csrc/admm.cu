@@ -1050,17 +1050,30 @@ static nlos_status step_alg1(JobRun& j) {
   const int ntiles = tiled ? stencil_steps(g) : 0;  // (tile, x plane) steps
   const int pre_grid = std::min(ntiles, P.sms * 3), post_grid = std::min(ntiles, P.sms * 2);
   const int post_blocks = tiled ? post_grid : stencil_blocks(P);
-  { KTimer kt_(P, KC_PRE, st);
+  // The pre stencil (reads u-bar, Lambda, phi; writes reg) and the start of
+  // A_D^T (reads the cached A u, tau0 and beta; writes the spectrum scratch)
+  // are independent: in a captured graph the pre stencil is a parallel
+  // branch (HBM-bound, next to the ALU-bound lateral pass), joined before the
+  // u-step reads reg.
+  cudaStream_t pst = st;
+  if (j.aux) {
+    NLOS_CUDA(cudaEventRecord(j.ev_fork, st));
+    NLOS_CUDA(cudaStreamWaitEvent(j.aux, j.ev_fork, 0));
+    pst = j.aux;
+  }
+  { KTimer kt_(P, KC_PRE, pst);
   if (tiled)
-    k_pre1_pipe<false><<<pre_grid, kTileThreads, kPre1PipeSmem, st>>>(s->ub, s->lam, s->ph, s->reg, g, ntiles,
-                                                                      (float)p.mu, V, FTerm{});
+    k_pre1_pipe<false><<<pre_grid, kTileThreads, kPre1PipeSmem, pst>>>(s->ub, s->lam, s->ph, s->reg, g, ntiles,
+                                                                       (float)p.mu, V, FTerm{});
   else
-    k_pre1<<<stencil_blocks(P), kStencilThreads, 0, st>>>(s->ub, s->lam, s->ph, s->reg, g, vi, (float)p.mu, V);
+    k_pre1<<<stencil_blocks(P), kStencilThreads, 0, pst>>>(s->ub, s->lam, s->ph, s->reg, g, vi, (float)p.mu, V);
   }
   NLOS_LAUNCH_CHECK("k_pre1");
+  if (j.aux) NLOS_CUDA(cudaEventRecord(j.ev_join, pst));
   Lin3 r{{s->cache[j.cur], s->cache[j.prev], s->tau0c}, {0.f, 0.f, 0.f}, s->sc};
   NLOS_TRY(launch_tfwd_rtt(P, r, P.ncols, P.d_Sc, P.ncols, st));
   NLOS_TRY(launch_conv(P, P.d_Sc, true, P.d_S, false, true, st));
+  if (j.aux) NLOS_CUDA(cudaStreamWaitEvent(st, j.ev_join, 0));
   const bool host_check = j.L_host < 1.5 * j.norm2;
   UStepArgs ua{s->reg, p.mu, true, s->tau0c, p.eta, p.max_backtracks, s->cache[j.nxt], s->cache[j.cur],
                s->cache[j.prev]};
@@ -1216,6 +1229,12 @@ void free_graphs(Plan* P) {
     if (b) cudaStreamDestroy(b);
     b = nullptr;
   }
+  if (P->aux_stream) cudaStreamDestroy(P->aux_stream);
+  P->aux_stream = nullptr;
+  for (auto& e : P->aux_ev) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
 }
 
 // Captures (on c.st, which is capturing) a run whose iteration count is
@@ -1310,8 +1329,14 @@ static nlos_status job_graph(JobRun& j, cudaStream_t st, cudaGraphExec_t* exec) 
   if (looped)
     for (auto& b : P.body_stream)
       if (!b) NLOS_CUDA(cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking));
+  if (!P.aux_stream) NLOS_CUDA(cudaStreamCreateWithFlags(&P.aux_stream, cudaStreamNonBlocking));
+  for (auto& e : P.aux_ev)
+    if (!e) NLOS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   JobRun c = j;
   c.st = P.capture_stream;
+  c.aux = P.aux_stream;
+  c.ev_fork = P.aux_ev[0];
+  c.ev_join = P.aux_ev[1];
   NLOS_CUDA(cudaStreamBeginCapture(c.st, cudaStreamCaptureModeThreadLocal));
   nlos_status s = NLOS_OK;
   if (looped) {

@@ -236,6 +236,9 @@ struct Plan {
   };
   std::vector<GraphEntry> graphs;
   cudaStream_t capture_stream = nullptr;
+  // parallel branch of a captured iteration (JobRun::aux) and its events
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t aux_ev[2] = {nullptr, nullptr};
   // streams that capture the bodies of conditional nodes (iteration loop,
   // pointer-phase switch, backtracking loop)
   cudaStream_t body_stream[3] = {nullptr, nullptr, nullptr};
@@ -340,6 +343,12 @@ struct JobRun {
   // backtracking loop body is captured (the u-step then repeats on the device
   // until the test accepts); nullptr otherwise.
   cudaStream_t bt_stream = nullptr;
+  // While a graph is captured: a second stream and a fork/join event pair, so
+  // that work of an iteration that does not depend on the rest of it (the
+  // Algorithm-1 pre stencil next to the start of A_D^T) becomes a parallel
+  // branch of the graph; nullptr otherwise (everything on st).
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 // Allocates the solver state on first use, computes (once per plan) the
 // operator norm with a host synchronisation, and enqueues the initial state.

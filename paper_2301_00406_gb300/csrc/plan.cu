@@ -258,6 +258,8 @@ Plan* plan_clone_workspace(const Plan& base, nlos_status* status) {
   P->graphs.clear();
   P->capture_stream = nullptr;
   for (auto& b : P->body_stream) b = nullptr;  // the base's streams stay the base's
+  P->aux_stream = nullptr;
+  P->aux_ev[0] = P->aux_ev[1] = nullptr;
   P->lateral = nullptr;                         // a clone uses the FFT lateral stage
   nlos_status s = alloc_workspace(P);
   if (s != NLOS_OK) {
