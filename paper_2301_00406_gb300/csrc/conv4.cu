@@ -102,13 +102,19 @@ __device__ __forceinline__ int fold_k(int k) {
   return k <= N ? k : 2 * N - k;
 }
 
-// Phase 2: forward y transform of every row for bins ky = 4 k + Q.
-template <int N, int Q>
+// Phase 2: forward y transform of every row for bins ky = 4 k + Q.  LAT:
+// only the rows x = 4 v + r0 (v < N / 4) hold input, and each warp step
+// takes four such rows (the swizzle of x = 4 v + r0 is swz(4 v) ^ swz(r0),
+// the bits of 4 v and r0 being disjoint).
+template <int N, int Q, bool LAT>
 __device__ __forceinline__ void c4_yfwd(float2* __restrict__ plane, const float2* const (&stage)[4],
                                         const float2* __restrict__ gsrc, const float2* __restrict__ tw,
-                                        const int* __restrict__ rowin, int warp, int lane) {
+                                        const int* __restrict__ rowin, int r0, int warp, int lane) {
   using C = C4<N>;
   constexpr int M = C::M, R2 = C::R2, RW = C::RW, SP = C::SP, ROWS = C::ROWS;
+  constexpr int NR = LAT ? N / 4 : N;  // rows visited
+  auto xr = [&](int v) { return LAT ? 4 * v + r0 : v; };
+  auto sw = [&](int v) { return LAT ? swz<N>(4 * v) : swz<N>(v); };
   const int rsub = lane / R2, n2 = lane % R2;
   // inter-step twiddles w^(n2 (Q + 4 k1)), k1 = 0..7 (the fold twist w^(Q n2) merged in)
   float2 twa[8];
@@ -123,8 +129,8 @@ __device__ __forceinline__ void c4_yfwd(float2* __restrict__ plane, const float2
   // row group's 16 values per lane are fetched while the current one computes.
   float2 pu[8], pv[8];
   auto fetch = [&](int it) {
-    const int x = it * RW + rsub;
-    if (it < N / RW && rowin[x]) {
+    const int x = xr(it * RW + rsub);
+    if (it < NR / RW && rowin[x]) {
       if (gsrc) {
         const float2* row = gsrc + x * N;
 #pragma unroll
@@ -146,15 +152,15 @@ __device__ __forceinline__ void c4_yfwd(float2* __restrict__ plane, const float2
   };
   // swizzles of the lane's row offsets within a row group (rsub, and the
   // step-2 items' rows lane / 8 + 4 j)
-  const int s_rsub = swz<N>(rsub);
+  const int s_rsub = sw(rsub);
   int s_item[8 / R2];
 #pragma unroll
-  for (int j = 0; j < 8 / R2; ++j) s_item[j] = swz<N>((lane + 32 * j) / 8);
+  for (int j = 0; j < 8 / R2; ++j) s_item[j] = sw((lane + 32 * j) / 8);
   fetch(warp);
-  for (int it = warp; it < N / RW; it += C::WARPS) {
-    const int s_it = swz<N>(it * RW);
+  for (int it = warp; it < NR / RW; it += C::WARPS) {
+    const int s_it = sw(it * RW) ^ (LAT ? swz<N>(r0) : 0);
     {
-      const int x = it * RW + rsub;
+      const int x = xr(it * RW + rsub);
       float2 cu[8], cv[8];
 #pragma unroll
       for (int n1 = 0; n1 < 8; ++n1) {
@@ -184,7 +190,7 @@ __device__ __forceinline__ void c4_yfwd(float2* __restrict__ plane, const float2
     float2 b[8 / R2][R2];
 #pragma unroll
     for (int j = 0; j < 8 / R2; ++j) {
-      const int i = lane + 32 * j, xx = it * RW + i / 8, k1 = i % 8;
+      const int i = lane + 32 * j, xx = xr(it * RW + i / 8), k1 = i % 8;
       if (rowin[xx]) {
         const float2* pr = plane + xx * M;
         const int ss = s_it ^ s_item[j];
@@ -199,7 +205,7 @@ __device__ __forceinline__ void c4_yfwd(float2* __restrict__ plane, const float2
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < 8 / R2; ++j) {
-      const int i = lane + 32 * j, xx = it * RW + i / 8, k1 = i % 8;
+      const int i = lane + 32 * j, xx = xr(it * RW + i / 8), k1 = i % 8;
       float2* pr = plane + xx * M;
       const int ss = s_it ^ s_item[j];
 #pragma unroll
@@ -209,12 +215,16 @@ __device__ __forceinline__ void c4_yfwd(float2* __restrict__ plane, const float2
   }
 }
 
-// Phase 4: inverse y transform of every row, times w^(-Q n) (n < M).
-template <int N, int Q>
+// Phase 4: inverse y transform of every row, times w^(-Q n) (n < M).  LAT:
+// only the rows x = 4 v + r0 are wanted, four of them per warp step.
+template <int N, int Q, bool LAT>
 __device__ __forceinline__ void c4_yinv(float2* __restrict__ plane, const float2* __restrict__ tw,
-                                        const int* __restrict__ rowout, int warp, int lane) {
+                                        const int* __restrict__ rowout, int r0, int warp, int lane) {
   using C = C4<N>;
   constexpr int M = C::M, R2 = C::R2, RW = C::RW;
+  constexpr int NR = LAT ? N / 4 : N;  // rows visited
+  auto xr = [&](int v) { return LAT ? 4 * v + r0 : v; };
+  auto sw = [&](int v) { return LAT ? swz<N>(4 * v) : swz<N>(v); };
   const int rsub = lane / R2, n2 = lane % R2;
   const int k1l = lane % 8;
   // w^(-m (4 k1 + Q)), m < R2, for this lane's k1
@@ -225,16 +235,16 @@ __device__ __forceinline__ void c4_yinv(float2* __restrict__ plane, const float2
 #pragma unroll
     for (int m = 1; m < R2; ++m) twi[m] = cmul(twi[m - 1], st);
   }
-  const int s_rsub = swz<N>(rsub);
+  const int s_rsub = sw(rsub);
   int s_item[8 / R2];
 #pragma unroll
-  for (int j = 0; j < 8 / R2; ++j) s_item[j] = swz<N>((lane + 32 * j) / 8);
-  for (int it = warp; it < N / RW; it += C::WARPS) {
-    const int s_it = swz<N>(it * RW);
+  for (int j = 0; j < 8 / R2; ++j) s_item[j] = sw((lane + 32 * j) / 8);
+  for (int it = warp; it < NR / RW; it += C::WARPS) {
+    const int s_it = sw(it * RW) ^ (LAT ? swz<N>(r0) : 0);
     float2 b[8 / R2][R2];
 #pragma unroll
     for (int j = 0; j < 8 / R2; ++j) {
-      const int i = lane + 32 * j, xx = it * RW + i / 8, k1 = i % 8;
+      const int i = lane + 32 * j, xx = xr(it * RW + i / 8), k1 = i % 8;
       if (rowout[xx]) {
         const float2* pr = plane + xx * M;
         const int ss = s_it ^ s_item[j];
@@ -248,7 +258,7 @@ __device__ __forceinline__ void c4_yinv(float2* __restrict__ plane, const float2
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < 8 / R2; ++j) {
-      const int i = lane + 32 * j, xx = it * RW + i / 8, k1 = i % 8;
+      const int i = lane + 32 * j, xx = xr(it * RW + i / 8), k1 = i % 8;
       if (rowout[xx]) {
         float2* pr = plane + xx * M;
         const int ss = s_it ^ s_item[j];
@@ -257,7 +267,7 @@ __device__ __forceinline__ void c4_yinv(float2* __restrict__ plane, const float2
       }
     }
     __syncwarp();
-    const int x = it * RW + rsub;
+    const int x = xr(it * RW + rsub);
     float2 e[8];
     const bool live = rowout[x] != 0;
     float2* prow = plane + x * M;
@@ -608,10 +618,10 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(256, 2)
     cluster.sync();
   }
   switch (q) {
-    case 0: c4_yfwd<N, 0>(plane, stage, gsrc, tw, rowin, warp, lane); break;
-    case 1: c4_yfwd<N, 1>(plane, stage, gsrc, tw, rowin, warp, lane); break;
-    case 2: c4_yfwd<N, 2>(plane, stage, gsrc, tw, rowin, warp, lane); break;
-    default: c4_yfwd<N, 3>(plane, stage, gsrc, tw, rowin, warp, lane); break;
+    case 0: c4_yfwd<N, 0, XM == 2>(plane, stage, gsrc, tw, rowin, r0, warp, lane); break;
+    case 1: c4_yfwd<N, 1, XM == 2>(plane, stage, gsrc, tw, rowin, r0, warp, lane); break;
+    case 2: c4_yfwd<N, 2, XM == 2>(plane, stage, gsrc, tw, rowin, r0, warp, lane); break;
+    default: c4_yfwd<N, 3, XM == 2>(plane, stage, gsrc, tw, rowin, r0, warp, lane); break;
   }
   if (in_cols == nullptr)
     __syncthreads();  // plane complete
@@ -626,10 +636,10 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(256, 2)
 
   // 4. inverse y transform
   switch (q) {
-    case 0: c4_yinv<N, 0>(plane, tw, rowout, warp, lane); break;
-    case 1: c4_yinv<N, 1>(plane, tw, rowout, warp, lane); break;
-    case 2: c4_yinv<N, 2>(plane, tw, rowout, warp, lane); break;
-    default: c4_yinv<N, 3>(plane, tw, rowout, warp, lane); break;
+    case 0: c4_yinv<N, 0, XM == 1>(plane, tw, rowout, r0, warp, lane); break;
+    case 1: c4_yinv<N, 1, XM == 1>(plane, tw, rowout, r0, warp, lane); break;
+    case 2: c4_yinv<N, 2, XM == 1>(plane, tw, rowout, r0, warp, lane); break;
+    default: c4_yinv<N, 3, XM == 1>(plane, tw, rowout, r0, warp, lane); break;
   }
   cluster.sync();
 
