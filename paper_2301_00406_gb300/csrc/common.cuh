@@ -173,6 +173,7 @@ struct Plan {
   int ncols;          // number of sampled columns
   bool full_mask;     // every column sampled
   int lattice_rx = -1;  // r when every sampled column has x = r (mod 4) and some column is unsampled, else -1
+  int lattice_ry = -1;  // r' when the sampled columns are exactly x = lattice_rx, y = r' (mod 4), else -1
   int device;
   int sms;            // streaming multiprocessors of the device (queried at plan creation); sets the
                       // grid of the grid-stride reductions, hence their summation order

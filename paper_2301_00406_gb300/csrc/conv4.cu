@@ -106,10 +106,14 @@ __device__ __forceinline__ int fold_k(int k) {
 // only the rows x = 4 v + r0 (v < N / 4) hold input, and each warp step
 // takes four such rows (the swizzle of x = 4 v + r0 is swz(4 v) ^ swz(r0),
 // the bits of 4 v and r0 being disjoint).
+// csrc (LAT only, nullable): the compact input of a full stride-4 lattice
+// (sampled columns x = 4 mx + r0, y = 4 my + ry, compact index mx N/4 + my),
+// read in place of the staging buffers.
 template <int N, int Q, bool LAT>
 __device__ __forceinline__ void c4_yfwd(float2* __restrict__ plane, const float2* const (&stage)[4],
-                                        const float2* __restrict__ gsrc, const float2* __restrict__ tw,
-                                        const int* __restrict__ rowin, int r0, int warp, int lane) {
+                                        const float2* __restrict__ gsrc, const float2* __restrict__ csrc, int ry,
+                                        const float2* __restrict__ tw, const int* __restrict__ rowin, int r0,
+                                        int warp, int lane) {
   using C = C4<N>;
   constexpr int M = C::M, R2 = C::R2, RW = C::RW, SP = C::SP, ROWS = C::ROWS;
   constexpr int NR = LAT ? N / 4 : N;  // rows visited
@@ -131,7 +135,16 @@ __device__ __forceinline__ void c4_yfwd(float2* __restrict__ plane, const float2
   auto fetch = [&](int it) {
     const int x = xr(it * RW + rsub);
     if (it < NR / RW && rowin[x]) {
-      if (gsrc) {
+      if (LAT && csrc) {
+        // this lane's y = n2 + R2 n1 (+ M) are lattice columns only when n2 = ry (mod 4)
+        const bool live = (n2 & 3) == ry;
+        const float2* rowc = csrc + (it * RW + rsub) * (N / 4) + (n2 >> 2);
+#pragma unroll
+        for (int n1 = 0; n1 < 8; ++n1) {
+          pu[n1] = live ? __ldg(rowc + (R2 / 4) * n1) : make_float2(0.f, 0.f);
+          pv[n1] = live ? __ldg(rowc + (R2 / 4) * n1 + M / 4) : make_float2(0.f, 0.f);
+        }
+      } else if (gsrc) {
         const float2* row = gsrc + x * N;
 #pragma unroll
         for (int n1 = 0; n1 < 8; ++n1) {
@@ -567,7 +580,7 @@ template <int N, int XM>
 __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(256, 2)
     k_conv4(const float2* __restrict__ Sin, int in_pitch, const int32_t* __restrict__ in_cols, int in_n,
             float2* __restrict__ Sout, int out_pitch, const int32_t* __restrict__ out_cols, int out_n,
-            const float2* __restrict__ H, int adj, const float2* __restrict__ twg, int r0) {
+            const float2* __restrict__ H, int adj, const float2* __restrict__ twg, int r0, int ry) {
   using C = C4<N>;
   constexpr int M = C::M, ROWS = C::ROWS, SP = C::SP;
   extern __shared__ float4 smem_f4[];
@@ -603,8 +616,12 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(256, 2)
 #pragma unroll
   for (int r = 0; r < 4; ++r) stage[r] = cluster.map_shared_rank(region, r);
   const float2* gsrc = nullptr;
+  const float2* csrc = nullptr;  // full lattice: compact rows read in place
   if (in_cols == nullptr) {
     gsrc = src;
+    __syncthreads();
+  } else if (XM == 2 && ry >= 0) {
+    csrc = src;
     __syncthreads();
   } else {
     for (int i = tid; i < ROWS * SP; i += C::THREADS) region[i] = make_float2(0.f, 0.f);
@@ -618,12 +635,12 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(256, 2)
     cluster.sync();
   }
   switch (q) {
-    case 0: c4_yfwd<N, 0, XM == 2>(plane, stage, gsrc, tw, rowin, r0, warp, lane); break;
-    case 1: c4_yfwd<N, 1, XM == 2>(plane, stage, gsrc, tw, rowin, r0, warp, lane); break;
-    case 2: c4_yfwd<N, 2, XM == 2>(plane, stage, gsrc, tw, rowin, r0, warp, lane); break;
-    default: c4_yfwd<N, 3, XM == 2>(plane, stage, gsrc, tw, rowin, r0, warp, lane); break;
+    case 0: c4_yfwd<N, 0, XM == 2>(plane, stage, gsrc, csrc, ry, tw, rowin, r0, warp, lane); break;
+    case 1: c4_yfwd<N, 1, XM == 2>(plane, stage, gsrc, csrc, ry, tw, rowin, r0, warp, lane); break;
+    case 2: c4_yfwd<N, 2, XM == 2>(plane, stage, gsrc, csrc, ry, tw, rowin, r0, warp, lane); break;
+    default: c4_yfwd<N, 3, XM == 2>(plane, stage, gsrc, csrc, ry, tw, rowin, r0, warp, lane); break;
   }
-  if (in_cols == nullptr)
+  if (in_cols == nullptr || csrc)
     __syncthreads();  // plane complete
   else
     cluster.sync();   // plane complete; no CTA reads the staging buffers any more
@@ -728,7 +745,7 @@ nlos_status launch_conv4(const Plan& P, const float2* Sin, bool in_compact, floa
     NLOS_TRY(ensure_smem(kern, smem));
     kern<<<4 * (P.nt + 1), 256, smem, st>>>(Sin, in_pitch, in_compact ? P.d_cols : nullptr, P.ncols, Sout,
                                             out_pitch, out_compact ? P.d_cols : nullptr, P.ncols, P.d_H,
-                                            adj ? 1 : 0, P.d_twx, P.lattice_rx);
+                                            adj ? 1 : 0, P.d_twx, P.lattice_rx, P.lattice_ry);
     NLOS_LAUNCH_CHECK("k_conv4");
     return NLOS_OK;
   };

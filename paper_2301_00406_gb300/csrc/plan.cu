@@ -325,11 +325,17 @@ static nlos_status host_plan(const nlos_geometry* g, Plan* P, std::vector<int32_
   P->ncols = (int)P->h_cols.size();
   P->full_mask = P->ncols == full;
   P->lattice_rx = -1;
+  P->lattice_ry = -1;
   if (!P->full_mask) {
     const int r = P->h_cols[0] / P->ny % 4;
     bool one_class = true;
     for (int c : P->h_cols) one_class = one_class && (c / P->ny) % 4 == r;
     if (one_class) P->lattice_rx = r;
+    // the full Cartesian lattice x = r, y = r' (mod 4): its compact index is (x / 4) (ny / 4) + y / 4
+    const int ry = P->h_cols[0] % P->ny % 4;
+    bool cart = one_class && P->nx % 4 == 0 && P->ny % 4 == 0 && P->ncols == (P->nx / 4) * (P->ny / 4);
+    for (int c : P->h_cols) cart = cart && c % P->ny % 4 == ry;
+    if (cart) P->lattice_ry = ry;
   }
   if (P->ncols == 0) return fail(NLOS_ERR_INVALID_ARG, "mask samples no scan point");
   build_tables(*P);
