@@ -324,6 +324,7 @@ static nlos_status host_plan(const nlos_geometry* g, Plan* P, std::vector<int32_
     }
   P->ncols = (int)P->h_cols.size();
   P->full_mask = P->ncols == full;
+  if (P->ncols == 0) return fail(NLOS_ERR_INVALID_ARG, "mask samples no scan point");
   P->lattice_rx = -1;
   P->lattice_ry = -1;
   if (!P->full_mask) {
@@ -337,7 +338,6 @@ static nlos_status host_plan(const nlos_geometry* g, Plan* P, std::vector<int32_
     for (int c : P->h_cols) cart = cart && c % P->ny % 4 == ry;
     if (cart) P->lattice_ry = ry;
   }
-  if (P->ncols == 0) return fail(NLOS_ERR_INVALID_ARG, "mask samples no scan point");
   build_tables(*P);
   return NLOS_OK;
 }
