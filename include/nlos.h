@@ -145,7 +145,14 @@ nlos_status nlos_params_default(int32_t model, nlos_params* out);
  * two-tap tables in FP64 on the host, the sampled-column list of the mask,
  * and the cone-kernel spectrum H on the device (queued on `stream`, which is
  * synchronised before return).  All device memory the plan needs for the
- * operator is allocated here.  *out is set only on success. */
+ * operator is allocated here.  *out is set only on success.
+ * The first plan of a time-axis length and sampled-column count in a process
+ * times the candidate launch shapes of the t-passes (columns per CTA) on the
+ * plan's own buffers and keeps the fastest; the choices are also written to
+ * a tuning file ($NLOS_TUNE_CACHE, else $XDG_CACHE_HOME/nlos-gb300/
+ * tpass_tuning, else $HOME/.cache/nlos-gb300/tpass_tuning; NLOS_TUNE_CACHE=off
+ * disables it), keyed by device name, SM count and library build, from which
+ * later processes read them instead of timing again. */
 nlos_status nlos_plan_create(const nlos_geometry* geom, void* stream, nlos_plan* out);
 
 /* Release a plan and all its device memory.  Synchronises the device first.

@@ -1,11 +1,17 @@
 // Runtime dispatch of the t-pass launchers to their per-size instances
 // (tpass_*.cu), and the launch-shape tuner of the t-passes.
+#include <sys/stat.h>
+#include <unistd.h>
+
+#include <cstdio>
+#include <cstdlib>
 #include <functional>
 #include <map>
-#include <vector>
 #include <mutex>
+#include <string>
 #include <tuple>
 #include <type_traits>
+#include <vector>
 
 #include "tpass.cuh"
 
@@ -83,6 +89,72 @@ namespace {
 std::mutex g_tp_mu;
 std::map<std::tuple<int, int, int>, int> g_tp_cols;  // (kind, nt, ncols) -> cols | hb << 8
 thread_local int g_tp_force = 0;                       // candidate under test (tuner only)
+bool g_tp_loaded = false;                              // tuning file read (under g_tp_mu)
+
+// Tuning file: the tuner's choices persist across processes, keyed by the
+// device name, its SM count and this build of the library (a choice made for
+// other kernels or another GPU is never reused).  Path: $NLOS_TUNE_CACHE, or
+// $XDG_CACHE_HOME/nlos-gb300/tpass_tuning, or $HOME/.cache/nlos-gb300/
+// tpass_tuning; NLOS_TUNE_CACHE=off (or empty) keeps the choices in the
+// process only.  Read and write failures leave the in-process behaviour
+// unchanged.
+const char kTuneMagic[] = "nlos-gb300 t-pass tuning v1";
+const char kBuildId[] = __DATE__ " " __TIME__;
+
+std::string tune_path() {
+  if (const char* e = std::getenv("NLOS_TUNE_CACHE")) {
+    const std::string v(e);
+    return v == "off" ? std::string() : v;
+  }
+  std::string dir;
+  if (const char* x = std::getenv("XDG_CACHE_HOME"); x && *x)
+    dir = std::string(x) + "/nlos-gb300";
+  else if (const char* h = std::getenv("HOME"); h && *h)
+    dir = std::string(h) + "/.cache/nlos-gb300";
+  else
+    return std::string();
+  return dir + "/tpass_tuning";
+}
+
+std::string tune_key() {
+  int dev = 0;
+  cudaDeviceProp prop{};
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return std::string();
+  }
+  return std::string(prop.name) + " | " + std::to_string(prop.multiProcessorCount) + " SMs | " + kBuildId;
+}
+
+void tune_load_locked() {
+  g_tp_loaded = true;
+  const std::string path = tune_path(), key = tune_key();
+  if (path.empty() || key.empty()) return;
+  FILE* f = std::fopen(path.c_str(), "r");
+  if (!f) return;
+  char line[512];
+  const bool ok = std::fgets(line, sizeof line, f) && std::string(line) == std::string(kTuneMagic) + "\n" &&
+                  std::fgets(line, sizeof line, f) && std::string(line) == key + "\n";
+  int kind = 0, nt = 0, ncols = 0, v = 0;
+  while (ok && std::fscanf(f, "%d %d %d %d", &kind, &nt, &ncols, &v) == 4)
+    g_tp_cols.emplace(std::make_tuple(kind, nt, ncols), v);
+  std::fclose(f);
+}
+
+void tune_save_locked() {
+  const std::string path = tune_path(), key = tune_key();
+  if (path.empty() || key.empty()) return;
+  for (size_t i = 1; i < path.size(); ++i)  // create the directories of the path
+    if (path[i] == '/') mkdir(path.substr(0, i).c_str(), 0755);
+  const std::string tmp = path + ".tmp" + std::to_string((long long)getpid());
+  FILE* f = std::fopen(tmp.c_str(), "w");
+  if (!f) return;
+  std::fprintf(f, "%s\n%s\n", kTuneMagic, key.c_str());
+  for (const auto& e : g_tp_cols)
+    std::fprintf(f, "%d %d %d %d\n", std::get<0>(e.first), std::get<1>(e.first), std::get<2>(e.first), e.second);
+  const bool ok = std::fclose(f) == 0;
+  if (!ok || std::rename(tmp.c_str(), path.c_str()) != 0) std::remove(tmp.c_str());
+}
 }  // namespace
 
 int tp_cols_for(int kind, int nt, int ncols) {
@@ -142,6 +214,11 @@ nlos_status autotune_tpass(Plan& P, cudaStream_t st) {
         {TPK_TINV_STORE, nc, false, [&, nc] { return launch_tinv_store(P, P.d_Sc, nc, nc, f1, nullptr, st); }});
   }
   const int max_cols = nt >= 1024 ? 8 : 16;
+  {
+    std::lock_guard<std::mutex> lock(g_tp_mu);
+    if (!g_tp_loaded) tune_load_locked();
+  }
+  bool added = false;
   for (const Case& c : cases) {
     if (status != NLOS_OK) break;
     {
@@ -160,12 +237,12 @@ nlos_status autotune_tpass(Plan& P, cudaStream_t st) {
       g_tp_force = cols | hb << 8;
       float t = 0.f;
       status = c.run();  // warm-up
-      // best of 3 timings of 4 back-to-back launches (the launch latency of a
+      // best of 2 timings of 2 back-to-back launches (the launch latency of a
       // short kernel, and any per-launch overhead of a tool, is amortised)
-      for (int rep = 0; rep < 3 && status == NLOS_OK; ++rep) {
+      for (int rep = 0; rep < 2 && status == NLOS_OK; ++rep) {
         float ms = 0.f;
         if (cudaEventRecord(e0, st) != cudaSuccess) status = fail(NLOS_ERR_CUDA, "autotune: event");
-        for (int l = 0; l < 4 && status == NLOS_OK; ++l) status = c.run();
+        for (int l = 0; l < 2 && status == NLOS_OK; ++l) status = c.run();
         if (status == NLOS_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
                                   cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
           status = fail(NLOS_ERR_CUDA, "autotune: timing");
@@ -179,8 +256,12 @@ nlos_status autotune_tpass(Plan& P, cudaStream_t st) {
     }
     if (status == NLOS_OK && best) {
       std::lock_guard<std::mutex> lock(g_tp_mu);
-      g_tp_cols.emplace(std::make_tuple(c.kind, nt, c.ncols), best);  // first plan of this key decides
+      added = g_tp_cols.emplace(std::make_tuple(c.kind, nt, c.ncols), best).second || added;  // first plan decides
     }
+  }
+  if (status == NLOS_OK && added) {
+    std::lock_guard<std::mutex> lock(g_tp_mu);
+    tune_save_locked();
   }
   g_tp_force = 0;
   if (e0) cudaEventDestroy(e0);
