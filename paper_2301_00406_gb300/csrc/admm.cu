@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kStencilThreads)
             float* __restrict__ lam, float* __restrict__ ph, float* __restrict__ ubn, const DevScalars* __restrict__ sc,
             Vox g, VoxIter vi, float mu, float a, float b, int kind, float eps2, size_t V, double* __restrict__ partials) {
   const float inv_mu = 1.0f / mu;
-  const float beta = (float)sc->beta;
+  const float beta = (float)sc->beta_next;
   SumAcc<2> ca;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V; i += (size_t)gridDim.x * blockDim.x) {
     int x, y, t;
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(kStencilThreads)
             const float* __restrict__ tau0, const int32_t* __restrict__ colpos, const DevScalars* __restrict__ sc, Vox g,
             VoxIter vi, Alg2Coef c, size_t V, double* __restrict__ partials) {
   const float im1 = 1.0f / c.mu1, im2 = 1.0f / c.mu2;
-  const float beta = (float)sc->beta;
+  const float beta = (float)sc->beta_next;
   SumAcc<7> ca;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V; i += (size_t)gridDim.x * blockDim.x) {
     int x, y, t;
@@ -375,16 +375,40 @@ __global__ void k_select_copy(float* __restrict__ o, const float* __restrict__ a
     o[i] = __ldg(src + i);
 }
 
+// The FISTA step that the next accepted test takes from the current t.
+__device__ __forceinline__ void set_next_step(DevScalars* sc) {
+  const double tn = (1.0 + sqrt(1.0 + 4.0 * sc->t * sc->t)) / 2.0;
+  sc->t_next = tn;
+  sc->beta_next = (sc->t - 1.0) / tn;
+}
+
 // End of an iteration: energy, relative change, restart, bookkeeping.
 // model 1: E = f_fit + sum phi |grad u|; model 2: E from the post partials.
+// fold_test (model 1, a test that cannot reject): the accepting test's
+// bookkeeping (k_test with force_accept) is done here first, from the fit
+// partials pf of nbf blocks, so the iteration needs no separate k_test launch.
 __global__ void __launch_bounds__(kSumThreads)
     k_finalize(DevScalars* sc, const double* __restrict__ pp, int nb, int model, double lam_w, int restart,
-               double eps_stop) {
+               double eps_stop, const double* __restrict__ pf, int nbf, int fold_test) {
   const int terms[7] = {0, 1, 2, 3, 4, 5, 6};
   double v[7];
   sum_partials_block<7>(pp, nb, terms, v);
+  double f[2] = {0.0, 0.0};
+  if (fold_test) {
+    const int t01[2] = {0, 1};
+    sum_partials_block<2>(pf, nbf, t01, f);
+  }
   if (threadIdx.x != 0) return;
   if (sc->status != NLOS_OK) return;
+  if (fold_test) {
+    sc->test_lhs = f[1];
+    sc->test_rhs = sc->L * 0.0;
+    sc->accept = 1;
+    sc->f_fit = 0.5 * f[0];
+    sc->beta = sc->beta_next;
+    sc->t = sc->t_next;
+    sc->rej_iter = 0;
+  }
   double E, pres2;
   if (model == 1) {
     E = sc->f_fit + v[0];
@@ -408,6 +432,7 @@ __global__ void __launch_bounds__(kSumThreads)
   sc->primal_res = sqrt(pres2);
   sc->iter += 1;
   if (eps_stop > 0.0 && e <= eps_stop) sc->stop = 1;
+  set_next_step(sc);
 }
 
 // End of an Algorithm-2 iteration from the partials of the split post step
@@ -441,6 +466,7 @@ __global__ void __launch_bounds__(kSumThreads)
   sc->primal_res = sqrt(u[1]);
   sc->iter += 1;
   if (eps_stop > 0.0 && e <= eps_stop) sc->stop = 1;
+  set_next_step(sc);
 }
 
 // Initial scalar block; E_prev = s0 sum(pe0) + s1 sum(pe1) + s2 sum(pe2) over
@@ -459,6 +485,7 @@ __global__ void __launch_bounds__(kSumThreads)
   sc->t = 1.0;
   sc->E_prev = s0 * v0[0] + s1 * v1[0] + s2 * v2[0];
   sc->status = NLOS_OK;
+  set_next_step(sc);
 }
 
 // partials[b][0] = sum phi |grad u| (forward differences, periodic): the
@@ -823,7 +850,13 @@ static nlos_status u_trial(Plan& P, SolverState* s, const UStepArgs& a, bool tes
 // the trials repeat in a conditional loop node on the device.  Otherwise the
 // trial is accepted without a host round trip.
 static nlos_status u_step(Plan& P, SolverState* s, const UStepArgs& a, bool host_check, double* L_host,
-                          cudaStream_t bt_stream, cudaStream_t st) {
+                          cudaStream_t bt_stream, cudaStream_t st, int* nbf_fold = nullptr) {
+  // a test that cannot reject: the caller's k_finalize does its bookkeeping
+  // from the fit partials (nbf_fold receives their block count)
+  if (!host_check && nbf_fold) {
+    int nbd = 0;
+    return u_trial(P, s, a, false, &nbd, nbf_fold, st);
+  }
   if (host_check && bt_stream) {
     cudaGraphConditionalHandle redo = 0;
     NLOS_TRY(cond_handle(st, 0, 0, &redo));
@@ -1077,7 +1110,9 @@ static nlos_status step_alg1(JobRun& j) {
   const bool host_check = j.L_host < 1.5 * j.norm2;
   UStepArgs ua{s->reg, p.mu, true, s->tau0c, p.eta, p.max_backtracks, s->cache[j.nxt], s->cache[j.cur],
                s->cache[j.prev]};
-  NLOS_TRY(u_step(P, s, ua, host_check, &j.L_host, j.bt_stream, st));
+  int nbf_fold = 0;  // test folded into k_finalize (it cannot reject): fit partial blocks
+  NLOS_TRY(u_step(P, s, ua, host_check, &j.L_host, j.bt_stream, st, &nbf_fold));
+  const int fold = host_check ? 0 : 1;
   { KTimer kt_(P, KC_POST, st);
   if (tiled)
     k_post1_pipe<false><<<post_grid, kTileThreads, kPost1PipeSmem, st>>>(
@@ -1089,7 +1124,8 @@ static nlos_status step_alg1(JobRun& j) {
   }
   NLOS_LAUNCH_CHECK("k_post1");
   { KTimer kt_(P, KC_SMALL, st);
-  k_finalize<<<1, kSumThreads, 0, st>>>(s->sc, s->pc, post_blocks, 1, 0.0, j.restart, p.eps_stop);
+  k_finalize<<<1, kSumThreads, 0, st>>>(s->sc, s->pc, post_blocks, 1, 0.0, j.restart, p.eps_stop, s->pb, nbf_fold,
+                                        fold);
   }
   NLOS_LAUNCH_CHECK("k_finalize");
   swap_ptr(s->uk, s->unew);
@@ -1163,7 +1199,8 @@ static nlos_status step_alg2(JobRun& j) {
     }
     NLOS_LAUNCH_CHECK("k_post2");
     { KTimer kt_(P, KC_SMALL, st);
-    k_finalize<<<1, kSumThreads, 0, st>>>(s->sc, s->pc, stencil_blocks(P), 2, p.lambda, j.restart, p.eps_stop);
+    k_finalize<<<1, kSumThreads, 0, st>>>(s->sc, s->pc, stencil_blocks(P), 2, p.lambda, j.restart, p.eps_stop,
+                                          nullptr, 0, 0);
     }
     NLOS_LAUNCH_CHECK("k_finalize");
   }

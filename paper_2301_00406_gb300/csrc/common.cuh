@@ -81,6 +81,10 @@ struct DevScalars {
   double t;           // FISTA t_k
   double beta_prev;   // weight that formed the current u-bar (cached A u-bar)
   double beta;        // weight for the next extrapolation (set after the test)
+  double t_next, beta_next;  // what the next accepted test sets t and beta to ((1 + sqrt(1 + 4 t^2)) / 2 and
+                             // (t - 1) / t_next from the current t): set at the start and at the end of
+                             // every iteration, so the post stencil reads the extrapolation weight
+                             // without waiting for the test
   double E_prev;      // energy before this iteration
   double E, e;        // energy and relative change of the last iteration
   double f_fit;       // data term of the last accepted iterate

@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
   float* N = I + kPostI;
   const int iy = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const float inv_mu = 1.0f / mu;
-  const float beta = (float)sc->beta;
+  const float beta = (float)sc->beta_next;
   const float* ifields[5] = {lam, lam + V, lam + 2 * V, ph, uk};
   // 1 / (lambda M + mu3) for M = 1 and M = 0
   const float l3_d1 = L3 ? 1.0f / (l3.lam_w + l3.mu3) : 0.0f, l3_d0 = L3 ? 1.0f / l3.mu3 : 0.0f;
