@@ -46,6 +46,7 @@ nlos_status launch_tfwd_rz(const Plan& P, const float* u, int ncols, float2* S, 
   NLOS_DISPATCH_NT(P.nt, tfwd_rz(P, u, ncols, S, pitch, st));
 }
 nlos_status launch_tfwd_rtt(const Plan& P, const Lin3& r, int ncols, float2* S, int pitch, cudaStream_t st) {
+  if (tpass_warp_applies(P, ncols, pitch)) return launch_tfwd_rtt_warp(P, r, S, pitch, st);
   NLOS_DISPATCH_NT(P.nt, tfwd_rtt(P, r, ncols, S, pitch, st));
 }
 nlos_status launch_tinv_store(const Plan& P, const float2* S, int pitch, int ncols, float* out,
@@ -54,6 +55,7 @@ nlos_status launch_tinv_store(const Plan& P, const float2* S, int pitch, int nco
 }
 nlos_status launch_tinv_fit(const Plan& P, const float2* S, int pitch, int ncols, float* out, const FitArgs& fa,
                             int* nblocks, cudaStream_t st) {
+  if (tpass_warp_applies(P, ncols, pitch)) return launch_tinv_fit_warp(P, S, pitch, out, fa, nblocks, st);
   NLOS_DISPATCH_NT(P.nt, tinv_fit(P, S, pitch, ncols, out, fa, nblocks, st));
 }
 nlos_status launch_tadj_store(const Plan& P, const float2* S, int pitch, int ncols, float* out, cudaStream_t st) {
@@ -69,6 +71,7 @@ nlos_status launch_sfwd(const Plan& P, const float* x, int ncols, float2* Sp, cu
 }
 nlos_status launch_sinv(const Plan& P, const float2* Sp, int ncols, float* x, const float* ref, double* partials,
                         int* nblocks, cudaStream_t st) {
+  if (tpass_warp_applies(P, ncols, ncols)) return launch_sinv_warp(P, Sp, ncols, x, ref, partials, nblocks, st);
   NLOS_DISPATCH_NT(P.nt, sinv(P, Sp, ncols, x, ref, partials, nblocks, st));
 }
 nlos_status launch_sinv_rz(const Plan& P, const float2* Sp, int ncols, float* x, const float* ref,
@@ -226,7 +229,9 @@ nlos_status autotune_tpass(Plan& P, cudaStream_t st) {
       if (g_tp_cols.count(std::make_tuple(c.kind, nt, c.ncols))) continue;
     }
     // the warp-per-pair kernels have a fixed shape: nothing to tune
-    if ((c.kind == TPK_TADJ_SOLVE || c.kind == TPK_SINV_RZ) && tpass_warp_applies(P, c.ncols, c.ncols)) continue;
+    const bool warp_kind = c.kind == TPK_TADJ_SOLVE || c.kind == TPK_SINV_RZ || c.kind == TPK_SINV ||
+                           c.kind == TPK_TINV_FIT || c.kind == TPK_TFWD_RTT;
+    if (warp_kind && tpass_warp_applies(P, c.ncols, c.ncols)) continue;
     const bool halves = c.kind != TPK_SFWD && c.kind != TPK_SINV;  // sinv_rz: its forward half
     int best = 0;
     float best_ms = 0.f;

@@ -70,13 +70,20 @@ nlos_status launch_sinv_rz(const Plan& P, const float2* Sp, int ncols, float* x,
 // Full-grid tadj (solve mode) and sinv_rz passes with one warp per column
 // pair and TMA tile transfers (tpass_warp.cu), for nt in {128, 256, 512};
 // launch_tadj_solve and launch_sinv_rz dispatch to them when
-// tpass_warp_applies.
+// tpass_warp_applies (the column count and pitch are the full grid).
 bool tpass_warp_applies(const Plan& P, int ncols, int pitch);
 nlos_status prepare_tpass_warp(int nt);
 nlos_status launch_tadj_solve_warp(const Plan& P, const float2* S, int pitch, const SolveRhs& sr, float2* Sp,
                                    cudaStream_t st);
 nlos_status launch_sinv_rz_warp(const Plan& P, const float2* Sp, int pitch, float* x, const float* ref,
                                 double* partials, int* nblocks, float2* S, DevScalars* sc, cudaStream_t st);
+// ... and the full-grid sinv, tinv (fit) and tfwd (R_t^{-T}) passes, to which
+// launch_sinv, launch_tinv_fit and launch_tfwd_rtt dispatch likewise.
+nlos_status launch_sinv_warp(const Plan& P, const float2* Sp, int pitch, float* x, const float* ref,
+                             double* partials, int* nblocks, cudaStream_t st);
+nlos_status launch_tinv_fit_warp(const Plan& P, const float2* S, int pitch, float* out, const FitArgs& fa,
+                                 int* nblocks, cudaStream_t st);
+nlos_status launch_tfwd_rtt_warp(const Plan& P, const Lin3& r, float2* S, int pitch, cudaStream_t st);
 // Lateral 2-D zero-padded convolution of each kt plane with H (adj: conj H).
 // in_cols/out_cols: nullptr = full plane [nx][ny]; else compact column lists
 // (the plan's sampled columns) with plane pitch ncols.
