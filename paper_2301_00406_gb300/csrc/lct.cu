@@ -55,7 +55,7 @@ nlos_status launch_tinv_store(const Plan& P, const float2* S, int pitch, int nco
 }
 nlos_status launch_tinv_fit(const Plan& P, const float2* S, int pitch, int ncols, float* out, const FitArgs& fa,
                             int* nblocks, cudaStream_t st) {
-  if (tpass_warp_applies(P, ncols, pitch)) return launch_tinv_fit_warp(P, S, pitch, out, fa, nblocks, st);
+  if (tpass_warp_applies_cols(P, ncols, pitch)) return launch_tinv_fit_warp(P, S, pitch, out, fa, nblocks, st);
   NLOS_DISPATCH_NT(P.nt, tinv_fit(P, S, pitch, ncols, out, fa, nblocks, st));
 }
 nlos_status launch_tadj_store(const Plan& P, const float2* S, int pitch, int ncols, float* out, cudaStream_t st) {
@@ -231,7 +231,10 @@ nlos_status autotune_tpass(Plan& P, cudaStream_t st) {
     // the warp-per-pair kernels have a fixed shape: nothing to tune
     const bool warp_kind = c.kind == TPK_TADJ_SOLVE || c.kind == TPK_SINV_RZ || c.kind == TPK_SINV ||
                            c.kind == TPK_TINV_FIT || c.kind == TPK_TFWD_RTT;
-    if (warp_kind && tpass_warp_applies(P, c.ncols, c.ncols)) continue;
+    const bool compact_kind = c.kind == TPK_TINV_FIT;
+    if (warp_kind && (compact_kind ? tpass_warp_applies_cols(P, c.ncols, c.ncols)
+                                   : tpass_warp_applies(P, c.ncols, c.ncols)))
+      continue;
     const bool halves = c.kind != TPK_SFWD && c.kind != TPK_SINV;  // sinv_rz: its forward half
     int best = 0;
     float best_ms = 0.f;

@@ -72,6 +72,9 @@ nlos_status launch_sinv_rz(const Plan& P, const float2* Sp, int ncols, float* x,
 // launch_tadj_solve and launch_sinv_rz dispatch to them when
 // tpass_warp_applies (the column count and pitch are the full grid).
 bool tpass_warp_applies(const Plan& P, int ncols, int pitch);
+// The fit pass also runs on compact columns (the sampled columns of A_D)
+// when their count is a multiple of 16.
+bool tpass_warp_applies_cols(const Plan& P, int ncols, int pitch);
 nlos_status prepare_tpass_warp(int nt);
 nlos_status launch_tadj_solve_warp(const Plan& P, const float2* S, int pitch, const SolveRhs& sr, float2* Sp,
                                    cudaStream_t st);

@@ -837,6 +837,10 @@ bool tpass_warp_applies(const Plan& P, int ncols, int pitch) {
          ncols % kWarpCols == 0;
 }
 
+bool tpass_warp_applies_cols(const Plan& P, int ncols, int pitch) {
+  return (P.nt == 128 || P.nt == 256 || P.nt == 512) && pitch == ncols && ncols % kWarpCols == 0;
+}
+
 nlos_status prepare_tpass_warp(int nt) {
   switch (nt) {
     case 128: return prepare_w<4>();
