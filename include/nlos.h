@@ -393,6 +393,19 @@ nlos_status nlos_midpoint_confocal(int32_t nx, int32_t ny, int32_t nt, double bi
                                    double laser_x_m, double laser_y_m, const float* tau_nc_dev, float* tau_c_dev,
                                    void* stream);
 
+/* Self-test of the bounded waits (failure detection without a GPU fault).
+ * The kernels that wait on an mbarrier (the TMA tile loads of the t-passes,
+ * the tensor-core lateral stage) give up after a time limit, record
+ * NLOS_ERR_TIMEOUT and run to their end, so the context stays usable.  This
+ * launches one CTA on `stream` that waits with the same code on an mbarrier
+ * whose expected bytes no copy delivers; the wait gives up after wait_ms
+ * milliseconds (1 to 5000) and the kernel writes NLOS_ERR_TIMEOUT to
+ * *status_dev (a device int32 the caller owns; NLOS_OK had the wait
+ * completed).  Queued on `stream`, no host synchronisation.  Errors: wait_ms
+ * out of range or a null pointer (NLOS_ERR_INVALID_ARG), CUDA
+ * (NLOS_ERR_CUDA). */
+nlos_status nlos_selftest_wait_timeout(int32_t wait_ms, int32_t* status_dev, void* stream);
+
 /* Per-launch timing of a plan's kernels, for profiling.  When enabled, every
  * kernel the plan launches is bracketed by a pair of CUDA events recorded on
  * its launch stream.  nlos_timing_read synchronises the device, returns per

@@ -87,6 +87,8 @@ nlos_status launch_sinv_warp(const Plan& P, const float2* Sp, int pitch, float* 
 nlos_status launch_tinv_fit_warp(const Plan& P, const float2* S, int pitch, float* out, const FitArgs& fa,
                                  int* nblocks, cudaStream_t st);
 nlos_status launch_tfwd_rtt_warp(const Plan& P, const Lin3& r, float2* S, int pitch, cudaStream_t st);
+// nlos_selftest_wait_timeout (tpass_warp.cu).
+nlos_status selftest_wait_timeout(int32_t wait_ms, int32_t* status_dev, cudaStream_t st);
 // Lateral 2-D zero-padded convolution of each kt plane with H (adj: conj H).
 // in_cols/out_cols: nullptr = full plane [nx][ny]; else compact column lists
 // (the plan's sampled columns) with plane pitch ncols.

@@ -720,6 +720,10 @@ nlos_status nlos_reconstruct_prepare(nlos_plan plan, const nlos_params* params, 
   })
 }
 
+nlos_status nlos_selftest_wait_timeout(int32_t wait_ms, int32_t* status_dev, void* stream) {
+  return selftest_wait_timeout(wait_ms, status_dev, reinterpret_cast<cudaStream_t>(stream));
+}
+
 nlos_status nlos_timing_enable(nlos_plan plan, int32_t enable) {
   API_GUARD({
     if (!plan) return fail(NLOS_ERR_INVALID_ARG, "null plan");

@@ -44,11 +44,12 @@ __device__ __forceinline__ uint64_t tma_global_ns() {
   return t;
 }
 
-// Waits for the phase of `bar` with the given parity, for at most one second.
-// On giving up: *fail = 1 and, if status is given, *status = NLOS_ERR_TIMEOUT
-// (when it still holds NLOS_OK).  Returns immediately once *fail is set.
+// Waits for the phase of `bar` with the given parity, for at most limit_ns
+// (one second by default).  On giving up: *fail = 1 and, if status is given,
+// *status = NLOS_ERR_TIMEOUT (when it still holds NLOS_OK).  Returns
+// immediately once *fail is set.
 __device__ __forceinline__ void mbar_wait_bounded(uint32_t bar, uint32_t parity, volatile int* fail,
-                                                  int32_t* status) {
+                                                  int32_t* status, uint64_t limit_ns = 1000000000ull) {
   if (*fail) return;
   const uint64_t t0 = tma_global_ns();
   for (;;) {
@@ -59,7 +60,7 @@ __device__ __forceinline__ void mbar_wait_bounded(uint32_t bar, uint32_t parity,
         : "r"(bar), "r"(parity)
         : "memory");
     if (done) return;
-    if (tma_global_ns() - t0 > 1000000000ull) {
+    if (tma_global_ns() - t0 > limit_ns) {
       *fail = 1;
       if (status) atomicCAS(reinterpret_cast<int*>(status), NLOS_OK, NLOS_ERR_TIMEOUT);
       return;

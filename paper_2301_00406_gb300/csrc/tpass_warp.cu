@@ -697,6 +697,24 @@ __global__ void __launch_bounds__(kWarpThreads, 2)
   tile_store_wait();
 }
 
+// Self-test of the bounded wait: an mbarrier that expects 128 transaction
+// bytes which no copy delivers (nothing is issued, so nothing is in flight
+// when the CTA exits); the wait gives up after limit_ns and records
+// NLOS_ERR_TIMEOUT.
+__global__ void k_wait_selftest(uint64_t limit_ns, int32_t* status) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int fail;
+  const uint32_t b = smem_u32(&bar);
+  if (threadIdx.x == 0) {
+    fail = 0;
+    *status = NLOS_OK;
+    mbar_init(b, 1);
+    mbar_expect_tx(b, 128);
+  }
+  __syncthreads();
+  mbar_wait_bounded(b, 0, &fail, status, limit_ns);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -897,6 +915,14 @@ nlos_status launch_tfwd_rtt_warp(const Plan& P, const Lin3& r, float2* S, int pi
     case 512: return tfwd_rtt_w<16>(P, r, S, pitch, st);
   }
   return fail(NLOS_ERR_INVALID_ARG, "warp t-pass: unsupported nt");
+}
+
+nlos_status selftest_wait_timeout(int32_t wait_ms, int32_t* status_dev, cudaStream_t st) {
+  if (wait_ms < 1 || wait_ms > 5000 || !status_dev)
+    return fail(NLOS_ERR_INVALID_ARG, "nlos_selftest_wait_timeout: wait_ms in [1, 5000] and a status pointer");
+  k_wait_selftest<<<1, 32, 0, st>>>((uint64_t)wait_ms * 1000000ull, status_dev);
+  NLOS_LAUNCH_CHECK("k_wait_selftest");
+  return NLOS_OK;
 }
 
 }  // namespace nlos

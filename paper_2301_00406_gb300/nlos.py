@@ -103,6 +103,7 @@ _SIGS = {
     "nlos_server_destroy": (ctypes.c_int32, [_P, ctypes.c_int32, ctypes.c_double]),
     "nlos_midpoint_confocal": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                                 ctypes.c_double, ctypes.c_double, ctypes.c_double, _P, _P, _P]),
+    "nlos_selftest_wait_timeout": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "nlos_timing_enable": (ctypes.c_int32, [_P, ctypes.c_int32]),
     "nlos_plan_set_lateral": (ctypes.c_int32, [_P, ctypes.c_int32, _P]),
     "nlos_timing_read": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32]),
@@ -416,3 +417,10 @@ def reconstruct_t(plan, params, tau0, want_tau=False):
     stats = plan.reconstruct(params, tau0.data_ptr(), u.data_ptr(), tau.data_ptr() if tau is not None else 0,
                              _stream())
     return (u, tau, stats) if want_tau else (u, stats)
+
+
+def selftest_wait_timeout(wait_ms, status_t):
+    """Queue the bounded-wait self-test on torch's current stream; the kernel
+    writes its status (NLOS_ERR_TIMEOUT when the wait gave up) to the int32
+    CUDA tensor ``status_t``."""
+    check(load().nlos_selftest_wait_timeout(int(wait_ms), ctypes.c_void_p(status_t.data_ptr()), _stream()))
