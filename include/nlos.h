@@ -151,7 +151,7 @@ nlos_status nlos_params_default(int32_t model, nlos_params* out);
  * plan's own buffers and keeps the fastest; the choices are also written to
  * a tuning file ($NLOS_TUNE_CACHE, else $XDG_CACHE_HOME/nlos-gb300/
  * tpass_tuning, else $HOME/.cache/nlos-gb300/tpass_tuning; NLOS_TUNE_CACHE=off
- * disables it), keyed by device name, SM count and library build, from which
+ * disables it), keyed by device name, SM count and the library's compile time, from which
  * later processes read them instead of timing again. */
 nlos_status nlos_plan_create(const nlos_geometry* geom, void* stream, nlos_plan* out);
 

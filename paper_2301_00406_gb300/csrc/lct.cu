@@ -95,7 +95,7 @@ thread_local int g_tp_force = 0;                       // candidate under test (
 bool g_tp_loaded = false;                              // tuning file read (under g_tp_mu)
 
 // Tuning file: the tuner's choices persist across processes, keyed by the
-// device name, its SM count and this build of the library (a choice made for
+// device name, its SM count and the compile time of the library (a choice made for
 // other kernels or another GPU is never reused).  Path: $NLOS_TUNE_CACHE, or
 // $XDG_CACHE_HOME/nlos-gb300/tpass_tuning, or $HOME/.cache/nlos-gb300/
 // tpass_tuning; NLOS_TUNE_CACHE=off (or empty) keeps the choices in the

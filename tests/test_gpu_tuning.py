@@ -1,7 +1,7 @@
 """The t-pass launch-shape tuning persists across processes: the first plan
 of a geometry writes its choices to the tuning file (NLOS_TUNE_CACHE), a
 later process reads them instead of timing again (so it writes nothing), and
-a file made under another key (device, SM count, build) is ignored and
+a file made under another key (device, SM count, compile time) is ignored and
 replaced."""
 
 import os
