@@ -64,10 +64,14 @@ struct C4 {
 
 // Row swizzle of the plane: element (x, k) lives at x M + (k ^ swz(x)), swz
 // linear over GF(2) in the bits of x.  The coefficients make every access
-// pattern of the three phases hit distinct banks.
+// pattern of the three phases hit distinct banks, at N = 128 also those that
+// visit only the rows x = 4 v + r0 of a stride-4 lattice (the y transforms
+// four lattice rows per warp step, the lattice x passes eight rows 4 apart
+// times two columns 8 apart): bits 2-4, which alone vary there, map to
+// independent slot offsets (a bank model of every pattern chose them).
 template <int N>
 __host__ __device__ constexpr int swc(int bit) {
-  return N == 128 ? (bit == 0 ? 8 : bit == 1 ? 1 : bit == 2 ? 2 : bit == 6 ? 4 : 0)
+  return N == 128 ? (bit == 0 ? 8 : bit == 1 ? 1 : bit == 2 ? 14 : bit == 3 ? 15 : bit == 4 ? 13 : bit == 5 ? 8 : bit == 6 ? 4 : 0)
          : N == 64 ? (bit == 0 ? 8 : bit == 1 ? 15 : bit == 2 ? 10 : bit == 3 ? 8 : bit == 4 ? 3 : bit == 5 ? 14 : 0)
                    : (bit == 0 ? 8 : bit == 1 ? 3 : bit == 2 ? 12 : bit == 3 ? 11 : bit == 4 ? 15 : 0);
 }
