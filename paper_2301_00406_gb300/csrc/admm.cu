@@ -510,6 +510,9 @@ struct SolverState {
   int model = 0;
   size_t V = 0;
   float *uk = nullptr, *unew = nullptr, *ub = nullptr, *ubn = nullptr, *lam = nullptr, *ph = nullptr, *reg = nullptr;
+  // Algorithm 1 with the fused post and pre step: Lambda and phi of the next
+  // iteration (swapped with lam and ph after every iteration)
+  float *lamn = nullptr, *phn = nullptr;
   float *tk = nullptr, *tnew = nullptr, *tb = nullptr, *tbn = nullptr, *lam2 = nullptr, *lam3 = nullptr,
         *pht = nullptr, *regt = nullptr, *tmp = nullptr;
   float* tau0c = nullptr;
@@ -557,6 +560,7 @@ static nlos_status get_solver(Plan& P, int model, SolverState** out) {
   for (int i = 0; i < 3; ++i) A(&s->cache[i], cachesz);
   if (model == 1) {
     A(&s->tau0c, (size_t)P.ncols * P.nt * sizeof(float));
+    A(&s->lamn, 3 * F); A(&s->phn, F);
   } else {
     A(&s->tk, F); A(&s->tnew, F); A(&s->tb, F); A(&s->tbn, F); A(&s->lam2, 3 * F); A(&s->lam3, F);
     A(&s->pht, F); A(&s->regt, F); A(&s->tmp, F);
@@ -743,6 +747,31 @@ nlos_status prepare_stencils() {
   NLOS_TRY(ensure_smem(k_pre1_pipe<true>, kPre1PipeSmem));
   NLOS_TRY(ensure_smem(k_post1_pipe<false>, kPost1PipeSmem));
   NLOS_TRY(ensure_smem(k_post1_pipe<true>, kPost1PipeSmem));
+  NLOS_TRY(ensure_smem(k_post1_pre, kPostPreSmem));
+  return NLOS_OK;
+}
+
+// The pipelined halo-tiled stencils apply when the grid tiles evenly (TT =
+// 128 along t, TY = 8 rows in y); the plain per-voxel kernels otherwise.
+// Tiled Algorithm-1 runs fuse each iteration's post step with the next
+// iteration's pre step (k_post1_pre), so only the run's start launches the
+// pre step by itself.
+static bool stencils_tiled(const Plan& P) { return P.nt % kTT == 0 && P.ny % kTY == 0; }
+
+// reg = -mu div (v + Lambda/mu), v = shrink(grad u-bar - Lambda/mu, phi/mu)
+// (Algorithm 1's pre step) on stream st.
+static nlos_status pre1(Plan& P, SolverState* s, const nlos_params& p, cudaStream_t st) {
+  const Vox g = make_vox(P.nx, P.ny, P.nt);
+  KTimer kt_(P, KC_PRE, st);
+  if (stencils_tiled(P)) {
+    const int ntiles = stencil_steps(g);
+    k_pre1_pipe<false><<<std::min(ntiles, P.sms * 3), kTileThreads, kPre1PipeSmem, st>>>(
+        s->ub, s->lam, s->ph, s->reg, g, ntiles, (float)p.mu, s->V, FTerm{});
+  } else {
+    const VoxIter vi{ilog2i(P.nt), ilog2i(P.ny)};
+    k_pre1<<<stencil_blocks(P), kStencilThreads, 0, st>>>(s->ub, s->lam, s->ph, s->reg, g, vi, (float)p.mu, s->V);
+  }
+  NLOS_LAUNCH_CHECK("k_pre1");
   return NLOS_OK;
 }
 
@@ -1007,6 +1036,9 @@ static nlos_status init_run(JobRun& j, const float* u_init) {
       NLOS_TRY(fill(s->ph, phi_zero(p.a, p.b, p.phi), V, st));
       NLOS_TRY(init_scalars(P, s, j.L0, s->tau0c, C, 0.5, st));
     }
+    // the first iteration's right-hand side term (later ones come from the
+    // fused post and pre step)
+    if (stencils_tiled(P)) NLOS_TRY(pre1(P, s, p, st));
   } else {
     for (float* f : {s->tk, s->tb, s->lam3}) NLOS_TRY(zero(f, V, st));
     NLOS_TRY(zero(s->lam, 3 * V, st));
@@ -1077,36 +1109,30 @@ static nlos_status step_alg1(JobRun& j) {
   const Vox g = make_vox(P.nx, P.ny, P.nt);
   const VoxIter vi{ilog2i(P.nt), ilog2i(P.ny)};
   const float eps2 = (float)(p.eps_normal * p.eps_normal);
-  // pipelined halo-tiled stencils when the grid tiles evenly (TT = 128 along
-  // t, 8 rows in y, 4 planes in x); the plain per-voxel kernels otherwise
-  const bool tiled = P.nt % kTT == 0 && P.ny % kTY == 0;
+  const bool tiled = stencils_tiled(P);
   const int ntiles = tiled ? stencil_steps(g) : 0;  // (tile, x plane) steps
-  const int pre_grid = std::min(ntiles, P.sms * 3), post_grid = std::min(ntiles, P.sms * 2);
+  const int post_grid = std::min(ntiles, P.sms * 2);
   const int post_blocks = tiled ? post_grid : stencil_blocks(P);
-  // The pre stencil (reads u-bar, Lambda, phi; writes reg) and the start of
-  // A_D^T (reads the cached A u, tau0 and beta; writes the spectrum scratch)
-  // are independent: in a captured graph the pre stencil is a parallel
-  // branch (HBM-bound, next to the ALU-bound lateral pass), joined before the
-  // u-step reads reg.
-  cudaStream_t pst = st;
-  if (j.aux) {
-    NLOS_CUDA(cudaEventRecord(j.ev_fork, st));
-    NLOS_CUDA(cudaStreamWaitEvent(j.aux, j.ev_fork, 0));
-    pst = j.aux;
+  // Untiled grids: the pre stencil (reads u-bar, Lambda, phi; writes reg) and
+  // the start of A_D^T (reads the cached A u, tau0 and beta; writes the
+  // spectrum scratch) are independent, so in a captured graph the pre
+  // stencil is a parallel branch, joined before the u-step reads reg.  Tiled
+  // grids have reg from the previous iteration's fused post and pre step.
+  const bool fork = !tiled && j.aux;
+  if (!tiled) {
+    cudaStream_t pst = st;
+    if (fork) {
+      NLOS_CUDA(cudaEventRecord(j.ev_fork, st));
+      NLOS_CUDA(cudaStreamWaitEvent(j.aux, j.ev_fork, 0));
+      pst = j.aux;
+    }
+    NLOS_TRY(pre1(P, s, p, pst));
+    if (fork) NLOS_CUDA(cudaEventRecord(j.ev_join, pst));
   }
-  { KTimer kt_(P, KC_PRE, pst);
-  if (tiled)
-    k_pre1_pipe<false><<<pre_grid, kTileThreads, kPre1PipeSmem, pst>>>(s->ub, s->lam, s->ph, s->reg, g, ntiles,
-                                                                       (float)p.mu, V, FTerm{});
-  else
-    k_pre1<<<stencil_blocks(P), kStencilThreads, 0, pst>>>(s->ub, s->lam, s->ph, s->reg, g, vi, (float)p.mu, V);
-  }
-  NLOS_LAUNCH_CHECK("k_pre1");
-  if (j.aux) NLOS_CUDA(cudaEventRecord(j.ev_join, pst));
   Lin3 r{{s->cache[j.cur], s->cache[j.prev], s->tau0c}, {0.f, 0.f, 0.f}, s->sc};
   NLOS_TRY(launch_tfwd_rtt(P, r, P.ncols, P.d_Sc, P.ncols, st));
   NLOS_TRY(launch_conv(P, P.d_Sc, true, P.d_S, false, true, st));
-  if (j.aux) NLOS_CUDA(cudaStreamWaitEvent(st, j.ev_join, 0));
+  if (fork) NLOS_CUDA(cudaStreamWaitEvent(st, j.ev_join, 0));
   const bool host_check = j.L_host < 1.5 * j.norm2;
   UStepArgs ua{s->reg, p.mu, true, s->tau0c, p.eta, p.max_backtracks, s->cache[j.nxt], s->cache[j.cur],
                s->cache[j.prev]};
@@ -1115,9 +1141,9 @@ static nlos_status step_alg1(JobRun& j) {
   const int fold = host_check ? 0 : 1;
   { KTimer kt_(P, KC_POST, st);
   if (tiled)
-    k_post1_pipe<false><<<post_grid, kTileThreads, kPost1PipeSmem, st>>>(
-        s->unew, s->uk, s->ub, s->lam, s->ph, s->ubn, s->sc, g, ntiles, (float)p.mu, (float)p.a, (float)p.b, p.phi,
-        eps2, V, s->pc, L3Term{});
+    k_post1_pre<<<post_grid, kTileThreads, kPostPreSmem, st>>>(s->unew, s->uk, s->ub, s->lam, s->ph, s->lamn, s->phn,
+                                                              s->ubn, s->reg, s->sc, g, ntiles, (float)p.mu,
+                                                              (float)p.a, (float)p.b, p.phi, eps2, V, s->pc);
   else
     k_post1<<<stencil_blocks(P), kStencilThreads, 0, st>>>(s->unew, s->uk, s->ub, s->lam, s->ph, s->ubn, s->sc, g, vi,
                                                         (float)p.mu, (float)p.a, (float)p.b, p.phi, eps2, V, s->pc);
@@ -1130,6 +1156,10 @@ static nlos_status step_alg1(JobRun& j) {
   NLOS_LAUNCH_CHECK("k_finalize");
   swap_ptr(s->uk, s->unew);
   swap_ptr(s->ub, s->ubn);
+  if (tiled) {
+    swap_ptr(s->lam, s->lamn);
+    swap_ptr(s->ph, s->phn);
+  }
   return NLOS_OK;
 }
 
@@ -1292,8 +1322,8 @@ static nlos_status capture_looped(JobRun& c, cudaStream_t* bs) {
   const float* t1 = s->tnew;
   const JobRun start = c;
   auto phase_ptrs = [s]() {
-    return std::array<const float*, 11>{s->uk, s->unew, s->ub, s->ubn, s->tk, s->tnew, s->tb, s->tbn,
-                                        s->cache[0], s->cache[1], s->cache[2]};
+    return std::array<const float*, 13>{s->uk, s->unew, s->ub, s->ubn, s->tk, s->tnew, s->tb, s->tbn,
+                                        s->cache[0], s->cache[1], s->cache[2], s->lam, s->ph};
   };
   const auto ptrs_start = phase_ptrs();
   cudaGraphConditionalHandle cont = 0;

@@ -284,7 +284,7 @@ size_t workspace_bytes(const Plan& P, int model) {
                                (size_t)(P.nt / 2 + 1) * full) +
              C + sizeof(double) * 4096 * kMaxTerms + 4096;
   const size_t partials = 3 * sizeof(double) * kMaxTerms * 4096;
-  if (model == 1 || model == 3) b += 9 * F + 4 * C + partials;
+  if (model == 1 || model == 3) b += 13 * F + 4 * C + partials;
   if (model == 2 || model == 3) b += 21 * F + partials;
   return b;
 }

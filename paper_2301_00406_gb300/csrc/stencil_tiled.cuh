@@ -41,6 +41,10 @@ __device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
 }
+__device__ __forceinline__ void cp_async8(float* smem, const float* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+}
 __device__ __forceinline__ void cp_async16(float* smem, const float* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
@@ -372,6 +376,272 @@ __global__ void __launch_bounds__(kTileThreads, 3)
     }
     cp_async_wait_all();
   }
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1's post step fused with the next iteration's pre step.
+//
+// The post step of iteration k (Lambda, phi and u-bar of iteration k + 1,
+// Eq. 12 and the extrapolation) and the pre step of iteration k + 1 (the
+// right-hand side reg = -mu div q, q = v' + Lambda_{k+1}/mu with v' =
+// shrink(grad u-bar_{k+1} - Lambda_{k+1}/mu, phi_{k+1}/mu), Eq. 7 and the
+// PDE above Eq. 11) read the same neighbourhoods, so one pass forms q from
+// the values it has just computed instead of storing them and reading them
+// back in a second launch.  The backward divergence needs q at the tile's
+// voxels and at its -1 halo: the row above the tile and the column before it
+// (the plane before is the previous step of the march).  A halo voxel's q
+// needs Lambda and phi there in their state before this step, while the
+// block that owns the voxel writes the new values: Lambda and phi are
+// therefore read from one pair of buffers and written to another (the caller
+// swaps them after every iteration).
+//
+// Shared layout (floats):
+//   U [3][TY+3][kP]     u+ planes, rows y0 - 2 .. y0 + TY, t0 - 2 .. t0 + TT
+//   B [3][TY+2][kP]     u-bar planes, rows y0 - 1 .. y0 + TY, t0 - 1 .. t0 + TT
+//   K [3][TY+2][kP]     u^k planes, same extent as B
+//   N [3][TY+2][TT+2]   normal field of u+, rows y0 - 2 .., t0 - 2 ..
+//   Q [3][TY+1][TT+1]   q, rows y0 - 1 .., t0 - 1 ..
+//   H [kFusHalo]        n_x of u+ on the plane before, at the halo voxels of Q
+constexpr int kFusUH = kTY + 3, kFusNH = kTY + 2, kFusNW = kTT + 2;
+constexpr int kFusHalo = kRW + kTY;  // halo voxels of Q: its first row, then its first column below it
+static_assert(kFusHalo <= kTileThreads, "one halo voxel per thread");
+constexpr int kFusU = 3 * kFusUH * kP, kFusB = 3 * kUH * kP, kFusN = 3 * kFusNH * kFusNW, kFusQ = 3 * kRH * kRW;
+static_assert(kFusU % 4 == 0 && kFusB % 4 == 0, "staging regions must keep 16-byte alignment");
+constexpr size_t kPostPreSmem = sizeof(float) * (kFusU + 2 * kFusB + kFusN + kFusQ + ((kFusHalo + 3) & ~3));
+
+// Stage rows y0 - 2 + r (r < H, periodic) of plane x: columns t0 .. t0 + TT -
+// 1 at kC .., t0 - 2 and t0 - 1 at kC - 2 (one 8-byte copy: t0 - 2 is even,
+// so the pair is aligned and never straddles the wrap), t0 + TT at kC + TT.
+__device__ __forceinline__ void stage_rows_lo2_async(float* __restrict__ tile, int H, const float* __restrict__ f,
+                                                     const Vox& g, int x, int y0, int t0) {
+  constexpr int Q = kTT / 4;
+  for (int i = threadIdx.x; i < H * Q; i += kTileThreads) {
+    const int r = i / Q, q = i - r * Q;
+    const int y = (y0 - 2 + r) & g.my;
+    cp_async16(tile + r * kP + kC + 4 * q, f + g.idx(x, y, t0 + 4 * q));
+  }
+  for (int i = threadIdx.x; i < 2 * H; i += kTileThreads) {
+    const int r = i >> 1;
+    const int y = (y0 - 2 + r) & g.my;
+    if (i & 1)
+      cp_async4(tile + r * kP + kC + kTT, f + g.idx(x, y, (t0 + kTT) & g.mt));
+    else
+      cp_async8(tile + r * kP + kC - 2, f + g.idx(x, y, (t0 - 2) & g.mt));
+  }
+}
+
+// One voxel c of the fused step.  u, b, k: u+, u-bar and u^k at c, c + e_x,
+// c + e_y, c + e_t; l, ph: Lambda and phi at c before the step; kap:
+// kappa(u+) at c.
+struct FusedPoint {
+  float3 lam;  // Lambda_{k+1} = Lambda + mu (v - grad u+)
+  float phi;   // phi(kappa(u+))
+  float ubn;   // u-bar_{k+1} = u+ + beta (u+ - u^k)
+  float3 q;    // v' + Lambda_{k+1} / mu
+  float gn;    // |grad u+|
+  float d2;    // |v - grad u+|^2
+};
+__device__ __forceinline__ FusedPoint fused_point(float4 u, float4 b, float4 k, float3 l, float ph, float kap,
+                                                  float mu, float inv_mu, float beta, float pa, float pb, int kind) {
+  FusedPoint o;
+  const float3 gu = make_float3(u.y - u.x, u.z - u.x, u.w - u.x);
+  const float3 av = make_float3(b.y - b.x - l.x * inv_mu, b.z - b.x - l.y * inv_mu, b.w - b.x - l.z * inv_mu);
+  const float3 v = shrink3(av, ph * inv_mu);
+  const float3 d = make_float3(v.x - gu.x, v.y - gu.y, v.z - gu.z);
+  o.lam = make_float3(l.x + mu * d.x, l.y + mu * d.y, l.z + mu * d.z);
+  o.phi = phi_of(kap, pa, pb, kind);
+  const float n0 = u.x + beta * (u.x - k.x), n1 = u.y + beta * (u.y - k.y), n2 = u.z + beta * (u.z - k.z),
+              n3 = u.w + beta * (u.w - k.w);
+  o.ubn = n0;
+  const float3 an = make_float3(n1 - n0 - o.lam.x * inv_mu, n2 - n0 - o.lam.y * inv_mu, n3 - n0 - o.lam.z * inv_mu);
+  const float3 vn = shrink3(an, o.phi * inv_mu);
+  o.q = make_float3(vn.x + o.lam.x * inv_mu, vn.y + o.lam.y * inv_mu, vn.z + o.lam.z * inv_mu);
+  o.gn = sqrtf(gu.x * gu.x + gu.y * gu.y + gu.z * gu.z);
+  o.d2 = d.x * d.x + d.y * d.y + d.z * d.z;
+  return o;
+}
+
+// f at c, c + e_x, c + e_y, c + e_t from global memory (periodic).
+__device__ __forceinline__ float4 fwd4(const float* __restrict__ f, const Vox& g, int x, int y, int t) {
+  return make_float4(__ldg(f + g.idx(x, y, t)), __ldg(f + g.idx((x + 1) & g.mx, y, t)),
+                     __ldg(f + g.idx(x, (y + 1) & g.my, t)), __ldg(f + g.idx(x, y, (t + 1) & g.mt)));
+}
+
+// q_x of the fused step at one voxel, every input from global memory (the
+// plane before a run's first plane).
+__device__ __forceinline__ float fused_qx_at(const float* __restrict__ unew, const float* __restrict__ uk,
+                                             const float* __restrict__ ub, const float* __restrict__ lam,
+                                             const float* __restrict__ ph, const Vox& g, size_t V, int x, int y,
+                                             int t, float mu, float inv_mu, float beta, float pa, float pb, int kind,
+                                             float eps2) {
+  const int i = g.idx(x, y, t);
+  const float3 l = make_float3(__ldg(lam + i), __ldg(lam + V + i), __ldg(lam + 2 * V + i));
+  const float kap = curvature_at(unew, g, x, y, t, eps2, nullptr);
+  return fused_point(fwd4(unew, g, x, y, t), fwd4(ub, g, x, y, t), fwd4(uk, g, x, y, t), l, __ldg(ph + i), kap, mu,
+                     inv_mu, beta, pa, pb, kind)
+      .q.x;
+}
+
+// lamo = Lambda_{k+1}, pho = phi(kappa(u+)), ubn = u-bar_{k+1} (as k_post1_pipe)
+// and reg = -mu div q for the next iteration (as k_pre1_pipe on those
+// outputs); lam, ph: Lambda and phi before the step (not written).
+// Partials 0 = sum phi |grad u+|, 1 = sum |v - grad u+|^2.
+__global__ void __launch_bounds__(kTileThreads, 2)
+    k_post1_pre(const float* __restrict__ unew, const float* __restrict__ uk, const float* __restrict__ ub,
+                const float* __restrict__ lam, const float* __restrict__ ph, float* __restrict__ lamo,
+                float* __restrict__ pho, float* __restrict__ ubn, float* __restrict__ reg,
+                const DevScalars* __restrict__ sc, Vox g, int nsteps, float mu, float pa, float pb, int kind,
+                float eps2, size_t V, double* __restrict__ partials) {
+  extern __shared__ float4 smem_f4[];
+  float* U = reinterpret_cast<float*>(smem_f4);
+  float* B = U + kFusU;
+  float* K = B + kFusB;
+  float* N = K + kFusB;
+  float* Q = N + kFusN;
+  float* H = Q + kFusQ;
+  constexpr int SN = kFusNH * kFusNW, SQ = kRH * kRW;
+  constexpr int SU = kFusUH * kP, SB = kUH * kP;
+  const int iy = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float inv_mu = 1.0f / mu;
+  const float beta = (float)sc->beta_next;
+  // this thread's halo voxel of Q (threads < kFusHalo): Q row hy, column ht
+  const int h = threadIdx.x;
+  const bool has_halo = h < kFusHalo;
+  const int hy = h < kRW ? 0 : h - kRW + 1, ht = h < kRW ? h : 0;
+  SumAcc<2> ca;
+  int cur, end;
+  block_share(nsteps, cur, end);
+  while (cur < end) {
+    const TileRun T = run_at(cur, end, g);
+    cur += T.cnt;
+    const int y = T.y0 + iy;
+    const int hyv = (T.y0 - 1 + hy) & g.my, htv = (T.t0 - 1 + ht) & g.mt;
+    // the plane before the run: n_x of u+ at the own and halo voxels, q_x at
+    // the own voxels
+    const int xm = (T.x0 - 1) & g.mx;
+    float nx_prev[4], qx_prev[4];
+    for (int j = 0; j < 4; ++j) {
+      const int t = T.t0 + lane + 32 * j;
+      nx_prev[j] = normal_of(grad_at(unew, g, xm, y, t), eps2).x;
+      qx_prev[j] = fused_qx_at(unew, uk, ub, lam, ph, g, V, xm, y, t, mu, inv_mu, beta, pa, pb, kind, eps2);
+    }
+    if (has_halo) H[h] = normal_of(grad_at(unew, g, xm, hyv, htv), eps2).x;
+    // prologue: planes x0 (group 0) and x0 + 1 (group 1)
+    stage_rows_lo2_async(U, kFusUH, unew, g, T.x0, T.y0, T.t0);
+    stage_rows_async<true, true>(B, kUH, ub, g, T.x0, T.y0, -1, T.t0);
+    stage_rows_async<true, true>(K, kUH, uk, g, T.x0, T.y0, -1, T.t0);
+    cp_async_commit();
+    stage_rows_lo2_async(U + SU, kFusUH, unew, g, (T.x0 + 1) & g.mx, T.y0, T.t0);
+    stage_rows_async<true, true>(B + SB, kUH, ub, g, (T.x0 + 1) & g.mx, T.y0, -1, T.t0);
+    stage_rows_async<true, true>(K + SB, kUH, uk, g, (T.x0 + 1) & g.mx, T.y0, -1, T.t0);
+    cp_async_commit();
+    for (int s = 0; s < T.cnt; ++s) {
+      const int x = T.x0 + s;
+      if (s + 1 < T.cnt) {
+        const int xn = (x + 2) & g.mx, sl = (s + 2) % 3;
+        stage_rows_lo2_async(U + sl * SU, kFusUH, unew, g, xn, T.y0, T.t0);
+        stage_rows_async<true, true>(B + sl * SB, kUH, ub, g, xn, T.y0, -1, T.t0);
+        stage_rows_async<true, true>(K + sl * SB, kUH, uk, g, xn, T.y0, -1, T.t0);
+      }
+      cp_async_commit();
+      // Lambda and phi before the step at the own and halo voxels, loaded
+      // now so that their latency overlaps the normal pass
+      float3 lj[4];
+      float pj[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const size_t gi = g.idx(x, y, T.t0 + lane + 32 * j);
+        lj[j] = make_float3(__ldg(lam + gi), __ldg(lam + V + gi), __ldg(lam + 2 * V + gi));
+        pj[j] = __ldg(ph + gi);
+      }
+      float3 lh = make_float3(0.f, 0.f, 0.f);
+      float phh = 0.f;
+      if (has_halo) {
+        const size_t hi = g.idx(x, hyv, htv);
+        lh = make_float3(__ldg(lam + hi), __ldg(lam + V + hi), __ldg(lam + 2 * V + hi));
+        phh = __ldg(ph + hi);
+      }
+      cp_async_wait_all_but_one();
+      __syncthreads();
+      const float* Ux = U + (s % 3) * SU;
+      const float* Un = U + ((s + 1) % 3) * SU;
+      const float* Bx = B + (s % 3) * SB;
+      const float* Bn = B + ((s + 1) % 3) * SB;
+      const float* Kx = K + (s % 3) * SB;
+      const float* Kn = K + ((s + 1) % 3) * SB;
+      // normals over rows y0 - 2 .. y0 + TY - 1, t0 - 2 .. t0 + TT - 1
+      for (int i = threadIdx.x; i < SN; i += kTileThreads) {
+        const int yy = i / kFusNW, tt = i - yy * kFusNW;
+        const int o = yy * kP + tt + kC - 2;
+        const float c = Ux[o];
+        const float3 n = normal_of(make_float3(Un[o] - c, Ux[o + kP] - c, Ux[o + 1] - c), eps2);
+        N[i] = n.x;
+        N[SN + i] = n.y;
+        N[2 * SN + i] = n.z;
+      }
+      __syncthreads();
+      // the own voxels: outputs of the post step, q
+      float3 qj[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int it = lane + 32 * j;
+        const int u = (iy + 2) * kP + kC + it;   // staged u+ index
+        const int bk = (iy + 1) * kP + kC + it;  // staged u-bar / u^k index
+        const int r2 = (iy + 2) * kFusNW + it + 2;
+        const int r1 = (iy + 1) * kRW + it + 1;
+        const float kap = (N[r2] - nx_prev[j]) + (N[SN + r2] - N[SN + r2 - kFusNW]) + (N[2 * SN + r2] - N[2 * SN + r2 - 1]);
+        nx_prev[j] = N[r2];
+        const FusedPoint fp = fused_point(make_float4(Ux[u], Un[u], Ux[u + kP], Ux[u + 1]),
+                                          make_float4(Bx[bk], Bn[bk], Bx[bk + kP], Bx[bk + 1]),
+                                          make_float4(Kx[bk], Kn[bk], Kx[bk + kP], Kx[bk + 1]), lj[j], pj[j], kap, mu,
+                                          inv_mu, beta, pa, pb, kind);
+        const size_t gi = g.idx(x, y, T.t0 + it);
+        lamo[gi] = fp.lam.x;
+        lamo[V + gi] = fp.lam.y;
+        lamo[2 * V + gi] = fp.lam.z;
+        pho[gi] = fp.phi;
+        ubn[gi] = fp.ubn;
+        ca.add(0, fp.phi * fp.gn);
+        ca.add(1, fp.d2);
+        Q[r1] = fp.q.x;
+        Q[SQ + r1] = fp.q.y;
+        Q[2 * SQ + r1] = fp.q.z;
+        qj[j] = fp.q;
+      }
+      // the halo voxel: q only
+      if (has_halo) {
+        const int u = (hy + 1) * kP + kC - 1 + ht;
+        const int bk = hy * kP + kC - 1 + ht;
+        const int r2 = (hy + 1) * kFusNW + ht + 1;
+        const int r1 = hy * kRW + ht;
+        const float kap = (N[r2] - H[h]) + (N[SN + r2] - N[SN + r2 - kFusNW]) + (N[2 * SN + r2] - N[2 * SN + r2 - 1]);
+        H[h] = N[r2];
+        const FusedPoint fp = fused_point(make_float4(Ux[u], Un[u], Ux[u + kP], Ux[u + 1]),
+                                          make_float4(Bx[bk], Bn[bk], Bx[bk + kP], Bx[bk + 1]),
+                                          make_float4(Kx[bk], Kn[bk], Kx[bk + kP], Kx[bk + 1]), lh, phh, kap, mu,
+                                          inv_mu, beta, pa, pb, kind);
+        Q[r1] = fp.q.x;
+        Q[SQ + r1] = fp.q.y;
+        Q[2 * SQ + r1] = fp.q.z;
+      }
+      __syncthreads();
+      // reg = -mu sum_d (q_d(c) - q_d(c - e_d)) at the own voxels
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int it = lane + 32 * j;
+        const int r1 = (iy + 1) * kRW + it + 1;
+        const float div =
+            (qj[j].x - qx_prev[j]) + (qj[j].y - Q[SQ + r1 - kRW]) + (qj[j].z - Q[2 * SQ + r1 - 1]);
+        reg[g.idx(x, y, T.t0 + it)] = -mu * div;
+        qx_prev[j] = qj[j].x;
+      }
+      // the next step's first shared writes (the prefetch into this step's
+      // slots, then N and Q) all come after a barrier that follows every
+      // read of them above
+    }
+    cp_async_wait_all();
+  }
+  block_reduce_acc(ca, partials);
 }
 
 }  // namespace nlos
