@@ -433,6 +433,14 @@ __device__ __forceinline__ void stage_rows_lo2_async(float* __restrict__ tile, i
 // One voxel c of the fused step.  u, b, k: u+, u-bar and u^k at c, c + e_x,
 // c + e_y, c + e_t; l, ph: Lambda and phi at c before the step; kap:
 // kappa(u+) at c.
+// shrink3 with a select in place of its early return (same value for every
+// input).
+__device__ __forceinline__ float3 shrink3_nb(float3 a, float th) {
+  const float n2 = a.x * a.x + a.y * a.y + a.z * a.z;
+  const float s = n2 > 0.0f ? fmaxf(1.0f - th * rsqrtf(n2), 0.0f) : 0.0f;
+  return make_float3(a.x * s, a.y * s, a.z * s);
+}
+
 struct FusedPoint {
   float3 lam;  // Lambda_{k+1} = Lambda + mu (v - grad u+)
   float phi;   // phi(kappa(u+))
@@ -446,7 +454,7 @@ __device__ __forceinline__ FusedPoint fused_point(float4 u, float4 b, float4 k, 
   FusedPoint o;
   const float3 gu = make_float3(u.y - u.x, u.z - u.x, u.w - u.x);
   const float3 av = make_float3(b.y - b.x - l.x * inv_mu, b.z - b.x - l.y * inv_mu, b.w - b.x - l.z * inv_mu);
-  const float3 v = shrink3(av, ph * inv_mu);
+  const float3 v = shrink3_nb(av, ph * inv_mu);
   const float3 d = make_float3(v.x - gu.x, v.y - gu.y, v.z - gu.z);
   o.lam = make_float3(l.x + mu * d.x, l.y + mu * d.y, l.z + mu * d.z);
   o.phi = phi_of(kap, pa, pb, kind);
@@ -454,7 +462,7 @@ __device__ __forceinline__ FusedPoint fused_point(float4 u, float4 b, float4 k, 
               n3 = u.w + beta * (u.w - k.w);
   o.ubn = n0;
   const float3 an = make_float3(n1 - n0 - o.lam.x * inv_mu, n2 - n0 - o.lam.y * inv_mu, n3 - n0 - o.lam.z * inv_mu);
-  const float3 vn = shrink3(an, o.phi * inv_mu);
+  const float3 vn = shrink3_nb(an, o.phi * inv_mu);
   o.q = make_float3(vn.x + o.lam.x * inv_mu, vn.y + o.lam.y * inv_mu, vn.z + o.lam.z * inv_mu);
   o.gn = sqrtf(gu.x * gu.x + gu.y * gu.y + gu.z * gu.z);
   o.d2 = d.x * d.x + d.y * d.y + d.z * d.z;
@@ -516,16 +524,6 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     cur += T.cnt;
     const int y = T.y0 + iy;
     const int hyv = (T.y0 - 1 + hy) & g.my, htv = (T.t0 - 1 + ht) & g.mt;
-    // the plane before the run: n_x of u+ at the own and halo voxels, q_x at
-    // the own voxels
-    const int xm = (T.x0 - 1) & g.mx;
-    float nx_prev[4], qx_prev[4];
-    for (int j = 0; j < 4; ++j) {
-      const int t = T.t0 + lane + 32 * j;
-      nx_prev[j] = normal_of(grad_at(unew, g, xm, y, t), eps2).x;
-      qx_prev[j] = fused_qx_at(unew, uk, ub, lam, ph, g, V, xm, y, t, mu, inv_mu, beta, pa, pb, kind, eps2);
-    }
-    if (has_halo) H[h] = normal_of(grad_at(unew, g, xm, hyv, htv), eps2).x;
     // prologue: planes x0 (group 0) and x0 + 1 (group 1)
     stage_rows_lo2_async(U, kFusUH, unew, g, T.x0, T.y0, T.t0);
     stage_rows_async<true, true>(B, kUH, ub, g, T.x0, T.y0, -1, T.t0);
@@ -535,6 +533,16 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     stage_rows_async<true, true>(B + SB, kUH, ub, g, (T.x0 + 1) & g.mx, T.y0, -1, T.t0);
     stage_rows_async<true, true>(K + SB, kUH, uk, g, (T.x0 + 1) & g.mx, T.y0, -1, T.t0);
     cp_async_commit();
+    // (while those copies are in flight) the plane before the run: n_x of u+ at the own and halo voxels, q_x at
+    // the own voxels
+    const int xm = (T.x0 - 1) & g.mx;
+    float nx_prev[4], qx_prev[4];
+    for (int j = 0; j < 4; ++j) {
+      const int t = T.t0 + lane + 32 * j;
+      nx_prev[j] = normal_of(grad_at(unew, g, xm, y, t), eps2).x;
+      qx_prev[j] = fused_qx_at(unew, uk, ub, lam, ph, g, V, xm, y, t, mu, inv_mu, beta, pa, pb, kind, eps2);
+    }
+    if (has_halo) H[h] = normal_of(grad_at(unew, g, xm, hyv, htv), eps2).x;
     for (int s = 0; s < T.cnt; ++s) {
       const int x = T.x0 + s;
       if (s + 1 < T.cnt) {

@@ -41,12 +41,12 @@
 #include "fft.cuh"
 #include "passes.cuh"
 #include "tma.cuh"
+#include "wfft.cuh"
 
 namespace nlos {
 
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarpThreads = 256;  // 8 warps: 8 column pairs, 16 columns per CTA
 constexpr int kWarpCols = 16;
 
@@ -89,10 +89,6 @@ __device__ __forceinline__ int natp(int k) {
   return k + ((k / (V * V)) % G) * (16 / G);
 }
 
-__device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
-  return make_float2(__shfl_xor_sync(kFull, v.x, m), __shfl_xor_sync(kFull, v.y, m));
-}
-
 // Streaming load: read once, not kept in L1 (the tables read through L1 stay there).
 __device__ __forceinline__ float ld_stream(const float* p) {
   float v;
@@ -112,101 +108,6 @@ __device__ __forceinline__ void cp_async_wait() {
 // Pulls a contiguous range (16-byte aligned, a multiple of 16 bytes) into L2.
 __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
-template <int G>
-__device__ __forceinline__ int rev_bits(int g) {
-  int r = 0;
-#pragma unroll
-  for (int b = 1; b < G; b <<= 1) r = (r << 1) | ((g & b) ? 1 : 0);
-  return r;
-}
-
-// G-point DFT across the lanes g of each sequence (every register a), radix
-// 2.  Forward: decimation in frequency, natural lane order in, bit-reversed
-// out; each stage of half-size h takes (u, v) = (lane g, lane g + h) to
-// (u + v, (u - v) w_2h^(g mod h)).  Inverse: the stages backwards with
-// conjugate twiddles (unnormalised).  The twiddle w_2h^j is w_2N^(j N / h).
-template <int V, bool INV>
-__device__ __forceinline__ void lane_dft(float2 (&b)[V], int g, const float2* twc) {
-  constexpr int G = 32 / V, N = 32 * V;
-  if constexpr (G > 1) {
-    if constexpr (!INV) {
-#pragma unroll
-      for (int h = G / 2; h >= 1; h >>= 1) {
-        const bool up = (g & h) != 0;
-        const float s = up ? -1.0f : 1.0f;
-        const float2 w = h > 1 && up ? twc[(g & (h - 1)) * (N / h)] : make_float2(1.0f, 0.0f);
-#pragma unroll
-        for (int a = 0; a < V; ++a) {
-          const float2 p = shfl_xor2(b[a], h);
-          // lower lane: u + v; upper lane: u - v (u the lower lane's value)
-          const float2 r = __ffma2_rn(b[a], make_float2(s, s), p);
-          b[a] = h > 1 ? cmul(r, w) : r;
-        }
-      }
-    } else {
-#pragma unroll
-      for (int h = 1; h < G; h <<= 1) {
-        const bool up = (g & h) != 0;
-        const float s = up ? -1.0f : 1.0f;
-        const float2 w = h > 1 && up ? twc[(g & (h - 1)) * (N / h)] : make_float2(1.0f, 0.0f);
-#pragma unroll
-        for (int a = 0; a < V; ++a) {
-          const float2 t = h > 1 ? cmulc(b[a], w) : b[a];
-          const float2 p = shfl_xor2(t, h);
-          b[a] = __ffma2_rn(t, make_float2(s, s), p);
-        }
-      }
-    }
-  }
-}
-
-// Forward length-N transform of the warp's sequence: natural order in, the
-// order of the file header out.  scr: the warp's scratch.
-template <int V>
-__device__ __forceinline__ void wfft_fwd(float2 (&a)[V], float2* scr, const float2* tw1, const float2* twc,
-                                         int lane) {
-  constexpr int G = WP<V>::G, XP = WP<V>::XP;
-  dft_reg<V, false>(a);
-#pragma unroll
-  for (int k1 = 1; k1 < V; ++k1) a[k1] = cmul(a[k1], tw1[k1 * 32 + lane]);
-#pragma unroll
-  for (int k1 = 0; k1 < V; ++k1) scr[k1 * XP + lane] = a[k1];
-  __syncwarp();
-  const int k1 = lane / G, g = lane % G;
-#pragma unroll
-  for (int j = 0; j < V; ++j) a[j] = scr[k1 * XP + g + G * j];
-  __syncwarp();
-  dft_reg<V, false>(a);
-  if constexpr (G > 1) {
-#pragma unroll
-    for (int q = 1; q < V; ++q) a[q] = cmul(a[q], tw1[q * 32 + V * g]);
-  }
-  lane_dft<V, false>(a, g, twc);
-}
-
-// Inverse of wfft_fwd (times N): the header's order in, natural order out.
-template <int V>
-__device__ __forceinline__ void wfft_inv(float2 (&a)[V], float2* scr, const float2* tw1, const float2* twc,
-                                         int lane) {
-  constexpr int G = WP<V>::G, XP = WP<V>::XP;
-  const int k1 = lane / G, g = lane % G;
-  lane_dft<V, true>(a, g, twc);
-  if constexpr (G > 1) {
-#pragma unroll
-    for (int q = 1; q < V; ++q) a[q] = cmulc(a[q], tw1[q * 32 + V * g]);
-  }
-  dft_reg<V, true>(a);
-#pragma unroll
-  for (int j = 0; j < V; ++j) scr[k1 * XP + g + G * j] = a[j];
-  __syncwarp();
-#pragma unroll
-  for (int q = 0; q < V; ++q) a[q] = scr[q * XP + lane];
-  __syncwarp();
-#pragma unroll
-  for (int q = 1; q < V; ++q) a[q] = cmulc(a[q], tw1[q * 32 + lane]);
-  dft_reg<V, true>(a);
 }
 
 // Bin kt in [0, 2N) of the padded spectrum of the pair in chunk c of the

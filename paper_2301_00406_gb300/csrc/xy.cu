@@ -25,6 +25,7 @@
 
 #include "fft.cuh"
 #include "passes.cuh"
+#include "wfft.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -287,6 +288,120 @@ __global__ void __launch_bounds__(kConvThreads)
   for (int i = tid; i < N * N; i += nthr) g[i] = plane[(i / N) * P + (i % N)];
 }
 
+// The same solve for N >= 32 with every transform held in registers by a
+// half-warp (wfft.cuh with L = 16 lanes, V = N / 16 values per lane): 32
+// groups of 16 lanes per CTA, N / 32 rows (then columns, then rows) per
+// group, so a plane passes through shared memory three times with two CTA
+// barriers, instead of once per transform step.
+//  1. rows: load row x (lane l: elements l + 16 m, coalesced), forward
+//     transform over y, store in the transform's output order (position
+//     l + 16 m) into the plane (pitch N + 1: the column reads of step 2 fall
+//     in distinct banks);
+//  2. columns (one output position q = ky slot per group pass): forward
+//     transform over x, divide by c0 + c1 (lambda(kx) + lambda(ky) +
+//     lambda_t(kt)) and by N^2, inverse transform, back into the plane;
+//  3. rows: inverse transform over y from the output order, store in
+//     natural order.
+template <int N>
+struct SW {
+  static constexpr int L = 16, V = N / L, G = L / V, XP = L + G;
+  static constexpr int P = N + 1;                  // plane row pitch (float2)
+  static constexpr int SCR = V * XP;               // exchange scratch per group
+  static constexpr int THREADS = 512, GROUPS = THREADS / L;
+  static constexpr int PER = N / GROUPS;           // rows or columns per group
+  static constexpr size_t smem = sizeof(float2) * (N * P + GROUPS * SCR + 2 * N) + sizeof(float) * N;
+  static_assert(N >= 32 && PER >= 1, "half-warp solve needs N >= 32");
+};
+
+// Frequency held by lane l (of a group), register m after the forward
+// transform.
+template <int N>
+__device__ __forceinline__ int sw_freq(int l, int m) {
+  using W = SW<N>;
+  return l / W::G + W::V * m + W::V * W::V * rev_bits<W::G>(l % W::G);
+}
+
+template <int N>
+__global__ void __launch_bounds__(SW<N>::THREADS, 1)
+    k_sxy_w(float2* __restrict__ Sp, const float* __restrict__ lamx, const float* __restrict__ lamt,
+            const DevScalars* __restrict__ sc, double c0_host, double c1, const float2* __restrict__ twg) {
+  using W = SW<N>;
+  constexpr int V = W::V, L = W::L, P = W::P;
+  extern __shared__ float4 smem_f4[];
+  float2* plane = reinterpret_cast<float2*>(smem_f4);
+  float2* scr = plane + N * P + (threadIdx.x / L) * W::SCR;
+  float2* tw1 = plane + N * P + W::GROUPS * W::SCR;
+  float2* twc = tw1 + N;
+  float* lx = reinterpret_cast<float*>(twc + N);
+  const int grp = threadIdx.x / L, l = threadIdx.x % L;
+  // tw1[k1 L + l] = w_N^(l k1) = w_2N^(2 l k1), twc[n] = w_2N^n
+  for (int i = threadIdx.x; i < N; i += W::THREADS) {
+    tw1[i] = __ldg(twg + ((2 * (i % L) * (i / L)) & (2 * N - 1)));
+    twc[i] = __ldg(twg + i);
+    lx[i] = __ldg(lamx + i);
+  }
+  const int kt = blockIdx.x;
+  float2* g = Sp + (size_t)kt * N * N;
+  // 1. rows, forward; the next row's loads are issued before this row's
+  // transform
+  float2 nxt[V];
+#pragma unroll
+  for (int m = 0; m < V; ++m) nxt[m] = g[grp * N + l + L * m];
+  __syncthreads();  // tables staged
+  WTwid<V> tw;
+  wtwid_load<V, L>(tw, tw1, l);
+#pragma unroll 1
+  for (int r = 0; r < W::PER; ++r) {
+    const int x = grp + W::GROUPS * r;
+    float2 a[V];
+#pragma unroll
+    for (int m = 0; m < V; ++m) a[m] = nxt[m];
+    if (r + 1 < W::PER) {
+#pragma unroll
+      for (int m = 0; m < V; ++m) nxt[m] = g[(x + W::GROUPS) * N + l + L * m];
+    }
+    wfft_fwd<V, L>(a, scr, tw, twc, l);
+#pragma unroll
+    for (int m = 0; m < V; ++m) plane[x * P + l + L * m] = a[m];
+  }
+  __syncthreads();
+  // 2. columns: forward over x, division, inverse
+  const float c0 = sc ? (float)sc->L : (float)c0_host;
+  const float c1f = (float)c1, lt = __ldg(lamt + kt), s = 1.0f / (float)(N * N);
+  float lk[V];
+#pragma unroll
+  for (int m = 0; m < V; ++m) lk[m] = lx[sw_freq<N>(l, m)];
+#pragma unroll 1
+  for (int r = 0; r < W::PER; ++r) {
+    const int q = grp + W::GROUPS * r;
+    const float ly = lx[sw_freq<N>(q % L, q / L)] + lt;
+    float2 b[V];
+#pragma unroll
+    for (int m = 0; m < V; ++m) b[m] = plane[(l + L * m) * P + q];
+    wfft_fwd<V, L>(b, scr, tw, twc, l);
+#pragma unroll
+    for (int m = 0; m < V; ++m) {
+      const float den = c0 + c1f * (lk[m] + ly);
+      b[m] = cscale(b[m], __frcp_rn(den) * s);
+    }
+    wfft_inv<V, L>(b, scr, tw, twc, l);
+#pragma unroll
+    for (int m = 0; m < V; ++m) plane[(l + L * m) * P + q] = b[m];
+  }
+  __syncthreads();
+  // 3. rows, inverse, natural order out
+#pragma unroll 1
+  for (int r = 0; r < W::PER; ++r) {
+    const int x = grp + W::GROUPS * r;
+    float2 a[V];
+#pragma unroll
+    for (int m = 0; m < V; ++m) a[m] = plane[x * P + l + L * m];
+    wfft_inv<V, L>(a, scr, tw, twc, l);
+#pragma unroll
+    for (int m = 0; m < V; ++m) g[x * N + l + L * m] = a[m];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Cone-kernel spectrum: H(kx, ky, kt) for kx, ky in [0, N], kt in [0, nt], the
 // DFT of h over the (2N, 2N, 2nt) grid.  One CTA per (kt, parity quadrant).
@@ -364,6 +479,7 @@ nlos_status prepare_xy(int n) {
     else
       NLOS_TRY(set_smem(k_conv<N>, CV<N>::smem));
     NLOS_TRY(set_smem(k_sxy<N>, sizeof(float2) * (N * (N + 1) + 2 * N)));
+    if constexpr (N >= 32) NLOS_TRY(set_smem(k_sxy_w<N>, SW<N>::smem));
     NLOS_TRY(set_smem(k_kspec<N>, sizeof(float2) * (N * (N + 1) + 2 * N)));
     return NLOS_OK;
   });
@@ -391,10 +507,16 @@ nlos_status launch_sxy(const Plan& P, float2* Sp, const DevScalars* sc, double c
   KTimer kt_(P, KC_SXY, st);
   return dispatch_n(P.nx, [&](auto nc) -> nlos_status {
     constexpr int N = decltype(nc)::value;
-    auto kern = k_sxy<N>;
-    const size_t sm = sizeof(float2) * (N * (N + 1) + 2 * N);
-    NLOS_TRY(set_smem(kern, sm));
-    kern<<<P.nt / 2 + 1, kConvThreads, sm, st>>>(Sp, P.nt, P.d_lamx, P.d_lamt, sc, c0_host, c1, P.d_twx);
+    if constexpr (N >= 32) {
+      NLOS_TRY(set_smem(k_sxy_w<N>, SW<N>::smem));
+      k_sxy_w<N><<<P.nt / 2 + 1, SW<N>::THREADS, SW<N>::smem, st>>>(Sp, P.d_lamx, P.d_lamt, sc, c0_host, c1,
+                                                                     P.d_twx);
+    } else {
+      auto kern = k_sxy<N>;
+      const size_t sm = sizeof(float2) * (N * (N + 1) + 2 * N);
+      NLOS_TRY(set_smem(kern, sm));
+      kern<<<P.nt / 2 + 1, kConvThreads, sm, st>>>(Sp, P.nt, P.d_lamx, P.d_lamt, sc, c0_host, c1, P.d_twx);
+    }
     NLOS_LAUNCH_CHECK("k_sxy");
     return NLOS_OK;
   });
