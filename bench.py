@@ -172,8 +172,8 @@ def algorithmic(cat, nx, nt, ncols):
         return "bytes", Sp + 2 * F, None
     if cat == "k_pre":    # u-bar, Lambda (3), phi in; reg out
         return "bytes", 6 * F, None
-    if cat == "k_post":   # u+, u^k, u-bar, Lambda (3), phi in; Lambda (3), phi, u-bar' out
-        return "bytes", 12 * F, None
+    if cat == "k_post":   # fused post and pre step: u+, u^k, u-bar, Lambda (3), phi in;
+        return "bytes", 13 * F, None   # Lambda (3), phi, u-bar', reg out
     return "bytes", 0.0, None
 
 
