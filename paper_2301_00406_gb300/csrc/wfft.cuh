@@ -14,7 +14,8 @@
 // to natural order (unnormalised).
 //
 // Tables (shared or global memory): tw1[k1 L + l] = w_N^(l k1) for k1 < V,
-// l < L; twc[n] = w_2N^n for n < N (only read when G > 2).  Scratch: V (L + G)
+// l < L (the second step reads it only when G > 2; for G = 2 its twiddles
+// are compile-time roots); twc[n] = w_2N^n for n < N (only read when G > 2).  Scratch: V (L + G)
 // float2 per group; the pitch L + G puts the strided reads of the exchange
 // in distinct banks.
 #pragma once
@@ -33,6 +34,15 @@ __device__ __forceinline__ int rev_bits(int g) {
 #pragma unroll
   for (int b = 1; b < G; b <<= 1) r = (r << 1) | ((g & b) ? 1 : 0);
   return r;
+}
+
+// The second-step twiddle w_N^(V g q) = w_L^(g q) when G = 2: 1 on the lanes
+// g = 0, the compile-time root w_L^q on the lanes g = 1 (q a constant after
+// unrolling), so no table read.
+template <int L, bool INV>
+__device__ __forceinline__ float2 twiddle_g2(float2 v, int q, int g) {
+  const float2 r = twmul64<INV>(v, (64 / L) * q);
+  return g ? r : v;
 }
 
 // G-point DFT across the lanes g of each sequence (every register a), radix
@@ -94,7 +104,10 @@ __device__ __forceinline__ void wfft_fwd(float2 (&a)[V], float2* scr, const floa
   for (int j = 0; j < V; ++j) a[j] = scr[k1 * XP + g + G * j];
   __syncwarp();
   dft_reg<V, false>(a);
-  if constexpr (G > 1) {
+  if constexpr (G == 2) {
+#pragma unroll
+    for (int q = 1; q < V; ++q) a[q] = twiddle_g2<L, false>(a[q], q, g);
+  } else if constexpr (G > 1) {
 #pragma unroll
     for (int q = 1; q < V; ++q) a[q] = cmul(a[q], tw1[q * L + V * g]);
   }
@@ -108,7 +121,10 @@ __device__ __forceinline__ void wfft_inv(float2 (&a)[V], float2* scr, const floa
   constexpr int G = L / V, XP = L + G;
   const int k1 = lane / G, g = lane % G;
   lane_dft<V, true, L>(a, g, twc);
-  if constexpr (G > 1) {
+  if constexpr (G == 2) {
+#pragma unroll
+    for (int q = 1; q < V; ++q) a[q] = twiddle_g2<L, true>(a[q], q, g);
+  } else if constexpr (G > 1) {
 #pragma unroll
     for (int q = 1; q < V; ++q) a[q] = cmulc(a[q], tw1[q * L + V * g]);
   }
@@ -137,7 +153,7 @@ __device__ __forceinline__ void wtwid_load(WTwid<V>& t, const float2* tw1, int l
 #pragma unroll
   for (int k = 0; k < V; ++k) {
     t.t1[k] = tw1[k * L + lane];
-    t.t2[k] = tw1[k * L + V * (lane % G)];
+    if constexpr (G != 2) t.t2[k] = tw1[k * L + V * (lane % G)];
   }
 }
 
@@ -157,7 +173,10 @@ __device__ __forceinline__ void wfft_fwd(float2 (&a)[V], float2* scr, const WTwi
   for (int j = 0; j < V; ++j) a[j] = scr[k1 * XP + g + G * j];
   __syncwarp();
   dft_reg<V, false>(a);
-  if constexpr (G > 1) {
+  if constexpr (G == 2) {
+#pragma unroll
+    for (int q = 1; q < V; ++q) a[q] = twiddle_g2<L, false>(a[q], q, g);
+  } else if constexpr (G > 1) {
 #pragma unroll
     for (int q = 1; q < V; ++q) a[q] = cmul(a[q], t.t2[q]);
   }
@@ -169,7 +188,10 @@ __device__ __forceinline__ void wfft_inv(float2 (&a)[V], float2* scr, const WTwi
   constexpr int G = L / V, XP = L + G;
   const int k1 = lane / G, g = lane % G;
   lane_dft<V, true, L>(a, g, twc);
-  if constexpr (G > 1) {
+  if constexpr (G == 2) {
+#pragma unroll
+    for (int q = 1; q < V; ++q) a[q] = twiddle_g2<L, true>(a[q], q, g);
+  } else if constexpr (G > 1) {
 #pragma unroll
     for (int q = 1; q < V; ++q) a[q] = cmulc(a[q], t.t2[q]);
   }
