@@ -747,7 +747,9 @@ nlos_status prepare_stencils() {
   NLOS_TRY(ensure_smem(k_pre1_pipe<true>, kPre1PipeSmem));
   NLOS_TRY(ensure_smem(k_post1_pipe<false>, kPost1PipeSmem));
   NLOS_TRY(ensure_smem(k_post1_pipe<true>, kPost1PipeSmem));
-  NLOS_TRY(ensure_smem(k_post1_pre, kPostPreSmem));
+  NLOS_TRY(ensure_smem(k_post1_pre<NLOS_PHI_TSC>, kPostPreSmem));
+  NLOS_TRY(ensure_smem(k_post1_pre<NLOS_PHI_TAC>, kPostPreSmem));
+  NLOS_TRY(ensure_smem(k_post1_pre<NLOS_PHI_TRV>, kPostPreSmem));
   return NLOS_OK;
 }
 
@@ -1140,11 +1142,14 @@ static nlos_status step_alg1(JobRun& j) {
   NLOS_TRY(u_step(P, s, ua, host_check, &j.L_host, j.bt_stream, st, &nbf_fold));
   const int fold = host_check ? 0 : 1;
   { KTimer kt_(P, KC_POST, st);
-  if (tiled)
-    k_post1_pre<<<post_grid, kTileThreads, kPostPreSmem, st>>>(s->unew, s->uk, s->ub, s->lam, s->ph, s->lamn, s->phn,
-                                                              s->ubn, s->reg, s->sc, g, ntiles, (float)p.mu,
-                                                              (float)p.a, (float)p.b, p.phi, eps2, V, s->pc);
-  else
+  if (tiled) {
+    auto kern = p.phi == NLOS_PHI_TAC   ? k_post1_pre<NLOS_PHI_TAC>
+                : p.phi == NLOS_PHI_TRV ? k_post1_pre<NLOS_PHI_TRV>
+                                        : k_post1_pre<NLOS_PHI_TSC>;
+    kern<<<post_grid, kTileThreads, kPostPreSmem, st>>>(s->unew, s->uk, s->ub, s->lam, s->ph, s->lamn, s->phn, s->ubn,
+                                                       s->reg, s->sc, g, ntiles, (float)p.mu, (float)p.a, (float)p.b,
+                                                       eps2, V, s->pc);
+  } else
     k_post1<<<stencil_blocks(P), kStencilThreads, 0, st>>>(s->unew, s->uk, s->ub, s->lam, s->ph, s->ubn, s->sc, g, vi,
                                                         (float)p.mu, (float)p.a, (float)p.b, p.phi, eps2, V, s->pc);
   }

@@ -449,15 +449,16 @@ struct FusedPoint {
   float gn;    // |grad u+|
   float d2;    // |v - grad u+|^2
 };
+template <int KIND>
 __device__ __forceinline__ FusedPoint fused_point(float4 u, float4 b, float4 k, float3 l, float ph, float kap,
-                                                  float mu, float inv_mu, float beta, float pa, float pb, int kind) {
+                                                  float mu, float inv_mu, float beta, float pa, float pb) {
   FusedPoint o;
   const float3 gu = make_float3(u.y - u.x, u.z - u.x, u.w - u.x);
   const float3 av = make_float3(b.y - b.x - l.x * inv_mu, b.z - b.x - l.y * inv_mu, b.w - b.x - l.z * inv_mu);
   const float3 v = shrink3_nb(av, ph * inv_mu);
   const float3 d = make_float3(v.x - gu.x, v.y - gu.y, v.z - gu.z);
   o.lam = make_float3(l.x + mu * d.x, l.y + mu * d.y, l.z + mu * d.z);
-  o.phi = phi_of(kap, pa, pb, kind);
+  o.phi = phi_of(kap, pa, pb, KIND);
   const float n0 = u.x + beta * (u.x - k.x), n1 = u.y + beta * (u.y - k.y), n2 = u.z + beta * (u.z - k.z),
               n3 = u.w + beta * (u.w - k.w);
   o.ubn = n0;
@@ -477,29 +478,32 @@ __device__ __forceinline__ float4 fwd4(const float* __restrict__ f, const Vox& g
 
 // q_x of the fused step at one voxel, every input from global memory (the
 // plane before a run's first plane).
+template <int KIND>
 __device__ __forceinline__ float fused_qx_at(const float* __restrict__ unew, const float* __restrict__ uk,
                                              const float* __restrict__ ub, const float* __restrict__ lam,
                                              const float* __restrict__ ph, const Vox& g, size_t V, int x, int y,
-                                             int t, float mu, float inv_mu, float beta, float pa, float pb, int kind,
+                                             int t, float mu, float inv_mu, float beta, float pa, float pb,
                                              float eps2) {
   const int i = g.idx(x, y, t);
   const float3 l = make_float3(__ldg(lam + i), __ldg(lam + V + i), __ldg(lam + 2 * V + i));
   const float kap = curvature_at(unew, g, x, y, t, eps2, nullptr);
-  return fused_point(fwd4(unew, g, x, y, t), fwd4(ub, g, x, y, t), fwd4(uk, g, x, y, t), l, __ldg(ph + i), kap, mu,
-                     inv_mu, beta, pa, pb, kind)
+  return fused_point<KIND>(fwd4(unew, g, x, y, t), fwd4(ub, g, x, y, t), fwd4(uk, g, x, y, t), l, __ldg(ph + i),
+                           kap, mu, inv_mu, beta, pa, pb)
       .q.x;
 }
 
 // lamo = Lambda_{k+1}, pho = phi(kappa(u+)), ubn = u-bar_{k+1} (as k_post1_pipe)
 // and reg = -mu div q for the next iteration (as k_pre1_pipe on those
 // outputs); lam, ph: Lambda and phi before the step (not written).
-// Partials 0 = sum phi |grad u+|, 1 = sum |v - grad u+|^2.
+// Partials 0 = sum phi |grad u+|, 1 = sum |v - grad u+|^2.  KIND: the phi of
+// the curvature (NLOS_PHI_*).
+template <int KIND>
 __global__ void __launch_bounds__(kTileThreads, 2)
     k_post1_pre(const float* __restrict__ unew, const float* __restrict__ uk, const float* __restrict__ ub,
                 const float* __restrict__ lam, const float* __restrict__ ph, float* __restrict__ lamo,
                 float* __restrict__ pho, float* __restrict__ ubn, float* __restrict__ reg,
-                const DevScalars* __restrict__ sc, Vox g, int nsteps, float mu, float pa, float pb, int kind,
-                float eps2, size_t V, double* __restrict__ partials) {
+                const DevScalars* __restrict__ sc, Vox g, int nsteps, float mu, float pa, float pb, float eps2,
+                size_t V, double* __restrict__ partials) {
   extern __shared__ float4 smem_f4[];
   float* U = reinterpret_cast<float*>(smem_f4);
   float* B = U + kFusU;
@@ -540,7 +544,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     for (int j = 0; j < 4; ++j) {
       const int t = T.t0 + lane + 32 * j;
       nx_prev[j] = normal_of(grad_at(unew, g, xm, y, t), eps2).x;
-      qx_prev[j] = fused_qx_at(unew, uk, ub, lam, ph, g, V, xm, y, t, mu, inv_mu, beta, pa, pb, kind, eps2);
+      qx_prev[j] = fused_qx_at<KIND>(unew, uk, ub, lam, ph, g, V, xm, y, t, mu, inv_mu, beta, pa, pb, eps2);
     }
     if (has_halo) H[h] = normal_of(grad_at(unew, g, xm, hyv, htv), eps2).x;
     for (int s = 0; s < T.cnt; ++s) {
@@ -577,16 +581,21 @@ __global__ void __launch_bounds__(kTileThreads, 2)
       const float* Bn = B + ((s + 1) % 3) * SB;
       const float* Kx = K + (s % 3) * SB;
       const float* Kn = K + ((s + 1) % 3) * SB;
-      // normals over rows y0 - 2 .. y0 + TY - 1, t0 - 2 .. t0 + TT - 1
-      for (int i = threadIdx.x; i < SN; i += kTileThreads) {
-        const int yy = i / kFusNW, tt = i - yy * kFusNW;
-        const int o = yy * kP + tt + kC - 2;
+      // normals over rows y0 - 2 .. y0 + TY - 1, t0 - 2 .. t0 + TT - 1: columns
+      // 0 .. TT - 1 of the region two rows per pass, then its last two
+      // columns
+      auto normal_at = [&](int yy, int tt) {
+        const int o = yy * kP + tt + kC - 2, i = yy * kFusNW + tt;
         const float c = Ux[o];
         const float3 n = normal_of(make_float3(Un[o] - c, Ux[o + kP] - c, Ux[o + 1] - c), eps2);
         N[i] = n.x;
         N[SN + i] = n.y;
         N[2 * SN + i] = n.z;
-      }
+      };
+      static_assert(kTileThreads == 2 * kTT && kFusNH % 2 == 0, "two region rows per pass");
+#pragma unroll
+      for (int yy = threadIdx.x / kTT; yy < kFusNH; yy += 2) normal_at(yy, threadIdx.x % kTT);
+      if (threadIdx.x < 2 * kFusNH) normal_at(threadIdx.x >> 1, kTT + (threadIdx.x & 1));
       __syncthreads();
       // the own voxels: outputs of the post step, q
       float3 qj[4];
@@ -599,10 +608,10 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         const int r1 = (iy + 1) * kRW + it + 1;
         const float kap = (N[r2] - nx_prev[j]) + (N[SN + r2] - N[SN + r2 - kFusNW]) + (N[2 * SN + r2] - N[2 * SN + r2 - 1]);
         nx_prev[j] = N[r2];
-        const FusedPoint fp = fused_point(make_float4(Ux[u], Un[u], Ux[u + kP], Ux[u + 1]),
-                                          make_float4(Bx[bk], Bn[bk], Bx[bk + kP], Bx[bk + 1]),
-                                          make_float4(Kx[bk], Kn[bk], Kx[bk + kP], Kx[bk + 1]), lj[j], pj[j], kap, mu,
-                                          inv_mu, beta, pa, pb, kind);
+        const FusedPoint fp = fused_point<KIND>(make_float4(Ux[u], Un[u], Ux[u + kP], Ux[u + 1]),
+                                                make_float4(Bx[bk], Bn[bk], Bx[bk + kP], Bx[bk + 1]),
+                                                make_float4(Kx[bk], Kn[bk], Kx[bk + kP], Kx[bk + 1]), lj[j], pj[j],
+                                                kap, mu, inv_mu, beta, pa, pb);
         const size_t gi = g.idx(x, y, T.t0 + it);
         lamo[gi] = fp.lam.x;
         lamo[V + gi] = fp.lam.y;
@@ -624,10 +633,10 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         const int r1 = hy * kRW + ht;
         const float kap = (N[r2] - H[h]) + (N[SN + r2] - N[SN + r2 - kFusNW]) + (N[2 * SN + r2] - N[2 * SN + r2 - 1]);
         H[h] = N[r2];
-        const FusedPoint fp = fused_point(make_float4(Ux[u], Un[u], Ux[u + kP], Ux[u + 1]),
-                                          make_float4(Bx[bk], Bn[bk], Bx[bk + kP], Bx[bk + 1]),
-                                          make_float4(Kx[bk], Kn[bk], Kx[bk + kP], Kx[bk + 1]), lh, phh, kap, mu,
-                                          inv_mu, beta, pa, pb, kind);
+        const FusedPoint fp = fused_point<KIND>(make_float4(Ux[u], Un[u], Ux[u + kP], Ux[u + 1]),
+                                                make_float4(Bx[bk], Bn[bk], Bx[bk + kP], Bx[bk + 1]),
+                                                make_float4(Kx[bk], Kn[bk], Kx[bk + kP], Kx[bk + 1]), lh, phh, kap,
+                                                mu, inv_mu, beta, pa, pb);
         Q[r1] = fp.q.x;
         Q[SQ + r1] = fp.q.y;
         Q[2 * SQ + r1] = fp.q.z;
