@@ -742,11 +742,23 @@ static void swap_ptr(T*& a, T*& b) {
   b = t;
 }
 
+// k_post1_pipe for a phi kind known at run time.
+template <bool L3>
+static auto post1_pipe_kernel(int kind) {
+  return kind == NLOS_PHI_TAC   ? k_post1_pipe<L3, NLOS_PHI_TAC>
+         : kind == NLOS_PHI_TRV ? k_post1_pipe<L3, NLOS_PHI_TRV>
+                                : k_post1_pipe<L3, NLOS_PHI_TSC>;
+}
+
 nlos_status prepare_stencils() {
   NLOS_TRY(ensure_smem(k_pre1_pipe<false>, kPre1PipeSmem));
   NLOS_TRY(ensure_smem(k_pre1_pipe<true>, kPre1PipeSmem));
-  NLOS_TRY(ensure_smem(k_post1_pipe<false>, kPost1PipeSmem));
-  NLOS_TRY(ensure_smem(k_post1_pipe<true>, kPost1PipeSmem));
+  NLOS_TRY(ensure_smem(post1_pipe_kernel<false>(NLOS_PHI_TSC), kPost1PipeSmem));
+  NLOS_TRY(ensure_smem(post1_pipe_kernel<false>(NLOS_PHI_TAC), kPost1PipeSmem));
+  NLOS_TRY(ensure_smem(post1_pipe_kernel<false>(NLOS_PHI_TRV), kPost1PipeSmem));
+  NLOS_TRY(ensure_smem(post1_pipe_kernel<true>(NLOS_PHI_TSC), kPost1PipeSmem));
+  NLOS_TRY(ensure_smem(post1_pipe_kernel<true>(NLOS_PHI_TAC), kPost1PipeSmem));
+  NLOS_TRY(ensure_smem(post1_pipe_kernel<true>(NLOS_PHI_TRV), kPost1PipeSmem));
   NLOS_TRY(ensure_smem(k_post1_pre<NLOS_PHI_TSC>, kPostPreSmem));
   NLOS_TRY(ensure_smem(k_post1_pre<NLOS_PHI_TAC>, kPostPreSmem));
   NLOS_TRY(ensure_smem(k_post1_pre<NLOS_PHI_TRV>, kPostPreSmem));
@@ -1212,13 +1224,13 @@ static nlos_status step_alg2(JobRun& j) {
     // elementwise Lambda_3 part.  The u-step partial buffer pa is free again
     // at this point.
     { KTimer kt_(P, KC_POST, st);
-    k_post1_pipe<false><<<post_grid, kTileThreads, kPost1PipeSmem, st>>>(
+    post1_pipe_kernel<false>(p.phi)<<<post_grid, kTileThreads, kPost1PipeSmem, st>>>(
         s->unew, s->uk, s->ub, s->lam, s->ph, s->ubn, s->sc, g, ntiles, (float)p.mu1, (float)p.a_u, (float)p.b_u,
-        p.phi, c.eps2, V, s->pc, L3Term{});
+        c.eps2, V, s->pc, L3Term{});
     const L3Term l3{j.tau0, s->cache[j.nxt], s->lam3, colpos, (float)p.lambda, (float)p.mu3};
-    k_post1_pipe<true><<<post_grid, kTileThreads, kPost1PipeSmem, st>>>(
+    post1_pipe_kernel<true>(p.phi)<<<post_grid, kTileThreads, kPost1PipeSmem, st>>>(
         s->tnew, s->tk, s->tb, s->lam2, s->pht, s->tbn, s->sc, g, ntiles, (float)p.mu2, (float)p.a_tau,
-        (float)p.b_tau, p.phi, c.eps2, V, s->pa, l3);
+        (float)p.b_tau, c.eps2, V, s->pa, l3);
     }
     NLOS_LAUNCH_CHECK("k_post2");
     { KTimer kt_(P, KC_SMALL, st);

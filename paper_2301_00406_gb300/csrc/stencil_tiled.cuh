@@ -134,13 +134,13 @@ struct L3Term {
 // (Algorithm 1); partials 0 = sum phi |grad u+|, 1 = sum |v - grad u+|^2,
 // v = shrink(grad ubar - lam/mu, phi/mu).  With L3 also the Lambda_3 update
 // above and partials 2 = sum (A u+ - tau+)^2, 3 = sum M (tau+ - tau0)^2,
-// 4 = sum (f - tau+)^2.
-template <bool L3>
+// 4 = sum (f - tau+)^2.  KIND: the phi of the curvature (NLOS_PHI_*).
+template <bool L3, int KIND>
 __global__ void __launch_bounds__(kTileThreads, 2)
     k_post1_pipe(const float* __restrict__ unew, const float* __restrict__ uk, const float* __restrict__ ub,
                  float* __restrict__ lam, float* __restrict__ ph, float* __restrict__ ubn,
-                 const DevScalars* __restrict__ sc, Vox g, int nsteps, float mu, float a, float b, int kind,
-                 float eps2, size_t V, double* __restrict__ partials, L3Term l3) {
+                 const DevScalars* __restrict__ sc, Vox g, int nsteps, float mu, float a, float b, float eps2,
+                 size_t V, double* __restrict__ partials, L3Term l3) {
   extern __shared__ float4 smem_f4[];
   float* U = reinterpret_cast<float*>(smem_f4);
   float* B = U + kPostU;
@@ -204,16 +204,20 @@ __global__ void __launch_bounds__(kTileThreads, 2)
           l3_l[j] = l3.lam3[gi];
         }
       }
-      // normals over the region: point (yy, tt) is voxel (y0 - 1 + yy, t0 - 1 + tt)
-      for (int i = threadIdx.x; i < kRH * kRW; i += kTileThreads) {
-        const int yy = i / kRW, tt = i - yy * kRW;
-        const int o = yy * kP + tt + kC - 1;
+      // normals over the region: point (yy, tt) is voxel (y0 - 1 + yy, t0 - 1 +
+      // tt); columns 0 .. TT - 1 two rows per pass, then the last column
+      auto normal_at = [&](int yy, int tt) {
+        const int o = yy * kP + tt + kC - 1, i = yy * kRW + tt;
         const float c = Ux[o];
         const float3 n = normal_of(make_float3(Un[o] - c, Ux[o + kP] - c, Ux[o + 1] - c), eps2);
         N[i] = n.x;
         N[kRH * kRW + i] = n.y;
         N[2 * kRH * kRW + i] = n.z;
-      }
+      };
+      static_assert(kTileThreads == 2 * kTT, "two region rows per pass");
+#pragma unroll
+      for (int yy = threadIdx.x / kTT; yy < kRH; yy += 2) normal_at(yy, threadIdx.x % kTT);
+      if (threadIdx.x < kRH) normal_at(threadIdx.x, kTT);
       __syncthreads();
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
@@ -237,7 +241,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         lam[gi] = l0 + mu * d.x;
         lam[V + gi] = l1 + mu * d.y;
         lam[2 * V + gi] = l2 + mu * d.z;
-        const float pn = phi_of(kap, a, b, kind);
+        const float pn = phi_of(kap, a, b, KIND);
         ph[gi] = pn;
         ubn[gi] = uc + beta * (uc - Ix[4 * kTY * kTT + ii]);
         ca.add(0, pn * sqrtf(gu.x * gu.x + gu.y * gu.y + gu.z * gu.z));
@@ -338,10 +342,10 @@ __global__ void __launch_bounds__(kTileThreads, 3)
           ft_l3[j] = __ldg(ft.lam3 + gi);
         }
       }
-      // q over the region: point (yy, tt) is voxel (y0 - 1 + yy, t0 - 1 + tt)
-      for (int i = threadIdx.x; i < kRH * kRW; i += kTileThreads) {
-        const int yy = i / kRW, tt = i - yy * kRW;
-        const int o = yy * kP + tt + kC - 1;
+      // q over the region: point (yy, tt) is voxel (y0 - 1 + yy, t0 - 1 + tt);
+      // columns 0 .. TT - 1 two rows per pass, then the last column
+      auto q_at = [&](int yy, int tt) {
+        const int o = yy * kP + tt + kC - 1, i = yy * kRW + tt;
         const float c = Ux[o];
         const float l0 = Lx[o], l1 = Lx[kRH * kP + o], l2 = Lx[2 * kRH * kP + o];
         const float3 av = make_float3(Un[o] - c - l0 * inv_mu, Ux[o + kP] - c - l1 * inv_mu,
@@ -350,7 +354,10 @@ __global__ void __launch_bounds__(kTileThreads, 3)
         Q[i] = v.x + l0 * inv_mu;
         Q[kRH * kRW + i] = v.y + l1 * inv_mu;
         Q[2 * kRH * kRW + i] = v.z + l2 * inv_mu;
-      }
+      };
+#pragma unroll
+      for (int yy = threadIdx.x / kTT; yy < kRH; yy += 2) q_at(yy, threadIdx.x % kTT);
+      if (threadIdx.x < kRH) q_at(threadIdx.x, kTT);
       __syncthreads();
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
