@@ -375,13 +375,6 @@ __global__ void k_select_copy(float* __restrict__ o, const float* __restrict__ a
     o[i] = __ldg(src + i);
 }
 
-// The FISTA step that the next accepted test takes from the current t.
-__device__ __forceinline__ void set_next_step(DevScalars* sc) {
-  const double tn = (1.0 + sqrt(1.0 + 4.0 * sc->t * sc->t)) / 2.0;
-  sc->t_next = tn;
-  sc->beta_next = (sc->t - 1.0) / tn;
-}
-
 // End of an iteration: energy, relative change, restart, bookkeeping.
 // model 1: E = f_fit + sum phi |grad u|; model 2: E from the post partials.
 // fold_test (model 1, a test that cannot reject): the accepting test's
@@ -399,40 +392,14 @@ __global__ void __launch_bounds__(kSumThreads)
     sum_partials_block<2>(pf, nbf, t01, f);
   }
   if (threadIdx.x != 0) return;
-  if (sc->status != NLOS_OK) return;
-  if (fold_test) {
-    sc->test_lhs = f[1];
-    sc->test_rhs = sc->L * 0.0;
-    sc->accept = 1;
-    sc->f_fit = 0.5 * f[0];
-    sc->beta = sc->beta_next;
-    sc->t = sc->t_next;
-    sc->rej_iter = 0;
-  }
-  double E, pres2;
   if (model == 1) {
-    E = sc->f_fit + v[0];
-    pres2 = v[1];
-  } else {
-    const double fit = 0.5 * v[2];
-    E = fit + 0.5 * lam_w * v[3] + v[0] + v[1];
-    sc->f_fit = fit;
-    pres2 = v[4];
+    finalize1(sc, v[0], v[1], f[0], f[1], fold_test, restart, eps_stop);
+    return;
   }
-  const double e = E != 0.0 ? fabs(sc->E_prev - E) / fabs(E) : 0.0;
-  if (!isfinite(E)) sc->status = NLOS_ERR_DIVERGED;
-  if (restart && E > sc->E_prev) {
-    sc->t = 1.0;
-    sc->restarts += 1;
-  }
-  sc->beta_prev = sc->beta;
-  sc->E = E;
-  sc->e = e;
-  sc->E_prev = E;
-  sc->primal_res = sqrt(pres2);
-  sc->iter += 1;
-  if (eps_stop > 0.0 && e <= eps_stop) sc->stop = 1;
-  set_next_step(sc);
+  if (sc->status != NLOS_OK) return;
+  const double fit = 0.5 * v[2];
+  sc->f_fit = fit;
+  finalize_tail(sc, fit + 0.5 * lam_w * v[3] + v[0] + v[1], v[4], restart, eps_stop);
 }
 
 // End of an Algorithm-2 iteration from the partials of the split post step
@@ -451,22 +418,8 @@ __global__ void __launch_bounds__(kSumThreads)
   if (threadIdx.x != 0) return;
   if (sc->status != NLOS_OK) return;
   const double fit = 0.5 * e3[0];
-  const double E = fit + 0.5 * lam_w * e3[1] + u[0] + t[0];
   sc->f_fit = fit;
-  const double e = E != 0.0 ? fabs(sc->E_prev - E) / fabs(E) : 0.0;
-  if (!isfinite(E)) sc->status = NLOS_ERR_DIVERGED;
-  if (restart && E > sc->E_prev) {
-    sc->t = 1.0;
-    sc->restarts += 1;
-  }
-  sc->beta_prev = sc->beta;
-  sc->E = E;
-  sc->e = e;
-  sc->E_prev = E;
-  sc->primal_res = sqrt(u[1]);
-  sc->iter += 1;
-  if (eps_stop > 0.0 && e <= eps_stop) sc->stop = 1;
-  set_next_step(sc);
+  finalize_tail(sc, fit + 0.5 * lam_w * e3[1] + u[0] + t[0], u[1], restart, eps_stop);
 }
 
 // Initial scalar block; E_prev = s0 sum(pe0) + s1 sum(pe1) + s2 sum(pe2) over
@@ -730,9 +683,9 @@ static void fill_stats(const DevScalars& d, nlos_stats* o) {
   o->status = d.status;
   o->L = d.L;
   o->energy = d.E;
-  o->rel_change = d.e;
+  o->rel_change = d.E != 0.0 ? std::fabs(d.dE) / std::fabs(d.E) : 0.0;
   o->data_fit = d.f_fit;
-  o->primal_res = d.primal_res;
+  o->primal_res = std::sqrt(d.pres2);
 }
 
 template <typename T>
@@ -894,8 +847,9 @@ static nlos_status u_trial(Plan& P, SolverState* s, const UStepArgs& a, bool tes
 // trial is accepted without a host round trip.
 static nlos_status u_step(Plan& P, SolverState* s, const UStepArgs& a, bool host_check, double* L_host,
                           cudaStream_t bt_stream, cudaStream_t st, int* nbf_fold = nullptr) {
-  // a test that cannot reject: the caller's k_finalize does its bookkeeping
-  // from the fit partials (nbf_fold receives their block count)
+  // a test that cannot reject: the iteration's end (k_finalize, or the last
+  // block of the fused post and pre step) does its bookkeeping from the fit
+  // partials (nbf_fold receives their block count)
   if (!host_check && nbf_fold) {
     int nbd = 0;
     return u_trial(P, s, a, false, &nbd, nbf_fold, st);
@@ -1150,27 +1104,32 @@ static nlos_status step_alg1(JobRun& j) {
   const bool host_check = j.L_host < 1.5 * j.norm2;
   UStepArgs ua{s->reg, p.mu, true, s->tau0c, p.eta, p.max_backtracks, s->cache[j.nxt], s->cache[j.cur],
                s->cache[j.prev]};
-  int nbf_fold = 0;  // test folded into k_finalize (it cannot reject): fit partial blocks
+  int nbf_fold = 0;  // test folded into the iteration's end (it cannot reject): fit partial blocks
   NLOS_TRY(u_step(P, s, ua, host_check, &j.L_host, j.bt_stream, st, &nbf_fold));
   const int fold = host_check ? 0 : 1;
-  { KTimer kt_(P, KC_POST, st);
   if (tiled) {
+    // the fused post and pre step; its last block ends the iteration
+    KTimer kt_(P, KC_POST, st);
     auto kern = p.phi == NLOS_PHI_TAC   ? k_post1_pre<NLOS_PHI_TAC>
                 : p.phi == NLOS_PHI_TRV ? k_post1_pre<NLOS_PHI_TRV>
                                         : k_post1_pre<NLOS_PHI_TSC>;
+    const IterEnd ie{s->sc, s->pb, nbf_fold, fold, j.restart, p.eps_stop};
     kern<<<post_grid, kTileThreads, kPostPreSmem, st>>>(s->unew, s->uk, s->ub, s->lam, s->ph, s->lamn, s->phn, s->ubn,
-                                                       s->reg, s->sc, g, ntiles, (float)p.mu, (float)p.a, (float)p.b,
+                                                       s->reg, ie, g, ntiles, (float)p.mu, (float)p.a, (float)p.b,
                                                        eps2, V, s->pc);
-  } else
+    NLOS_LAUNCH_CHECK("k_post1_pre");
+  } else {
+    { KTimer kt_(P, KC_POST, st);
     k_post1<<<stencil_blocks(P), kStencilThreads, 0, st>>>(s->unew, s->uk, s->ub, s->lam, s->ph, s->ubn, s->sc, g, vi,
                                                         (float)p.mu, (float)p.a, (float)p.b, p.phi, eps2, V, s->pc);
+    }
+    NLOS_LAUNCH_CHECK("k_post1");
+    { KTimer kt_(P, KC_SMALL, st);
+    k_finalize<<<1, kSumThreads, 0, st>>>(s->sc, s->pc, post_blocks, 1, 0.0, j.restart, p.eps_stop, s->pb, nbf_fold,
+                                          fold);
+    }
+    NLOS_LAUNCH_CHECK("k_finalize");
   }
-  NLOS_LAUNCH_CHECK("k_post1");
-  { KTimer kt_(P, KC_SMALL, st);
-  k_finalize<<<1, kSumThreads, 0, st>>>(s->sc, s->pc, post_blocks, 1, 0.0, j.restart, p.eps_stop, s->pb, nbf_fold,
-                                        fold);
-  }
-  NLOS_LAUNCH_CHECK("k_finalize");
   swap_ptr(s->uk, s->unew);
   swap_ptr(s->ub, s->ubn);
   if (tiled) {

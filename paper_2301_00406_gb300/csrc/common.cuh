@@ -86,7 +86,8 @@ struct DevScalars {
                              // every iteration, so the post stencil reads the extrapolation weight
                              // without waiting for the test
   double E_prev;      // energy before this iteration
-  double E, e;        // energy and relative change of the last iteration
+  double E, dE;       // energy of the last iteration and its change E_prev - E (the relative change
+                      // |dE| / |E| is formed on the host)
   double f_fit;       // data term of the last accepted iterate
   double L_norm_ok;   // L above which acceptance is guaranteed (||A_D||^2 (1 + margin))
   int32_t iter;       // iterations done
@@ -97,7 +98,9 @@ struct DevScalars {
   int32_t rej_iter;   // rejections in the current iteration
   int32_t stop;       // relative-energy stop reached
   int32_t trips;      // trips of a graph-resident iteration loop
-  double primal_res;  // ||v - grad u|| of the last iteration
+  uint32_t arrivals;  // blocks of the fused Algorithm-1 post step that have finished (its last block ends
+                      // the iteration and resets the count)
+  double pres2;       // ||v - grad u||^2 of the last iteration (its root is taken on the host)
   double test_lhs, test_rhs;  // ||A d||^2 and L ||d||^2 of the last test
 };
 

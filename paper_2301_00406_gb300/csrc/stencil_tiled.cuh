@@ -24,6 +24,7 @@
 #pragma once
 
 #include "fft.cuh"
+#include "iter_end.cuh"
 #include "stencil.cuh"
 
 namespace nlos {
@@ -502,15 +503,15 @@ __device__ __forceinline__ float fused_qx_at(const float* __restrict__ unew, con
 // lamo = Lambda_{k+1}, pho = phi(kappa(u+)), ubn = u-bar_{k+1} (as k_post1_pipe)
 // and reg = -mu div q for the next iteration (as k_pre1_pipe on those
 // outputs); lam, ph: Lambda and phi before the step (not written).
-// Partials 0 = sum phi |grad u+|, 1 = sum |v - grad u+|^2.  KIND: the phi of
-// the curvature (NLOS_PHI_*).
+// Partials 0 = sum phi |grad u+|, 1 = sum |v - grad u+|^2; the last block to
+// finish sums every block's partials and ends the iteration on ie.sc (the
+// work of k_finalize).  KIND: the phi of the curvature (NLOS_PHI_*).
 template <int KIND>
 __global__ void __launch_bounds__(kTileThreads, 2)
     k_post1_pre(const float* __restrict__ unew, const float* __restrict__ uk, const float* __restrict__ ub,
                 const float* __restrict__ lam, const float* __restrict__ ph, float* __restrict__ lamo,
-                float* __restrict__ pho, float* __restrict__ ubn, float* __restrict__ reg,
-                const DevScalars* __restrict__ sc, Vox g, int nsteps, float mu, float pa, float pb, float eps2,
-                size_t V, double* __restrict__ partials) {
+                float* __restrict__ pho, float* __restrict__ ubn, float* __restrict__ reg, IterEnd ie, Vox g,
+                int nsteps, float mu, float pa, float pb, float eps2, size_t V, double* __restrict__ partials) {
   extern __shared__ float4 smem_f4[];
   float* U = reinterpret_cast<float*>(smem_f4);
   float* B = U + kFusU;
@@ -522,7 +523,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
   constexpr int SU = kFusUH * kP, SB = kUH * kP;
   const int iy = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const float inv_mu = 1.0f / mu;
-  const float beta = (float)sc->beta_next;
+  const float beta = (float)ie.sc->beta_next;
   // this thread's halo voxel of Q (threads < kFusHalo): Q row hy, column ht
   const int h = threadIdx.x;
   const bool has_halo = h < kFusHalo;
@@ -666,6 +667,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     cp_async_wait_all();
   }
   block_reduce_acc(ca, partials);
+  end_iteration_if_last(ie, partials);
 }
 
 }  // namespace nlos
