@@ -463,8 +463,9 @@ struct SolverState {
   int model = 0;
   size_t V = 0;
   float *uk = nullptr, *unew = nullptr, *ub = nullptr, *ubn = nullptr, *lam = nullptr, *ph = nullptr, *reg = nullptr;
-  // Algorithm 1 with the fused post and pre step: Lambda and phi of the next
-  // iteration (swapped with lam and ph after every iteration)
+  // the fused post and pre step (Algorithm 1; Algorithm 2's u half): Lambda
+  // and phi of the next iteration (swapped with lam and ph after every
+  // iteration)
   float *lamn = nullptr, *phn = nullptr;
   float *tk = nullptr, *tnew = nullptr, *tb = nullptr, *tbn = nullptr, *lam2 = nullptr, *lam3 = nullptr,
         *pht = nullptr, *regt = nullptr, *tmp = nullptr;
@@ -511,9 +512,9 @@ static nlos_status get_solver(Plan& P, int model, SolverState** out) {
   A(&s->uk, F); A(&s->unew, F); A(&s->ub, F); A(&s->ubn, F); A(&s->lam, 3 * F); A(&s->ph, F); A(&s->reg, F);
   const size_t cachesz = model == 1 ? (size_t)P.ncols * P.nt * sizeof(float) : F;
   for (int i = 0; i < 3; ++i) A(&s->cache[i], cachesz);
+  A(&s->lamn, 3 * F); A(&s->phn, F);
   if (model == 1) {
     A(&s->tau0c, (size_t)P.ncols * P.nt * sizeof(float));
-    A(&s->lamn, 3 * F); A(&s->phn, F);
   } else {
     A(&s->tk, F); A(&s->tnew, F); A(&s->tb, F); A(&s->tbn, F); A(&s->lam2, 3 * F); A(&s->lam3, F);
     A(&s->pht, F); A(&s->regt, F); A(&s->tmp, F);
@@ -706,9 +707,6 @@ static auto post1_pipe_kernel(int kind) {
 nlos_status prepare_stencils() {
   NLOS_TRY(ensure_smem(k_pre1_pipe<false>, kPre1PipeSmem));
   NLOS_TRY(ensure_smem(k_pre1_pipe<true>, kPre1PipeSmem));
-  NLOS_TRY(ensure_smem(post1_pipe_kernel<false>(NLOS_PHI_TSC), kPost1PipeSmem));
-  NLOS_TRY(ensure_smem(post1_pipe_kernel<false>(NLOS_PHI_TAC), kPost1PipeSmem));
-  NLOS_TRY(ensure_smem(post1_pipe_kernel<false>(NLOS_PHI_TRV), kPost1PipeSmem));
   NLOS_TRY(ensure_smem(post1_pipe_kernel<true>(NLOS_PHI_TSC), kPost1PipeSmem));
   NLOS_TRY(ensure_smem(post1_pipe_kernel<true>(NLOS_PHI_TAC), kPost1PipeSmem));
   NLOS_TRY(ensure_smem(post1_pipe_kernel<true>(NLOS_PHI_TRV), kPost1PipeSmem));
@@ -726,17 +724,18 @@ nlos_status prepare_stencils() {
 static bool stencils_tiled(const Plan& P) { return P.nt % kTT == 0 && P.ny % kTY == 0; }
 
 // reg = -mu div (v + Lambda/mu), v = shrink(grad u-bar - Lambda/mu, phi/mu)
-// (Algorithm 1's pre step) on stream st.
-static nlos_status pre1(Plan& P, SolverState* s, const nlos_params& p, cudaStream_t st) {
+// (Algorithm 1's pre step, and Algorithm 2's for u with mu = mu1) on stream
+// st.
+static nlos_status pre1(Plan& P, SolverState* s, double mu, cudaStream_t st) {
   const Vox g = make_vox(P.nx, P.ny, P.nt);
   KTimer kt_(P, KC_PRE, st);
   if (stencils_tiled(P)) {
     const int ntiles = stencil_steps(g);
     k_pre1_pipe<false><<<std::min(ntiles, P.sms * 3), kTileThreads, kPre1PipeSmem, st>>>(
-        s->ub, s->lam, s->ph, s->reg, g, ntiles, (float)p.mu, s->V, FTerm{});
+        s->ub, s->lam, s->ph, s->reg, g, ntiles, (float)mu, s->V, FTerm{});
   } else {
     const VoxIter vi{ilog2i(P.nt), ilog2i(P.ny)};
-    k_pre1<<<stencil_blocks(P), kStencilThreads, 0, st>>>(s->ub, s->lam, s->ph, s->reg, g, vi, (float)p.mu, s->V);
+    k_pre1<<<stencil_blocks(P), kStencilThreads, 0, st>>>(s->ub, s->lam, s->ph, s->reg, g, vi, (float)mu, s->V);
   }
   NLOS_LAUNCH_CHECK("k_pre1");
   return NLOS_OK;
@@ -1006,7 +1005,7 @@ static nlos_status init_run(JobRun& j, const float* u_init) {
     }
     // the first iteration's right-hand side term (later ones come from the
     // fused post and pre step)
-    if (stencils_tiled(P)) NLOS_TRY(pre1(P, s, p, st));
+    if (stencils_tiled(P)) NLOS_TRY(pre1(P, s, p.mu, st));
   } else {
     for (float* f : {s->tk, s->tb, s->lam3}) NLOS_TRY(zero(f, V, st));
     NLOS_TRY(zero(s->lam, 3 * V, st));
@@ -1040,6 +1039,9 @@ static nlos_status init_run(JobRun& j, const float* u_init) {
     NLOS_TRY(gather_columns(P, j.tau0, s->tmp, st));
     NLOS_TRY(init_scalars(P, s, j.L0, s->tmp, (size_t)P.ncols * P.nt, 0.5 * p.lambda, st,
                           u_init ? s->cache[j.cur] : nullptr, s->uk, s->ph));
+    // the first iteration's u right-hand side term (later ones come from the
+    // fused post and pre step of the u half)
+    if (stencils_tiled(P)) NLOS_TRY(pre1(P, s, p.mu1, st));
   }
   return NLOS_OK;
 }
@@ -1094,7 +1096,7 @@ static nlos_status step_alg1(JobRun& j) {
       NLOS_CUDA(cudaStreamWaitEvent(j.aux, j.ev_fork, 0));
       pst = j.aux;
     }
-    NLOS_TRY(pre1(P, s, p, pst));
+    NLOS_TRY(pre1(P, s, p.mu, pst));
     if (fork) NLOS_CUDA(cudaEventRecord(j.ev_join, pst));
   }
   Lin3 r{{s->cache[j.cur], s->cache[j.prev], s->tau0c}, {0.f, 0.f, 0.f}, s->sc};
@@ -1113,7 +1115,7 @@ static nlos_status step_alg1(JobRun& j) {
     auto kern = p.phi == NLOS_PHI_TAC   ? k_post1_pre<NLOS_PHI_TAC>
                 : p.phi == NLOS_PHI_TRV ? k_post1_pre<NLOS_PHI_TRV>
                                         : k_post1_pre<NLOS_PHI_TSC>;
-    const IterEnd ie{s->sc, s->pb, nbf_fold, fold, j.restart, p.eps_stop};
+    const IterEnd ie{s->sc, 1, s->pb, nbf_fold, fold, j.restart, p.eps_stop};
     kern<<<post_grid, kTileThreads, kPostPreSmem, st>>>(s->unew, s->uk, s->ub, s->lam, s->ph, s->lamn, s->phn, s->ubn,
                                                        s->reg, ie, g, ntiles, (float)p.mu, (float)p.a, (float)p.b,
                                                        eps2, V, s->pc);
@@ -1156,8 +1158,8 @@ static nlos_status step_alg2(JobRun& j) {
   const int pre_grid = std::min(ntiles, P.sms * 3), post_grid = std::min(ntiles, P.sms * 2);
   { KTimer kt_(P, KC_PRE, st);
   if (tiled) {
-    k_pre1_pipe<false><<<pre_grid, kTileThreads, kPre1PipeSmem, st>>>(s->ub, s->lam, s->ph, s->reg, g, ntiles,
-                                                                      (float)p.mu1, V, FTerm{});
+    // the u half's reg comes from the previous iteration's fused post and pre
+    // step (or the run's start)
     const FTerm ft{j.tau0, s->lam3, colpos, (float)p.lambda, (float)p.mu3};
     k_pre1_pipe<true><<<pre_grid, kTileThreads, kPre1PipeSmem, st>>>(s->tb, s->lam2, s->pht, s->regt, g, ntiles,
                                                                      (float)p.mu2, V, ft);
@@ -1183,9 +1185,13 @@ static nlos_status step_alg2(JobRun& j) {
     // elementwise Lambda_3 part.  The u-step partial buffer pa is free again
     // at this point.
     { KTimer kt_(P, KC_POST, st);
-    post1_pipe_kernel<false>(p.phi)<<<post_grid, kTileThreads, kPost1PipeSmem, st>>>(
-        s->unew, s->uk, s->ub, s->lam, s->ph, s->ubn, s->sc, g, ntiles, (float)p.mu1, (float)p.a_u, (float)p.b_u,
-        c.eps2, V, s->pc, L3Term{});
+    auto kern = p.phi == NLOS_PHI_TAC   ? k_post1_pre<NLOS_PHI_TAC>
+                : p.phi == NLOS_PHI_TRV ? k_post1_pre<NLOS_PHI_TRV>
+                                        : k_post1_pre<NLOS_PHI_TSC>;
+    const IterEnd ie{s->sc, 0, nullptr, 0, 0, 0, 0.0};  // k_finalize2 ends the iteration
+    kern<<<post_grid, kTileThreads, kPostPreSmem, st>>>(s->unew, s->uk, s->ub, s->lam, s->ph, s->lamn, s->phn, s->ubn,
+                                                       s->reg, ie, g, ntiles, (float)p.mu1, (float)p.a_u,
+                                                       (float)p.b_u, c.eps2, V, s->pc);
     const L3Term l3{j.tau0, s->cache[j.nxt], s->lam3, colpos, (float)p.lambda, (float)p.mu3};
     post1_pipe_kernel<true>(p.phi)<<<post_grid, kTileThreads, kPost1PipeSmem, st>>>(
         s->tnew, s->tk, s->tb, s->lam2, s->pht, s->tbn, s->sc, g, ntiles, (float)p.mu2, (float)p.a_tau,
@@ -1214,6 +1220,10 @@ static nlos_status step_alg2(JobRun& j) {
   swap_ptr(s->ub, s->ubn);
   swap_ptr(s->tk, s->tnew);
   swap_ptr(s->tb, s->tbn);
+  if (tiled) {
+    swap_ptr(s->lam, s->lamn);
+    swap_ptr(s->ph, s->phn);
+  }
   return NLOS_OK;
 }
 

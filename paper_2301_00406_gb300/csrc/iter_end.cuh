@@ -126,10 +126,12 @@ __device__ __forceinline__ void block_sum_2x2(const double* pa, int na, const do
   __syncthreads();
 }
 
-// What the last block of the fused Algorithm-1 post and pre step needs to end
-// the iteration.
+// What the last block of the fused post and pre step needs to end the
+// iteration (Algorithm 1; Algorithm 2's u half leaves that to k_finalize2,
+// which also needs the tau half's sums).
 struct IterEnd {
   DevScalars* sc;
+  int end_here;      // 1: the last block ends the iteration
   const double* pf;  // fit partials of a folded test
   int nbf;           // their block count
   int fold;          // 1: the test cannot reject and is folded in here
@@ -144,6 +146,7 @@ struct IterEnd {
 // the others' partials.  The arrival counter is zero at the start of a run
 // and is reset by the last block.
 __device__ __forceinline__ void end_iteration_if_last(const IterEnd& ie, const double* partials) {
+  if (!ie.end_here) return;
   __shared__ int s_last;
   if (threadIdx.x == 0) {
     __threadfence();

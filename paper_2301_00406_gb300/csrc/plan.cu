@@ -285,7 +285,7 @@ size_t workspace_bytes(const Plan& P, int model) {
              C + sizeof(double) * 4096 * kMaxTerms + 4096;
   const size_t partials = 3 * sizeof(double) * kMaxTerms * 4096;
   if (model == 1 || model == 3) b += 13 * F + 4 * C + partials;
-  if (model == 2 || model == 3) b += 21 * F + partials;
+  if (model == 2 || model == 3) b += 25 * F + partials;
   return b;
 }
 

@@ -503,9 +503,11 @@ __device__ __forceinline__ float fused_qx_at(const float* __restrict__ unew, con
 // lamo = Lambda_{k+1}, pho = phi(kappa(u+)), ubn = u-bar_{k+1} (as k_post1_pipe)
 // and reg = -mu div q for the next iteration (as k_pre1_pipe on those
 // outputs); lam, ph: Lambda and phi before the step (not written).
-// Partials 0 = sum phi |grad u+|, 1 = sum |v - grad u+|^2; the last block to
-// finish sums every block's partials and ends the iteration on ie.sc (the
-// work of k_finalize).  KIND: the phi of the curvature (NLOS_PHI_*).
+// Partials 0 = sum phi |grad u+|, 1 = sum |v - grad u+|^2; with
+// ie.end_here the last block to finish sums every block's partials and ends
+// the iteration on ie.sc (the work of k_finalize).  Also Algorithm 2's u
+// half (Lambda_1, phi_u, u-bar, and reg of the next u-step).  KIND: the phi
+// of the curvature (NLOS_PHI_*).
 template <int KIND>
 __global__ void __launch_bounds__(kTileThreads, 2)
     k_post1_pre(const float* __restrict__ unew, const float* __restrict__ uk, const float* __restrict__ ub,
