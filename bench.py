@@ -219,6 +219,40 @@ CONV4_TRAFFIC = {"bytes": 117.32e6, "workload": (128, 128, 512, 1024),
                  "digest": "a364346b7731e3005ecf0a438cf84ec2"}
 
 
+TUNE_KINDS = ["tfwd_rz", "tfwd_rtt", "tinv_store", "tinv_fit", "tadj_store", "tadj_solve", "sfwd", "sinv",
+              "sinv_rz", "lateral_solve"]
+
+
+def tuning_choices(nt, nx, columns=None):
+    """The plan tuner's recorded choices for this geometry (t-pass launch
+    shapes per kind and launch column count, restricted to `columns` when
+    given; the lateral solve's kernel), read back from the library's tuning
+    file; None where there is no file."""
+    path = os.environ.get("NLOS_TUNE_CACHE")
+    if path is None:
+        base = os.environ.get("XDG_CACHE_HOME") or (os.path.join(os.environ["HOME"], ".cache")
+                                                     if os.environ.get("HOME") else None)
+        path = os.path.join(base, "nlos-gb300", "tpass_tuning") if base else None
+    if not path or path == "off" or not os.path.exists(path):
+        return None
+    out = {"tpass": [], "lateral_solve": None}
+    with open(path) as fh:
+        for line in fh.read().splitlines()[2:]:
+            f = line.split()
+            if len(f) != 4:
+                continue
+            kind, knt, ncols, v = map(int, f)
+            if knt != nt or not 0 <= kind < len(TUNE_KINDS):
+                continue
+            if TUNE_KINDS[kind] == "lateral_solve":
+                if ncols == nx:
+                    out["lateral_solve"] = {1: "shared-memory passes", 2: "half-warp transforms"}.get(v, v)
+            elif columns is None or ncols in columns:
+                out["tpass"].append({"kind": TUNE_KINDS[kind], "columns": ncols, "cols_per_cta": v & 255,
+                                     "batched_halves": bool(v >> 8)})
+    return out
+
+
 def conv4_traffic(nx, ny, nt, ncols):
     t = CONV4_TRAFFIC
     if (nx, ny, nt, ncols) != t["workload"]:
@@ -424,7 +458,8 @@ def run_ours(args):
                    "lateral_stage": {0: "FP32 FFT kernels", 1: "split-BF16 tcgen05", 2: "BF16 tcgen05"}[args.lateral],
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "working set ~0.7 GB > 129 MB L2; no flush needed",
-                   "graph": "whole reconstruction captured before the timed region" if graphed else "no graph"},
+                   "graph": "whole reconstruction captured before the timed region" if graphed else "no graph",
+                   "tuning": tuning_choices(nt, nx, (nx * ny, ncols))},
         "clocks": clocks,
         "e2e": {"value": round(job_rate(per, world, e2e_ms), 2), "unit": "iter/s",
                 "h2d_bytes_per_step": nbytes / per, "d2h_bytes_per_step": nbytes / per,

@@ -169,7 +169,7 @@ int tp_cols_for(int kind, int nt, int ncols) {
 
 // Times every column count (and, for the kernels with two halves, both the
 // sequential and the batched halves) for each t-pass kind the plan launches
-// and keeps the fastest.  Inputs are the plan's scratch buffers with whatever they hold
+// and keeps the fastest; likewise the two kernels of the lateral solve.  Inputs are the plan's scratch buffers with whatever they hold
 // (the kernels' addressing depends only on the tables and the shape, so any
 // contents are safe); nothing outside the plan is written.
 nlos_status autotune_tpass(Plan& P, cudaStream_t st) {
@@ -209,6 +209,10 @@ nlos_status autotune_tpass(Plan& P, cudaStream_t st) {
       {TPK_SINV_RZ, full, true,
        [&] { return launch_sinv_rz(P, P.d_Sp, full, f1, f2, P.d_partials, &nb, P.d_S, full, st); }},
   };
+  // the lateral solve's kernel (its input, the periodic spectrum scratch,
+  // holds whatever it holds; the denominators c0 + c1 (...) are >= 1)
+  if (P.nx >= 32)
+    cases.push_back({TPK_SXY, P.nx, false, [&] { return launch_sxy(P, P.d_Sp, nullptr, 1.0, 1.0, st); }});
   if (nc < full) {
     cases.push_back({TPK_TFWD_RTT, nc, false, [&, nc] { return launch_tfwd_rtt(P, r_comp, nc, P.d_Sc, nc, st); }});
     cases.push_back(
@@ -236,13 +240,19 @@ nlos_status autotune_tpass(Plan& P, cudaStream_t st) {
                                    : tpass_warp_applies(P, c.ncols, c.ncols)))
       continue;
     const bool halves = c.kind != TPK_SFWD && c.kind != TPK_SINV;  // sinv_rz: its forward half
+    const bool variant = c.kind == TPK_SXY;  // a choice between two kernels, not a shape
     int best = 0;
     float best_ms = 0.f;
     for (int cand = 0; cand < 8 && status == NLOS_OK; ++cand) {
       const int cols = max_cols >> (cand >> 1), hb = cand & 1;
-      if (cols < 2 || (hb && !halves)) continue;
-      if (c.partials && (c.ncols + cols - 1) / cols > P.partial_blocks) continue;
-      g_tp_force = cols | hb << 8;
+      if (variant) {
+        if (cand >= 2) break;
+        g_tp_force = cand == 0 ? kSxyHalfWarp : kSxyPasses;
+      } else {
+        if (cols < 2 || (hb && !halves)) continue;
+        if (c.partials && (c.ncols + cols - 1) / cols > P.partial_blocks) continue;
+        g_tp_force = cols | hb << 8;
+      }
       float t = 0.f;
       status = c.run();  // warm-up
       // best of 2 timings of 2 back-to-back launches (the launch latency of a
@@ -256,9 +266,10 @@ nlos_status autotune_tpass(Plan& P, cudaStream_t st) {
           status = fail(NLOS_ERR_CUDA, "autotune: timing");
         if (rep == 0 || ms < t) t = ms;
       }
+      const int chosen = g_tp_force;
       g_tp_force = 0;
       if (status == NLOS_OK && (best == 0 || t < best_ms)) {
-        best = cols | hb << 8;
+        best = chosen;
         best_ms = t;
       }
     }

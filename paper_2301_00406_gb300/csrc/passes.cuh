@@ -123,11 +123,16 @@ nlos_status launch_kernel_spectrum(const Plan& P, const int32_t* m0, const float
 // timing at plan creation (autotune_tpass, on the plan's own scratch
 // buffers); the choice is cached for the whole process per (kind, nt, launch
 // column count), so all plans of a geometry launch the same shapes and their
-// block-partial reductions sum in the same order.
+// block-partial reductions sum in the same order.  TPK_SXY is not a t-pass:
+// for the lateral periodic solve of N x N planes (N >= 32) it picks the
+// kernel, keyed by (TPK_SXY, nt, N): kSxyPasses (the transform steps as
+// CTA-wide passes over the plane in shared memory, k_sxy) or kSxyHalfWarp
+// (every transform in the registers of a half-warp, k_sxy_w).
 enum TpKind {
   TPK_TFWD_RZ, TPK_TFWD_RTT, TPK_TINV_STORE, TPK_TINV_FIT, TPK_TADJ_STORE, TPK_TADJ_SOLVE, TPK_SFWD, TPK_SINV,
-  TPK_SINV_RZ
+  TPK_SINV_RZ, TPK_SXY
 };
+constexpr int kSxyPasses = 1, kSxyHalfWarp = 2;
 // Tuned shape of a launch, cols | hb << 8, or 0 (use the default rule).
 int tp_cols_for(int kind, int nt, int ncols);
 nlos_status autotune_tpass(Plan& P, cudaStream_t st);

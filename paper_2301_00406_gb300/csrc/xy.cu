@@ -507,16 +507,21 @@ nlos_status launch_sxy(const Plan& P, float2* Sp, const DevScalars* sc, double c
   KTimer kt_(P, KC_SXY, st);
   return dispatch_n(P.nx, [&](auto nc) -> nlos_status {
     constexpr int N = decltype(nc)::value;
+    // the tuned choice for this plane size (the half-warp kernel unless the
+    // plan's timing found the shared-memory passes faster)
     if constexpr (N >= 32) {
-      NLOS_TRY(set_smem(k_sxy_w<N>, SW<N>::smem));
-      k_sxy_w<N><<<P.nt / 2 + 1, SW<N>::THREADS, SW<N>::smem, st>>>(Sp, P.d_lamx, P.d_lamt, sc, c0_host, c1,
-                                                                     P.d_twx);
-    } else {
-      auto kern = k_sxy<N>;
-      const size_t sm = sizeof(float2) * (N * (N + 1) + 2 * N);
-      NLOS_TRY(set_smem(kern, sm));
-      kern<<<P.nt / 2 + 1, kConvThreads, sm, st>>>(Sp, P.nt, P.d_lamx, P.d_lamt, sc, c0_host, c1, P.d_twx);
+      if (tp_cols_for(TPK_SXY, P.nt, N) != kSxyPasses) {
+        NLOS_TRY(set_smem(k_sxy_w<N>, SW<N>::smem));
+        k_sxy_w<N><<<P.nt / 2 + 1, SW<N>::THREADS, SW<N>::smem, st>>>(Sp, P.d_lamx, P.d_lamt, sc, c0_host, c1,
+                                                                       P.d_twx);
+        NLOS_LAUNCH_CHECK("k_sxy_w");
+        return NLOS_OK;
+      }
     }
+    auto kern = k_sxy<N>;
+    const size_t sm = sizeof(float2) * (N * (N + 1) + 2 * N);
+    NLOS_TRY(set_smem(kern, sm));
+    kern<<<P.nt / 2 + 1, kConvThreads, sm, st>>>(Sp, P.nt, P.d_lamx, P.d_lamt, sc, c0_host, c1, P.d_twx);
     NLOS_LAUNCH_CHECK("k_sxy");
     return NLOS_OK;
   });

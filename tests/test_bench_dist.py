@@ -1,6 +1,7 @@
-"""The bench's multi-rank path on CPU: two gloo ranks (replicas) each time
-their own work; the job's time is the slowest rank's and its throughput is
-the units of all ranks over that time."""
+"""The bench's host logic on CPU: the multi-rank path (two gloo ranks, as
+replicas, each time their own work; the job's time is the slowest rank's and
+its throughput is the units of all ranks over that time) and the read-back of
+the plan tuner's choices for the bench line."""
 import os
 import socket
 import sys
@@ -57,3 +58,21 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.max_over_ranks(12.5, 1, "cpu") == 12.5
     assert bench.job_rate(50, 1, 100.0) == pytest.approx(500.0)
+
+
+def test_tuning_choices_read_back_for_the_geometry(tmp_path, monkeypatch):
+    """The bench line's record of the plan tuner: the entries of this nt, the
+    lateral solve's kernel of this plane size, nothing from other sizes."""
+    import bench
+    path = tmp_path / "tune"
+    path.write_text("nlos-gb300 t-pass tuning v1\nsome GPU | 152 SMs | build\n"
+                    "0 512 16384 8\n3 512 1024 260\n9 512 128 2\n9 512 64 1\n9 256 32 1\n4 256 1024 16\n")
+    monkeypatch.setenv("NLOS_TUNE_CACHE", str(path))
+    got = bench.tuning_choices(512, 128)
+    assert got["lateral_solve"] == "half-warp transforms"
+    assert got["tpass"] == [{"kind": "tfwd_rz", "columns": 16384, "cols_per_cta": 8, "batched_halves": False},
+                            {"kind": "tinv_fit", "columns": 1024, "cols_per_cta": 4, "batched_halves": True}]
+    assert [e["columns"] for e in bench.tuning_choices(512, 128, (16384,))["tpass"]] == [16384]
+    assert bench.tuning_choices(256, 32)["lateral_solve"] == "shared-memory passes"
+    monkeypatch.setenv("NLOS_TUNE_CACHE", "off")
+    assert bench.tuning_choices(512, 128) is None

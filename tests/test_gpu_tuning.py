@@ -1,5 +1,6 @@
-"""The t-pass launch-shape tuning persists across processes: the first plan
-of a geometry writes its choices to the tuning file (NLOS_TUNE_CACHE), a
+"""The t-pass launch-shape tuning (and the lateral solve's kernel choice)
+persists across processes: the first plan of a geometry writes its choices to
+the tuning file (NLOS_TUNE_CACHE), a
 later process reads them instead of timing again (so it writes nothing), and
 a file made under another key (device, SM count, compile time) is ignored and
 replaced."""
@@ -13,6 +14,7 @@ import pytest
 pytestmark = pytest.mark.gpu
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 MAGIC = "nlos-gb300 t-pass tuning v1"
+SXY_KIND = 9  # the lateral-solve entry of the tuning file (after the nine t-pass kinds)
 
 SCRIPT = r"""
 import sys, time
@@ -44,7 +46,12 @@ def test_tuning_file_written_then_reused(tmp_path):
     assert " SMs | " in lines[1]
     entries = [tuple(map(int, l.split())) for l in lines[2:]]
     assert entries and all(len(e) == 4 and e[1] == 256 for e in entries)
-    assert {e[2] for e in entries} == {32 * 32, 8 * 8}   # full grid and the 8 x 8 sampled columns
+    tpass = [e for e in entries if e[0] != SXY_KIND]
+    sxy = [e for e in entries if e[0] == SXY_KIND]
+    assert {e[2] for e in tpass} == {32 * 32, 8 * 8}   # full grid and the 8 x 8 sampled columns
+    # the lateral solve's kernel for 32 x 32 planes: the shared-memory passes
+    # (1) or the half-warp transforms (2), chosen once for both plans
+    assert len(sxy) == 1 and sxy[0][2] == 32 and sxy[0][3] in (1, 2)
     before = (path.stat().st_mtime_ns, path.read_text())
     _run(path)                                          # read, nothing new to time: not rewritten
     assert (path.stat().st_mtime_ns, path.read_text()) == before
